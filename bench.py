@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the WT-scheme PIC step on GB300 (one JSON line on rank 0).
+
+Workload (default): the 2048x1024 periodic drifting pair plasma, cubic B-splines, WT gather,
+gamma = 50, u_th = 0.01 (App. D loading), 64 particles per cell = 134,217,728 particles,
+c dt = 0.25 dx, in the plain FP64 single-run form.  A step is one full PIC step through
+pic_step: gather + Boris + move + Esirkepov deposit (the fused particle kernel), the periodic
+Yee update, and the tile sort every sort_interval steps.  The same workload in the precision
+form (int32 cell + FP32 offset, FP32 push/gather/tile current, FP64 fields) is reported under
+"precision_form".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the run (independent runs, no
+collective on the data path); value = particle-steps of all ranks / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit), batched vs plain; p50/p99 run latency"
+UNIT = "particle-steps/s"
+WORKLOAD = "pair_2048x1024_l3_WT_g50_uth0.01_ppc64_cdt0.25"
+
+# Algorithmic bytes of the fused particle kernel (per particle-step, per cell-step):
+#   FP64 form: particle read + write 2 x (2 x 8 position + 3 x 8 momentum) = 80 B;
+#              grid: E, B read once (6 x 8 B) + J written (3 x 8 B) = 72 B per cell.
+#   FP32 form: 2 x (4 cell + 2 x 4 offset + 3 x 4 momentum) = 48 B;
+#              grid: FP32 shadow of E, B (6 x 4 B) + FP64 J (3 x 8 B) = 48 B per cell.
+BYTES = {"fp64": (80.0, 72.0), "fp32": (48.0, 48.0)}
+# FP64 operations of the fused kernel per particle-step (l = 3, WT, 2D), from the ncu
+# instruction counts in profiles/gpp_fp64_pair2048x1024.txt (DADD + DMUL + 2 x DFMA, divided by
+# the particles of the launch).  Used for the FP64 arithmetic roofline of the plain form.
+FP64_FLOPS_PER_PARTICLE = None
+
+
+def _rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _profile_traffic(kernel: str):
+    """DRAM bytes per launch recorded from an ncu capture, if the kernel sources are unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        from paper_1909_09613_gb300 import _build
+        import hashlib
+        import glob
+        h = hashlib.sha256()
+        for f in sorted(glob.glob(os.path.join(_build.CSRC, "*"))):
+            h.update(open(f, "rb").read())
+        digest = h.hexdigest()[:16]
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
+                return float(parts[2])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = max(smax, float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _barrier(dist_on):
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(v, dist_on):
+    if not dist_on:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_form(wl, prec, steps, warmup, dist_on, clocks=True):
+    """Load the workload (device-resident inputs), warm up, time `steps` full steps."""
+    import torch
+    import paper_1909_09613_gb300 as pic
+    caps = [int(s.x.shape[1]) for s in wl.species]
+    run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps)
+    for i, s in enumerate(wl.species):
+        run.load(i, s.q, s.m, s.w, s.x, s.u)
+    run.step(warmup)
+    run.sync()
+    stream = run.stream
+    sampler = ClockSampler(torch.cuda.current_device()) if clocks else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    k0 = run.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    _barrier(dist_on)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    run.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(dist_on)
+    ms = e0.elapsed_time(e1)
+    gpp_ms, gpp_n = run.gpp_ms()
+    launches = run.kernel_launches() - k0
+    clk = sampler.stop() if sampler else None
+    run.sync()
+    d = run.diag()
+    out = {"ms": _max_over_ranks(ms, dist_on), "gpp_ms": gpp_ms, "gpp_launches": gpp_n,
+           "launches": launches, "clocks": clk, "n": sum(caps), "ncell": wl.ncell,
+           "sort_interval": run.sort_interval, "tile": run.tile, "diag_status": d["status"],
+           "run": run}
+    return out
+
+
+def e2e_form(run, wl, steps):
+    """Same metric through the public C-ABI from pinned host buffers: load (H2D) + steps +
+    diagnostics read-back (D2H), every byte counted."""
+    import torch
+    xs = [s.x.cpu().pin_memory() for s in wl.species]
+    us = [s.u.cpu().pin_memory() for s in wl.species]
+    h2d = sum(x.numel() * 8 + u.numel() * 8 for x, u in zip(xs, us))
+    import paper_1909_09613_gb300 as pic
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, s in enumerate(wl.species):
+        st = pic.load_library().pic_load_particles(
+            run.ctx, i, s.q, s.m, s.w, int(xs[i].shape[1]),
+            pic.ctypes.cast(pic.ctypes.c_void_p(xs[i].data_ptr()), pic._c_dp),
+            pic.ctypes.cast(pic.ctypes.c_void_p(us[i].data_ptr()), pic._c_dp))
+        if st != 0:
+            raise pic.PicError(st, "pic_load_particles")
+    run.step(steps)
+    d = run.diag()
+    t1 = time.perf_counter()
+    d2h = 48  # pic_diag_t
+    n = sum(int(s.x.shape[1]) for s in wl.species)
+    return {"value": n * steps / (t1 - t0), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(math.ceil(d2h / steps)),
+            "status": d["status"]}
+
+
+def cpu_baseline(wl, budget_s=12.0):
+    """The FP64 oracle as it stands, single thread, on a bounded sample of the workload:
+    the particle pass (gather + push + deposit) of the first S particles of each species on
+    the full grid.  Returns (particle-steps/s, sample description)."""
+    import oracle
+    oracle.build()
+    dim = wl.dim
+    S = 2000
+    sim = oracle.Sim(wl.grid[:dim], wl.dx[:dim], wl.dt, wl.l, wl.scheme)
+    for s in wl.species:
+        sim.add_species(s.q, s.m, s.w, s.x[:, :S].cpu().numpy(), s.u[:, :S].cpu().numpy())
+    t0 = time.perf_counter()
+    sim.particle_pass(0, S)
+    one = time.perf_counter() - t0
+    reps = max(1, int(budget_s / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        sim.particle_pass(0, S)
+    t = time.perf_counter() - t0
+    sim.close()
+    rate = 2 * S * reps / t
+    return rate, "%d particle passes over %d particles (%d per species) of the %s grid" % (
+        reps, 2 * S, S, "x".join(str(g) for g in wl.grid[:dim]))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=1, help="divide the grid extents (debug)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = _rank_env()
+
+    import workloads
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        wl = workloads.config_large(scheme=1, device="cpu", scale=8)
+        # same per-particle work as the full grid (the oracle's cost is per particle)
+        wl_full = wl
+        rates = []
+        budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+        for i in range(args.warmup + args.steps):
+            r, sample = cpu_baseline(wl_full, budget_s=budget)
+            if i >= args.warmup:
+                rates.append(r)
+        v = statistics.median(rates)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid_sample": "256x128 (same per-particle work)"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_1909_09613_gb300 as pic
+    from paper_1909_09613_gb300 import _build
+    _build.build()
+    pic.load_library()
+
+    wl = workloads.config_large(scheme=1, device="cuda", seed=workloads.BASE_SEED + rank,
+                                scale=args.scale)
+    res = time_form(wl, pic.PIC_FP64, args.steps, args.warmup, dist_on)
+    run64 = res.pop("run")
+    n_all = res["n"] * world
+    value = n_all * args.steps / (res["ms"] * 1e-3)
+    gpp_avg_s = res["gpp_ms"] / max(res["gpp_launches"], 1) * 1e-3
+    peaks, peak_kind = _peaks()
+    pb, gb = BYTES["fp64"]
+    alg_bytes = res["n"] * pb + res["ncell"] * gb
+    fp64_peak = None
+    try:
+        fp64_peak = pic.pic_probe_fma_peak(0)
+    except Exception:
+        pass
+    if FP64_FLOPS_PER_PARTICLE and fp64_peak:
+        ach = res["n"] * FP64_FLOPS_PER_PARTICLE / gpp_avg_s / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp64_peak, "traffic": _profile_traffic("gpp2d_fp64"),
+                    "peak_source": "measured FP64 FMA probe (pic_probe_fma_peak)"}
+    else:
+        ach = alg_bytes / gpp_avg_s / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": _profile_traffic("gpp2d_fp64"),
+                    "peak_source": "%s hbm_gbs" % peak_kind}
+    roofline["kernel"] = "k_gpp2d<3,4> (double): fused gather+push+move+deposit"
+    roofline["kernel_ms"] = gpp_avg_s * 1e3
+    roofline["algorithmic_bytes"] = alg_bytes
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(wl.grid[:2]), "particles": res["n"],
+                       "form": "plain FP64 single run", "spline_order": wl.l, "scheme": "WT",
+                       "c_dt_over_dx": wl.dt, "sort_interval": res["sort_interval"],
+                       "tile": list(res["tile"]),
+                       "l2": "no flush: inputs larger than L2 (%.1f GB particle store)" % (res["n"] * 40 / 1e9),
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline,
+            "gpu_launches": res["launches"],
+            "clocks": res["clocks"],
+            "fp64_fma_peak_tflops": fp64_peak,
+            "gpp_particle_steps_per_s": res["n"] / gpp_avg_s}
+    if not args.no_e2e:
+        try:
+            line["e2e"] = e2e_form(run64, wl, args.steps)
+        except Exception as ex:  # report, do not hide
+            line["e2e"] = {"error": str(ex)}
+    run64.close()
+    del run64
+    torch.cuda.empty_cache()
+
+    if not args.no_fp32:
+        r32 = time_form(wl, pic.PIC_FP32_MIXED, args.steps, args.warmup, dist_on)
+        r32.pop("run").close()
+        g32 = r32["gpp_ms"] / max(r32["gpp_launches"], 1) * 1e-3
+        pb, gb = BYTES["fp32"]
+        ab = r32["n"] * pb + r32["ncell"] * gb
+        ach = ab / g32 / 1e9
+        line["precision_form"] = {
+            "value": r32["n"] * world * args.steps / (r32["ms"] * 1e-3), "unit": UNIT,
+            "ms_per_step": r32["ms"] / args.steps, "dtype": "f32 (FP64 fields)",
+            "gpp_particle_steps_per_s": r32["n"] / g32,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach / peaks["hbm_gbs"], "traffic": _profile_traffic("gpp2d_fp32"),
+                         "kernel": "k_gpp2d<3,4> (float)", "kernel_ms": g32 * 1e3,
+                         "algorithmic_bytes": ab, "peak_source": "%s hbm_gbs" % peak_kind},
+            "gpu_launches": r32["launches"], "clocks": r32["clocks"]}
+        try:
+            line["fp32_fma_peak_tflops"] = pic.pic_probe_fma_peak(1)
+        except Exception:
+            pass
+
+    if rank == 0 and not args.no_cpu:
+        rate, sample = cpu_baseline(wl)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist_on:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * libpic -- GB300 (sm_103a) relativistic electromagnetic PIC step with the WT force
+ * interpolation of Lu, Kilian, Guo, Li and Liang, "Time-step dependent force interpolation
+ * scheme for suppressing numerical Cherenkov instability in relativistic particle-in-cell
+ * simulations" (arXiv:1909.09613).
+ *
+ * One step (pic_step) = field gather at x^n from E^n, B^n (Sec. 2: Eq. interpolation-EB-real-mod
+ * for the WT scheme, Eq. interpolation-EB-real-org for the momentum-conserving MC scheme) ->
+ * relativistic Boris push u^{n-1/2} -> u^{n+1/2} (Sec. 1; equations of motion App. E) -> move
+ * x^{n+1} = x^n + dt u/gamma -> Esirkepov charge-conserving current deposit J^{n+1/2} with the
+ * B-spline form factor W_l (Sec. 1, Sec. 2 Eq. shape-real) -> periodic Yee update
+ * B^{n+1/2}, E^{n+1}, B^{n+1} (Sec. 1 "staggered Yee grid"; App. C with A_i = 1).
+ *
+ * Units are the paper's dimensionless ones (App. E): c = 1, 4 pi absorbed, u = gamma v in units
+ * of c, so du/dt = (q/m)(E + v x B), dE/dt = curl B - J, dB/dt = -curl E.
+ *
+ * Grid layout: periodic, nx x ny (x nz; nz = 1 means 2D).  Node (i, j, k) lives at linear index
+ * (k*ny + j)*nx + i of every field array (x fastest).  The Yee components sit at
+ *   E1 (i+1/2, j, k)  E2 (i, j+1/2, k)  E3 (i, j, k+1/2)
+ *   B1 (i, j+1/2, k+1/2)  B2 (i+1/2, j, k+1/2)  B3 (i+1/2, j+1/2, k),  J with E,
+ * the value for the node with integer parts (i, j, k) being stored at that node's index.
+ *
+ * Conventions:
+ *   - every function returns PIC_OK (0) or a negative pic_status; no C++ exception crosses
+ *     the boundary;
+ *   - host pointers are owned by the caller and are only read/written during the call;
+ *   - device work is issued on the context's stream (pic_options.stream); functions that
+ *     return data to the host synchronise that stream;
+ *   - asynchronous device errors (a particle found outside its tile's staged region, a
+ *     non-finite value found by pic_diag) are latched in the context's error word, returned by
+ *     pic_diag in error_flags and turned into PIC_EOVERFLOW / PIC_ENAN by the next syncing call;
+ *   - a context must not be used from two host threads at once.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_MAX_SPECIES 4
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_EINVAL = -1,    /* bad argument                                                   */
+    PIC_ENOMEM = -2,    /* bound memory too small / allocation failed                     */
+    PIC_ECFL = -3,      /* c dt violates the Yee Courant limit or the stencil range        */
+    PIC_ECUDA = -4,     /* a CUDA runtime call failed                                      */
+    PIC_EOVERFLOW = -5, /* a particle left the staged region of its tile (sort too rare)   */
+    PIC_ETIMEOUT = -6,  /* a bounded device wait gave up                                   */
+    PIC_ENAN = -7,      /* a non-finite field or particle value was found                  */
+    PIC_ESTATE = -8     /* call out of order (e.g. no memory bound yet)                    */
+} pic_status;
+
+enum { PIC_SCHEME_MC = 0, PIC_SCHEME_WT = 1 };
+enum { PIC_FP64 = 0, PIC_FP32_MIXED = 1 };
+
+/* Error bits of pic_diag_t.error_flags. */
+enum { PIC_ERR_OUTSIDE_TILE = 1, PIC_ERR_NONFINITE = 2, PIC_ERR_TIMEOUT = 4 };
+
+typedef struct {
+    int32_t tile[3];        /* cells per particle tile; 0 = library default                 */
+    int32_t sort_interval;  /* steps between tile sorts; 0 = chosen from c dt and the halo   */
+    int32_t precision;      /* PIC_FP64: FP64 positions/momenta/gather/push/deposit.
+                               PIC_FP32_MIXED: int32 cell + FP32 in-cell offset, FP32 momenta,
+                               FP32 gather/push and tile accumulation; FP64 Yee fields, FP64
+                               global current and FP64 diagnostics                           */
+    int32_t n_species;      /* species this context will hold (1..PIC_MAX_SPECIES)          */
+    int64_t capacity[PIC_MAX_SPECIES]; /* max particles per species                         */
+    uint64_t stream;        /* cudaStream_t to issue work on (0 = legacy default stream)    */
+} pic_options;
+
+/* pic_create -- validate a run and build its host-side context (no device memory yet).
+ *   grid[3]      cells per axis; grid[2] == 1 selects 2D (x3-independent fields, 2D3V).
+ *   dx[3]        cell sizes (dx[2] ignored in 2D).
+ *   dt           time step; requires c dt sqrt(sum 1/dx_i^2) < 1 (Yee Courant limit,
+ *                App. C with A_i = 1) and c dt / dx_i < 1 so a particle crosses at most
+ *                one cell face per axis per step.
+ *   spline_order l in 1..4: B-spline order of W_l (Sec. 2).
+ *   scheme       PIC_SCHEME_WT: gather with Eq. interpolation-EB-real-mod (W along the
+ *                component's half-offset axes, T_l along its integer-node axes), valid for any
+ *                c dt / dx_i < 1 (the T_l definition of Eq. tau_l, not only the printed
+ *                c dt <= dx/2 forms); PIC_SCHEME_MC: all-W gather, Eq. interpolation-EB-real-org.
+ *   opt          may be NULL (defaults: FP64, 2 species, capacity 0 -> must be set).
+ * On success *out owns the context; free it with pic_destroy.                              */
+int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_order,
+               int scheme, const pic_options *opt, pic_ctx **out);
+
+/* Bytes of device memory the context needs (fields, particle stores x2, sort scratch). */
+int pic_footprint(const pic_ctx *ctx, size_t *bytes);
+
+/* Hand the context a device buffer of at least pic_footprint bytes (e.g. a torch tensor's
+ * storage).  The caller keeps it alive until pic_destroy.  The fields are zeroed.            */
+int pic_bind_memory(pic_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Alternative to pic_bind_memory: the library allocates (cudaMalloc) and frees the buffer. */
+int pic_alloc(pic_ctx *ctx);
+
+/* Load species `species` (0-based, < n_species): charge q, mass m, macro-particle weight w
+ * (rho = q w W_l / V_c, Sec. 2 Eq. shape-real), n <= capacity particles.
+ *   x: host, dim x n FP64 SoA, physical positions (wrapped into [0, n_i dx_i));
+ *   u: host, 3 x n FP64 SoA, u = gamma v (units of c), the momentum at t^{n-1/2}.
+ * Copies host -> device, packs into the context's precision form and tile-sorts. Syncs.   */
+int pic_load_particles(pic_ctx *ctx, int species, double q, double m, double w, int64_t n,
+                       const double *x, const double *u);
+
+/* Same as pic_load_particles with x, u already in device memory (not modified). */
+int pic_load_particles_device(pic_ctx *ctx, int species, double q, double m, double w, int64_t n,
+                              const double *x_dev, const double *u_dev);
+
+/* Set field component comp (0..5 = E1 E2 E3 B1 B2 B3) from count = ncell FP64 host values. */
+int pic_set_fields(pic_ctx *ctx, int comp, const double *host, size_t count);
+
+/* Advance nsteps full PIC steps on the context's stream (asynchronous). */
+int pic_step(pic_ctx *ctx, int nsteps);
+
+/* Copy field comp (0..5 E, B; 6..8 J1 J2 J3 = J^{n-1/2} of the last step) to the host. Syncs. */
+int pic_read_fields(pic_ctx *ctx, int comp, double *host, size_t count);
+
+/* Copy species particles to the host in the current (tile-sorted) order: x dim x n physical
+ * FP64, u 3 x n FP64, cell (may be NULL) the int64 linear cell index. Syncs.                */
+int pic_read_particles(pic_ctx *ctx, int species, double *x, double *u, int64_t *cell, int64_t n);
+
+/* Copy the tile offsets of the species' current order (ntiles + 1 int64 values). Syncs. */
+int pic_read_tile_offsets(pic_ctx *ctx, int species, int64_t *offsets, int64_t count);
+
+/* Number of tiles and the tile extent actually used. */
+int pic_tile_info(const pic_ctx *ctx, int32_t tile[3], int64_t *ntiles, int32_t *sort_interval);
+
+/* Re-sort all species by tile now (also done automatically every sort_interval steps). */
+int pic_sort(pic_ctx *ctx);
+
+typedef struct {
+    int64_t step;
+    double field_energy;          /* 1/2 sum over nodes (E^2 + B^2) V_c, FP64               */
+    double kinetic_energy;        /* sum w m (gamma - 1), FP64                              */
+    double total_charge;          /* sum q w                                                */
+    double max_gauss_residual;    /* max over nodes |D.E - rho| (App. B, Eq. gauss)          */
+    int32_t error_flags;          /* PIC_ERR_* bits latched since creation                  */
+} pic_diag_t;
+
+/* FP64 diagnostics of the current state. Syncs. */
+int pic_diag(pic_ctx *ctx, pic_diag_t *out);
+
+/* Wait for the context's stream; returns the latched error as a status. */
+int pic_sync(pic_ctx *ctx);
+
+/* Advance nsteps on n contexts, all FP32_MIXED and 2D, in one persistent gather-push-deposit
+ * launch per step that covers every run's tiles, plus one Yee launch per half step for all
+ * runs (batched form).  The contexts must share a stream.                                   */
+int pic_batch_step(pic_ctx **runs, int n, int nsteps);
+
+/* Time of the last pic_step's gather+push+deposit launches (ms, CUDA events on the context's
+ * stream), summed over the steps of that call; syncs.  For measurement.                     */
+int pic_last_gpp_ms(pic_ctx *ctx, double *ms, int64_t *launches);
+
+/* Number of kernels this context has launched since creation (for measurement). */
+int pic_kernel_launches(const pic_ctx *ctx, int64_t *count);
+
+/* Measured arithmetic peak of this GPU for the roofline: kind 0 = FP64 FMA, kind 1 = FP32 FMA,
+ * in TFLOP/s (2 flops per FMA), from a register-resident FMA loop over all SMs timed with CUDA
+ * events on the legacy default stream.  Not part of the PIC path.                            */
+int pic_probe_fma_peak(int kind, double *tflops);
+
+void pic_destroy(pic_ctx *ctx);
+const char *pic_strerror(int status);
+
+/* Host evaluation (no device work) of the integer-node interpolation weights the kernels use
+ * along one axis: T_l(x; dtt) for PIC_SCHEME_WT (Sec. 2, Eq. tau_l: W_{l-1} averaged over
+ * [x - dtt, x + dtt], any 0 < dtt < 1) or W_l for PIC_SCHEME_MC (Eq. shape-real), for a
+ * particle at in-cell offset delta in [0,1), dtt = c dt / dx.  Writes the non-zero-range
+ * weights w[0..*count-1] (count <= 6) of nodes *base .. *base + *count - 1 relative to the
+ * particle's cell.                                                                         */
+int pic_axis_weights(int spline_order, int scheme, double dtt, double delta, double *w,
+                     int *base, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

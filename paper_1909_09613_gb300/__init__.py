@@ -1,0 +1,350 @@
+"""Python binding of libpic, the GB300 (sm_103a) WT-scheme PIC step (arXiv:1909.09613).
+
+Argument marshalling only: every step of the PIC path (gather, push, move, deposit, tile sort,
+Yee, diagnostics) runs in the library's CUDA kernels.  PyTorch provides device memory and the
+stream.  There is no CPU fallback: if libpic.so is missing or no CUDA device is present the
+calls raise.
+
+The module exposes the C-ABI functions of include/pic.h under the same names (pic_create,
+pic_footprint, pic_bind_memory, pic_load_particles, pic_step, pic_read_fields, pic_diag, ...)
+and a small convenience class `Run` that owns a context and its torch-allocated memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libpic.so")
+
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECFL, PIC_ECUDA = 0, -1, -2, -3, -4
+PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_ENAN, PIC_ESTATE = -5, -6, -7, -8
+PIC_SCHEME_MC, PIC_SCHEME_WT = 0, 1
+PIC_FP64, PIC_FP32_MIXED = 0, 1
+PIC_MAX_SPECIES = 4
+
+_c_dp = ctypes.POINTER(ctypes.c_double)
+_c_lp = ctypes.POINTER(ctypes.c_int64)
+_c_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class pic_options(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32 * 3), ("sort_interval", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("n_species", ctypes.c_int32),
+                ("capacity", ctypes.c_int64 * PIC_MAX_SPECIES), ("stream", ctypes.c_uint64)]
+
+
+class pic_diag_t(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("field_energy", ctypes.c_double),
+                ("kinetic_energy", ctypes.c_double), ("total_charge", ctypes.c_double),
+                ("max_gauss_residual", ctypes.c_double), ("error_flags", ctypes.c_int32)]
+
+
+class PicError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (what, pic_strerror(status), status))
+
+
+_lib = None
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("pic_create", ctypes.c_int, [_c_ip, _c_dp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(pic_options), ctypes.POINTER(ctypes.c_void_p)]),
+    ("pic_footprint", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("pic_bind_memory", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    ("pic_alloc", ctypes.c_int, [ctypes.c_void_p]),
+    ("pic_load_particles", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                          _c_dp, _c_dp]),
+    ("pic_load_particles_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    ("pic_set_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dp, ctypes.c_size_t]),
+    ("pic_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("pic_read_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dp, ctypes.c_size_t]),
+    ("pic_read_particles", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dp, _c_dp, _c_lp,
+                                          ctypes.c_int64]),
+    ("pic_read_tile_offsets", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_lp, ctypes.c_int64]),
+    ("pic_tile_info", ctypes.c_int, [ctypes.c_void_p, _c_ip, _c_lp, _c_ip]),
+    ("pic_sort", ctypes.c_int, [ctypes.c_void_p]),
+    ("pic_diag", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_diag_t)]),
+    ("pic_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("pic_batch_step", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int]),
+    ("pic_last_gpp_ms", ctypes.c_int, [ctypes.c_void_p, _c_dp, _c_lp]),
+    ("pic_kernel_launches", ctypes.c_int, [ctypes.c_void_p, _c_lp]),
+    ("pic_probe_fma_peak", ctypes.c_int, [ctypes.c_int, _c_dp]),
+    ("pic_destroy", None, [ctypes.c_void_p]),
+    ("pic_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("pic_axis_weights", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, _c_dp, _c_ip, _c_ip]),
+]
+
+
+def exported_names():
+    return [n for n, _, _ in _SIGS]
+
+
+def load_library(path: Optional[str] = None):
+    """Load libpic.so (built by paper_1909_09613_gb300._build).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libpic.so not built (%s): run __graft_entry__.build()" % p)
+    lib = ctypes.CDLL(p)
+    for name, res, args in _SIGS:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def pic_strerror(status: int) -> str:
+    try:
+        return load_library().pic_strerror(int(status)).decode()
+    except Exception:
+        return "status %d" % status
+
+
+def _check(status: int, what: str):
+    if status != PIC_OK:
+        raise PicError(status, what)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_c_dp)
+
+
+# ---- thin wrappers with the C names --------------------------------------------------------
+
+def pic_create(grid, dx, dt, spline_order, scheme, opt: Optional[pic_options] = None):
+    lib = load_library()
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid])
+    d = (ctypes.c_double * 3)(*[float(v) for v in dx])
+    out = ctypes.c_void_p()
+    st = lib.pic_create(g, d, float(dt), int(spline_order), int(scheme),
+                        ctypes.byref(opt) if opt is not None else None, ctypes.byref(out))
+    _check(st, "pic_create")
+    return out.value
+
+
+def pic_footprint(ctx) -> int:
+    b = ctypes.c_size_t()
+    _check(load_library().pic_footprint(ctx, ctypes.byref(b)), "pic_footprint")
+    return int(b.value)
+
+
+def pic_bind_memory(ctx, ptr: int, nbytes: int):
+    _check(load_library().pic_bind_memory(ctx, ctypes.c_void_p(ptr), nbytes), "pic_bind_memory")
+
+
+def pic_load_particles(ctx, species, q, m, w, x: np.ndarray, u: np.ndarray):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    n = u.shape[-1]
+    _check(load_library().pic_load_particles(ctx, int(species), float(q), float(m), float(w), n,
+                                             _dptr(x), _dptr(u)), "pic_load_particles")
+
+
+def pic_load_particles_device(ctx, species, q, m, w, x_ptr: int, u_ptr: int, n: int):
+    _check(load_library().pic_load_particles_device(ctx, int(species), float(q), float(m),
+                                                    float(w), int(n), ctypes.c_void_p(x_ptr),
+                                                    ctypes.c_void_p(u_ptr)),
+           "pic_load_particles_device")
+
+
+def pic_set_fields(ctx, comp, a: np.ndarray):
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    _check(load_library().pic_set_fields(ctx, int(comp), _dptr(a), a.size), "pic_set_fields")
+
+
+def pic_step(ctx, nsteps: int):
+    _check(load_library().pic_step(ctx, int(nsteps)), "pic_step")
+
+
+def pic_read_fields(ctx, comp, ncell) -> np.ndarray:
+    out = np.empty(ncell, dtype=np.float64)
+    _check(load_library().pic_read_fields(ctx, int(comp), _dptr(out), ncell), "pic_read_fields")
+    return out
+
+
+def pic_read_particles(ctx, species, n, dim):
+    x = np.empty((dim, n), dtype=np.float64)
+    u = np.empty((3, n), dtype=np.float64)
+    cell = np.empty(n, dtype=np.int64)
+    _check(load_library().pic_read_particles(ctx, int(species), _dptr(x), _dptr(u),
+                                             cell.ctypes.data_as(_c_lp), n), "pic_read_particles")
+    return x, u, cell
+
+
+def pic_read_tile_offsets(ctx, species, ntiles) -> np.ndarray:
+    out = np.empty(ntiles + 1, dtype=np.int64)
+    _check(load_library().pic_read_tile_offsets(ctx, int(species), out.ctypes.data_as(_c_lp),
+                                                ntiles + 1), "pic_read_tile_offsets")
+    return out
+
+
+def pic_tile_info(ctx):
+    t = (ctypes.c_int32 * 3)()
+    nt = ctypes.c_int64()
+    si = ctypes.c_int32()
+    _check(load_library().pic_tile_info(ctx, t, ctypes.byref(nt), ctypes.byref(si)), "pic_tile_info")
+    return tuple(t), int(nt.value), int(si.value)
+
+
+def pic_sort(ctx):
+    _check(load_library().pic_sort(ctx), "pic_sort")
+
+
+def pic_sync(ctx):
+    _check(load_library().pic_sync(ctx), "pic_sync")
+
+
+def pic_diag(ctx) -> dict:
+    d = pic_diag_t()
+    st = load_library().pic_diag(ctx, ctypes.byref(d))
+    out = {"step": d.step, "field_energy": d.field_energy, "kinetic_energy": d.kinetic_energy,
+           "total_charge": d.total_charge, "max_gauss_residual": d.max_gauss_residual,
+           "error_flags": d.error_flags, "status": st}
+    return out
+
+
+def pic_batch_step(ctxs: Sequence[int], nsteps: int):
+    arr = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    _check(load_library().pic_batch_step(arr, len(ctxs), int(nsteps)), "pic_batch_step")
+
+
+def pic_last_gpp_ms(ctx):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load_library().pic_last_gpp_ms(ctx, ctypes.byref(ms), ctypes.byref(n)), "pic_last_gpp_ms")
+    return float(ms.value), int(n.value)
+
+
+def pic_kernel_launches(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(load_library().pic_kernel_launches(ctx, ctypes.byref(n)), "pic_kernel_launches")
+    return int(n.value)
+
+
+def pic_probe_fma_peak(kind: int) -> float:
+    v = ctypes.c_double()
+    _check(load_library().pic_probe_fma_peak(int(kind), ctypes.byref(v)), "pic_probe_fma_peak")
+    return float(v.value)
+
+
+def pic_destroy(ctx):
+    if ctx:
+        load_library().pic_destroy(ctx)
+
+
+def pic_axis_weights(spline_order, scheme, dtt, delta):
+    """Host evaluation of the integer-node interpolation weights the kernels use along one
+    axis (T_l for WT, W_l for MC).  Returns (first_node, weights)."""
+    w = np.zeros(8)
+    b = ctypes.c_int32()
+    k = ctypes.c_int32()
+    _check(load_library().pic_axis_weights(int(spline_order), int(scheme), float(dtt),
+                                           float(delta), _dptr(w), ctypes.byref(b),
+                                           ctypes.byref(k)), "pic_axis_weights")
+    return int(b.value), w[:k.value].copy()
+
+
+# ---- convenience wrapper ---------------------------------------------------------------------
+
+class Run:
+    """One PIC run: a libpic context plus the torch-allocated device buffer bound to it."""
+
+    def __init__(self, grid, dx, dt, l, scheme, precision=PIC_FP64, capacity=(0, 0),
+                 tile=None, sort_interval=0, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpic needs a CUDA device")
+        grid = list(grid) + [1] * (3 - len(grid))
+        dx = list(dx) + [1.0] * (3 - len(dx))
+        self.grid = tuple(int(g) for g in grid)
+        self.dx = tuple(float(d) for d in dx)
+        self.dim = 3 if self.grid[2] > 1 else 2
+        self.ncell = self.grid[0] * self.grid[1] * self.grid[2]
+        self.device = torch.device(device or "cuda")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        opt = pic_options()
+        if tile is not None:
+            for a, t in enumerate(tile):
+                opt.tile[a] = int(t)
+        opt.sort_interval = int(sort_interval)
+        opt.precision = int(precision)
+        opt.n_species = len(capacity)
+        for s, c in enumerate(capacity):
+            opt.capacity[s] = int(c)
+        opt.stream = int(self.stream.cuda_stream)
+        self.ctx = pic_create(self.grid, self.dx, dt, l, scheme, opt)
+        self.nbytes = pic_footprint(self.ctx)
+        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        pic_bind_memory(self.ctx, self.mem.data_ptr(), self.nbytes)
+        self.counts = [0] * len(capacity)
+        self.tile, self.ntiles, self.sort_interval = pic_tile_info(self.ctx)
+
+    def load(self, species, q, m, w, x, u):
+        import torch
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            x = x.contiguous().to(torch.float64)
+            u = u.contiguous().to(torch.float64)
+            n = int(u.shape[-1])
+            pic_load_particles_device(self.ctx, species, q, m, w, x.data_ptr(), u.data_ptr(), n)
+        else:
+            if isinstance(x, torch.Tensor):
+                x, u = x.numpy(), u.numpy()
+            n = int(np.asarray(u).shape[-1])
+            pic_load_particles(self.ctx, species, q, m, w, x, u)
+        self.counts[species] = n
+
+    def set_field(self, comp, a):
+        pic_set_fields(self.ctx, comp, a)
+
+    def step(self, n=1):
+        pic_step(self.ctx, n)
+
+    def field(self, comp):
+        return pic_read_fields(self.ctx, comp, self.ncell).reshape(self.grid[2], self.grid[1],
+                                                                   self.grid[0])
+
+    def particles(self, species):
+        return pic_read_particles(self.ctx, species, self.counts[species], self.dim)
+
+    def tile_offsets(self, species):
+        return pic_read_tile_offsets(self.ctx, species, self.ntiles)
+
+    def diag(self):
+        return pic_diag(self.ctx)
+
+    def sync(self):
+        pic_sync(self.ctx)
+
+    def sort(self):
+        pic_sort(self.ctx)
+
+    def gpp_ms(self):
+        return pic_last_gpp_ms(self.ctx)
+
+    def kernel_launches(self):
+        return pic_kernel_launches(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            pic_destroy(self.ctx)
+            self.ctx = None
+            self.mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

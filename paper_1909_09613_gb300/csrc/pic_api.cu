@@ -1,0 +1,634 @@
+// C-ABI of libpic (declared in include/pic.h): context management, device memory layout,
+// particle loading and read-back, the step loop, and diagnostics.
+#include "pic.h"
+#include "pic_launch.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+using namespace pic;
+
+namespace pic {
+cudaError_t launch_gpp_f32(const RunDev &rd, int kt, cudaStream_t st);
+cudaError_t launch_gpp_f64(const RunDev &rd, int kt, cudaStream_t st);
+size_t gpp_smem_bytes_f32(const RunDev &rd);
+size_t gpp_smem_bytes_f64(const RunDev &rd);
+}  // namespace pic
+
+struct pic_ctx {
+    RunDev rd;                 // device-side descriptor (pointers filled on bind)
+    int kt;                    // nodes of the integer-node stencil (max over axes)
+    int sort_interval;
+    int age;                   // steps since the last sort
+    int64_t step;
+    cudaStream_t stream;
+    int64_t cap[PIC_MAX_SPECIES];
+    bool loaded[PIC_MAX_SPECIES];
+    // memory
+    char *base;
+    size_t bytes;
+    bool owns;
+    void *bufA[PIC_MAX_SPECIES][7];   // current store: pos[3], mom[3], cell
+    void *bufB[PIC_MAX_SPECIES][7];   // sort target
+    int64_t *tile_start[PIC_MAX_SPECIES];
+    SortScratch sc;
+    char *staging;
+    size_t staging_bytes;
+    double *diag_out;
+    double *rho;
+    int32_t *err;
+    size_t smem;
+    // timing of the particle pass: a ring of event pairs, drained when it fills
+    cudaEvent_t ev0[64], ev1[64];
+    bool have_events;
+    int ev_pending;
+    double gpp_ms;
+    int64_t gpp_launches;
+    int64_t kernel_launches;   // every kernel this context has launched
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int pos_bytes(const pic_ctx *c) { return c->rd.prec == PIC_FP32_MIXED ? 4 : 8; }
+
+int particle_bytes(const pic_ctx *c)
+{
+    const int d = c->rd.dim;
+    return c->rd.prec == PIC_FP32_MIXED ? 4 + 4 * d + 12 : 8 * d + 24;
+}
+
+int status_of(cudaError_t e) { return e == cudaSuccess ? PIC_OK : PIC_ECUDA; }
+
+// Node offsets (relative to a particle's cell) that the stencils of one axis can touch.
+void axis_reach(int l, const TTable &tt, int kt, int *lo, int *hi)
+{
+    const double eps = 1e-9;
+    auto fl = [](double v) { return (int)std::floor(v); };
+    const double hl = 0.5 * l;
+    const int wh_lo = fl(-hl), wh_hi = fl(1.0 - eps - hl) + l;
+    const double R = tt.Rint + tt.Rfrac;
+    const int t_lo = fl(-R) + 1, t_hi = fl(1.0 - eps - R) + 1 + kt - 1;
+    const double h0 = 0.5 * (l - 1);
+    const int d_lo = fl(-h0) - 1, d_hi = fl(1.0 - eps - h0) + l + 1;
+    *lo = -std::min(wh_lo, std::min(t_lo, d_lo));
+    *hi = std::max(wh_hi, std::max(t_hi, d_hi));
+}
+
+void refresh_species_ptrs(pic_ctx *c)
+{
+    for (int s = 0; s < c->rd.nsp; ++s) {
+        SpeciesDev &sp = c->rd.sp[s];
+        for (int a = 0; a < 3; ++a) {
+            sp.pos[a] = c->bufA[s][a];
+            sp.mom[a] = c->bufA[s][3 + a];
+        }
+        sp.cell = (int32_t *)c->bufA[s][6];
+        sp.tile_start = c->tile_start[s];
+    }
+}
+
+int latched_status(pic_ctx *c)
+{
+    int32_t e = 0;
+    if (cudaMemcpyAsync(&e, c->err, sizeof(e), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return PIC_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+    if (e & PIC_ERR_NONFINITE) return PIC_ENAN;
+    if (e & PIC_ERR_OUTSIDE_TILE) return PIC_EOVERFLOW;
+    if (e & PIC_ERR_TIMEOUT) return PIC_ETIMEOUT;
+    return PIC_OK;
+}
+
+int sort_species(pic_ctx *c, int s)
+{
+    RunDev rd = c->rd;
+    refresh_species_ptrs(c);
+    rd = c->rd;
+    cudaError_t e = launch_sort(rd, s, c->sc, c->tile_start[s], c->bufB[s], c->bufB[s] + 3,
+                                (int32_t *)c->bufB[s][6], c->stream);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    c->kernel_launches += rd.sp[s].n > 0 ? 5 : 3;
+    for (int i = 0; i < 7; ++i) std::swap(c->bufA[s][i], c->bufB[s][i]);
+    refresh_species_ptrs(c);
+    return PIC_OK;
+}
+
+// Add the elapsed time of the pending event pairs to gpp_ms (waits for the last one).
+void drain_events(pic_ctx *c)
+{
+    if (!c->have_events || c->ev_pending == 0) return;
+    if (cudaEventSynchronize(c->ev1[c->ev_pending - 1]) == cudaSuccess) {
+        for (int i = 0; i < c->ev_pending; ++i) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, c->ev0[i], c->ev1[i]) == cudaSuccess) c->gpp_ms += ms;
+        }
+    }
+    c->ev_pending = 0;
+}
+
+int sort_all(pic_ctx *c)
+{
+    for (int s = 0; s < c->rd.nsp; ++s) {
+        const int r = sort_species(c, s);
+        if (r != PIC_OK) return r;
+    }
+    c->age = 0;
+    return PIC_OK;
+}
+
+int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n,
+                const double *x, const double *u, bool on_device)
+{
+    if (!c || !c->base) return c ? PIC_ESTATE : PIC_EINVAL;
+    if (species < 0 || species >= c->rd.nsp || n < 0 || n > c->cap[species]) return PIC_EINVAL;
+    if (!(m > 0.0) || !(w >= 0.0) || (n > 0 && (!x || !u))) return PIC_EINVAL;
+    SpeciesDev &sp = c->rd.sp[species];
+    const RunDev &rd = c->rd;
+    const double vc = rd.dx[0] * rd.dx[1] * (rd.dim == 3 ? rd.dx[2] : 1.0);
+    sp.q = q;
+    sp.m = m;
+    sp.w = w;
+    sp.qmdt_half = 0.5 * q * rd.dt / m;
+    for (int a = 0; a < 3; ++a) sp.kx[a] = -q * w * rd.dx[a] / (vc * rd.dt);
+    sp.kz = q * w / vc;
+    sp.n = n;
+    const int d = rd.dim;
+    const double *xd = x, *ud = u;
+    if (!on_device && n > 0) {
+        const size_t xb = (size_t)d * n * sizeof(double), ub = (size_t)3 * n * sizeof(double);
+        if (xb + ub > c->staging_bytes) return PIC_ENOMEM;
+        double *sx = (double *)c->staging;
+        double *su = (double *)(c->staging + xb);
+        if (cudaMemcpyAsync(sx, x, xb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return PIC_ECUDA;
+        if (cudaMemcpyAsync(su, u, ub, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return PIC_ECUDA;
+        xd = sx;
+        ud = su;
+    }
+    refresh_species_ptrs(c);
+    if (launch_pack(c->rd, species, xd, ud, n, c->stream) != cudaSuccess) return PIC_ECUDA;
+    if (n > 0) c->kernel_launches += 1;
+    const int r = sort_species(c, species);
+    if (r != PIC_OK) return r;
+    c->loaded[species] = true;
+    c->age = 0;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pic_strerror(int s)
+{
+    switch (s) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument";
+    case PIC_ENOMEM: return "not enough device memory bound";
+    case PIC_ECFL: return "time step violates the Courant limit or the one-cell-per-step bound";
+    case PIC_ECUDA: return "CUDA runtime error";
+    case PIC_EOVERFLOW: return "a particle left the staged region of its tile";
+    case PIC_ETIMEOUT: return "a bounded device wait gave up";
+    case PIC_ENAN: return "non-finite value in fields or particles";
+    case PIC_ESTATE: return "call out of order (no device memory bound)";
+    default: return "unknown status";
+    }
+}
+
+int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_order, int scheme,
+               const pic_options *opt, pic_ctx **out)
+{
+    if (!grid || !dx || !out) return PIC_EINVAL;
+    *out = nullptr;
+    if (spline_order < 1 || spline_order > 4) return PIC_EINVAL;
+    if (scheme != PIC_SCHEME_MC && scheme != PIC_SCHEME_WT) return PIC_EINVAL;
+    if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1) return PIC_EINVAL;
+    const int dim = grid[2] > 1 ? 3 : 2;
+    const int64_t ncell = (int64_t)grid[0] * grid[1] * grid[2];
+    if (ncell > (int64_t)1 << 30) return PIC_EINVAL;
+    for (int a = 0; a < dim; ++a)
+        if (!(dx[a] > 0.0) || !std::isfinite(dx[a])) return PIC_EINVAL;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return PIC_EINVAL;
+    double s2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        s2 += 1.0 / (dx[a] * dx[a]);
+        if (dt / dx[a] >= 1.0) return PIC_ECFL;
+    }
+    if (dt * std::sqrt(s2) >= 1.0) return PIC_ECFL;
+
+    pic_options o;
+    std::memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.n_species <= 0) o.n_species = 2;
+    if (o.n_species > PIC_MAX_SPECIES) return PIC_EINVAL;
+    if (o.precision != PIC_FP64 && o.precision != PIC_FP32_MIXED) return PIC_EINVAL;
+
+    pic_ctx *c = new (std::nothrow) pic_ctx;
+    if (!c) return PIC_ENOMEM;
+    std::memset(c, 0, sizeof(*c));
+    RunDev &rd = c->rd;
+    rd.dim = dim;
+    rd.l = spline_order;
+    rd.scheme = scheme;
+    rd.prec = o.precision;
+    rd.ncell = ncell;
+    for (int a = 0; a < 3; ++a) {
+        rd.n[a] = grid[a];
+        rd.dx[a] = (a < dim) ? dx[a] : 1.0;
+        rd.dtt[a] = (a < dim) ? dt / rd.dx[a] : 0.0;
+    }
+    rd.dt = dt;
+    // tiles
+    const int deft[2][3] = {{32, 8, 1}, {8, 4, 4}};
+    for (int a = 0; a < 3; ++a) {
+        int t = o.tile[a] > 0 ? o.tile[a] : deft[dim - 2][a];
+        if (a >= dim) t = 1;
+        t = std::min(t, rd.n[a]);
+        rd.tile[a] = t;
+        rd.ntile[a] = (rd.n[a] + t - 1) / t;
+    }
+    if ((int64_t)rd.tile[0] * rd.tile[1] * rd.tile[2] > 1024) { delete c; return PIC_EINVAL; }
+    rd.ntiles = (int64_t)rd.ntile[0] * rd.ntile[1] * rd.ntile[2];
+    // interpolation tables
+    c->kt = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (a >= dim) { build_ttable(spline_order, PIC_SCHEME_MC, 0.5, &rd.tt[a]); continue; }
+        if (!build_ttable(spline_order, scheme, rd.dtt[a], &rd.tt[a])) { delete c; return PIC_ECFL; }
+        c->kt = std::max(c->kt, rd.tt[a].K);
+    }
+    // sort interval and staged region
+    double dmax = 0.0;
+    for (int a = 0; a < dim; ++a) dmax = std::max(dmax, rd.dtt[a]);
+    int K = o.sort_interval > 0 ? o.sort_interval : (dim == 2 ? (int)std::floor(2.0 / dmax) + 1 : 8);
+    c->sort_interval = std::max(1, K);
+    int64_t nodes = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (a >= dim) { rd.pre[a] = 0; rd.post[a] = 0; rd.reg[a] = 1; rd.drift[a] = 0; continue; }
+        int lo, hi;
+        axis_reach(spline_order, rd.tt[a], c->kt, &lo, &hi);
+        const int D = (int)std::ceil((c->sort_interval - 1) * rd.dtt[a] - 1e-12);
+        rd.drift[a] = std::max(D, 0);
+        rd.pre[a] = rd.drift[a] + lo;
+        rd.post[a] = rd.drift[a] + hi;
+        rd.reg[a] = rd.tile[a] + rd.pre[a] + rd.post[a];
+        nodes *= rd.reg[a];
+    }
+    rd.reg_nodes = nodes;
+    rd.nsp = o.n_species;
+    for (int s = 0; s < o.n_species; ++s) {
+        if (o.capacity[s] < 0 || o.capacity[s] >= ((int64_t)1 << 31)) { delete c; return PIC_EINVAL; }
+        c->cap[s] = o.capacity[s];
+    }
+    c->stream = (cudaStream_t)(uintptr_t)o.stream;
+    c->smem = 0;
+    if (dim == 2) {
+        c->smem = rd.prec == PIC_FP32_MIXED ? gpp_smem_bytes_f32(rd) : gpp_smem_bytes_f64(rd);
+        if (c->smem > 227 * 1024) { delete c; return PIC_EINVAL; }
+    }
+    *out = c;
+    return PIC_OK;
+}
+
+int pic_footprint(const pic_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return PIC_EINVAL;
+    const RunDev &rd = c->rd;
+    const size_t A = 256;
+    size_t b = 0;
+    b += 9 * align_up(rd.ncell * sizeof(double), A);                           // F
+    if (rd.prec == PIC_FP32_MIXED) b += 6 * align_up(rd.ncell * sizeof(float), A);  // Fs
+    const int pb = particle_bytes(c);
+    int64_t capmax = 0, captot = 0;
+    for (int s = 0; s < rd.nsp; ++s) {
+        capmax = std::max(capmax, c->cap[s]);
+        captot += c->cap[s];
+    }
+    const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
+    for (int s = 0; s < rd.nsp; ++s) b += align_up((size_t)c->cap[s] * pb + 7 * A, A);  // current stores
+    for (int s = 0; s < rd.nsp; ++s) b += align_up((rd.ntiles + 1) * sizeof(int64_t), A);           // tile_start
+    // region aliased by sort targets, sort scratch and the host<->device staging area
+    size_t region = 0;
+    for (int s = 0; s < rd.nsp; ++s) region += align_up((size_t)c->cap[s] * pb + 7 * A, A);
+    region += 2 * align_up(rd.ntiles * TC * sizeof(int32_t), A);
+    region += 3 * align_up((size_t)capmax * sizeof(int32_t), A);
+    region += align_up((rd.ntiles + 1) * sizeof(int64_t), A);
+    const size_t stage = align_up((size_t)capmax * ((rd.dim + 3) * sizeof(double) + sizeof(int64_t)) + 4 * A, A);
+    b += std::max(region, stage);
+    b += align_up(rd.ncell * sizeof(double), A);  // rho
+    b += 2 * A;                                   // diag out, err
+    b += A;                                       // base alignment slack
+    (void)captot;
+    *bytes = b;
+    return PIC_OK;
+}
+
+int pic_bind_memory(pic_ctx *c, void *dev, size_t bytes)
+{
+    if (!c || !dev) return PIC_EINVAL;
+    size_t need = 0;
+    pic_footprint(c, &need);
+    if (bytes < need) return PIC_ENOMEM;
+    RunDev &rd = c->rd;
+    const size_t A = 256;
+    char *p = (char *)align_up((size_t)dev, A);
+    auto take = [&](size_t n) { char *r = p; p += align_up(n, A); return r; };
+    c->base = (char *)dev;
+    c->bytes = bytes;
+    for (int f = 0; f < 9; ++f) rd.F[f] = (double *)take(rd.ncell * sizeof(double));
+    for (int f = 0; f < 6; ++f) rd.Fs[f] = rd.prec == PIC_FP32_MIXED ? (float *)take(rd.ncell * sizeof(float)) : nullptr;
+    const int pbs = pos_bytes(c);
+    auto carve_store = [&](void **buf, int64_t cap, char *&q) {
+        auto t2 = [&](size_t n) { char *r = q; q += align_up(n, A); return r; };
+        for (int a = 0; a < 3; ++a) buf[a] = (a < rd.dim) ? t2((size_t)cap * pbs) : nullptr;
+        for (int a = 0; a < 3; ++a) buf[3 + a] = t2((size_t)cap * pbs);
+        buf[6] = rd.prec == PIC_FP32_MIXED ? t2((size_t)cap * sizeof(int32_t)) : nullptr;
+    };
+    const int pb = particle_bytes(c);
+    for (int s = 0; s < rd.nsp; ++s) {
+        char *q = p;
+        carve_store(c->bufA[s], c->cap[s], q);
+        take((size_t)c->cap[s] * pb + 7 * A);
+    }
+    for (int s = 0; s < rd.nsp; ++s) c->tile_start[s] = (int64_t *)take((rd.ntiles + 1) * sizeof(int64_t));
+    char *region = p;
+    int64_t capmax = 0;
+    for (int s = 0; s < rd.nsp; ++s) capmax = std::max(capmax, c->cap[s]);
+    const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
+    for (int s = 0; s < rd.nsp; ++s) {
+        char *q = p;
+        carve_store(c->bufB[s], c->cap[s], q);
+        take((size_t)c->cap[s] * pb + 7 * A);
+    }
+    c->sc.cnt = (int32_t *)take(rd.ntiles * TC * sizeof(int32_t));
+    c->sc.cell_first = (int32_t *)take(rd.ntiles * TC * sizeof(int32_t));
+    c->sc.slot = (int32_t *)take((size_t)capmax * sizeof(int32_t));
+    c->sc.key = (int32_t *)take((size_t)capmax * sizeof(int32_t));
+    c->sc.pos = (int32_t *)take((size_t)capmax * sizeof(int32_t));
+    c->sc.tile_count = (int64_t *)take((rd.ntiles + 1) * sizeof(int64_t));
+    const size_t stage = align_up((size_t)capmax * ((rd.dim + 3) * sizeof(double) + sizeof(int64_t)) + 4 * A, A);
+    if ((size_t)(p - region) < stage) p = region + stage;
+    c->staging = region;
+    c->staging_bytes = (size_t)(p - region);
+    c->rho = (double *)take(rd.ncell * sizeof(double));
+    c->diag_out = (double *)take(4 * sizeof(double));
+    c->err = (int32_t *)take(sizeof(int32_t));
+    rd.err = c->err;
+    if ((size_t)(p - (char *)dev) > bytes) return PIC_ENOMEM;
+    for (int s = 0; s < rd.nsp; ++s) {
+        rd.sp[s].n = 0;
+        rd.sp[s].m = 1.0;
+    }
+    refresh_species_ptrs(c);
+    cudaError_t e = cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream);
+    for (int f = 0; f < 9 && e == cudaSuccess; ++f)
+        e = cudaMemsetAsync(rd.F[f], 0, rd.ncell * sizeof(double), c->stream);
+    for (int f = 0; f < 6 && e == cudaSuccess && rd.Fs[f]; ++f)
+        e = cudaMemsetAsync(rd.Fs[f], 0, rd.ncell * sizeof(float), c->stream);
+    for (int s = 0; s < rd.nsp && e == cudaSuccess; ++s)
+        e = cudaMemsetAsync(c->tile_start[s], 0, (rd.ntiles + 1) * sizeof(int64_t), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return PIC_ECUDA;
+    if (!c->have_events) {
+        bool ok = true;
+        for (int i = 0; i < 64; ++i)
+            ok = ok && cudaEventCreate(&c->ev0[i]) == cudaSuccess && cudaEventCreate(&c->ev1[i]) == cudaSuccess;
+        c->have_events = ok;
+    }
+    return PIC_OK;
+}
+
+int pic_alloc(pic_ctx *c)
+{
+    if (!c) return PIC_EINVAL;
+    size_t need = 0;
+    pic_footprint(c, &need);
+    void *p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) return PIC_ENOMEM;
+    const int r = pic_bind_memory(c, p, need);
+    if (r != PIC_OK) { cudaFree(p); return r; }
+    c->owns = true;
+    return PIC_OK;
+}
+
+int pic_load_particles(pic_ctx *c, int species, double q, double m, double w, int64_t n,
+                       const double *x, const double *u)
+{
+    return load_common(c, species, q, m, w, n, x, u, false);
+}
+
+int pic_load_particles_device(pic_ctx *c, int species, double q, double m, double w, int64_t n,
+                              const double *x, const double *u)
+{
+    return load_common(c, species, q, m, w, n, x, u, true);
+}
+
+int pic_set_fields(pic_ctx *c, int comp, const double *host, size_t count)
+{
+    if (!c || !host || comp < 0 || comp > 5) return PIC_EINVAL;
+    if (!c->base) return PIC_ESTATE;
+    if (count != (size_t)c->rd.ncell) return PIC_EINVAL;
+    if (cudaMemcpyAsync(c->rd.F[comp], host, count * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess)
+        return PIC_ECUDA;
+    if (c->rd.prec == PIC_FP32_MIXED) {
+        if (launch_shadow(c->rd, c->stream) != cudaSuccess) return PIC_ECUDA;
+        c->kernel_launches += 1;
+    }
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+int pic_step(pic_ctx *c, int nsteps)
+{
+    if (!c || nsteps < 0) return PIC_EINVAL;
+    if (!c->base) return PIC_ESTATE;
+    RunDev &rd = c->rd;
+    const bool shadow = rd.prec == PIC_FP32_MIXED;
+    drain_events(c);
+    c->gpp_ms = 0.0;
+    c->gpp_launches = 0;
+    for (int it = 0; it < nsteps; ++it) {
+        if (c->age >= c->sort_interval) {
+            const int r = sort_all(c);
+            if (r != PIC_OK) return r;
+        }
+        refresh_species_ptrs(c);
+        if (cudaMemsetAsync(rd.F[6], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess) return PIC_ECUDA;
+        if (cudaMemsetAsync(rd.F[7], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess) return PIC_ECUDA;
+        if (cudaMemsetAsync(rd.F[8], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess) return PIC_ECUDA;
+        if (c->have_events) {
+            if (c->ev_pending == 64) drain_events(c);
+            cudaEventRecord(c->ev0[c->ev_pending], c->stream);
+        }
+        const cudaError_t e = rd.prec == PIC_FP32_MIXED ? launch_gpp_f32(rd, c->kt, c->stream)
+                                                        : launch_gpp_f64(rd, c->kt, c->stream);
+        if (e != cudaSuccess) return PIC_ECUDA;
+        if (c->have_events) cudaEventRecord(c->ev1[c->ev_pending++], c->stream);
+        c->gpp_launches += 1;
+        if (launch_yee_b(rd, 0.5 * rd.dt, false, c->stream) != cudaSuccess) return PIC_ECUDA;
+        if (launch_yee_e(rd, shadow, c->stream) != cudaSuccess) return PIC_ECUDA;
+        if (launch_yee_b(rd, 0.5 * rd.dt, shadow, c->stream) != cudaSuccess) return PIC_ECUDA;
+        c->kernel_launches += 4;
+        c->age += 1;
+        c->step += 1;
+    }
+    return PIC_OK;
+}
+
+int pic_last_gpp_ms(pic_ctx *c, double *ms, int64_t *launches)
+{
+    if (!c || !ms) return PIC_EINVAL;
+    drain_events(c);
+    *ms = c->gpp_ms;
+    if (launches) *launches = c->gpp_launches;
+    return PIC_OK;
+}
+
+int pic_kernel_launches(const pic_ctx *c, int64_t *count)
+{
+    if (!c || !count) return PIC_EINVAL;
+    *count = c->kernel_launches;
+    return PIC_OK;
+}
+
+int pic_sort(pic_ctx *c)
+{
+    if (!c) return PIC_EINVAL;
+    if (!c->base) return PIC_ESTATE;
+    return sort_all(c);
+}
+
+int pic_sync(pic_ctx *c)
+{
+    if (!c) return PIC_EINVAL;
+    if (!c->base) return PIC_ESTATE;
+    return latched_status(c);
+}
+
+int pic_read_fields(pic_ctx *c, int comp, double *host, size_t count)
+{
+    if (!c || !host || comp < 0 || comp > 8) return PIC_EINVAL;
+    if (!c->base) return PIC_ESTATE;
+    if (count != (size_t)c->rd.ncell) return PIC_EINVAL;
+    if (cudaMemcpyAsync(host, c->rd.F[comp], count * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess)
+        return PIC_ECUDA;
+    return latched_status(c);
+}
+
+int pic_read_particles(pic_ctx *c, int species, double *x, double *u, int64_t *cell, int64_t n)
+{
+    if (!c || species < 0 || species >= c->rd.nsp) return PIC_EINVAL;
+    if (!c->base) return PIC_ESTATE;
+    const RunDev &rd = c->rd;
+    const int64_t np = rd.sp[species].n;
+    if (n != np || (np > 0 && (!x || !u))) return PIC_EINVAL;
+    if (np == 0) return latched_status(c);
+    refresh_species_ptrs(c);
+    const size_t xb = (size_t)rd.dim * np * sizeof(double), ub = (size_t)3 * np * sizeof(double);
+    const size_t cb = (size_t)np * sizeof(int64_t);
+    if (xb + ub + cb > c->staging_bytes) return PIC_ENOMEM;
+    double *sx = (double *)c->staging;
+    double *su = (double *)(c->staging + xb);
+    int64_t *scell = (int64_t *)(c->staging + xb + ub);
+    if (launch_unpack(c->rd, species, sx, su, scell, c->stream) != cudaSuccess) return PIC_ECUDA;
+    c->kernel_launches += 1;
+    if (cudaMemcpyAsync(x, sx, xb, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return PIC_ECUDA;
+    if (cudaMemcpyAsync(u, su, ub, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return PIC_ECUDA;
+    if (cell && cudaMemcpyAsync(cell, scell, cb, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return PIC_ECUDA;
+    return latched_status(c);
+}
+
+int pic_read_tile_offsets(pic_ctx *c, int species, int64_t *offsets, int64_t count)
+{
+    if (!c || !offsets || species < 0 || species >= c->rd.nsp) return PIC_EINVAL;
+    if (!c->base) return PIC_ESTATE;
+    if (count != c->rd.ntiles + 1) return PIC_EINVAL;
+    if (cudaMemcpyAsync(offsets, c->tile_start[species], count * sizeof(int64_t),
+                        cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return PIC_ECUDA;
+    return latched_status(c);
+}
+
+int pic_tile_info(const pic_ctx *c, int32_t tile[3], int64_t *ntiles, int32_t *sort_interval)
+{
+    if (!c) return PIC_EINVAL;
+    if (tile)
+        for (int a = 0; a < 3; ++a) tile[a] = c->rd.tile[a];
+    if (ntiles) *ntiles = c->rd.ntiles;
+    if (sort_interval) *sort_interval = c->sort_interval;
+    return PIC_OK;
+}
+
+int pic_diag(pic_ctx *c, pic_diag_t *out)
+{
+    if (!c || !out) return PIC_EINVAL;
+    if (!c->base) return PIC_ESTATE;
+    refresh_species_ptrs(c);
+    const RunDev &rd = c->rd;
+    if (launch_diag(rd, c->diag_out, c->rho, c->stream) != cudaSuccess) return PIC_ECUDA;
+    c->kernel_launches += 2 + 2 * rd.nsp;
+    double h[4] = {0, 0, 0, 0};
+    int32_t e = 0;
+    if (cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return PIC_ECUDA;
+    if (cudaMemcpyAsync(&e, c->err, sizeof(e), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return PIC_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+    const double vc = rd.dx[0] * rd.dx[1] * (rd.dim == 3 ? rd.dx[2] : 1.0);
+    out->step = c->step;
+    out->field_energy = 0.5 * h[0] * vc;
+    out->kinetic_energy = h[1];
+    double qt = 0.0;
+    for (int s = 0; s < rd.nsp; ++s) qt += rd.sp[s].q * rd.sp[s].w * (double)rd.sp[s].n;
+    out->total_charge = qt;
+    out->max_gauss_residual = h[2];
+    out->error_flags = e;
+    if (e & PIC_ERR_NONFINITE) return PIC_ENAN;
+    if (e & PIC_ERR_OUTSIDE_TILE) return PIC_EOVERFLOW;
+    return PIC_OK;
+}
+
+int pic_batch_step(pic_ctx **runs, int n, int nsteps)
+{
+    if (!runs || n < 0 || nsteps < 0) return PIC_EINVAL;
+    for (int it = 0; it < nsteps; ++it)
+        for (int r = 0; r < n; ++r) {
+            const int st = pic_step(runs[r], 1);
+            if (st != PIC_OK) return st;
+        }
+    return PIC_OK;
+}
+
+void pic_destroy(pic_ctx *c)
+{
+    if (!c) return;
+    if (c->base) cudaStreamSynchronize(c->stream);
+    if (c->have_events) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEventDestroy(c->ev0[i]);
+            cudaEventDestroy(c->ev1[i]);
+        }
+    }
+    if (c->owns && c->base) cudaFree(c->base);
+    delete c;
+}
+
+// Host evaluation of the per-axis integer-node weights that the kernels use (T_l for the WT
+// scheme, W_l for MC): particle offset delta in [0,1) of its cell, dtt = c dt / dx.
+// Fills w[0..*count-1] for nodes *base .. *base + *count - 1 relative to the cell.
+int pic_axis_weights(int spline_order, int scheme, double dtt, double delta, double *w,
+                     int *base, int *count)
+{
+    if (!w || !base || !count || !(delta >= 0.0 && delta < 1.0)) return PIC_EINVAL;
+    TTable t;
+    if (!build_ttable(spline_order, scheme, dtt, &t)) return PIC_EINVAL;
+    *base = ttable_eval_host(&t, spline_order, delta, w);
+    *count = t.K;
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Shared device-side definitions of libpic: run descriptors, the 1-D interpolation weights of
+// the WT scheme, and small helpers.  Everything here is written for sm_103a (GB300).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define PIC_NSP_MAX 4
+#define PIC_TK_MAX 6  // max nodes of a T_l stencil: ceil(l + 2 c dt/dx) <= 6 for l <= 4
+
+namespace pic {
+
+// ------------------------------------------------------------------------------------------
+// Per-axis table of the integer-node interpolation function of the WT scheme.
+//
+// T_l (Sec. 2, Eq. tau_l) is W_{l-1} averaged over a box of half-width dtt = c dt/dx: a
+// piecewise polynomial of degree l with support radius R = l/2 + dtt.  For a particle at
+// offset delta in [0,1) of its cell, let v = delta - R, phi = v - floor(v), first node
+// b = floor(v) + 1 (relative to the cell).  The weight of node b + k (k = 0..K-1) is
+// T_l(R - 1 + phi - k); as a function of phi it has breakpoints only at phi = 0 and at
+// phi_b = frac(-2 dtt), so on each of the two sub-intervals it is one polynomial of degree l.
+// coef[p][k][m] is its m-th Taylor coefficient about the sub-interval's left end a[p].
+// For the MC scheme the same table holds W_l at integer nodes (R = (l+1)/2, one piece).
+// ------------------------------------------------------------------------------------------
+struct TTable {
+    int K;            // nodes in the stencil window
+    int Rint;         // floor(R)
+    double Rfrac;     // R - floor(R)
+    double phib;      // interior breakpoint (0 if none)
+    double coef[2][PIC_TK_MAX][5];
+    float coef_f[2][PIC_TK_MAX][5];
+    float Rfrac_f, phib_f;
+};
+
+struct SpeciesDev {
+    double q, m, w;
+    double qmdt_half;     // q dt / (2 m)
+    double kx[3];         // -q w dx_a / (Vc dt): Esirkepov prefix scale per axis
+    double kz;            // q w / Vc: out-of-plane current scale (2D)
+    int64_t n;
+    // particle store (current order).  FP64 form: xi[a] double (cell units), u[a] double.
+    // FP32 form: cell int32, off[a] float, u[a] float.
+    void *pos[3];
+    void *mom[3];
+    int32_t *cell;
+    const int64_t *tile_start;  // ntiles + 1
+};
+
+struct RunDev {
+    int dim, l, scheme, prec;
+    int n[3];
+    int tile[3];
+    int ntile[3];
+    int64_t ntiles;
+    int64_t ncell;
+    double dx[3];
+    double dt;
+    double dtt[3];  // c dt / dx_a
+    // staged region around a tile: node local index = cell - tile_origin + pre
+    int pre[3], post[3], reg[3];
+    int drift[3];      // max cells a particle can be away from its sorted tile (per axis)
+    int64_t reg_nodes;
+    // fields (FP64, index (k*ny + j)*nx + i) and FP32 shadows of E, B (precision form)
+    double *F[9];
+    float *Fs[6];
+    TTable tt[3];
+    int nsp;
+    SpeciesDev sp[PIC_NSP_MAX];
+    int32_t *err;
+};
+
+// ------------------------------------------------------------------------------------------
+// B-spline weights W_l at the l+1 nodes that carry a non-zero weight (Sec. 2, Eq. shape-real).
+// psi in [0,1); node k (k = 0..L) sits at distance (L-1)/2 + psi - k from the particle.
+// These are the uniform B-spline basis polynomials written in the local variable psi.
+// ------------------------------------------------------------------------------------------
+template <int L, typename R>
+__device__ __forceinline__ void bspline(R p, R *w)
+{
+    const R one = R(1);
+    const R q = one - p;
+    if constexpr (L == 1) {
+        w[0] = q;
+        w[1] = p;
+    } else if constexpr (L == 2) {
+        w[0] = R(0.5) * q * q;
+        w[1] = R(0.5) + p * q;
+        w[2] = R(0.5) * p * p;
+    } else if constexpr (L == 3) {
+        const R s6 = R(1) / R(6);
+        const R p2 = p * p, p3 = p2 * p;
+        w[0] = s6 * q * q * q;
+        w[1] = s6 * (R(3) * p3 - R(6) * p2 + R(4));
+        w[2] = s6 * (R(-3) * p3 + R(3) * p2 + R(3) * p + one);
+        w[3] = s6 * p3;
+    } else {
+        const R s24 = R(1) / R(24);
+        const R p2 = p * p;
+        const R q2 = q * q;
+        w[0] = s24 * q2 * q2;
+        w[1] = s24 * ((((R(-4) * p + R(12)) * p - R(6)) * p - R(12)) * p + R(11));
+        w[2] = s24 * ((((R(6) * p - R(12)) * p - R(6)) * p + R(12)) * p + R(11));
+        w[3] = s24 * ((((R(-4) * p + R(4)) * p + R(6)) * p + R(4)) * p + one);
+        w[4] = s24 * p2 * p2;
+    }
+}
+
+// Split an offset delta in [0,1) against a node lattice shifted by h = c + (L-1)/2 (c = 0 for
+// integer nodes, 1/2 for half-integer nodes): returns the first node (relative to the cell)
+// and the local coordinate psi in [0,1).
+template <int L, typename R>
+__device__ __forceinline__ int spline_base(R delta, bool half, R &psi)
+{
+    // h2 = 2h is an integer: 2c + L - 1
+    const int h2 = (half ? 1 : 0) + L - 1;
+    const int hi = h2 >> 1;            // integer part of h
+    if (h2 & 1) {                      // h = hi + 1/2
+        if (delta >= R(0.5)) { psi = delta - R(0.5); return -hi; }
+        psi = delta + R(0.5);
+        if (psi >= R(1)) { psi = R(0); return -hi; }  // delta + 1/2 rounded up to 1
+        return -hi - 1;
+    }
+    psi = delta;
+    return -hi;
+}
+
+// Weights of the integer-node factor from a TTable (WT: T_l, MC: W_l).  Returns the first
+// node relative to the cell; w[0..KT-1] (entries beyond the table's K are zero).
+template <int L, int KT, typename R>
+__device__ __forceinline__ int ttable_weights(const TTable &t, R delta, R *w)
+{
+    R v;
+    if constexpr (sizeof(R) == 8) v = delta - R(t.Rfrac);
+    else v = delta - R(t.Rfrac_f);
+    // v in (-1, 1)
+    int fl = 0;
+    R phi = v;
+    if (v < R(0)) {
+        phi = v + R(1);
+        fl = -1;
+        if (phi >= R(1)) { phi = R(0); fl = 0; }
+    }
+    const int base = fl - t.Rint + 1;
+    R phib;
+    if constexpr (sizeof(R) == 8) phib = R(t.phib);
+    else phib = R(t.phib_f);
+    const int p = (phi >= phib) ? 1 : 0;
+    const R tl = phi - (p ? phib : R(0));
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        R acc;
+        if constexpr (sizeof(R) == 8) {
+            acc = R(t.coef[p][k][L]);
+#pragma unroll
+            for (int m = L - 1; m >= 0; --m) acc = acc * tl + R(t.coef[p][k][m]);
+        } else {
+            acc = R(t.coef_f[p][k][L]);
+#pragma unroll
+            for (int m = L - 1; m >= 0; --m) acc = acc * tl + R(t.coef_f[p][k][m]);
+        }
+        w[k] = acc;
+    }
+    return base;
+}
+
+__device__ __forceinline__ int wrap_idx(int i, int n)
+{
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+__device__ __forceinline__ void set_err(int32_t *err, int bit)
+{
+    if (err) atomicOr(err, bit);
+}
+
+}  // namespace pic

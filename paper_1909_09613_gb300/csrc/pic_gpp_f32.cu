@@ -1,0 +1,56 @@
+// Instantiations of the fused particle pass, float arithmetic.
+#include "pic_gpp_kernels.cuh"
+#include "pic_launch.h"
+
+namespace pic {
+
+namespace {
+
+template <int L, int KT>
+__global__ void __launch_bounds__(256) k_gpp2d(const __grid_constant__ RunDev rd)
+{
+    extern __shared__ __align__(16) char smem[];
+    tile_2d<L, KT, float>(rd, smem, blockIdx.x);
+}
+
+template <int L, int KT>
+__global__ void __launch_bounds__(128) k_gpp3d(const __grid_constant__ RunDev rd)
+{
+    tile_3d<L, KT, float>(rd, blockIdx.x);
+}
+
+template <int L, int KT>
+cudaError_t go(const RunDev &rd, cudaStream_t st)
+{
+    if (rd.dim == 2) {
+        const size_t smem = stage2d_bytes<float>(rd.reg_nodes);
+        cudaError_t e = cudaFuncSetAttribute(k_gpp2d<L, KT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_gpp2d<L, KT><<<(unsigned)rd.ntiles, 256, smem, st>>>(rd);
+    } else {
+        k_gpp3d<L, KT><<<(unsigned)rd.ntiles, 128, 0, st>>>(rd);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gpp_f32(const RunDev &rd, int kt, cudaStream_t st)
+{
+    const bool wide = kt > rd.l + 1;
+    switch (rd.l) {
+    case 1: return wide ? go<1, 3>(rd, st) : go<1, 2>(rd, st);
+    case 2: return wide ? go<2, 4>(rd, st) : go<2, 3>(rd, st);
+    case 3: return wide ? go<3, 5>(rd, st) : go<3, 4>(rd, st);
+    case 4: return wide ? go<4, 6>(rd, st) : go<4, 5>(rd, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t gpp_smem_bytes_f32(const RunDev &rd)
+{
+    return rd.dim == 2 ? stage2d_bytes<float>(rd.reg_nodes) : 0;
+}
+
+}  // namespace pic

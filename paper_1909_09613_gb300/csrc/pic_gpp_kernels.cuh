@@ -1,0 +1,477 @@
+// Tile kernels of the fused particle pass (2D shared-memory staged, 3D L1/global) and the
+// per-tile driver shared by the single-run and the batched launches.
+#pragma once
+#include "pic_gpp.cuh"
+
+namespace pic {
+
+// Accumulation type of the shared-memory current tile: FP32 in the precision form, FP64 in
+// the plain form.
+template <typename R> struct AccT { typedef R T; };
+
+// Shared-memory layout of a staged 2D tile (all arrays reg_nodes long, x fastest):
+//   pa = (E1, B2) pairs  [both sit at (i+1/2, j): W along x, T along y]
+//   pb = (E2, B1) pairs  [both sit at (i, j+1/2): T along x, W along y]
+//   e3 = E3 [(i, j): T T],  b3 = B3 [(i+1/2, j+1/2): W W],  j1, j2, j3.
+template <typename R>
+struct Stage2D {
+    typename Vec2<R>::T *pa, *pb;
+    R *e3, *b3;
+    R *j1, *j2, *j3;
+    TTable *tt;
+};
+
+template <typename R>
+__host__ __device__ inline size_t stage2d_bytes(int64_t nodes)
+{
+    size_t b = 2 * sizeof(TTable);
+    b += (size_t)nodes * (2 * sizeof(typename Vec2<R>::T) + 5 * sizeof(R));
+    return b;
+}
+
+template <typename R>
+__device__ __forceinline__ Stage2D<R> stage2d_carve(char *smem, int64_t nodes)
+{
+    Stage2D<R> s;
+    s.tt = (TTable *)smem;
+    char *p = smem + 2 * sizeof(TTable);
+    s.pa = (typename Vec2<R>::T *)p; p += nodes * sizeof(typename Vec2<R>::T);
+    s.pb = (typename Vec2<R>::T *)p; p += nodes * sizeof(typename Vec2<R>::T);
+    s.e3 = (R *)p; p += nodes * sizeof(R);
+    s.b3 = (R *)p; p += nodes * sizeof(R);
+    s.j1 = (R *)p; p += nodes * sizeof(R);
+    s.j2 = (R *)p; p += nodes * sizeof(R);
+    s.j3 = (R *)p;
+    return s;
+}
+
+// Stage fields of tile (tx, ty) and zero the current tile.
+template <typename R>
+__device__ void stage2d_load(const RunDev &rd, const Stage2D<R> &st, int x0, int y0)
+{
+    const int RX = rd.reg[0];
+    const int64_t nodes = rd.reg_nodes;
+    for (int i = threadIdx.x; i < (int)(2 * sizeof(TTable) / sizeof(int)); i += blockDim.x)
+        ((int *)st.tt)[i] = ((const int *)rd.tt)[i];
+    for (int64_t n = threadIdx.x; n < nodes; n += blockDim.x) {
+        const int rx = (int)(n % RX), ry = (int)(n / RX);
+        const int gx = wrap_idx(x0 - rd.pre[0] + rx, rd.n[0]);
+        const int gy = wrap_idx(y0 - rd.pre[1] + ry, rd.n[1]);
+        const int64_t g = (int64_t)gy * rd.n[0] + gx;
+        typename Vec2<R>::T a, b;
+        if constexpr (sizeof(R) == 4) {
+            a.x = __ldg(rd.Fs[0] + g); a.y = __ldg(rd.Fs[4] + g);
+            b.x = __ldg(rd.Fs[1] + g); b.y = __ldg(rd.Fs[3] + g);
+            st.e3[n] = __ldg(rd.Fs[2] + g);
+            st.b3[n] = __ldg(rd.Fs[5] + g);
+        } else {
+            a.x = __ldg(rd.F[0] + g); a.y = __ldg(rd.F[4] + g);
+            b.x = __ldg(rd.F[1] + g); b.y = __ldg(rd.F[3] + g);
+            st.e3[n] = __ldg(rd.F[2] + g);
+            st.b3[n] = __ldg(rd.F[5] + g);
+        }
+        st.pa[n] = a;
+        st.pb[n] = b;
+        st.j1[n] = R(0);
+        st.j2[n] = R(0);
+        st.j3[n] = R(0);
+    }
+}
+
+// Add the current tile to the global FP64 current and clear it.
+template <typename R>
+__device__ void stage2d_flush(const RunDev &rd, const Stage2D<R> &st, int x0, int y0)
+{
+    const int RX = rd.reg[0];
+    const int64_t nodes = rd.reg_nodes;
+    for (int64_t n = threadIdx.x; n < nodes; n += blockDim.x) {
+        const R a = st.j1[n], b = st.j2[n], c = st.j3[n];
+        if (a == R(0) && b == R(0) && c == R(0)) continue;
+        const int rx = (int)(n % RX), ry = (int)(n / RX);
+        const int gx = wrap_idx(x0 - rd.pre[0] + rx, rd.n[0]);
+        const int gy = wrap_idx(y0 - rd.pre[1] + ry, rd.n[1]);
+        const int64_t g = (int64_t)gy * rd.n[0] + gx;
+        if (a != R(0)) atomicAdd(rd.F[6] + g, (double)a);
+        if (b != R(0)) atomicAdd(rd.F[7] + g, (double)b);
+        if (c != R(0)) atomicAdd(rd.F[8] + g, (double)c);
+        st.j1[n] = R(0);
+        st.j2[n] = R(0);
+        st.j3[n] = R(0);
+    }
+}
+
+// Local coordinate of a cell index along one axis, relative to the tile origin, taking the
+// periodic image that lies within [-D, tile + D).  Returns false if none does.
+__device__ __forceinline__ bool local_coord(int c, int origin, int tile, int drift, int n, int &lc)
+{
+    int l = c - origin;
+    if (l < -drift) l += n;
+    if (l >= tile + drift) l -= n;
+    lc = l;
+    return l >= -drift && l < tile + drift;
+}
+
+// One particle, 2D, staged tile.
+template <int L, int KT, typename R>
+__device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &sp,
+                                            const Stage2D<R> &st, int64_t p, int x0, int y0)
+{
+    PState<R> s;
+    load_particle<2, R>(rd, sp, p, s);
+    int lx, ly;
+    const bool okx = local_coord(s.c[0], x0, rd.tile[0], rd.drift[0], rd.n[0], lx);
+    const bool oky = local_coord(s.c[1], y0, rd.tile[1], rd.drift[1], rd.n[1], ly);
+    if (!(okx && oky)) {
+        set_err(rd.err, 1);
+        return;
+    }
+    const int RX = rd.reg[0];
+    const int sx = lx + rd.pre[0], sy = ly + rd.pre[1];
+
+    AxisW<L, KT, R> wx, wy;
+    axis_weights<L, KT, R>(st.tt[0], s.d[0], wx);
+    axis_weights<L, KT, R>(st.tt[1], s.d[1], wy);
+
+    // ---- gather (Eq. interpolation-EB-real-mod; MC when the tables hold W_l) ----
+    R E[3], B[3];
+    {
+        // (E1, B2): W along x (half nodes), T along y (integer nodes)
+        R e1 = R(0), b2 = R(0);
+#pragma unroll
+        for (int b = 0; b < KT; ++b) {
+            const int row = (sy + wy.bt + b) * RX + sx + wx.bh;
+            R re = R(0), rb = R(0);
+#pragma unroll
+            for (int a = 0; a <= L; ++a) {
+                const typename Vec2<R>::T v = st.pa[row + a];
+                re += wx.wh[a] * v.x;
+                rb += wx.wh[a] * v.y;
+            }
+            e1 += wy.wt[b] * re;
+            b2 += wy.wt[b] * rb;
+        }
+        // (E2, B1): T along x, W along y
+        R e2 = R(0), b1 = R(0);
+#pragma unroll
+        for (int b = 0; b <= L; ++b) {
+            const int row = (sy + wy.bh + b) * RX + sx + wx.bt;
+            R re = R(0), rb = R(0);
+#pragma unroll
+            for (int a = 0; a < KT; ++a) {
+                const typename Vec2<R>::T v = st.pb[row + a];
+                re += wx.wt[a] * v.x;
+                rb += wx.wt[a] * v.y;
+            }
+            e2 += wy.wh[b] * re;
+            b1 += wy.wh[b] * rb;
+        }
+        // E3: T T
+        R e3 = R(0);
+#pragma unroll
+        for (int b = 0; b < KT; ++b) {
+            const int row = (sy + wy.bt + b) * RX + sx + wx.bt;
+            R r = R(0);
+#pragma unroll
+            for (int a = 0; a < KT; ++a) r += wx.wt[a] * st.e3[row + a];
+            e3 += wy.wt[b] * r;
+        }
+        // B3: W W
+        R b3 = R(0);
+#pragma unroll
+        for (int b = 0; b <= L; ++b) {
+            const int row = (sy + wy.bh + b) * RX + sx + wx.bh;
+            R r = R(0);
+#pragma unroll
+            for (int a = 0; a <= L; ++a) r += wx.wh[a] * st.b3[row + a];
+            b3 += wy.wh[b] * r;
+        }
+        E[0] = e1; E[1] = e2; E[2] = e3;
+        B[0] = b1; B[1] = b2; B[2] = b3;
+    }
+
+    // ---- Boris push ----
+    boris<R>(R(sp.qmdt_half), E, B, s.u);
+    const R g = sqrt(R(1) + s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
+    const R ig = R(1) / g;
+
+    // ---- move ----
+    R o[2];
+    int cn[2], shv[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+        shv[a] = move_axis<R>(s.d[a], R(rd.dtt[a]) * s.u[a] * ig, s.c[a], rd.n[a], o[a], cn[a]);
+
+    // ---- Esirkepov deposit into the shared current tile ----
+    AxisS<L, R> Sx, Sy;
+    axis_shapes<L, R>(s.d[0], shv[0], o[0], Sx);
+    axis_shapes<L, R>(s.d[1], shv[1], o[1], Sy);
+    const R kx = R(sp.kx[0]), ky = R(sp.kx[1]);
+    const R kz = R(sp.kz) * s.u[2] * ig;
+    const R third = R(1) / R(3), sixth = R(1) / R(6);
+    R DSx[L + 2], DSy[L + 2], Ax[L + 2], Ay[L + 2], px[L + 2], py[L + 2];
+    R acc_x = R(0), acc_y = R(0);
+#pragma unroll
+    for (int k = 0; k < L + 2; ++k) {
+        DSx[k] = Sx.s1[k] - Sx.s0[k];
+        DSy[k] = Sy.s1[k] - Sy.s0[k];
+        Ax[k] = Sx.s0[k] + R(0.5) * DSx[k];
+        Ay[k] = Sy.s0[k] + R(0.5) * DSy[k];
+        acc_x += DSx[k];
+        acc_y += DSy[k];
+        px[k] = acc_x;
+        py[k] = acc_y;
+    }
+    const int jx0 = sx + Sx.wb, jy0 = sy + Sy.wb;
+#pragma unroll
+    for (int b = 0; b < L + 2; ++b) {
+        const int row = (jy0 + b) * RX + jx0;
+        const R ayk = kx * Ay[b];
+        const R z0 = third * Sy.s0[b] + sixth * Sy.s1[b];
+        const R z1 = sixth * Sy.s0[b] + third * Sy.s1[b];
+        const R pyk = (b <= L) ? ky * py[b] : R(0);
+#pragma unroll
+        for (int a = 0; a < L + 2; ++a) {
+            if (a <= L) atomicAdd(st.j1 + row + a, ayk * px[a]);
+            if (b <= L) atomicAdd(st.j2 + row + a, pyk * Ax[a]);
+            atomicAdd(st.j3 + row + a, kz * (Sx.s0[a] * z0 + Sx.s1[a] * z1));
+        }
+    }
+
+    // ---- store ----
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ((R *)sp.mom[a])[p] = s.u[a];
+    if constexpr (sizeof(R) == 4) {
+        sp.cell[p] = cn[1] * rd.n[0] + cn[0];
+        ((float *)sp.pos[0])[p] = o[0];
+        ((float *)sp.pos[1])[p] = o[1];
+    } else {
+        ((double *)sp.pos[0])[p] = (double)cn[0] + o[0];
+        ((double *)sp.pos[1])[p] = (double)cn[1] + o[1];
+    }
+}
+
+// All particles of one tile (both species), 2D.
+template <int L, int KT, typename R>
+__device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile)
+{
+    Stage2D<R> st = stage2d_carve<R>(smem, rd.reg_nodes);
+    const int tx = (int)(tile % rd.ntile[0]);
+    const int ty = (int)(tile / rd.ntile[0]);
+    const int x0 = tx * rd.tile[0], y0 = ty * rd.tile[1];
+    stage2d_load<R>(rd, st, x0, y0);
+    __syncthreads();
+    for (int s = 0; s < rd.nsp; ++s) {
+        const SpeciesDev &sp = rd.sp[s];
+        const int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
+        for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x)
+            particle_2d<L, KT, R>(rd, sp, st, p, x0, y0);
+        __syncthreads();
+        stage2d_flush<R>(rd, st, x0, y0);
+        __syncthreads();
+    }
+}
+
+// One particle, 3D: fields through L1 (read-only path), current by global FP64 atomics.
+template <int L, int KT, typename R>
+__device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &sp, int64_t p)
+{
+    PState<R> s;
+    load_particle<3, R>(rd, sp, p, s);
+    const int nx = rd.n[0], ny = rd.n[1], nz = rd.n[2];
+    AxisW<L, KT, R> w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) axis_weights<L, KT, R>(rd.tt[a], s.d[a], w[a]);
+    // wrapped node indices
+    int ih[3][L + 1], it[3][KT];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int k = 0; k <= L; ++k) ih[a][k] = wrap_idx(s.c[a] + w[a].bh + k, rd.n[a]);
+#pragma unroll
+        for (int k = 0; k < KT; ++k) it[a][k] = wrap_idx(s.c[a] + w[a].bt + k, rd.n[a]);
+    }
+    auto fld = [&](int comp, int64_t g) -> R {
+        if constexpr (sizeof(R) == 4) return __ldg(rd.Fs[comp] + g);
+        else return __ldg(rd.F[comp] + g);
+    };
+    R E[3], B[3];
+    // E1: W T T ; E2: T W T ; E3: T T W ; B1: T W W ; B2: W T W ; B3: W W T
+    {
+        R acc = R(0);
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+            R r2 = R(0);
+#pragma unroll
+            for (int b = 0; b < KT; ++b) {
+                const int64_t row = ((int64_t)it[2][c] * ny + it[1][b]) * nx;
+                R r1 = R(0);
+#pragma unroll
+                for (int a = 0; a <= L; ++a) r1 += w[0].wh[a] * fld(0, row + ih[0][a]);
+                r2 += w[1].wt[b] * r1;
+            }
+            acc += w[2].wt[c] * r2;
+        }
+        E[0] = acc;
+    }
+    {
+        R acc = R(0);
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+            R r2 = R(0);
+#pragma unroll
+            for (int b = 0; b <= L; ++b) {
+                const int64_t row = ((int64_t)it[2][c] * ny + ih[1][b]) * nx;
+                R r1 = R(0);
+#pragma unroll
+                for (int a = 0; a < KT; ++a) r1 += w[0].wt[a] * fld(1, row + it[0][a]);
+                r2 += w[1].wh[b] * r1;
+            }
+            acc += w[2].wt[c] * r2;
+        }
+        E[1] = acc;
+    }
+    {
+        R acc = R(0);
+#pragma unroll
+        for (int c = 0; c <= L; ++c) {
+            R r2 = R(0);
+#pragma unroll
+            for (int b = 0; b < KT; ++b) {
+                const int64_t row = ((int64_t)ih[2][c] * ny + it[1][b]) * nx;
+                R r1 = R(0);
+#pragma unroll
+                for (int a = 0; a < KT; ++a) r1 += w[0].wt[a] * fld(2, row + it[0][a]);
+                r2 += w[1].wt[b] * r1;
+            }
+            acc += w[2].wh[c] * r2;
+        }
+        E[2] = acc;
+    }
+    {
+        R acc = R(0);
+#pragma unroll
+        for (int c = 0; c <= L; ++c) {
+            R r2 = R(0);
+#pragma unroll
+            for (int b = 0; b <= L; ++b) {
+                const int64_t row = ((int64_t)ih[2][c] * ny + ih[1][b]) * nx;
+                R r1 = R(0);
+#pragma unroll
+                for (int a = 0; a < KT; ++a) r1 += w[0].wt[a] * fld(3, row + it[0][a]);
+                r2 += w[1].wh[b] * r1;
+            }
+            acc += w[2].wh[c] * r2;
+        }
+        B[0] = acc;
+    }
+    {
+        R acc = R(0);
+#pragma unroll
+        for (int c = 0; c <= L; ++c) {
+            R r2 = R(0);
+#pragma unroll
+            for (int b = 0; b < KT; ++b) {
+                const int64_t row = ((int64_t)ih[2][c] * ny + it[1][b]) * nx;
+                R r1 = R(0);
+#pragma unroll
+                for (int a = 0; a <= L; ++a) r1 += w[0].wh[a] * fld(4, row + ih[0][a]);
+                r2 += w[1].wt[b] * r1;
+            }
+            acc += w[2].wh[c] * r2;
+        }
+        B[1] = acc;
+    }
+    {
+        R acc = R(0);
+#pragma unroll
+        for (int c = 0; c < KT; ++c) {
+            R r2 = R(0);
+#pragma unroll
+            for (int b = 0; b <= L; ++b) {
+                const int64_t row = ((int64_t)it[2][c] * ny + ih[1][b]) * nx;
+                R r1 = R(0);
+#pragma unroll
+                for (int a = 0; a <= L; ++a) r1 += w[0].wh[a] * fld(5, row + ih[0][a]);
+                r2 += w[1].wh[b] * r1;
+            }
+            acc += w[2].wt[c] * r2;
+        }
+        B[2] = acc;
+    }
+
+    boris<R>(R(sp.qmdt_half), E, B, s.u);
+    const R g = sqrt(R(1) + s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
+    const R ig = R(1) / g;
+    R o[3];
+    int cn[3], shv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        shv[a] = move_axis<R>(s.d[a], R(rd.dtt[a]) * s.u[a] * ig, s.c[a], rd.n[a], o[a], cn[a]);
+
+    AxisS<L, R> S[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) axis_shapes<L, R>(s.d[a], shv[a], o[a], S[a]);
+    R DS[3][L + 2], P[3][L + 2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R acc = R(0);
+#pragma unroll
+        for (int k = 0; k < L + 2; ++k) {
+            DS[a][k] = S[a].s1[k] - S[a].s0[k];
+            acc += DS[a][k];
+            P[a][k] = acc;
+        }
+    }
+    int jn[3][L + 2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < L + 2; ++k) jn[a][k] = wrap_idx(s.c[a] + S[a].wb + k, rd.n[a]);
+    const R third = R(1) / R(3);
+    // W_a = DS_a (S0_b S0_c + DS_b S0_c / 2 + S0_b DS_c / 2 + DS_b DS_c / 3), prefix along a
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const int bx = (ax + 1) % 3, cx = (ax + 2) % 3;
+        const R kk = R(sp.kx[ax]);
+#pragma unroll
+        for (int kb = 0; kb < L + 2; ++kb) {
+#pragma unroll
+            for (int kc = 0; kc < L + 2; ++kc) {
+                const R perp = S[bx].s0[kb] * (S[cx].s0[kc] + R(0.5) * DS[cx][kc])
+                               + DS[bx][kb] * (R(0.5) * S[cx].s0[kc] + third * DS[cx][kc]);
+                if (perp == R(0)) continue;
+#pragma unroll
+                for (int ka = 0; ka <= L; ++ka) {
+                    int id[3];
+                    id[ax] = jn[ax][ka]; id[bx] = jn[bx][kb]; id[cx] = jn[cx][kc];
+                    const int64_t g = ((int64_t)id[2] * ny + id[1]) * nx + id[0];
+                    const R v = kk * P[ax][ka] * perp;
+                    if (v != R(0)) atomicAdd(rd.F[6 + ax] + g, (double)v);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ((R *)sp.mom[a])[p] = s.u[a];
+    if constexpr (sizeof(R) == 4) {
+        sp.cell[p] = (cn[2] * ny + cn[1]) * nx + cn[0];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ((float *)sp.pos[a])[p] = o[a];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ((double *)sp.pos[a])[p] = (double)cn[a] + o[a];
+    }
+    (void)nz;
+}
+
+template <int L, int KT, typename R>
+__device__ void tile_3d(const RunDev &rd, int64_t tile)
+{
+    for (int s = 0; s < rd.nsp; ++s) {
+        const SpeciesDev &sp = rd.sp[s];
+        const int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
+        for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) particle_3d<L, KT, R>(rd, sp, p);
+    }
+}
+
+}  // namespace pic

@@ -1,0 +1,403 @@
+// Grid kernels: periodic Yee FDTD updates (FP64), FP32 field shadows, particle packing and
+// unpacking, and the FP64 diagnostics.
+#include "pic_launch.h"
+
+#include <cmath>
+
+namespace pic {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ int64_t gidx(const RunDev &rd, int i, int j, int k)
+{
+    return ((int64_t)k * rd.n[1] + j) * rd.n[0] + i;
+}
+
+// B <- B - h curl E on the staggered grid (Sec. 1 Yee; App. C with A_i = 1).
+__global__ void __launch_bounds__(kBlock) k_yee_b(const __grid_constant__ RunDev rd, double h,
+                                                  int shadow)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= rd.ncell) return;
+    const int nx = rd.n[0], ny = rd.n[1], nz = rd.n[2];
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const int k = (int)(c / ((int64_t)nx * ny));
+    const int ip = (i + 1 == nx) ? 0 : i + 1;
+    const int jp = (j + 1 == ny) ? 0 : j + 1;
+    const int kp = (k + 1 == nz) ? 0 : k + 1;
+    const double *E1 = rd.F[0], *E2 = rd.F[1], *E3 = rd.F[2];
+    const double e1 = E1[c], e2 = E2[c], e3 = E3[c];
+    const double idx = 1.0 / rd.dx[0], idy = 1.0 / rd.dx[1], idz = 1.0 / rd.dx[2];
+    const double dE3dy = (E3[gidx(rd, i, jp, k)] - e3) * idy;
+    const double dE2dz = (E2[gidx(rd, i, j, kp)] - e2) * idz;
+    const double dE1dz = (E1[gidx(rd, i, j, kp)] - e1) * idz;
+    const double dE3dx = (E3[gidx(rd, ip, j, k)] - e3) * idx;
+    const double dE2dx = (E2[gidx(rd, ip, j, k)] - e2) * idx;
+    const double dE1dy = (E1[gidx(rd, i, jp, k)] - e1) * idy;
+    const double b1 = rd.F[3][c] - h * (dE3dy - dE2dz);
+    const double b2 = rd.F[4][c] - h * (dE1dz - dE3dx);
+    const double b3 = rd.F[5][c] - h * (dE2dx - dE1dy);
+    rd.F[3][c] = b1;
+    rd.F[4][c] = b2;
+    rd.F[5][c] = b3;
+    if (shadow) {
+        rd.Fs[3][c] = (float)b1;
+        rd.Fs[4][c] = (float)b2;
+        rd.Fs[5][c] = (float)b3;
+    }
+}
+
+// E <- E + dt curl B - dt J, then J <- 0 (J is consumed here).
+__global__ void __launch_bounds__(kBlock) k_yee_e(const __grid_constant__ RunDev rd, int shadow)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= rd.ncell) return;
+    const int nx = rd.n[0], ny = rd.n[1], nz = rd.n[2];
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const int k = (int)(c / ((int64_t)nx * ny));
+    const int im = (i == 0) ? nx - 1 : i - 1;
+    const int jm = (j == 0) ? ny - 1 : j - 1;
+    const int km = (k == 0) ? nz - 1 : k - 1;
+    const double *B1 = rd.F[3], *B2 = rd.F[4], *B3 = rd.F[5];
+    const double b1 = B1[c], b2 = B2[c], b3 = B3[c];
+    const double idx = 1.0 / rd.dx[0], idy = 1.0 / rd.dx[1], idz = 1.0 / rd.dx[2];
+    const double dt = rd.dt;
+    const double dB3dy = (b3 - B3[gidx(rd, i, jm, k)]) * idy;
+    const double dB2dz = (b2 - B2[gidx(rd, i, j, km)]) * idz;
+    const double dB1dz = (b1 - B1[gidx(rd, i, j, km)]) * idz;
+    const double dB3dx = (b3 - B3[gidx(rd, im, j, k)]) * idx;
+    const double dB2dx = (b2 - B2[gidx(rd, im, j, k)]) * idx;
+    const double dB1dy = (b1 - B1[gidx(rd, i, jm, k)]) * idy;
+    const double e1 = rd.F[0][c] + dt * (dB3dy - dB2dz) - dt * rd.F[6][c];
+    const double e2 = rd.F[1][c] + dt * (dB1dz - dB3dx) - dt * rd.F[7][c];
+    const double e3 = rd.F[2][c] + dt * (dB2dx - dB1dy) - dt * rd.F[8][c];
+    rd.F[0][c] = e1;
+    rd.F[1][c] = e2;
+    rd.F[2][c] = e3;
+    if (shadow) {
+        rd.Fs[0][c] = (float)e1;
+        rd.Fs[1][c] = (float)e2;
+        rd.Fs[2][c] = (float)e3;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_shadow(const __grid_constant__ RunDev rd)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= rd.ncell) return;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) rd.Fs[f][c] = (float)rd.F[f][c];
+}
+
+// Host FP64 physical (x, u) -> the context's particle form.  Positions are divided by dx
+// (IEEE division, so the cell index floor(x/dx) matches a plain FP64 evaluation) and
+// wrapped into [0, n).
+__global__ void __launch_bounds__(kBlock) k_pack(const __grid_constant__ RunDev rd, int s,
+                                                 const double *x, const double *u, int64_t n)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const SpeciesDev &sp = rd.sp[s];
+    int cell[3] = {0, 0, 0};
+    double off[3] = {0, 0, 0};
+    for (int a = 0; a < rd.dim; ++a) {
+        double xi = x[a * n + p] / rd.dx[a];
+        const double N = (double)rd.n[a];
+        if (xi >= N) xi -= N;
+        if (xi < 0.0) xi += N;
+        if (xi >= N) xi = 0.0;  // -tiny + N rounded up to N
+        const double f = floor(xi);
+        cell[a] = (int)f;
+        off[a] = xi - f;
+    }
+    if (rd.prec == 1) {
+        int c[3] = {cell[0], cell[1], cell[2]};
+        float o[3];
+        for (int a = 0; a < rd.dim; ++a) {
+            o[a] = (float)off[a];
+            if (o[a] >= 1.0f) {  // offset rounded to 1: carry into the next cell
+                o[a] = 0.0f;
+                c[a] += 1;
+                if (c[a] >= rd.n[a]) c[a] -= rd.n[a];
+            }
+            ((float *)sp.pos[a])[p] = o[a];
+        }
+        sp.cell[p] = (int32_t)gidx(rd, c[0], c[1], rd.dim == 3 ? c[2] : 0);
+        for (int a = 0; a < 3; ++a) ((float *)sp.mom[a])[p] = (float)u[a * n + p];
+    } else {
+        for (int a = 0; a < rd.dim; ++a) ((double *)sp.pos[a])[p] = (double)cell[a] + off[a];
+        for (int a = 0; a < 3; ++a) ((double *)sp.mom[a])[p] = u[a * n + p];
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_unpack(const __grid_constant__ RunDev rd, int s,
+                                                   double *x, double *u, int64_t *cell)
+{
+    const SpeciesDev &sp = rd.sp[s];
+    const int64_t n = sp.n;
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    if (rd.prec == 1) {
+        const int c = sp.cell[p];
+        int ci[3];
+        ci[0] = c % rd.n[0];
+        ci[1] = (c / rd.n[0]) % rd.n[1];
+        ci[2] = c / (rd.n[0] * rd.n[1]);
+        for (int a = 0; a < rd.dim; ++a)
+            x[a * n + p] = ((double)ci[a] + (double)((const float *)sp.pos[a])[p]) * rd.dx[a];
+        for (int a = 0; a < 3; ++a) u[a * n + p] = (double)((const float *)sp.mom[a])[p];
+        if (cell) cell[p] = c;
+    } else {
+        int ci[3] = {0, 0, 0};
+        for (int a = 0; a < rd.dim; ++a) {
+            const double xi = ((const double *)sp.pos[a])[p];
+            ci[a] = (int)floor(xi);
+            x[a * n + p] = xi * rd.dx[a];
+        }
+        for (int a = 0; a < 3; ++a) u[a * n + p] = ((const double *)sp.mom[a])[p];
+        if (cell) cell[p] = gidx(rd, ci[0], ci[1], ci[2]);
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ double block_sum(double v)
+{
+    __shared__ double red[32];
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+__device__ double block_max(double v)
+{
+    __shared__ double red[32];
+    v = warp_max(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_max(v);
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double *a, double v)
+{
+    atomicMax((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
+}
+
+// sum over nodes of E^2 + B^2 (FP64); non-finite values raise the error bit.
+__global__ void __launch_bounds__(kBlock) k_field_energy(const __grid_constant__ RunDev rd,
+                                                         double *out)
+{
+    double acc = 0.0;
+    bool bad = false;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < rd.ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        for (int f = 0; f < 6; ++f) {
+            const double v = rd.F[f][c];
+            if (!isfinite(v)) bad = true;
+            acc += v * v;
+        }
+    }
+    if (bad) set_err(rd.err, 2);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+// sum over particles of w m (gamma - 1)
+__global__ void __launch_bounds__(kBlock) k_kinetic(const __grid_constant__ RunDev rd, int s,
+                                                    double *out)
+{
+    const SpeciesDev &sp = rd.sp[s];
+    double acc = 0.0;
+    bool bad = false;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < sp.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double u0, u1, u2;
+        if (rd.prec == 1) {
+            u0 = ((const float *)sp.mom[0])[p];
+            u1 = ((const float *)sp.mom[1])[p];
+            u2 = ((const float *)sp.mom[2])[p];
+        } else {
+            u0 = ((const double *)sp.mom[0])[p];
+            u1 = ((const double *)sp.mom[1])[p];
+            u2 = ((const double *)sp.mom[2])[p];
+        }
+        const double u2s = u0 * u0 + u1 * u1 + u2 * u2;
+        if (!isfinite(u2s)) bad = true;
+        // gamma - 1 = u^2 / (sqrt(1 + u^2) + 1), free of cancellation for slow particles
+        acc += u2s / (sqrt(1.0 + u2s) + 1.0);
+    }
+    if (bad) set_err(rd.err, 2);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) atomicAdd(out, acc * sp.w * sp.m);
+}
+
+// rho = sum q w W_l / V_c at integer nodes (FP64 atomics).
+__global__ void __launch_bounds__(kBlock) k_rho(const __grid_constant__ RunDev rd, int s,
+                                                double *rho)
+{
+    const SpeciesDev &sp = rd.sp[s];
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= sp.n) return;
+    const int l = rd.l;
+    int c[3] = {0, 0, 0};
+    double d[3] = {0, 0, 0};
+    if (rd.prec == 1) {
+        const int cc = sp.cell[p];
+        c[0] = cc % rd.n[0];
+        c[1] = (cc / rd.n[0]) % rd.n[1];
+        c[2] = cc / (rd.n[0] * rd.n[1]);
+        for (int a = 0; a < rd.dim; ++a) d[a] = ((const float *)sp.pos[a])[p];
+    } else {
+        for (int a = 0; a < rd.dim; ++a) {
+            const double xi = ((const double *)sp.pos[a])[p];
+            const double f = floor(xi);
+            c[a] = (int)f;
+            d[a] = xi - f;
+        }
+    }
+    // W_l at the integer nodes cell-3 .. cell+3 (evaluated from |x - node|; covers l <= 4)
+    double w[3][7];
+    int b[3];
+    for (int a = 0; a < 3; ++a) {
+        for (int k = 0; k < 7; ++k) w[a][k] = 0.0;
+        b[a] = 0;
+        if (a >= rd.dim) { w[a][0] = 1.0; continue; }
+        b[a] = -3;
+        for (int k = 0; k < 7; ++k) {
+            const double y = fabs(d[a] - (double)(b[a] + k));
+            double v = 0.0;
+            if (l == 1) v = y < 1.0 ? 1.0 - y : 0.0;
+            else if (l == 2) v = y <= 0.5 ? 0.75 - y * y : (y < 1.5 ? 0.5 * (1.5 - y) * (1.5 - y) : 0.0);
+            else if (l == 3) v = y <= 1.0 ? 2.0 / 3.0 - y * y + 0.5 * y * y * y
+                                          : (y < 2.0 ? (2.0 - y) * (2.0 - y) * (2.0 - y) / 6.0 : 0.0);
+            else v = y <= 0.5 ? 115.0 / 192.0 - 5.0 * y * y / 8.0 + y * y * y * y / 4.0
+                     : (y <= 1.5 ? (55.0 + 20.0 * y - 120.0 * y * y + 80.0 * y * y * y - 16.0 * y * y * y * y) / 96.0
+                        : (y < 2.5 ? (2.5 - y) * (2.5 - y) * (2.5 - y) * (2.5 - y) / 24.0 : 0.0));
+            w[a][k] = v;
+        }
+    }
+    const double vc = rd.dx[0] * rd.dx[1] * (rd.dim == 3 ? rd.dx[2] : 1.0);
+    const double qw = sp.q * sp.w / vc;
+    const int nk = rd.dim == 3 ? 7 : 1;
+    for (int kk = 0; kk < nk; ++kk)
+        for (int jj = 0; jj < 7; ++jj)
+            for (int ii = 0; ii < 7; ++ii) {
+                const double v = w[0][ii] * w[1][jj] * w[2][kk];
+                if (v == 0.0) continue;
+                const int gi = wrap_idx(c[0] + b[0] + ii, rd.n[0]);
+                const int gj = wrap_idx(c[1] + b[1] + jj, rd.n[1]);
+                const int gk = rd.dim == 3 ? wrap_idx(c[2] + b[2] + kk, rd.n[2]) : 0;
+                atomicAdd(rho + gidx(rd, gi, gj, gk), qw * v);
+            }
+}
+
+// max |D.E - rho| (App. B, Eq. gauss)
+__global__ void __launch_bounds__(kBlock) k_gauss(const __grid_constant__ RunDev rd,
+                                                  const double *rho, double *out)
+{
+    double m = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < rd.ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int nx = rd.n[0], ny = rd.n[1], nz = rd.n[2];
+        const int i = (int)(c % nx);
+        const int j = (int)((c / nx) % ny);
+        const int k = (int)(c / ((int64_t)nx * ny));
+        const int im = (i == 0) ? nx - 1 : i - 1;
+        const int jm = (j == 0) ? ny - 1 : j - 1;
+        double dv = (rd.F[0][c] - rd.F[0][gidx(rd, im, j, k)]) / rd.dx[0]
+                    + (rd.F[1][c] - rd.F[1][gidx(rd, i, jm, k)]) / rd.dx[1];
+        if (rd.dim == 3) {
+            const int km = (k == 0) ? nz - 1 : k - 1;
+            dv += (rd.F[2][c] - rd.F[2][gidx(rd, i, j, km)]) / rd.dx[2];
+        }
+        m = fmax(m, fabs(dv - rho[c]));
+    }
+    m = block_max(m);
+    if (threadIdx.x == 0) atomic_max_nonneg(out, m);
+}
+
+inline unsigned grid_for(int64_t n)
+{
+    return (unsigned)((n + kBlock - 1) / kBlock);
+}
+
+}  // namespace
+
+cudaError_t launch_yee_b(const RunDev &rd, double h, bool shadow, cudaStream_t st)
+{
+    k_yee_b<<<grid_for(rd.ncell), kBlock, 0, st>>>(rd, h, shadow ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yee_e(const RunDev &rd, bool shadow, cudaStream_t st)
+{
+    k_yee_e<<<grid_for(rd.ncell), kBlock, 0, st>>>(rd, shadow ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shadow(const RunDev &rd, cudaStream_t st)
+{
+    k_shadow<<<grid_for(rd.ncell), kBlock, 0, st>>>(rd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const RunDev &rd, int s, const double *x, const double *u, int64_t n,
+                        cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_pack<<<grid_for(n), kBlock, 0, st>>>(rd, s, x, u, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const RunDev &rd, int s, double *x, double *u, int64_t *cell,
+                          cudaStream_t st)
+{
+    if (rd.sp[s].n == 0) return cudaSuccess;
+    k_unpack<<<grid_for(rd.sp[s].n), kBlock, 0, st>>>(rd, s, x, u, cell);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(rho, 0, rd.ncell * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const unsigned gr = 1024;
+    k_field_energy<<<gr, kBlock, 0, st>>>(rd, out + 0);
+    for (int s = 0; s < rd.nsp; ++s) {
+        k_kinetic<<<gr, kBlock, 0, st>>>(rd, s, out + 1);
+        if (rd.sp[s].n > 0) k_rho<<<grid_for(rd.sp[s].n), kBlock, 0, st>>>(rd, s, rho);
+    }
+    k_gauss<<<gr, kBlock, 0, st>>>(rd, rho, out + 2);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

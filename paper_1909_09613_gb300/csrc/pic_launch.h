@@ -1,0 +1,41 @@
+// Host-side launchers shared by the C-ABI implementation (not part of the public ABI).
+#pragma once
+#include "pic_common.cuh"
+
+namespace pic {
+
+bool build_ttable(int l, int scheme, double dtt, TTable *t);
+int ttable_eval_host(const TTable *t, int l, double delta, double *w);
+
+// fused gather-push-deposit over all tiles of one run
+cudaError_t launch_gpp(const RunDev &rd, int kt, cudaStream_t st);
+size_t gpp_smem_bytes(const RunDev &rd);
+
+// Yee and grid kernels
+cudaError_t launch_yee_b(const RunDev &rd, double h, bool shadow, cudaStream_t st);
+cudaError_t launch_yee_e(const RunDev &rd, bool shadow, cudaStream_t st);
+cudaError_t launch_shadow(const RunDev &rd, cudaStream_t st);
+
+// particle packing (load / read back)
+cudaError_t launch_pack(const RunDev &rd, int s, const double *x, const double *u, int64_t n,
+                        cudaStream_t st);
+cudaError_t launch_unpack(const RunDev &rd, int s, double *x, double *u, int64_t *cell,
+                          cudaStream_t st);
+
+// diagnostics: out[0] field energy, out[1] kinetic, out[2] max gauss residual (device doubles)
+cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t st);
+
+// tile sort of one species
+struct SortScratch {
+    int32_t *cnt;         // ntiles * TC
+    int32_t *cell_first;  // ntiles * TC
+    int32_t *slot;        // n_max
+    int32_t *key;         // n_max
+    int32_t *pos;         // n_max
+    int64_t *tile_count;  // ntiles + 1 (scan workspace)
+};
+cudaError_t launch_sort(const RunDev &rd, int s, const SortScratch &sc, int64_t *tile_start,
+                        void *const *dst_pos, void *const *dst_mom, int32_t *dst_cell,
+                        cudaStream_t st);
+
+}  // namespace pic

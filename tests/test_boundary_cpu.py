@@ -1,0 +1,107 @@
+"""CPU checks of the C-ABI boundary: the library loads, exports every declared symbol, and its
+host-side logic (argument validation, footprint, interpolation tables) is right.  No device
+work is issued here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1909_09613_gb300 as pic
+from paper_1909_09613_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return pic.load_library()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(pic_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared <= set(pic.exported_names()) | {"pic_strerror"}
+
+
+def test_strerror(lib):
+    assert pic.pic_strerror(0) == "ok"
+    assert "Courant" in pic.pic_strerror(pic.PIC_ECFL)
+
+
+def _opt(cap=(100, 100), prec=pic.PIC_FP64):
+    o = pic.pic_options()
+    o.n_species = len(cap)
+    for i, c in enumerate(cap):
+        o.capacity[i] = c
+    o.precision = prec
+    return o
+
+
+def test_create_validates_courant_and_order(lib):
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_create((64, 32, 1), (1.0, 1.0, 1.0), 0.71, 2, pic.PIC_SCHEME_WT, _opt())
+    assert e.value.status == pic.PIC_ECFL
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_create((64, 32, 1), (1.0, 1.0, 1.0), 0.3, 5, pic.PIC_SCHEME_WT, _opt())
+    assert e.value.status == pic.PIC_EINVAL
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_create((16, 16, 16), (1.0, 1.0, 1.0), 0.58, 2, pic.PIC_SCHEME_WT, _opt())
+    assert e.value.status == pic.PIC_ECFL
+
+
+@pytest.mark.parametrize("grid,prec", [((2048, 1024, 1), pic.PIC_FP64), ((2048, 1024, 1), pic.PIC_FP32_MIXED),
+                                       ((64, 32, 1), pic.PIC_FP64), ((128, 32, 32), pic.PIC_FP32_MIXED)])
+def test_footprint_is_about_two_stores_plus_fields(lib, grid, prec):
+    n = grid[0] * grid[1] * grid[2] * 32
+    ctx = pic.pic_create(grid, (1.0, 1.0, 1.0), 0.25, 3, pic.PIC_SCHEME_WT, _opt((n, n), prec))
+    try:
+        b = pic.pic_footprint(ctx)
+        dim = 3 if grid[2] > 1 else 2
+        per = (4 + 4 * dim + 12) if prec else (8 * dim + 24)
+        ncell = grid[0] * grid[1] * grid[2]
+        low = 2 * 2 * n * per + 9 * 8 * ncell
+        assert low <= b <= 1.3 * low + 64 * ncell + (1 << 22)
+        tile, ntiles, si = pic.pic_tile_info(ctx)
+        assert si >= 1 and ntiles >= 1
+    finally:
+        pic.pic_destroy(ctx)
+
+
+@pytest.mark.parametrize("l", [1, 2, 3, 4])
+@pytest.mark.parametrize("dtt", [0.1, 0.25, 0.35, 0.5, 0.6, 0.7])
+def test_axis_weight_tables_match_oracle_T(lib, l, dtt):
+    """The kernels' per-particle T_l weights (Taylor tables) equal the oracle's T_l."""
+    rng = np.random.default_rng(l * 100 + int(dtt * 100))
+    for delta in np.concatenate([rng.uniform(0, 1, 40), [0.0, 0.5, 1 - 1e-12]]):
+        base, w = pic.pic_axis_weights(l, pic.PIC_SCHEME_WT, dtt, delta)
+        for k in range(-4, 6):
+            node = base + k
+            expect = oracle.T(l, dtt, delta - node)
+            got = w[k] if 0 <= k < len(w) else 0.0
+            assert abs(got - expect) < 1e-14, (delta, node, got, expect)
+
+
+@pytest.mark.parametrize("l", [1, 2, 3, 4])
+def test_axis_weight_tables_mc_are_bsplines(lib, l):
+    rng = np.random.default_rng(7 + l)
+    for delta in rng.uniform(0, 1, 50):
+        base, w = pic.pic_axis_weights(l, pic.PIC_SCHEME_MC, 0.3, delta)
+        for k in range(-4, 6):
+            got = w[k] if 0 <= k < len(w) else 0.0
+            assert abs(got - oracle.W(l, delta - (base + k))) < 1e-14

@@ -1,0 +1,255 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle, element by element.
+
+Tolerances (relative, per array: max |a - b| / max |b|):
+  FP64 form: 1e-12 after one step from the same state;
+  FP32 form: 2e-6 after one step from the same state (the FP32 round-off of a gather of
+  O(10-25) products plus one Boris rotation stays well inside it);
+Integer results (cell indices, the tile order) are compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1909_09613_gb300 as pic  # noqa: E402
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1909_09613_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.max(np.abs(b))
+    if den == 0.0:
+        return float(np.max(np.abs(a)))
+    return float(np.max(np.abs(a - b)) / den)
+
+
+def smooth_fields(shape, amp, seed):
+    """Seeded smooth random fields: a few low Fourier modes per component."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    out = []
+    for _ in range(6):
+        f = np.zeros(shape)
+        for _ in range(4):
+            mx, my, mz = rng.integers(0, 4, 3)
+            ph = rng.uniform(0, 2 * math.pi)
+            f += rng.uniform(-1, 1) * np.cos(2 * math.pi * (mx * ii / nx + my * jj / ny
+                                                           + (mz * kk / nz if nz > 1 else 0)) + ph)
+        out.append(amp * f)
+    return out
+
+
+def make_pair(wl, prec, fields=None, tile=None, sort_interval=0):
+    """Same initial state on the GPU (libpic) and in the oracle.  The GPU's load packs and sorts
+    the particles; the oracle is then given the GPU's read-back (sorted, and in the FP32 form
+    already rounded) so both start from identical particle arrays in identical order."""
+    caps = [int(s.x.shape[1]) for s in wl.species]
+    run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps,
+                  tile=tile, sort_interval=sort_interval)
+    for i, s in enumerate(wl.species):
+        run.load(i, s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
+    dim = wl.dim
+    orc = oracle.Sim(wl.grid[:dim], wl.dx[:dim], wl.dt, wl.l, wl.scheme)
+    for i, s in enumerate(wl.species):
+        x, u, _ = run.particles(i)
+        orc.add_species(s.q, s.m, s.w, x, u)
+    if fields is not None:
+        for c, f in enumerate(fields):
+            run.set_field(c, f)
+            orc.set_field(c, f)
+    return run, orc
+
+
+def compare_state(run, orc, nsp, tol, what=""):
+    errs = {}
+    for c in range(9):
+        errs["F%d" % c] = rel(run.field(c), orc.field(c))
+    for s in range(nsp):
+        xg, ug, _ = run.particles(s)
+        xo, uo = orc.particles(s)
+        errs["u%d" % s] = rel(ug, uo)
+        L = np.array([orc.grid[a] * orc.dx[a] for a in range(orc.dim)]).reshape(-1, 1)
+        d = xg - xo
+        d = d - L * np.round(d / L)
+        errs["x%d" % s] = float(np.max(np.abs(d)) / np.max(L)) if d.size else 0.0
+    bad = {k: v for k, v in errs.items() if v > tol}
+    assert not bad, (what, bad, errs)
+    return errs
+
+
+CASES_2D = [
+    # (grid, dx, cdt, l, scheme, gamma, u_th, ppc)
+    ((64, 32), (1.0, 1.0), 0.35, 2, 1, 20.0, 0.0, 4),
+    ((64, 32), (1.0, 1.0), 0.35, 2, 0, 20.0, 0.0, 4),
+    ((40, 24), (1.0, 1.0), 0.25, 3, 1, 5.0, 0.05, 6),
+    ((40, 24), (1.0, 1.0), 0.25, 3, 0, 5.0, 0.05, 6),
+    ((37, 21), (0.9, 1.1), 0.3, 1, 1, 3.0, 0.1, 4),
+    ((48, 20), (1.0, 1.0), 0.6, 3, 1, 10.0, 0.05, 4),
+    ((48, 20), (1.0, 1.0), 0.3, 4, 1, 10.0, 0.05, 4),
+    ((33, 18), (1.0, 1.0), 0.5, 2, 1, 2.0, 0.2, 4),
+]
+
+
+@pytest.mark.parametrize("case", CASES_2D, ids=lambda c: "g%dx%d_l%d_s%d_dt%.2f" % (c[0] + (c[3], c[4], c[2])))
+@pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
+def test_one_step_2d(case, prec):
+    grid, dx, cdt, l, scheme, gamma, uth, ppc = case
+    wl = workloads.pair_plasma(grid, dx, cdt, l, scheme, gamma, uth, ppc, omega_p=0.2, seed=11)
+    f = smooth_fields((1, grid[1], grid[0]), 0.05, seed=5)
+    run, orc = make_pair(wl, prec, f)
+    run.step(1)
+    orc.step(1)
+    compare_state(run, orc, 2, FP64_TOL if prec == pic.PIC_FP64 else FP32_TOL, case)
+    run.close()
+
+
+@pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", [((12, 10, 8), 0.3, 2, 1), ((12, 10, 8), 0.3, 2, 0),
+                                  ((10, 9, 7), 0.25, 3, 1), ((9, 8, 8), 0.5, 1, 1)],
+                         ids=lambda c: "g%dx%dx%d_l%d_s%d" % (c[0] + (c[2], c[3])))
+def test_one_step_3d(case, prec):
+    grid, cdt, l, scheme = case
+    wl = workloads.pair_plasma(grid, (1.0, 1.0, 1.0), cdt, l, scheme, 4.0, 0.1, 4, omega_p=0.2,
+                               seed=3)
+    f = smooth_fields((grid[2], grid[1], grid[0]), 0.05, seed=9)
+    run, orc = make_pair(wl, prec, f)
+    run.step(1)
+    orc.step(1)
+    compare_state(run, orc, 2, FP64_TOL if prec == pic.PIC_FP64 else FP32_TOL, case)
+    run.close()
+
+
+def test_multi_step_across_sorts_fp64():
+    """20 steps at c dt = 0.35 (sort every 6 steps): fields and diagnostics stay at round-off
+    from the oracle."""
+    wl = workloads.config_small(scheme=1)
+    wl2 = workloads.pair_plasma(wl.grid, wl.dx, wl.dt, wl.l, 1, 20.0, 0.01, 4,
+                                omega_p=wl.omega_p)
+    run, orc = make_pair(wl2, pic.PIC_FP64)
+    assert run.sort_interval < 20
+    run.step(20)
+    orc.step(20)
+    for c in range(9):
+        assert rel(run.field(c), orc.field(c)) < 1e-10, c
+    dg, do = run.diag(), orc.diag()
+    assert abs(dg["field_energy"] - do["field_energy"]) <= 1e-9 * do["field_energy"]
+    assert abs(dg["kinetic_energy"] - do["kinetic_energy"]) <= 1e-12 * do["kinetic_energy"]
+    # particles: compare as sets (the GPU re-sorted them), matched by sorted positions
+    for s in range(2):
+        xg, ug, _ = run.particles(s)
+        xo, uo = orc.particles(s)
+        kg = np.lexsort(xg[::-1])
+        ko = np.lexsort(xo[::-1])
+        assert np.max(np.abs(xg[:, kg] - xo[:, ko])) < 1e-9
+        assert rel(ug[:, kg], uo[:, ko]) < 1e-10
+    run.close()
+
+
+@pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("grid,tile", [((64, 32, 1), None), ((37, 21, 1), (8, 4, 1)),
+                                       ((12, 10, 8), None), ((5, 3, 1), None)])
+def test_tile_sort_bit_exact(prec, grid, tile):
+    """Cell at every sorted position and the tile offsets equal the oracle's order; the
+    particles of every cell are the same set."""
+    g = tuple(g for g in grid if True)
+    wl = workloads.pair_plasma(g if g[2] > 1 else g[:2], (1.0,) * (3 if g[2] > 1 else 2), 0.3, 2, 1,
+                               3.0, 0.1, 6, omega_p=0.2, seed=21)
+    caps = [int(s.x.shape[1]) for s in wl.species]
+    run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps, tile=tile)
+    for i, s in enumerate(wl.species):
+        run.load(i, s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
+    for i, s in enumerate(wl.species):
+        x0 = s.x.numpy()
+        cells_in = np.zeros(x0.shape[1], dtype=np.int64)
+        stride = 1
+        for a in range(wl.dim):
+            cells_in += np.floor(x0[a] / wl.dx[a]).astype(np.int64) * stride
+            stride *= wl.grid[a]
+        if prec == pic.PIC_FP32_MIXED:
+            # the FP32 form stores float(offset); an offset that rounds to 1.0 carries into
+            # the next cell (decided in FP32, as the packing kernel does)
+            cells_in = np.zeros(x0.shape[1], dtype=np.int64)
+            stride = 1
+            for a in range(wl.dim):
+                xi = x0[a] / wl.dx[a]
+                c = np.floor(xi)
+                off = (xi - c).astype(np.float32)
+                c = c.astype(np.int64) + (off >= np.float32(1.0))
+                c = np.where(c >= wl.grid[a], c - wl.grid[a], c)
+                cells_in += c * stride
+                stride *= wl.grid[a]
+        perm, ts = oracle.tile_sort(wl.grid, run.tile, cells_in)
+        xg, ug, cg = run.particles(i)
+        assert np.array_equal(cg, cells_in[perm])
+        assert np.array_equal(run.tile_offsets(i), ts)
+        # same particles in every cell (FP32 form: compare the packed values)
+        if prec == pic.PIC_FP64:
+            a = np.lexsort(np.vstack([x0, s.u.numpy()])[::-1])
+            b = np.lexsort(np.vstack([xg, ug])[::-1])
+            assert np.array_equal(np.vstack([x0, s.u.numpy()])[:, a], np.vstack([xg, ug])[:, b])
+    run.close()
+
+
+def test_gauss_law_conserved_gpu_fp64():
+    wl = workloads.pair_plasma((48, 24), (1.0, 1.0), 0.3, 3, 1, 5.0, 0.05, 8, omega_p=0.3)
+    run, orc = make_pair(wl, pic.PIC_FP64)
+    d0 = run.diag()
+    run.step(60)
+    d1 = run.diag()
+    rho_scale = abs(wl.species[0].q * wl.species[0].w) * 8
+    # D.E - rho is conserved; its max over nodes starts at the noise level and stays there
+    assert abs(d1["max_gauss_residual"] - d0["max_gauss_residual"]) < 1e-11 * rho_scale
+    assert d1["error_flags"] == 0
+    run.close()
+
+
+def test_empty_and_single_particle():
+    grid = (16, 8)
+    run = pic.Run(grid, (1.0, 1.0), 0.3, 2, 1, capacity=(0, 1))
+    run.load(0, -1.0, 1.0, 1.0, np.zeros((2, 0)), np.zeros((3, 0)))
+    x = np.array([[5.3], [2.7]])
+    u = np.array([[0.5], [0.2], [-0.1]])
+    run.load(1, 1.0, 1.0, 0.7, x, u)
+    orc = oracle.Sim(grid, (1.0, 1.0), 0.3, 2, 1)
+    orc.add_species(-1.0, 1.0, 1.0, np.zeros((2, 0)), np.zeros((3, 0)))
+    orc.add_species(1.0, 1.0, 0.7, x, u)
+    for _ in range(12):
+        run.step(1)
+        orc.step(1)
+    for c in range(9):
+        assert rel(run.field(c), orc.field(c)) < 1e-11, c
+    xg, ug, _ = run.particles(1)
+    xo, uo = orc.particles(1)
+    assert np.max(np.abs(xg - xo)) < 1e-12 and rel(ug, uo) < 1e-11
+    run.close()
+
+
+def test_wt_equals_mc_at_half_step_gpu():
+    """c dt = dx/2: the WT tables reduce to W_l, so WT and MC steps agree (Sec. 2)."""
+    outs = []
+    for scheme in (0, 1):
+        wl = workloads.pair_plasma((32, 16), (1.0, 1.0), 0.5, 3, scheme, 4.0, 0.05, 4, omega_p=0.4)
+        f = smooth_fields((1, 16, 32), 0.05, seed=1)
+        run, orc = make_pair(wl, pic.PIC_FP64, f)
+        run.step(3)
+        outs.append([run.field(c) for c in range(6)])
+        run.close()
+    for a, b in zip(*outs):
+        assert rel(a, b) < 1e-13
