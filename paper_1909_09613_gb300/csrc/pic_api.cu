@@ -52,7 +52,16 @@ struct pic_ctx {
 
 namespace {
 
+// particles per host<->device staging chunk (load and read-back)
+constexpr int64_t kChunk = (int64_t)1 << 22;
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t staging_size(const RunDev &rd, int64_t capmax)
+{
+    const int64_t m = std::min<int64_t>(std::max<int64_t>(capmax, 1), kChunk);
+    return align_up((size_t)m * ((rd.dim + 3) * sizeof(double) + sizeof(int64_t)) + 4 * 256, 256);
+}
 
 int pos_bytes(const pic_ctx *c) { return c->rd.prec == PIC_FP32_MIXED ? 4 : 8; }
 
@@ -158,20 +167,29 @@ int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n
     sp.kz = q * w / vc;
     sp.n = n;
     const int d = rd.dim;
-    const double *xd = x, *ud = u;
-    if (!on_device && n > 0) {
-        const size_t xb = (size_t)d * n * sizeof(double), ub = (size_t)3 * n * sizeof(double);
-        if (xb + ub > c->staging_bytes) return PIC_ENOMEM;
-        double *sx = (double *)c->staging;
-        double *su = (double *)(c->staging + xb);
-        if (cudaMemcpyAsync(sx, x, xb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return PIC_ECUDA;
-        if (cudaMemcpyAsync(su, u, ub, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return PIC_ECUDA;
-        xd = sx;
-        ud = su;
-    }
     refresh_species_ptrs(c);
-    if (launch_pack(c->rd, species, xd, ud, n, c->stream) != cudaSuccess) return PIC_ECUDA;
-    if (n > 0) c->kernel_launches += 1;
+    if (on_device) {
+        if (launch_pack(c->rd, species, x, n, u, n, n, 0, c->stream) != cudaSuccess) return PIC_ECUDA;
+        if (n > 0) c->kernel_launches += 1;
+    } else {
+        // host arrays go through the staging buffer in chunks of kChunk particles
+        for (int64_t p0 = 0; p0 < n; p0 += kChunk) {
+            const int64_t mc = std::min(kChunk, n - p0);
+            double *sx = (double *)c->staging;
+            double *su = sx + (size_t)d * mc;
+            if ((size_t)(d + 3) * mc * sizeof(double) > c->staging_bytes) return PIC_ENOMEM;
+            for (int a = 0; a < d; ++a)
+                if (cudaMemcpyAsync(sx + (size_t)a * mc, x + (size_t)a * n + p0, mc * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+                    return PIC_ECUDA;
+            for (int a = 0; a < 3; ++a)
+                if (cudaMemcpyAsync(su + (size_t)a * mc, u + (size_t)a * n + p0, mc * sizeof(double),
+                                    cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+                    return PIC_ECUDA;
+            if (launch_pack(c->rd, species, sx, mc, su, mc, mc, p0, c->stream) != cudaSuccess) return PIC_ECUDA;
+            c->kernel_launches += 1;
+        }
+    }
     const int r = sort_species(c, species);
     if (r != PIC_OK) return r;
     c->loaded[species] = true;
@@ -311,14 +329,12 @@ int pic_footprint(const pic_ctx *c, size_t *bytes)
     const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
     for (int s = 0; s < rd.nsp; ++s) b += align_up((size_t)c->cap[s] * pb + 7 * A, A);  // current stores
     for (int s = 0; s < rd.nsp; ++s) b += align_up((rd.ntiles + 1) * sizeof(int64_t), A);           // tile_start
-    // region aliased by sort targets, sort scratch and the host<->device staging area
-    size_t region = 0;
-    for (int s = 0; s < rd.nsp; ++s) region += align_up((size_t)c->cap[s] * pb + 7 * A, A);
-    region += 2 * align_up(rd.ntiles * TC * sizeof(int32_t), A);
-    region += 3 * align_up((size_t)capmax * sizeof(int32_t), A);
-    region += align_up((rd.ntiles + 1) * sizeof(int64_t), A);
-    const size_t stage = align_up((size_t)capmax * ((rd.dim + 3) * sizeof(double) + sizeof(int64_t)) + 4 * A, A);
-    b += std::max(region, stage);
+    // sort targets and sort scratch
+    for (int s = 0; s < rd.nsp; ++s) b += align_up((size_t)c->cap[s] * pb + 7 * A, A);
+    b += 2 * align_up(rd.ntiles * TC * sizeof(int32_t), A);
+    b += 3 * align_up((size_t)capmax * sizeof(int32_t), A);
+    b += align_up((rd.ntiles + 1) * sizeof(int64_t), A);
+    b += staging_size(rd, capmax);                // host<->device staging (chunked)
     b += align_up(rd.ncell * sizeof(double), A);  // rho
     b += 2 * A;                                   // diag out, err
     b += A;                                       // base alignment slack
@@ -355,7 +371,6 @@ int pic_bind_memory(pic_ctx *c, void *dev, size_t bytes)
         take((size_t)c->cap[s] * pb + 7 * A);
     }
     for (int s = 0; s < rd.nsp; ++s) c->tile_start[s] = (int64_t *)take((rd.ntiles + 1) * sizeof(int64_t));
-    char *region = p;
     int64_t capmax = 0;
     for (int s = 0; s < rd.nsp; ++s) capmax = std::max(capmax, c->cap[s]);
     const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
@@ -370,10 +385,8 @@ int pic_bind_memory(pic_ctx *c, void *dev, size_t bytes)
     c->sc.key = (int32_t *)take((size_t)capmax * sizeof(int32_t));
     c->sc.pos = (int32_t *)take((size_t)capmax * sizeof(int32_t));
     c->sc.tile_count = (int64_t *)take((rd.ntiles + 1) * sizeof(int64_t));
-    const size_t stage = align_up((size_t)capmax * ((rd.dim + 3) * sizeof(double) + sizeof(int64_t)) + 4 * A, A);
-    if ((size_t)(p - region) < stage) p = region + stage;
-    c->staging = region;
-    c->staging_bytes = (size_t)(p - region);
+    c->staging_bytes = staging_size(rd, capmax);
+    c->staging = take(c->staging_bytes);
     c->rho = (double *)take(rd.ncell * sizeof(double));
     c->diag_out = (double *)take(4 * sizeof(double));
     c->err = (int32_t *)take(sizeof(int32_t));
@@ -529,18 +542,28 @@ int pic_read_particles(pic_ctx *c, int species, double *x, double *u, int64_t *c
     if (n != np || (np > 0 && (!x || !u))) return PIC_EINVAL;
     if (np == 0) return latched_status(c);
     refresh_species_ptrs(c);
-    const size_t xb = (size_t)rd.dim * np * sizeof(double), ub = (size_t)3 * np * sizeof(double);
-    const size_t cb = (size_t)np * sizeof(int64_t);
-    if (xb + ub + cb > c->staging_bytes) return PIC_ENOMEM;
-    double *sx = (double *)c->staging;
-    double *su = (double *)(c->staging + xb);
-    int64_t *scell = (int64_t *)(c->staging + xb + ub);
-    if (launch_unpack(c->rd, species, sx, su, scell, c->stream) != cudaSuccess) return PIC_ECUDA;
-    c->kernel_launches += 1;
-    if (cudaMemcpyAsync(x, sx, xb, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return PIC_ECUDA;
-    if (cudaMemcpyAsync(u, su, ub, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return PIC_ECUDA;
-    if (cell && cudaMemcpyAsync(cell, scell, cb, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
-        return PIC_ECUDA;
+    const int d = rd.dim;
+    for (int64_t p0 = 0; p0 < np; p0 += kChunk) {
+        const int64_t m = std::min(kChunk, np - p0);
+        double *sx = (double *)c->staging;
+        double *su = sx + (size_t)d * m;
+        int64_t *scell = (int64_t *)(su + (size_t)3 * m);
+        if (launch_unpack(c->rd, species, sx, su, scell, m, p0, c->stream) != cudaSuccess) return PIC_ECUDA;
+        c->kernel_launches += 1;
+        for (int a = 0; a < d; ++a)
+            if (cudaMemcpyAsync(x + (size_t)a * np + p0, sx + (size_t)a * m, m * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+                return PIC_ECUDA;
+        for (int a = 0; a < 3; ++a)
+            if (cudaMemcpyAsync(u + (size_t)a * np + p0, su + (size_t)a * m, m * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+                return PIC_ECUDA;
+        if (cell && cudaMemcpyAsync(cell + p0, scell, m * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    c->stream) != cudaSuccess)
+            return PIC_ECUDA;
+        // the staging buffer is reused by the next chunk
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+    }
     return latched_status(c);
 }
 

@@ -93,19 +93,22 @@ __global__ void __launch_bounds__(kBlock) k_shadow(const __grid_constant__ RunDe
     for (int f = 0; f < 6; ++f) rd.Fs[f][c] = (float)rd.F[f][c];
 }
 
-// Host FP64 physical (x, u) -> the context's particle form.  Positions are divided by dx
-// (IEEE division, so the cell index floor(x/dx) matches a plain FP64 evaluation) and
-// wrapped into [0, n).
+// FP64 physical (x, u) -> the context's particle form, for particles p0 .. p0 + m - 1.
+// x[a * xs + i], u[a * us + i] hold particle p0 + i.  Positions are divided by dx (IEEE
+// division, so the cell index floor(x/dx) matches a plain FP64 evaluation) and wrapped into
+// [0, n).
 __global__ void __launch_bounds__(kBlock) k_pack(const __grid_constant__ RunDev rd, int s,
-                                                 const double *x, const double *u, int64_t n)
+                                                 const double *x, int64_t xs, const double *u,
+                                                 int64_t us, int64_t m, int64_t p0)
 {
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t p = p0 + i;
     const SpeciesDev &sp = rd.sp[s];
     int cell[3] = {0, 0, 0};
     double off[3] = {0, 0, 0};
     for (int a = 0; a < rd.dim; ++a) {
-        double xi = x[a * n + p] / rd.dx[a];
+        double xi = x[a * xs + i] / rd.dx[a];
         const double N = (double)rd.n[a];
         if (xi >= N) xi -= N;
         if (xi < 0.0) xi += N;
@@ -127,20 +130,22 @@ __global__ void __launch_bounds__(kBlock) k_pack(const __grid_constant__ RunDev 
             ((float *)sp.pos[a])[p] = o[a];
         }
         sp.cell[p] = (int32_t)gidx(rd, c[0], c[1], rd.dim == 3 ? c[2] : 0);
-        for (int a = 0; a < 3; ++a) ((float *)sp.mom[a])[p] = (float)u[a * n + p];
+        for (int a = 0; a < 3; ++a) ((float *)sp.mom[a])[p] = (float)u[a * us + i];
     } else {
         for (int a = 0; a < rd.dim; ++a) ((double *)sp.pos[a])[p] = (double)cell[a] + off[a];
-        for (int a = 0; a < 3; ++a) ((double *)sp.mom[a])[p] = u[a * n + p];
+        for (int a = 0; a < 3; ++a) ((double *)sp.mom[a])[p] = u[a * us + i];
     }
 }
 
+// Particles p0 .. p0 + m - 1 -> FP64 physical x[a * m + i], u[a * m + i], cell[i].
 __global__ void __launch_bounds__(kBlock) k_unpack(const __grid_constant__ RunDev rd, int s,
-                                                   double *x, double *u, int64_t *cell)
+                                                   double *x, double *u, int64_t *cell,
+                                                   int64_t m, int64_t p0)
 {
     const SpeciesDev &sp = rd.sp[s];
-    const int64_t n = sp.n;
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t p = p0 + i;
     if (rd.prec == 1) {
         const int c = sp.cell[p];
         int ci[3];
@@ -148,18 +153,18 @@ __global__ void __launch_bounds__(kBlock) k_unpack(const __grid_constant__ RunDe
         ci[1] = (c / rd.n[0]) % rd.n[1];
         ci[2] = c / (rd.n[0] * rd.n[1]);
         for (int a = 0; a < rd.dim; ++a)
-            x[a * n + p] = ((double)ci[a] + (double)((const float *)sp.pos[a])[p]) * rd.dx[a];
-        for (int a = 0; a < 3; ++a) u[a * n + p] = (double)((const float *)sp.mom[a])[p];
-        if (cell) cell[p] = c;
+            x[a * m + i] = ((double)ci[a] + (double)((const float *)sp.pos[a])[p]) * rd.dx[a];
+        for (int a = 0; a < 3; ++a) u[a * m + i] = (double)((const float *)sp.mom[a])[p];
+        if (cell) cell[i] = c;
     } else {
         int ci[3] = {0, 0, 0};
         for (int a = 0; a < rd.dim; ++a) {
             const double xi = ((const double *)sp.pos[a])[p];
             ci[a] = (int)floor(xi);
-            x[a * n + p] = xi * rd.dx[a];
+            x[a * m + i] = xi * rd.dx[a];
         }
-        for (int a = 0; a < 3; ++a) u[a * n + p] = ((const double *)sp.mom[a])[p];
-        if (cell) cell[p] = gidx(rd, ci[0], ci[1], ci[2]);
+        for (int a = 0; a < 3; ++a) u[a * m + i] = ((const double *)sp.mom[a])[p];
+        if (cell) cell[i] = gidx(rd, ci[0], ci[1], ci[2]);
     }
 }
 
@@ -368,19 +373,19 @@ cudaError_t launch_shadow(const RunDev &rd, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const RunDev &rd, int s, const double *x, const double *u, int64_t n,
-                        cudaStream_t st)
+cudaError_t launch_pack(const RunDev &rd, int s, const double *x, int64_t xs, const double *u,
+                        int64_t us, int64_t m, int64_t p0, cudaStream_t st)
 {
-    if (n == 0) return cudaSuccess;
-    k_pack<<<grid_for(n), kBlock, 0, st>>>(rd, s, x, u, n);
+    if (m == 0) return cudaSuccess;
+    k_pack<<<grid_for(m), kBlock, 0, st>>>(rd, s, x, xs, u, us, m, p0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(const RunDev &rd, int s, double *x, double *u, int64_t *cell,
-                          cudaStream_t st)
+                          int64_t m, int64_t p0, cudaStream_t st)
 {
-    if (rd.sp[s].n == 0) return cudaSuccess;
-    k_unpack<<<grid_for(rd.sp[s].n), kBlock, 0, st>>>(rd, s, x, u, cell);
+    if (m == 0) return cudaSuccess;
+    k_unpack<<<grid_for(m), kBlock, 0, st>>>(rd, s, x, u, cell, m, p0);
     return cudaGetLastError();
 }
 

@@ -17,10 +17,12 @@ cudaError_t launch_yee_e(const RunDev &rd, bool shadow, cudaStream_t st);
 cudaError_t launch_shadow(const RunDev &rd, cudaStream_t st);
 
 // particle packing (load / read back)
-cudaError_t launch_pack(const RunDev &rd, int s, const double *x, const double *u, int64_t n,
-                        cudaStream_t st);
+// particles p0 .. p0 + m - 1; x[a * xs + i], u[a * us + i] hold particle p0 + i
+cudaError_t launch_pack(const RunDev &rd, int s, const double *x, int64_t xs, const double *u,
+                        int64_t us, int64_t m, int64_t p0, cudaStream_t st);
+// particles p0 .. p0 + m - 1 -> x[a * m + i], u[a * m + i], cell[i]
 cudaError_t launch_unpack(const RunDev &rd, int s, double *x, double *u, int64_t *cell,
-                          cudaStream_t st);
+                          int64_t m, int64_t p0, cudaStream_t st);
 
 // diagnostics: out[0] field energy, out[1] kinetic, out[2] max gauss residual (device doubles)
 cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t st);

@@ -76,7 +76,8 @@ def test_footprint_is_about_two_stores_plus_fields(lib, grid, prec):
         per = (4 + 4 * dim + 12) if prec else (8 * dim + 24)
         ncell = grid[0] * grid[1] * grid[2]
         low = 2 * 2 * n * per + 9 * 8 * ncell
-        assert low <= b <= 1.3 * low + 64 * ncell + (1 << 22)
+        staging = min(n, 1 << 22) * (dim + 4) * 8
+        assert low <= b <= 1.3 * low + 64 * ncell + staging + (1 << 22)
         tile, ntiles, si = pic.pic_tile_info(ctx)
         assert si >= 1 and ntiles >= 1
     finally:
