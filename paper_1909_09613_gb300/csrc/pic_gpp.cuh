@@ -78,14 +78,16 @@ __device__ __forceinline__ void axis_weights(const TTable &tt, R d, AxisW<L, KT,
     w.bt = ttable_weights<L, KT, R>(tt, d, w.wt);
 }
 
-// Esirkepov window of one axis: S0 (old), S1 (new) on l+2 nodes starting at wb.
+// Esirkepov window of one axis: S0 (old-position weights) and DS = S1 - S0 on l+2 nodes
+// starting at node wb (relative to the old cell).
 template <int L, typename R>
 struct AxisS {
     int wb;
     R s0[L + 2];
-    R s1[L + 2];
+    R ds[L + 2];
 };
 
+// FP64: S1 from the stored new position (cell shift sh, offset o_new), DS = S1 - S0.
 template <int L, typename R>
 __device__ __forceinline__ void axis_shapes(R d_old, int sh, R o_new, AxisS<L, R> &s)
 {
@@ -103,7 +105,90 @@ __device__ __forceinline__ void axis_shapes(R d_old, int sh, R o_new, AxisS<L, R
         const R c0 = (k <= L) ? w1[k] : R(0);
         const R c1 = (k >= 1) ? w1[k - 1] : R(0);
         s.s0[k] = sh0 ? a1 : a0;
-        s.s1[k] = sh1 ? c1 : c0;
+        s.ds[k] = (sh1 ? c1 : c0) - s.s0[k];
+    }
+}
+
+// Divided difference (P_k(b) - P_k(a)) / (b - a) of the B-spline basis polynomials of
+// bspline<L> (monomial coefficients in psi), evaluated without cancellation for a, b in [0,1].
+template <int L>
+__device__ __forceinline__ void bspline_dd(float a, float b, float *D)
+{
+    const float h1 = a + b;
+    if constexpr (L == 1) {
+        D[0] = -1.0f;
+        D[1] = 1.0f;
+    } else if constexpr (L == 2) {
+        D[0] = -1.0f + 0.5f * h1;
+        D[1] = 1.0f - h1;
+        D[2] = 0.5f * h1;
+    } else if constexpr (L == 3) {
+        const float h2 = a * a + a * b + b * b;
+        const float s6 = 1.0f / 6.0f;
+        D[0] = -0.5f + 0.5f * h1 - s6 * h2;
+        D[1] = -h1 + 0.5f * h2;
+        D[2] = 0.5f + 0.5f * h1 - 0.5f * h2;
+        D[3] = s6 * h2;
+    } else {
+        const float h2 = a * a + a * b + b * b;
+        const float h3 = (a * a + b * b) * h1;
+        const float s24 = 1.0f / 24.0f;
+        D[0] = s24 * (-4.0f + 6.0f * h1 - 4.0f * h2 + h3);
+        D[1] = s24 * (-12.0f - 6.0f * h1 + 12.0f * h2 - 4.0f * h3);
+        D[2] = s24 * (12.0f - 6.0f * h1 - 12.0f * h2 + 6.0f * h3);
+        D[3] = s24 * (4.0f + 6.0f * h1 + 4.0f * h2 - 4.0f * h3);
+        D[4] = s24 * h3;
+    }
+}
+
+// FP32: DS from the displacement delta (cell units) by divided differences, so the current of
+// a slowly moving particle is not lost to the cancellation of S1 - S0 in single precision.
+// The particle moves from psi0 to psi0 + delta on the spline's local lattice; if that leaves
+// [0,1) the stencil base moves by one node and the difference is split at the lattice point,
+// where the basis polynomials of neighbouring nodes agree (P_{k-1}(0) = P_k(1)).
+template <int L>
+__device__ __forceinline__ void axis_shapes_dd(float d_old, float delta, AxisS<L, float> &s)
+{
+    float p0, w0[L + 1];
+    const int b0 = spline_base<L, float>(d_old, false, p0);
+    bspline<L, float>(p0, w0);
+    const float p1 = p0 + delta;
+    if (p1 >= 1.0f) {            // base moves up: window starts at b0
+        s.wb = b0;
+        const float a = 1.0f - p0;     // part of the move before the lattice point
+        const float b = delta - a;     // part after it (new psi)
+        float Da[L + 1], Db[L + 1];
+        bspline_dd<L>(p0, 1.0f, Da);
+        bspline_dd<L>(0.0f, b, Db);
+#pragma unroll
+        for (int k = 0; k < L + 2; ++k) {
+            s.s0[k] = (k <= L) ? w0[k] : 0.0f;
+            const float up = (k >= 1) ? b * Db[k - 1] : 0.0f;
+            const float lo = (k <= L) ? a * Da[k] : 0.0f;
+            s.ds[k] = up + lo;
+        }
+    } else if (p1 < 0.0f) {      // base moves down: window starts at b0 - 1
+        s.wb = b0 - 1;
+        const float e = -delta - p0;   // overshoot below the lattice point (new psi = 1 - e)
+        float Da[L + 1], Db[L + 1];
+        bspline_dd<L>(1.0f - e, 1.0f, Da);
+        bspline_dd<L>(0.0f, p0, Db);
+#pragma unroll
+        for (int k = 0; k < L + 2; ++k) {
+            s.s0[k] = (k >= 1) ? w0[k - 1] : 0.0f;
+            const float a1 = (k <= L) ? -e * Da[k] : 0.0f;
+            const float a2 = (k >= 1) ? -p0 * Db[k - 1] : 0.0f;
+            s.ds[k] = a1 + a2;
+        }
+    } else {                     // same base
+        s.wb = b0;
+        float D[L + 1];
+        bspline_dd<L>(p0, p1, D);
+#pragma unroll
+        for (int k = 0; k < L + 2; ++k) {
+            s.s0[k] = (k <= L) ? w0[k] : 0.0f;
+            s.ds[k] = (k <= L) ? delta * D[k] : 0.0f;
+        }
     }
 }
 

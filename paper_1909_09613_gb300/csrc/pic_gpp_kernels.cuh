@@ -195,45 +195,52 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
     const R ig = R(1) / g;
 
     // ---- move ----
-    R o[2];
+    R o[2], dl[2];
     int cn[2], shv[2];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-        shv[a] = move_axis<R>(s.d[a], R(rd.dtt[a]) * s.u[a] * ig, s.c[a], rd.n[a], o[a], cn[a]);
+    for (int a = 0; a < 2; ++a) {
+        dl[a] = R(rd.dtt[a]) * s.u[a] * ig;
+        shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], rd.n[a], o[a], cn[a]);
+    }
 
     // ---- Esirkepov deposit into the shared current tile ----
     AxisS<L, R> Sx, Sy;
-    axis_shapes<L, R>(s.d[0], shv[0], o[0], Sx);
-    axis_shapes<L, R>(s.d[1], shv[1], o[1], Sy);
+    if constexpr (sizeof(R) == 4) {
+        axis_shapes_dd<L>(s.d[0], dl[0], Sx);
+        axis_shapes_dd<L>(s.d[1], dl[1], Sy);
+    } else {
+        axis_shapes<L, R>(s.d[0], shv[0], o[0], Sx);
+        axis_shapes<L, R>(s.d[1], shv[1], o[1], Sy);
+    }
     const R kx = R(sp.kx[0]), ky = R(sp.kx[1]);
     const R kz = R(sp.kz) * s.u[2] * ig;
-    const R third = R(1) / R(3), sixth = R(1) / R(6);
-    R DSx[L + 2], DSy[L + 2], Ax[L + 2], Ay[L + 2], px[L + 2], py[L + 2];
+    const R third = R(1) / R(3);
+    R Ax[L + 2], Ay[L + 2], Bx[L + 2], px[L + 2], py[L + 2];
     R acc_x = R(0), acc_y = R(0);
 #pragma unroll
     for (int k = 0; k < L + 2; ++k) {
-        DSx[k] = Sx.s1[k] - Sx.s0[k];
-        DSy[k] = Sy.s1[k] - Sy.s0[k];
-        Ax[k] = Sx.s0[k] + R(0.5) * DSx[k];
-        Ay[k] = Sy.s0[k] + R(0.5) * DSy[k];
-        acc_x += DSx[k];
-        acc_y += DSy[k];
+        Ax[k] = Sx.s0[k] + R(0.5) * Sx.ds[k];
+        Ay[k] = Sy.s0[k] + R(0.5) * Sy.ds[k];
+        Bx[k] = R(0.5) * Sx.s0[k] + third * Sx.ds[k];
+        acc_x += Sx.ds[k];
+        acc_y += Sy.ds[k];
         px[k] = acc_x;
         py[k] = acc_y;
     }
+    // W_x = DSx (S0y + DSy/2); W_y = DSy (S0x + DSx/2);
+    // W_z = S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3 = S0y Ax + DSy Bx
     const int jx0 = sx + Sx.wb, jy0 = sy + Sy.wb;
 #pragma unroll
     for (int b = 0; b < L + 2; ++b) {
         const int row = (jy0 + b) * RX + jx0;
         const R ayk = kx * Ay[b];
-        const R z0 = third * Sy.s0[b] + sixth * Sy.s1[b];
-        const R z1 = sixth * Sy.s0[b] + third * Sy.s1[b];
         const R pyk = (b <= L) ? ky * py[b] : R(0);
+        const R zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
 #pragma unroll
         for (int a = 0; a < L + 2; ++a) {
             if (a <= L) atomicAdd(st.j1 + row + a, ayk * px[a]);
             if (b <= L) atomicAdd(st.j2 + row + a, pyk * Ax[a]);
-            atomicAdd(st.j3 + row + a, kz * (Sx.s0[a] * z0 + Sx.s1[a] * z1));
+            atomicAdd(st.j3 + row + a, zs * Ax[a] + zd * Bx[a]);
         }
     }
 
@@ -402,22 +409,27 @@ __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &
     boris<R>(R(sp.qmdt_half), E, B, s.u);
     const R g = sqrt(R(1) + s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
     const R ig = R(1) / g;
-    R o[3];
+    R o[3], dl[3];
     int cn[3], shv[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        shv[a] = move_axis<R>(s.d[a], R(rd.dtt[a]) * s.u[a] * ig, s.c[a], rd.n[a], o[a], cn[a]);
+    for (int a = 0; a < 3; ++a) {
+        dl[a] = R(rd.dtt[a]) * s.u[a] * ig;
+        shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], rd.n[a], o[a], cn[a]);
+    }
 
     AxisS<L, R> S[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) axis_shapes<L, R>(s.d[a], shv[a], o[a], S[a]);
+    for (int a = 0; a < 3; ++a) {
+        if constexpr (sizeof(R) == 4) axis_shapes_dd<L>(s.d[a], dl[a], S[a]);
+        else axis_shapes<L, R>(s.d[a], shv[a], o[a], S[a]);
+    }
     R DS[3][L + 2], P[3][L + 2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         R acc = R(0);
 #pragma unroll
         for (int k = 0; k < L + 2; ++k) {
-            DS[a][k] = S[a].s1[k] - S[a].s0[k];
+            DS[a][k] = S[a].ds[k];
             acc += DS[a][k];
             P[a][k] = acc;
         }
