@@ -251,6 +251,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--form", default="both", choices=["both", "fp64", "fp32"],
+                    help="fp32: time only the precision form (for profiling runs)")
     args = ap.parse_args()
     rank, world, local = _rank_env()
 
@@ -295,6 +297,14 @@ def main():
 
     wl = workloads.config_large(scheme=1, device="cuda", seed=workloads.BASE_SEED + rank,
                                 scale=args.scale)
+    if args.form == "fp32":
+        r32 = time_form(wl, pic.PIC_FP32_MIXED, args.steps, args.warmup, dist_on, clocks=False)
+        r32.pop("run").close()
+        if rank == 0:
+            print(json.dumps({"form": "fp32", "ms_per_step": r32["ms"] / args.steps,
+                              "gpp_ms": r32["gpp_ms"] / max(r32["gpp_launches"], 1),
+                              "particles": r32["n"]}))
+        return
     res = time_form(wl, pic.PIC_FP64, args.steps, args.warmup, dist_on)
     run64 = res.pop("run")
     n_all = res["n"] * world
@@ -346,7 +356,7 @@ def main():
     del run64
     torch.cuda.empty_cache()
 
-    if not args.no_fp32:
+    if not args.no_fp32 and args.form == "both":
         r32 = time_form(wl, pic.PIC_FP32_MIXED, args.steps, args.warmup, dist_on)
         r32.pop("run").close()
         g32 = r32["gpp_ms"] / max(r32["gpp_launches"], 1) * 1e-3
