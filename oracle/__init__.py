@@ -128,7 +128,7 @@ def boris(qmdt: float, E, B, u) -> np.ndarray:
 
 
 def tile_sort(grid, tile, cells):
-    """Reference tile-sort order (tile, slot-in-cell, cell-in-tile); returns (perm, tile_start)."""
+    """Reference tile-sort order (tile, cell-in-tile, input order); returns (perm, tile_start)."""
     lib = _load()
     n = np.array(list(grid) + [1] * (3 - len(grid)), dtype=np.int32)
     t = np.array(list(tile) + [1] * (3 - len(tile)), dtype=np.int32)

@@ -611,9 +611,8 @@ void orc_gauss_residual(const orc_sim *s, double *res)
 
 /* Sort order: cells are grouped into tiles of tile[0] x tile[1] (x tile[2]) cells (ragged
  * at the high edge); the tiles are numbered x-fastest, and so are the cells inside a tile.
- * Each particle gets slot = its rank among the particles of its cell in the input order.
- * Particles are ordered by (tile, slot, cell-in-tile).  With that order the cell at every
- * output position is fixed by the cell counts alone, whichever particle fills each slot.
+ * Particles are ordered by (tile, cell-in-tile), and inside a cell by their input order.
+ * The cell at every output position is fixed by the cell counts alone.
  *
  * cell_of[i] = linear cell index (k*ny + j)*nx + i of particle i (input, computed by the
  * caller as floor(x/dx) per axis).  Outputs: perm[p] = input index placed at position p;
@@ -624,8 +623,8 @@ static int sort_rec_cmp(const void *pa, const void *pb)
 {
     const sort_rec *a = (const sort_rec *)pa, *b = (const sort_rec *)pb;
     if (a->tile != b->tile) return a->tile < b->tile ? -1 : 1;
-    if (a->slot != b->slot) return a->slot < b->slot ? -1 : 1;
     if (a->cell != b->cell) return a->cell < b->cell ? -1 : 1;
+    if (a->slot != b->slot) return a->slot < b->slot ? -1 : 1;
     return a->idx < b->idx ? -1 : (a->idx > b->idx);
 }
 

@@ -427,7 +427,7 @@ def test_tile_sort_order_brute_force(grid, tile):
         tid = ((k // t3[2]) * ntx[1] + j // t3[1]) * ntx[0] + i // t3[0]
         assert ts[tid] <= p < ts[tid + 1]
         local = ((k % t3[2]) * t3[1] + j % t3[1]) * t3[0] + i % t3[0]
-        key = (tid, slot[src], local)
+        key = (tid, local, slot[src])
         if prev is not None:
             assert key > prev
         prev = key
