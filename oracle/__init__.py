@@ -13,7 +13,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   W            closed forms, partition of unity, unit integral, convolution recurrence
   T            the paper's printed T_1..T_4, T_l(1/2) = W_l, partition of unity,
                dtt -> 0 limit, numerical Fourier transform = tau_l
-  gather       brute force over all nodes; WT = MC at c dt = dx/2; zero self-force (App. B)
+  gather       brute force over all nodes; WT = MC at c dt = dx/2; Fourier symbol of every
+               component (Eq. shapeEB); App. B self-force with transverse T
   boris        gyration angle and |u| conservation; E x B drift
   deposit      discrete continuity on every node; 1-D motion; static J_z closed form
   yee          vacuum dispersion relation (App. C, A_i = 1); Gauss's law conservation
@@ -94,7 +95,7 @@ def _load():
         lib.orc_diag.argtypes = [ctypes.c_void_p, _dp]
         lib.orc_gauss_residual.argtypes = [ctypes.c_void_p, _dp]
         lib.orc_tile_sort.restype = ctypes.c_long
-        lib.orc_tile_sort.argtypes = [_ip, _ip, ctypes.c_long, _lp, _lp, _lp]
+        lib.orc_tile_sort.argtypes = [_ip, _ip, ctypes.c_int, ctypes.c_long, _lp, _lp, _lp]
         _lib = lib
         return lib
 
@@ -127,8 +128,13 @@ def boris(qmdt: float, E, B, u) -> np.ndarray:
     return out
 
 
-def tile_sort(grid, tile, cells):
-    """Reference tile-sort order (tile, cell-in-tile, input order); returns (perm, tile_start)."""
+CELL_MAJOR, SLOT_MAJOR = 0, 1
+
+
+def tile_sort(grid, tile, cells, order=CELL_MAJOR):
+    """Reference tile-sort order; returns (perm, tile_start).
+    CELL_MAJOR: (tile, cell-in-tile, slot); SLOT_MAJOR: (tile, slot, cell-in-tile), where slot
+    is the particle's rank inside its cell in input order."""
     lib = _load()
     n = np.array(list(grid) + [1] * (3 - len(grid)), dtype=np.int32)
     t = np.array(list(tile) + [1] * (3 - len(tile)), dtype=np.int32)
@@ -136,7 +142,7 @@ def tile_sort(grid, tile, cells):
     ntiles = int(np.prod((n.astype(np.int64) + t - 1) // t))
     perm = np.zeros(max(len(cells), 1), dtype=np.int64)
     ts = np.zeros(ntiles + 1, dtype=np.int64)
-    lib.orc_tile_sort(n.ctypes.data_as(_ip), t.ctypes.data_as(_ip), len(cells),
+    lib.orc_tile_sort(n.ctypes.data_as(_ip), t.ctypes.data_as(_ip), int(order), len(cells),
                       cells.ctypes.data_as(_lp), perm.ctypes.data_as(_lp), ts.ctypes.data_as(_lp))
     return perm[:len(cells)], ts
 

@@ -609,17 +609,20 @@ void orc_gauss_residual(const orc_sim *s, double *res)
 /* Particle tile sort (not in the paper; the layout the GPU path streams particles in)     */
 /* ------------------------------------------------------------------------------------- */
 
-/* Sort order: cells are grouped into tiles of tile[0] x tile[1] (x tile[2]) cells (ragged
- * at the high edge); the tiles are numbered x-fastest, and so are the cells inside a tile.
- * Particles are ordered by (tile, cell-in-tile), and inside a cell by their input order.
- * The cell at every output position is fixed by the cell counts alone.
+/* Sort orders: cells are grouped into tiles of tile[0] x tile[1] (x tile[2]) cells (ragged at
+ * the high edge); the tiles are numbered x-fastest, and so are the cells inside a tile.  Each
+ * particle's slot is its rank among the particles of its cell in the input order.
+ *   order 0 ("cell-major"): by (tile, cell-in-tile, slot);
+ *   order 1 ("slot-major"): by (tile, slot, cell-in-tile), i.e. a tile runs through groups
+ *   holding one particle of every cell that has more than `slot` particles.
+ * In both, the cell at every output position is fixed by the cell counts alone.
  *
  * cell_of[i] = linear cell index (k*ny + j)*nx + i of particle i (input, computed by the
  * caller as floor(x/dx) per axis).  Outputs: perm[p] = input index placed at position p;
  * tile_start[t] = first position of tile t (ntiles + 1 entries).                           */
 typedef struct { long tile, slot, cell, idx; } sort_rec;
 
-static int sort_rec_cmp(const void *pa, const void *pb)
+static int sort_rec_cmp_cell(const void *pa, const void *pb)
 {
     const sort_rec *a = (const sort_rec *)pa, *b = (const sort_rec *)pb;
     if (a->tile != b->tile) return a->tile < b->tile ? -1 : 1;
@@ -628,8 +631,17 @@ static int sort_rec_cmp(const void *pa, const void *pb)
     return a->idx < b->idx ? -1 : (a->idx > b->idx);
 }
 
-long orc_tile_sort(const int *n, const int *tile, long np, const long *cell_of, long *perm,
-                   long *tile_start)
+static int sort_rec_cmp_slot(const void *pa, const void *pb)
+{
+    const sort_rec *a = (const sort_rec *)pa, *b = (const sort_rec *)pb;
+    if (a->tile != b->tile) return a->tile < b->tile ? -1 : 1;
+    if (a->slot != b->slot) return a->slot < b->slot ? -1 : 1;
+    if (a->cell != b->cell) return a->cell < b->cell ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx);
+}
+
+long orc_tile_sort(const int *n, const int *tile, int order, long np, const long *cell_of,
+                   long *perm, long *tile_start)
 {
     const long nx = n[0], ny = n[1], nz = n[2];
     const long tx = tile[0], ty = tile[1], tz = tile[2];
@@ -648,7 +660,7 @@ long orc_tile_sort(const int *n, const int *tile, long np, const long *cell_of, 
         r[p].slot = cnt[c]++;
         r[p].idx = p;
     }
-    qsort(r, (size_t)np, sizeof(sort_rec), sort_rec_cmp);
+    qsort(r, (size_t)np, sizeof(sort_rec), order == 1 ? sort_rec_cmp_slot : sort_rec_cmp_cell);
     for (long t = 0; t <= ntiles; ++t) tile_start[t] = 0;
     for (long p = 0; p < np; ++p) {
         perm[p] = r[p].idx;

@@ -111,19 +111,69 @@ __device__ __forceinline__ bool local_coord(int c, int origin, int tile, int dri
     return l >= -drift && l < tile + drift;
 }
 
-// One particle, 2D, staged tile.
+// Butterfly reduce-scatter across the 32 lanes of a warp: on entry every lane holds NP values
+// (NP a multiple of 32); on exit lane l holds in v[0 .. NP/32) the warp sums of the values
+// with indices l*NP/32 .. l*NP/32 + NP/32 - 1.  NP - NP/32 shuffles in total.
+template <int NP, typename R>
+__device__ __forceinline__ void warp_reduce_scatter(R *v, int lane)
+{
+    static_assert(NP % 32 == 0, "pad to a multiple of 32");
+#pragma unroll
+    for (int off = 16, n = NP; off >= 1; off >>= 1, n >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const R send = upper ? v[i] : v[i + n / 2];
+            const R keep = upper ? v[i + n / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+}
+
+constexpr int pad32(int v) { return (v + 31) / 32 * 32; }
+
+// Add a warp-summed (NA x NB) block of one current component to shared memory: the block's
+// node (A, B) goes to row y0 + B, column x0 + A.  Every lane writes distinct nodes.
+template <int NA, int NB, typename R>
+__device__ __forceinline__ void warp_block_add(R *v, int lane, R *j, int RX, int x0, int y0)
+{
+    constexpr int V = NA * NB, NP = pad32(V), PER = NP / 32;
+    warp_reduce_scatter<NP, R>(v, lane);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int idx = lane * PER + q;
+        if (idx < V && v[q] != R(0)) {
+            const int A = idx / NB, B = idx - A * NB;
+            atomicAdd(j + (y0 + B) * RX + x0 + A, v[q]);
+        }
+    }
+}
+
+// One particle per lane, 2D, staged tile.  Called by all 32 lanes of a warp together (the
+// deposit is warp-collective); lanes with act == false carry no particle.
 template <int L, int KT, typename R>
 __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &sp,
-                                            const Stage2D<R> &st, int64_t p, int x0, int y0)
+                                            const Stage2D<R> &st, int64_t p, bool act, int x0,
+                                            int y0)
 {
+    const int lane = threadIdx.x & 31;
     PState<R> s;
-    load_particle<2, R>(rd, sp, p, s);
-    int lx, ly;
-    const bool okx = local_coord(s.c[0], x0, rd.tile[0], rd.drift[0], rd.n[0], lx);
-    const bool oky = local_coord(s.c[1], y0, rd.tile[1], rd.drift[1], rd.n[1], ly);
-    if (!(okx && oky)) {
-        set_err(rd.err, 1);
-        return;
+    int lx = 0, ly = 0;
+    if (act) {
+        load_particle<2, R>(rd, sp, p, s);
+        const bool okx = local_coord(s.c[0], x0, rd.tile[0], rd.drift[0], rd.n[0], lx);
+        const bool oky = local_coord(s.c[1], y0, rd.tile[1], rd.drift[1], rd.n[1], ly);
+        if (!(okx && oky)) {
+            set_err(rd.err, 1);
+            act = false;
+        }
+    }
+    if (!act) {
+        // a harmless stand-in particle at the tile origin; its current is weighted by zero
+        s.c[0] = x0; s.c[1] = y0; s.c[2] = 0;
+        s.d[0] = R(0.5); s.d[1] = R(0.5); s.d[2] = R(0);
+        s.u[0] = s.u[1] = s.u[2] = R(0);
+        lx = 0; ly = 0;
     }
     const int RX = rd.reg[0];
     const int sx = lx + rd.pre[0], sy = ly + rd.pre[1];
@@ -203,7 +253,7 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
         shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], rd.n[a], o[a], cn[a]);
     }
 
-    // ---- Esirkepov deposit into the shared current tile ----
+    // ---- Esirkepov deposit ----
     AxisS<L, R> Sx, Sy;
     if constexpr (sizeof(R) == 4) {
         axis_shapes_dd<L>(s.d[0], dl[0], Sx);
@@ -212,9 +262,12 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
         axis_shapes<L, R>(s.d[0], shv[0], o[0], Sx);
         axis_shapes<L, R>(s.d[1], shv[1], o[1], Sy);
     }
-    const R kx = R(sp.kx[0]), ky = R(sp.kx[1]);
-    const R kz = R(sp.kz) * s.u[2] * ig;
+    const R wgt = act ? R(1) : R(0);
+    const R kx = wgt * R(sp.kx[0]), ky = wgt * R(sp.kx[1]);
+    const R kz = wgt * R(sp.kz) * s.u[2] * ig;
     const R third = R(1) / R(3);
+    // W_x = DSx (S0y + DSy/2), prefix along x; W_y = DSy (S0x + DSx/2), prefix along y;
+    // W_z = S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3 = S0y Ax + DSy Bx.
     R Ax[L + 2], Ay[L + 2], Bx[L + 2], px[L + 2], py[L + 2];
     R acc_x = R(0), acc_y = R(0);
 #pragma unroll
@@ -227,22 +280,85 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
         px[k] = acc_x;
         py[k] = acc_y;
     }
-    // W_x = DSx (S0y + DSy/2); W_y = DSy (S0x + DSx/2);
-    // W_z = S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3 = S0y Ax + DSy Bx
     const int jx0 = sx + Sx.wb, jy0 = sy + Sy.wb;
+
+    // Warp-collective path: when all lanes' windows start within one node of each other in
+    // both axes (lanes of one cell or of two neighbouring cells), place every lane's window
+    // in a common (L+3) x (L+3) block, sum the block over the warp by a reduce-scatter and add
+    // each node once.  Otherwise every lane adds its own window with shared atomics.
+    const int mnx = __reduce_min_sync(0xffffffffu, act ? jx0 : 0x7fffffff);
+    const int mxx = __reduce_max_sync(0xffffffffu, act ? jx0 : -0x7fffffff);
+    const int mny = __reduce_min_sync(0xffffffffu, act ? jy0 : 0x7fffffff);
+    const int mxy = __reduce_max_sync(0xffffffffu, act ? jy0 : -0x7fffffff);
+    if (mxx < mnx) return;  // no active lane
+    if (mxx - mnx <= 1 && mxy - mny <= 1) {
+        const bool ox = act && jx0 > mnx, oy = act && jy0 > mny;
+        // window vectors shifted by the lane's offset in the common block
+        R pxs[L + 3], Axs[L + 3], Bxs[L + 3], Ays[L + 3], pys[L + 3], S0ys[L + 3], DSys[L + 3];
 #pragma unroll
-    for (int b = 0; b < L + 2; ++b) {
-        const int row = (jy0 + b) * RX + jx0;
-        const R ayk = kx * Ay[b];
-        const R pyk = (b <= L) ? ky * py[b] : R(0);
-        const R zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
+        for (int A = 0; A < L + 3; ++A) {
+            const R px0 = (A <= L) ? px[A] : R(0), px1 = (A >= 1 && A - 1 <= L) ? px[A - 1] : R(0);
+            const R ax0 = (A <= L + 1) ? Ax[A] : R(0), ax1 = (A >= 1) ? Ax[A - 1] : R(0);
+            const R bx0 = (A <= L + 1) ? Bx[A] : R(0), bx1 = (A >= 1) ? Bx[A - 1] : R(0);
+            pxs[A] = ox ? px1 : px0;
+            Axs[A] = ox ? ax1 : ax0;
+            Bxs[A] = ox ? bx1 : bx0;
+            const R ay0 = (A <= L + 1) ? Ay[A] : R(0), ay1 = (A >= 1) ? Ay[A - 1] : R(0);
+            const R py0 = (A <= L) ? py[A] : R(0), py1 = (A >= 1 && A - 1 <= L) ? py[A - 1] : R(0);
+            const R s00 = (A <= L + 1) ? Sy.s0[A] : R(0), s01 = (A >= 1) ? Sy.s0[A - 1] : R(0);
+            const R d00 = (A <= L + 1) ? Sy.ds[A] : R(0), d01 = (A >= 1) ? Sy.ds[A - 1] : R(0);
+            Ays[A] = oy ? ay1 : ay0;
+            pys[A] = oy ? py1 : py0;
+            S0ys[A] = oy ? s01 : s00;
+            DSys[A] = oy ? d01 : d00;
+        }
+        {   // J1 on nodes A = 0..L+1 (x, prefix), B = 0..L+2 (y)
+            R v[pad32((L + 2) * (L + 3))];
 #pragma unroll
-        for (int a = 0; a < L + 2; ++a) {
-            if (a <= L) atomicAdd(st.j1 + row + a, ayk * px[a]);
-            if (b <= L) atomicAdd(st.j2 + row + a, pyk * Ax[a]);
-            atomicAdd(st.j3 + row + a, zs * Ax[a] + zd * Bx[a]);
+            for (int i = 0; i < pad32((L + 2) * (L + 3)); ++i) v[i] = R(0);
+#pragma unroll
+            for (int A = 0; A < L + 2; ++A)
+#pragma unroll
+                for (int Bn = 0; Bn < L + 3; ++Bn) v[A * (L + 3) + Bn] = kx * pxs[A] * Ays[Bn];
+            warp_block_add<L + 2, L + 3, R>(v, lane, st.j1, RX, mnx, mny);
+        }
+        {   // J2 on nodes A = 0..L+2 (x), B = 0..L+1 (y, prefix)
+            R v[pad32((L + 3) * (L + 2))];
+#pragma unroll
+            for (int i = 0; i < pad32((L + 3) * (L + 2)); ++i) v[i] = R(0);
+#pragma unroll
+            for (int A = 0; A < L + 3; ++A)
+#pragma unroll
+                for (int Bn = 0; Bn < L + 2; ++Bn) v[A * (L + 2) + Bn] = ky * Axs[A] * pys[Bn];
+            warp_block_add<L + 3, L + 2, R>(v, lane, st.j2, RX, mnx, mny);
+        }
+        {   // J3 on nodes A, B = 0..L+2
+            R v[pad32((L + 3) * (L + 3))];
+#pragma unroll
+            for (int i = 0; i < pad32((L + 3) * (L + 3)); ++i) v[i] = R(0);
+#pragma unroll
+            for (int A = 0; A < L + 3; ++A)
+#pragma unroll
+                for (int Bn = 0; Bn < L + 3; ++Bn)
+                    v[A * (L + 3) + Bn] = kz * (S0ys[Bn] * Axs[A] + DSys[Bn] * Bxs[A]);
+            warp_block_add<L + 3, L + 3, R>(v, lane, st.j3, RX, mnx, mny);
+        }
+    } else if (act) {
+#pragma unroll
+        for (int b = 0; b < L + 2; ++b) {
+            const int row = (jy0 + b) * RX + jx0;
+            const R ayk = kx * Ay[b];
+            const R pyk = (b <= L) ? ky * py[b] : R(0);
+            const R zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
+#pragma unroll
+            for (int a = 0; a < L + 2; ++a) {
+                if (a <= L) atomicAdd(st.j1 + row + a, ayk * px[a]);
+                if (b <= L) atomicAdd(st.j2 + row + a, pyk * Ax[a]);
+                atomicAdd(st.j3 + row + a, zs * Ax[a] + zd * Bx[a]);
+            }
         }
     }
+    if (!act) return;
 
     // ---- store ----
 #pragma unroll
@@ -270,8 +386,12 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile)
     for (int s = 0; s < rd.nsp; ++s) {
         const SpeciesDev &sp = rd.sp[s];
         const int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
-        for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x)
-            particle_2d<L, KT, R>(rd, sp, st, p, x0, y0);
+        // warp-uniform trip count: a warp's lanes take 32 consecutive particles
+        const int64_t wbase = a + (threadIdx.x & ~31);
+        for (int64_t q = wbase; q < b; q += blockDim.x) {
+            const int64_t p = q + (threadIdx.x & 31);
+            particle_2d<L, KT, R>(rd, sp, st, p, p < b, x0, y0);
+        }
         __syncthreads();
         stage2d_flush<R>(rd, st, x0, y0);
         __syncthreads();

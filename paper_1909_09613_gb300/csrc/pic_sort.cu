@@ -1,16 +1,16 @@
 // Tile sort of one species' particle store.
 //
-// Order: by tile, then by slot (the particle's rank among the particles of its cell), then by
-// cell inside the tile (x fastest).  Within a tile the store therefore runs through "one
-// particle of every occupied cell" groups, so the 32 lanes of a warp work on 32 neighbouring
-// cells: their shared-memory gathers hit consecutive words and their current deposits go to
-// distinct addresses.  The cell at every position is fixed by the cell counts; which of a
-// cell's particles takes which slot is decided by atomics and is not reproducible.
+// Order: by tile, then by cell inside the tile (x fastest), then by slot (the particle's rank
+// among the particles of its cell).  A warp's 32 consecutive particles therefore sit in one
+// cell or a few neighbouring ones: their shared-memory gathers broadcast, and their Esirkepov
+// currents can be summed across the warp in registers before they reach shared memory.  The
+// cell at every position is fixed by the cell counts; which of a cell's particles takes which
+// slot is decided by atomics and is not reproducible.
 //
 //   1. k_count   : tile-major cell key per particle, slot = atomicAdd(count[key], 1)
 //   2. k_tile_sum: particles per tile;  k_scan: exclusive scan over tiles -> tile_start
-//   3. k_layout  : one CTA per tile; for every (cell, slot) its position in the tile
-//   4. k_scatter : copy every particle to its position in the other buffer
+//   3. k_layout  : one CTA per tile; first position of every cell of the tile
+//   4. k_scatter : copy every particle to cell_first[key] + slot in the other buffer
 #include "pic_launch.h"
 
 namespace pic {
@@ -148,24 +148,9 @@ __global__ void k_layout(const __grid_constant__ RunDev rd, SortScratch sc,
     const int64_t t = blockIdx.x;
     const int c = threadIdx.x;
     __shared__ int tot;
-    __shared__ int maxc;
     const int cnt = (c < TC) ? sc.cnt[t * TC + c] : 0;
-    if (threadIdx.x == 0) maxc = 0;
-    __syncthreads();
-    if (cnt > 0) atomicMax(&maxc, cnt);
     const int first = block_excl_scan(cnt, &tot);
-    const int64_t base = tile_start[t];
-    if (c < TC) sc.cell_first[t * TC + c] = (int32_t)(base + first);
-    __syncthreads();
-    const int ms = maxc;
-    int goff = 0;
-    for (int s = 0; s < ms; ++s) {
-        const int flag = (cnt > s) ? 1 : 0;
-        const int rank = block_excl_scan(flag, &tot);
-        if (flag) sc.pos[base + first + s] = (int32_t)(base + goff + rank);
-        goff += tot;
-        __syncthreads();
-    }
+    if (c < TC) sc.cell_first[t * TC + c] = (int32_t)(tile_start[t] + first);
 }
 
 template <typename T>
@@ -181,7 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const __grid_constant__ RunD
     const SpeciesDev &sp = rd.sp[s];
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= sp.n) return;
-    const int64_t q = sc.pos[sc.cell_first[sc.key[p]] + sc.slot[p]];
+    const int64_t q = (int64_t)sc.cell_first[sc.key[p]] + sc.slot[p];
     void *dp[3] = {d0, d1, d2};
     void *dm[3] = {m0, m1, m2};
     if (rd.prec == 1) {

@@ -404,13 +404,14 @@ def test_wt_equals_mc_at_half_step_full_run():
 # Tile sort order
 # ------------------------------------------------------------------------------------------
 
+@pytest.mark.parametrize("order", [oracle.CELL_MAJOR, oracle.SLOT_MAJOR])
 @pytest.mark.parametrize("grid,tile", [((10, 7), (4, 3)), ((8, 8), (8, 8)), ((6, 5, 4), (4, 2, 3))])
-def test_tile_sort_order_brute_force(grid, tile):
+def test_tile_sort_order_brute_force(grid, tile, order):
     g3 = list(grid) + [1] * (3 - len(grid))
     t3 = list(tile) + [1] * (3 - len(tile))
     ncell = int(np.prod(g3))
     cells = RNG.integers(0, ncell, 300)
-    perm, ts = oracle.tile_sort(grid, tile, cells)
+    perm, ts = oracle.tile_sort(grid, tile, cells, order)
     assert sorted(perm.tolist()) == list(range(len(cells)))
 
     def coords(c):
@@ -427,7 +428,7 @@ def test_tile_sort_order_brute_force(grid, tile):
         tid = ((k // t3[2]) * ntx[1] + j // t3[1]) * ntx[0] + i // t3[0]
         assert ts[tid] <= p < ts[tid + 1]
         local = ((k % t3[2]) * t3[1] + j % t3[1]) * t3[0] + i % t3[0]
-        key = (tid, local, slot[src])
+        key = (tid, local, slot[src]) if order == oracle.CELL_MAJOR else (tid, slot[src], local)
         if prev is not None:
             assert key > prev
         prev = key
