@@ -332,7 +332,7 @@ int pic_footprint(const pic_ctx *c, size_t *bytes)
     // sort targets and sort scratch
     for (int s = 0; s < rd.nsp; ++s) b += align_up((size_t)c->cap[s] * pb + 7 * A, A);
     b += 2 * align_up(rd.ntiles * TC * sizeof(int32_t), A);
-    b += 2 * align_up((size_t)capmax * sizeof(int32_t), A);
+    b += 3 * align_up((size_t)capmax * sizeof(int32_t), A);
     b += align_up((rd.ntiles + 1) * sizeof(int64_t), A);
     b += staging_size(rd, capmax);                // host<->device staging (chunked)
     b += align_up(rd.ncell * sizeof(double), A);  // rho
@@ -383,6 +383,7 @@ int pic_bind_memory(pic_ctx *c, void *dev, size_t bytes)
     c->sc.cell_first = (int32_t *)take(rd.ntiles * TC * sizeof(int32_t));
     c->sc.slot = (int32_t *)take((size_t)capmax * sizeof(int32_t));
     c->sc.key = (int32_t *)take((size_t)capmax * sizeof(int32_t));
+    c->sc.pos = (int32_t *)take((size_t)capmax * sizeof(int32_t));
     c->sc.tile_count = (int64_t *)take((rd.ntiles + 1) * sizeof(int64_t));
     c->staging_bytes = staging_size(rd, capmax);
     c->staging = take(c->staging_bytes);

@@ -111,40 +111,44 @@ __device__ __forceinline__ bool local_coord(int c, int origin, int tile, int dri
     return l >= -drift && l < tile + drift;
 }
 
-// Butterfly reduce-scatter across the 32 lanes of a warp: on entry every lane holds NP values
-// (NP a multiple of 32); on exit lane l holds in v[0 .. NP/32) the warp sums of the values
-// with indices l*NP/32 .. l*NP/32 + NP/32 - 1.  NP - NP/32 shuffles in total.
-template <int NP, typename R>
-__device__ __forceinline__ void warp_reduce_scatter(R *v, int lane)
+// Butterfly reduce-scatter across the 32 lanes of a warp, levels OFF, OFF/2, .., 1: on entry
+// every lane holds N values; after the level with offset OFF the lanes whose OFF bit is set
+// keep the upper half of the array.  After the last level lane l holds in v[0 .. N/(2 OFF))
+// the warp sums of the values with indices l*N/(2 OFF) + q (for OFF = 16 entry: N/32 values).
+template <int N, int OFF, typename R>
+__device__ __forceinline__ void rs_levels(R *v, int lane)
 {
-    static_assert(NP % 32 == 0, "pad to a multiple of 32");
+    if constexpr (OFF >= 1) {
+        const bool upper = (lane & OFF) != 0;
 #pragma unroll
-    for (int off = 16, n = NP; off >= 1; off >>= 1, n >>= 1) {
-        const bool upper = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < n / 2; ++i) {
-            const R send = upper ? v[i] : v[i + n / 2];
-            const R keep = upper ? v[i + n / 2] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        for (int i = 0; i < N / 2; ++i) {
+            const R send = upper ? v[i] : v[i + N / 2];
+            const R keep = upper ? v[i + N / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
         }
+        rs_levels<N / 2, OFF / 2, R>(v, lane);
     }
 }
 
 constexpr int pad32(int v) { return (v + 31) / 32 * 32; }
 
-// Add a warp-summed (NA x NB) block of one current component to shared memory: the block's
-// node (A, B) goes to row y0 + B, column x0 + A.  Every lane writes distinct nodes.
-template <int NA, int NB, typename R>
-__device__ __forceinline__ void warp_block_add(R *v, int lane, R *j, int RX, int x0, int y0)
+// One lane's Esirkepov window added to the shared current tile with atomics.
+template <int L, typename R>
+__device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int jx0, int jy0, R kx,
+                                             R ky, R kz, const R *px, const R *py, const R *Ax,
+                                             const R *Ay, const R *Bx, const AxisS<L, R> &Sy)
 {
-    constexpr int V = NA * NB, NP = pad32(V), PER = NP / 32;
-    warp_reduce_scatter<NP, R>(v, lane);
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-        const int idx = lane * PER + q;
-        if (idx < V && v[q] != R(0)) {
-            const int A = idx / NB, B = idx - A * NB;
-            atomicAdd(j + (y0 + B) * RX + x0 + A, v[q]);
+    for (int b = 0; b < L + 2; ++b) {
+        const int row = (jy0 + b) * RX + jx0;
+        const R ayk = kx * Ay[b];
+        const R pyk = (b <= L) ? ky * py[b] : R(0);
+        const R zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
+#pragma unroll
+        for (int a = 0; a < L + 2; ++a) {
+            if (a <= L) atomicAdd(st.j1 + row + a, ayk * px[a]);
+            if (b <= L) atomicAdd(st.j2 + row + a, pyk * Ax[a]);
+            atomicAdd(st.j3 + row + a, zs * Ax[a] + zd * Bx[a]);
         }
     }
 }
@@ -282,81 +286,94 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
     }
     const int jx0 = sx + Sx.wb, jy0 = sy + Sy.wb;
 
-    // Warp-collective path: when all lanes' windows start within one node of each other in
-    // both axes (lanes of one cell or of two neighbouring cells), place every lane's window
-    // in a common (L+3) x (L+3) block, sum the block over the warp by a reduce-scatter and add
-    // each node once.  Otherwise every lane adds its own window with shared atomics.
-    const int mnx = __reduce_min_sync(0xffffffffu, act ? jx0 : 0x7fffffff);
-    const int mxx = __reduce_max_sync(0xffffffffu, act ? jx0 : -0x7fffffff);
-    const int mny = __reduce_min_sync(0xffffffffu, act ? jy0 : 0x7fffffff);
-    const int mxy = __reduce_max_sync(0xffffffffu, act ? jy0 : -0x7fffffff);
-    if (mxx < mnx) return;  // no active lane
-    if (mxx - mnx <= 1 && mxy - mny <= 1) {
-        const bool ox = act && jx0 > mnx, oy = act && jy0 > mny;
-        // window vectors shifted by the lane's offset in the common block
-        R pxs[L + 3], Axs[L + 3], Bxs[L + 3], Ays[L + 3], pys[L + 3], S0ys[L + 3], DSys[L + 3];
+    if constexpr (sizeof(R) == 4) {
+        // Warp-collective path (cell-major order): when all lanes' windows start within one
+        // node of each other in both axes (lanes of one cell or of two neighbouring cells),
+        // place every lane's window in a common (L+3) x (L+3) block, sum the block over the
+        // warp with one reduce-scatter and add each node once.  Otherwise every lane adds its
+        // own window with shared atomics.
+        const int mnx = __reduce_min_sync(0xffffffffu, act ? jx0 : 0x7fffffff);
+        const int mxx = __reduce_max_sync(0xffffffffu, act ? jx0 : -0x7fffffff);
+        const int mny = __reduce_min_sync(0xffffffffu, act ? jy0 : 0x7fffffff);
+        const int mxy = __reduce_max_sync(0xffffffffu, act ? jy0 : -0x7fffffff);
+        if (mxx < mnx) return;  // no active lane in this warp
+        if (mxx - mnx <= 1 && mxy - mny <= 1) {
+            const bool ox = act && jx0 > mnx, oy = act && jy0 > mny;
+            // lane vectors shifted into the common block, constants folded in
+            R pxs[L + 3], Axs[L + 3], Bxs[L + 3], Ays[L + 3], pys[L + 3], S0ys[L + 3], DSys[L + 3];
 #pragma unroll
-        for (int A = 0; A < L + 3; ++A) {
-            const R px0 = (A <= L) ? px[A] : R(0), px1 = (A >= 1 && A - 1 <= L) ? px[A - 1] : R(0);
-            const R ax0 = (A <= L + 1) ? Ax[A] : R(0), ax1 = (A >= 1) ? Ax[A - 1] : R(0);
-            const R bx0 = (A <= L + 1) ? Bx[A] : R(0), bx1 = (A >= 1) ? Bx[A - 1] : R(0);
-            pxs[A] = ox ? px1 : px0;
-            Axs[A] = ox ? ax1 : ax0;
-            Bxs[A] = ox ? bx1 : bx0;
-            const R ay0 = (A <= L + 1) ? Ay[A] : R(0), ay1 = (A >= 1) ? Ay[A - 1] : R(0);
-            const R py0 = (A <= L) ? py[A] : R(0), py1 = (A >= 1 && A - 1 <= L) ? py[A - 1] : R(0);
-            const R s00 = (A <= L + 1) ? Sy.s0[A] : R(0), s01 = (A >= 1) ? Sy.s0[A - 1] : R(0);
-            const R d00 = (A <= L + 1) ? Sy.ds[A] : R(0), d01 = (A >= 1) ? Sy.ds[A - 1] : R(0);
-            Ays[A] = oy ? ay1 : ay0;
-            pys[A] = oy ? py1 : py0;
-            S0ys[A] = oy ? s01 : s00;
-            DSys[A] = oy ? d01 : d00;
-        }
-        {   // J1 on nodes A = 0..L+1 (x, prefix), B = 0..L+2 (y)
-            R v[pad32((L + 2) * (L + 3))];
+            for (int A = 0; A < L + 3; ++A) {
+                const R px0 = (A <= L) ? px[A] : R(0), px1 = (A >= 1 && A - 1 <= L) ? px[A - 1] : R(0);
+                const R ax0 = (A <= L + 1) ? Ax[A] : R(0), ax1 = (A >= 1) ? Ax[A - 1] : R(0);
+                const R bx0 = (A <= L + 1) ? Bx[A] : R(0), bx1 = (A >= 1) ? Bx[A - 1] : R(0);
+                pxs[A] = kx * (ox ? px1 : px0);
+                Axs[A] = ox ? ax1 : ax0;
+                Bxs[A] = ox ? bx1 : bx0;
+                const R ay0 = (A <= L + 1) ? Ay[A] : R(0), ay1 = (A >= 1) ? Ay[A - 1] : R(0);
+                const R py0 = (A <= L) ? py[A] : R(0), py1 = (A >= 1 && A - 1 <= L) ? py[A - 1] : R(0);
+                const R s00 = (A <= L + 1) ? Sy.s0[A] : R(0), s01 = (A >= 1) ? Sy.s0[A - 1] : R(0);
+                const R d00 = (A <= L + 1) ? Sy.ds[A] : R(0), d01 = (A >= 1) ? Sy.ds[A - 1] : R(0);
+                Ays[A] = oy ? ay1 : ay0;
+                pys[A] = ky * (oy ? py1 : py0);
+                S0ys[A] = kz * (oy ? s01 : s00);
+                DSys[A] = kz * (oy ? d01 : d00);
+            }
+            // one block of all three components: J1 (L+2)x(L+3), J2 (L+3)x(L+2), J3 (L+3)^2;
+            // the first butterfly level is fused with forming the block so that only half of
+            // it is ever held in registers
+            constexpr int V1 = (L + 2) * (L + 3), V2 = (L + 3) * (L + 2), V3 = (L + 3) * (L + 3);
+            constexpr int V = V1 + V2 + V3, NP = pad32(V), PER = NP / 32;
+            auto jv = [&](int idx) -> R {  // idx is a compile-time constant after unrolling
+                if (idx < V1) {
+                    const int A = idx / (L + 3), Bn = idx % (L + 3);
+                    return pxs[A] * Ays[Bn];
+                }
+                if (idx < V1 + V2) {
+                    const int A = (idx - V1) / (L + 2), Bn = (idx - V1) % (L + 2);
+                    return Axs[A] * pys[Bn];
+                }
+                if (idx < V) {
+                    const int A = (idx - V1 - V2) / (L + 3), Bn = (idx - V1 - V2) % (L + 3);
+                    return S0ys[Bn] * Axs[A] + DSys[Bn] * Bxs[A];
+                }
+                return R(0);
+            };
+            R v[NP / 2];
+            {
+                const bool upper = (lane & 16) != 0;
 #pragma unroll
-            for (int i = 0; i < pad32((L + 2) * (L + 3)); ++i) v[i] = R(0);
+                for (int i = 0; i < NP / 2; ++i) {
+                    const R lo = jv(i), hi = jv(i + NP / 2);
+                    const R send = upper ? lo : hi;
+                    const R keep = upper ? hi : lo;
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
+            }
+            rs_levels<NP / 2, 8, R>(v, lane);
 #pragma unroll
-            for (int A = 0; A < L + 2; ++A)
-#pragma unroll
-                for (int Bn = 0; Bn < L + 3; ++Bn) v[A * (L + 3) + Bn] = kx * pxs[A] * Ays[Bn];
-            warp_block_add<L + 2, L + 3, R>(v, lane, st.j1, RX, mnx, mny);
-        }
-        {   // J2 on nodes A = 0..L+2 (x), B = 0..L+1 (y, prefix)
-            R v[pad32((L + 3) * (L + 2))];
-#pragma unroll
-            for (int i = 0; i < pad32((L + 3) * (L + 2)); ++i) v[i] = R(0);
-#pragma unroll
-            for (int A = 0; A < L + 3; ++A)
-#pragma unroll
-                for (int Bn = 0; Bn < L + 2; ++Bn) v[A * (L + 2) + Bn] = ky * Axs[A] * pys[Bn];
-            warp_block_add<L + 3, L + 2, R>(v, lane, st.j2, RX, mnx, mny);
-        }
-        {   // J3 on nodes A, B = 0..L+2
-            R v[pad32((L + 3) * (L + 3))];
-#pragma unroll
-            for (int i = 0; i < pad32((L + 3) * (L + 3)); ++i) v[i] = R(0);
-#pragma unroll
-            for (int A = 0; A < L + 3; ++A)
-#pragma unroll
-                for (int Bn = 0; Bn < L + 3; ++Bn)
-                    v[A * (L + 3) + Bn] = kz * (S0ys[Bn] * Axs[A] + DSys[Bn] * Bxs[A]);
-            warp_block_add<L + 3, L + 3, R>(v, lane, st.j3, RX, mnx, mny);
+            for (int q = 0; q < PER; ++q) {
+                const int idx = lane * PER + q;
+                if (idx < V && v[q] != R(0)) {
+                    R *j;
+                    int A, Bn;
+                    if (idx < V1) {
+                        j = st.j1; A = idx / (L + 3); Bn = idx - A * (L + 3);
+                    } else if (idx < V1 + V2) {
+                        const int r = idx - V1;
+                        j = st.j2; A = r / (L + 2); Bn = r - A * (L + 2);
+                    } else {
+                        const int r = idx - V1 - V2;
+                        j = st.j3; A = r / (L + 3); Bn = r - A * (L + 3);
+                    }
+                    atomicAdd(j + (mny + Bn) * RX + mnx + A, v[q]);
+                }
+            }
+            if (!act) return;
+        } else if (act) {
+            deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
         }
     } else if (act) {
-#pragma unroll
-        for (int b = 0; b < L + 2; ++b) {
-            const int row = (jy0 + b) * RX + jx0;
-            const R ayk = kx * Ay[b];
-            const R pyk = (b <= L) ? ky * py[b] : R(0);
-            const R zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
-#pragma unroll
-            for (int a = 0; a < L + 2; ++a) {
-                if (a <= L) atomicAdd(st.j1 + row + a, ayk * px[a]);
-                if (b <= L) atomicAdd(st.j2 + row + a, pyk * Ax[a]);
-                atomicAdd(st.j3 + row + a, zs * Ax[a] + zd * Bx[a]);
-            }
-        }
+        deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
     }
     if (!act) return;
 

@@ -33,6 +33,7 @@ struct SortScratch {
     int32_t *cell_first;  // ntiles * TC
     int32_t *slot;        // n_max
     int32_t *key;         // n_max
+    int32_t *pos;         // n_max (slot-major order only)
     int64_t *tile_count;  // ntiles + 1 (scan workspace)
 };
 cudaError_t launch_sort(const RunDev &rd, int s, const SortScratch &sc, int64_t *tile_start,

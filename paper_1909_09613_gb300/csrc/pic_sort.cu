@@ -1,16 +1,21 @@
 // Tile sort of one species' particle store.
 //
-// Order: by tile, then by cell inside the tile (x fastest), then by slot (the particle's rank
-// among the particles of its cell).  A warp's 32 consecutive particles therefore sit in one
-// cell or a few neighbouring ones: their shared-memory gathers broadcast, and their Esirkepov
-// currents can be summed across the warp in registers before they reach shared memory.  The
-// cell at every position is fixed by the cell counts; which of a cell's particles takes which
-// slot is decided by atomics and is not reproducible.
+// Two orders, both grouping particles by tile (tiles and cells in a tile numbered x-fastest);
+// slot = the particle's rank among the particles of its cell:
+//  * cell-major (FP32 form): by (tile, cell, slot).  A warp's 32 consecutive particles sit in
+//    one cell or two neighbouring ones: shared-memory gathers broadcast, and the warp's
+//    Esirkepov currents are summed in registers before they reach shared memory.
+//  * slot-major (FP64 form): by (tile, slot, cell).  A tile runs through groups holding one
+//    particle of every cell with more than `slot` particles, so a warp's lanes sit in 32
+//    different cells and their per-lane shared-memory atomics do not collide.
+// The cell at every position is fixed by the cell counts; which of a cell's particles takes
+// which slot is decided by atomics and is not reproducible.
 //
 //   1. k_count   : tile-major cell key per particle, slot = atomicAdd(count[key], 1)
 //   2. k_tile_sum: particles per tile;  k_scan: exclusive scan over tiles -> tile_start
-//   3. k_layout  : one CTA per tile; first position of every cell of the tile
-//   4. k_scatter : copy every particle to cell_first[key] + slot in the other buffer
+//   3. k_layout  : one CTA per tile; first position of every cell (cell-major) and, for the
+//                  slot-major order, the position of every (cell, slot)
+//   4. k_scatter : copy every particle to its position in the other buffer
 #include "pic_launch.h"
 
 namespace pic {
@@ -142,15 +147,31 @@ __global__ void k_scan(const int64_t *cnt, int64_t *start, int64_t nt)
 
 // One CTA per tile with TC threads (one per cell of the tile).
 __global__ void k_layout(const __grid_constant__ RunDev rd, SortScratch sc,
-                         const int64_t *tile_start)
+                         const int64_t *tile_start, int slot_major)
 {
     const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
     const int64_t t = blockIdx.x;
     const int c = threadIdx.x;
     __shared__ int tot;
+    __shared__ int maxc;
     const int cnt = (c < TC) ? sc.cnt[t * TC + c] : 0;
+    if (threadIdx.x == 0) maxc = 0;
+    __syncthreads();
+    if (cnt > 0) atomicMax(&maxc, cnt);
     const int first = block_excl_scan(cnt, &tot);
-    if (c < TC) sc.cell_first[t * TC + c] = (int32_t)(tile_start[t] + first);
+    const int64_t base = tile_start[t];
+    if (c < TC) sc.cell_first[t * TC + c] = (int32_t)(base + first);
+    if (!slot_major) return;
+    __syncthreads();
+    const int ms = maxc;
+    int goff = 0;
+    for (int s = 0; s < ms; ++s) {
+        const int flag = (cnt > s) ? 1 : 0;
+        const int rank = block_excl_scan(flag, &tot);
+        if (flag) sc.pos[base + first + s] = (int32_t)(base + goff + rank);
+        goff += tot;
+        __syncthreads();
+    }
 }
 
 template <typename T>
@@ -161,12 +182,14 @@ __device__ __forceinline__ void mv(const void *src, void *dst, int64_t p, int64_
 
 __global__ void __launch_bounds__(kBlock) k_scatter(const __grid_constant__ RunDev rd, int s,
                                                     SortScratch sc, void *d0, void *d1, void *d2,
-                                                    void *m0, void *m1, void *m2, int32_t *dcell)
+                                                    void *m0, void *m1, void *m2, int32_t *dcell,
+                                                    int slot_major)
 {
     const SpeciesDev &sp = rd.sp[s];
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= sp.n) return;
-    const int64_t q = (int64_t)sc.cell_first[sc.key[p]] + sc.slot[p];
+    const int64_t r = (int64_t)sc.cell_first[sc.key[p]] + sc.slot[p];
+    const int64_t q = slot_major ? (int64_t)sc.pos[r] : r;
     void *dp[3] = {d0, d1, d2};
     void *dm[3] = {m0, m1, m2};
     if (rd.prec == 1) {
@@ -194,11 +217,12 @@ cudaError_t launch_sort(const RunDev &rd, int s, const SortScratch &sc, int64_t 
     const int tb = ((TC + 31) / 32) * 32;
     k_tile_sum<<<(unsigned)rd.ntiles, tb, 0, st>>>(rd, sc);
     k_scan<<<1, 1024, 0, st>>>(sc.tile_count, tile_start, rd.ntiles);
-    k_layout<<<(unsigned)rd.ntiles, tb, 0, st>>>(rd, sc, tile_start);
+    const int slot_major = rd.prec == 1 ? 0 : 1;
+    k_layout<<<(unsigned)rd.ntiles, tb, 0, st>>>(rd, sc, tile_start, slot_major);
     if (n > 0)
         k_scatter<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(
             rd, s, sc, dst_pos[0], dst_pos[1], dst_pos[2], dst_mom[0], dst_mom[1], dst_mom[2],
-            dst_cell);
+            dst_cell, slot_major);
     return cudaGetLastError();
 }
 
