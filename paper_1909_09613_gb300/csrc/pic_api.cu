@@ -297,6 +297,7 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
         nodes *= rd.reg[a];
     }
     rd.reg_nodes = nodes;
+    rd.slot_major = rd.prec == PIC_FP32_MIXED ? 0 : 1;
     rd.nsp = o.n_species;
     for (int s = 0; s < o.n_species; ++s) {
         if (o.capacity[s] < 0 || o.capacity[s] >= ((int64_t)1 << 31)) { delete c; return PIC_EINVAL; }

@@ -217,7 +217,7 @@ cudaError_t launch_sort(const RunDev &rd, int s, const SortScratch &sc, int64_t 
     const int tb = ((TC + 31) / 32) * 32;
     k_tile_sum<<<(unsigned)rd.ntiles, tb, 0, st>>>(rd, sc);
     k_scan<<<1, 1024, 0, st>>>(sc.tile_count, tile_start, rd.ntiles);
-    const int slot_major = rd.prec == 1 ? 0 : 1;
+    const int slot_major = rd.slot_major;
     k_layout<<<(unsigned)rd.ntiles, tb, 0, st>>>(rd, sc, tile_start, slot_major);
     if (n > 0)
         k_scatter<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, st>>>(
