@@ -167,6 +167,28 @@ int pic_kernel_launches(const pic_ctx *ctx, int64_t *count);
  * events on the legacy default stream.  Not part of the PIC path.                            */
 int pic_probe_fma_peak(int kind, double *tflops);
 
+/* Tile sort that allocates no device memory.  No counterpart in the paper: it exists for
+ * callers that cannot allocate device memory when they need the sort (their device memory is
+ * owned by another allocator, or they cannot afford the device-wide synchronisation of
+ * cudaMalloc/cudaFree).  Its scratch is a fixed file-scope device array of about 16.5 MB that
+ * every GPU loading the library holds until the process exits.
+ *   grid[3], tile[3]  grid extent and tile extent in cells (tile <= grid, cells per tile <= 1024)
+ *   n                 particles, n <= 1,048,576
+ *   cell_dev          device, n int32 linear cell indices (k*ny + j)*nx + i; cells outside the
+ *                     grid are left out of the order
+ *   perm_dev          device, n int64 out: perm[p] = input index placed at position p of the
+ *                     cell-major tile order (by tile, then cell in tile, then an arbitrary slot)
+ *   tile_start_dev    device, ntiles + 1 int64 out: first position of every tile
+ *   stream            cudaStream_t (0 = legacy default stream); asynchronous on it
+ * Requires ntiles <= 65,536 and ntiles * cells-per-tile <= 1,048,576; larger sizes return
+ * PIC_EINVAL.  The first call on a device looks up the scratch array's device address (with
+ * that device current); make that first call before any stream capture.  Every call on a
+ * device uses the same scratch array, so calls that overlap on the GPU (other streams, other
+ * host threads) race: serialise them.                                                       */
+int pic_tile_sort_noalloc(const int32_t grid[3], const int32_t tile[3], int64_t n,
+                          const int32_t *cell_dev, int64_t *perm_dev, int64_t *tile_start_dev,
+                          uint64_t stream);
+
 void pic_destroy(pic_ctx *ctx);
 const char *pic_strerror(int status);
 

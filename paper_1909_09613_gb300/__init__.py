@@ -78,6 +78,8 @@ _SIGS = [
     ("pic_last_gpp_ms", ctypes.c_int, [ctypes.c_void_p, _c_dp, _c_lp]),
     ("pic_kernel_launches", ctypes.c_int, [ctypes.c_void_p, _c_lp]),
     ("pic_probe_fma_peak", ctypes.c_int, [ctypes.c_int, _c_dp]),
+    ("pic_tile_sort_noalloc", ctypes.c_int, [_c_ip, _c_ip, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
     ("pic_destroy", None, [ctypes.c_void_p]),
     ("pic_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("pic_axis_weights", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -238,6 +240,26 @@ def pic_probe_fma_peak(kind: int) -> float:
     v = ctypes.c_double()
     _check(load_library().pic_probe_fma_peak(int(kind), ctypes.byref(v)), "pic_probe_fma_peak")
     return float(v.value)
+
+
+def pic_tile_sort_noalloc(grid, tile, cells, stream=None):
+    """Cell-major tile order of `cells` (a CUDA int32 tensor) without any device allocation
+    inside the library; returns (perm, tile_start) as CUDA int64 tensors (allocated here by
+    torch, i.e. by the caller of the C entry point)."""
+    import torch
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid])
+    t = (ctypes.c_int32 * 3)(*[int(v) for v in tile])
+    ntiles = 1
+    for a in range(3):
+        ntiles *= (int(grid[a]) + int(tile[a]) - 1) // int(tile[a])
+    cells = cells.contiguous()
+    perm = torch.empty(cells.numel(), dtype=torch.int64, device=cells.device)
+    ts = torch.empty(ntiles + 1, dtype=torch.int64, device=cells.device)
+    st = stream if stream is not None else torch.cuda.current_stream(cells.device).cuda_stream
+    _check(load_library().pic_tile_sort_noalloc(g, t, cells.numel(), cells.data_ptr(),
+                                                perm.data_ptr(), ts.data_ptr(), int(st)),
+           "pic_tile_sort_noalloc")
+    return perm, ts
 
 
 def pic_destroy(ctx):
