@@ -150,10 +150,26 @@ int pic_diag(pic_ctx *ctx, pic_diag_t *out);
 /* Wait for the context's stream; returns the latched error as a status. */
 int pic_sync(pic_ctx *ctx);
 
-/* Advance nsteps on n contexts, all FP32_MIXED and 2D, in one persistent gather-push-deposit
- * launch per step that covers every run's tiles, plus one Yee launch per half step for all
- * runs (batched form).  The contexts must share a stream.                                   */
-int pic_batch_step(pic_ctx **runs, int n, int nsteps);
+/* ---- batched form ----
+ * Many independent runs (2D, PIC_FP32_MIXED, same species count, same stream; each created,
+ * bound and loaded as usual) advanced together.  One batch step = device-side choice of the runs
+ * due for a tile sort, the batched sort of those runs, ONE persistent gather-push-deposit
+ * launch over the tiles of every run (heaviest tiles first, pulled from a device counter), and
+ * one launch per Yee half/full update covering all runs.  The step's launch sequence is captured
+ * in a CUDA graph on the first pic_batch_step and replayed.  While a batch exists, its runs must
+ * not be stepped on their own; pic_batch_sync writes the batch's device state back into them.
+ * The physics of every run is exactly that of pic_step (same tile code).                    */
+typedef struct pic_batch pic_batch;
+int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out);
+int pic_batch_footprint(const pic_batch *batch, size_t *bytes);       /* device tables   */
+int pic_batch_bind_memory(pic_batch *batch, void *dev_ptr, size_t bytes);
+int pic_batch_alloc(pic_batch *batch);                                  /* cudaMalloc'd    */
+int pic_batch_step(pic_batch *batch, int nsteps);                       /* asynchronous    */
+/* one extra (uncaptured) batch step with CUDA events around the persistent particle kernel */
+int pic_batch_time_gpp(pic_batch *batch, double *ms);
+int pic_batch_info(const pic_batch *batch, int64_t *work_items, int64_t *launches_per_step);
+int pic_batch_sync(pic_batch *batch);                                   /* syncs           */
+void pic_batch_destroy(pic_batch *batch);
 
 /* Time of the last pic_step's gather+push+deposit launches (ms, CUDA events on the context's
  * stream), summed over the steps of that call; syncs.  For measurement.                     */

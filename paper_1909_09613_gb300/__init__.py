@@ -74,7 +74,16 @@ _SIGS = [
     ("pic_sort", ctypes.c_int, [ctypes.c_void_p]),
     ("pic_diag", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_diag_t)]),
     ("pic_sync", ctypes.c_int, [ctypes.c_void_p]),
-    ("pic_batch_step", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int]),
+    ("pic_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    ("pic_batch_footprint", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("pic_batch_bind_memory", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    ("pic_batch_alloc", ctypes.c_int, [ctypes.c_void_p]),
+    ("pic_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("pic_batch_time_gpp", ctypes.c_int, [ctypes.c_void_p, _c_dp]),
+    ("pic_batch_info", ctypes.c_int, [ctypes.c_void_p, _c_lp, _c_lp]),
+    ("pic_batch_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("pic_batch_destroy", None, [ctypes.c_void_p]),
     ("pic_last_gpp_ms", ctypes.c_int, [ctypes.c_void_p, _c_dp, _c_lp]),
     ("pic_kernel_launches", ctypes.c_int, [ctypes.c_void_p, _c_lp]),
     ("pic_probe_fma_peak", ctypes.c_int, [ctypes.c_int, _c_dp]),
@@ -218,9 +227,52 @@ def pic_diag(ctx) -> dict:
     return out
 
 
-def pic_batch_step(ctxs: Sequence[int], nsteps: int):
-    arr = (ctypes.c_void_p * len(ctxs))(*ctxs)
-    _check(load_library().pic_batch_step(arr, len(ctxs), int(nsteps)), "pic_batch_step")
+class Batch:
+    """Batched form: advance many `Run`s (2D, FP32 form, same stream) together with one
+    persistent particle kernel per step, replayed from a CUDA graph (pic_batch_*)."""
+
+    def __init__(self, runs):
+        import torch
+        self.runs = list(runs)
+        arr = (ctypes.c_void_p * len(self.runs))(*[r.ctx for r in self.runs])
+        h = ctypes.c_void_p()
+        lib = load_library()
+        _check(lib.pic_batch_create(arr, len(self.runs), ctypes.byref(h)), "pic_batch_create")
+        self.h = h.value
+        nb = ctypes.c_size_t()
+        _check(lib.pic_batch_footprint(self.h, ctypes.byref(nb)), "pic_batch_footprint")
+        self.mem = torch.empty(int(nb.value), dtype=torch.uint8, device=self.runs[0].device)
+        _check(lib.pic_batch_bind_memory(self.h, ctypes.c_void_p(self.mem.data_ptr()), nb.value),
+               "pic_batch_bind_memory")
+
+    def step(self, n=1):
+        _check(load_library().pic_batch_step(self.h, int(n)), "pic_batch_step")
+
+    def time_gpp(self):
+        ms = ctypes.c_double()
+        _check(load_library().pic_batch_time_gpp(self.h, ctypes.byref(ms)), "pic_batch_time_gpp")
+        return float(ms.value)
+
+    def info(self):
+        a = ctypes.c_int64()
+        b = ctypes.c_int64()
+        _check(load_library().pic_batch_info(self.h, ctypes.byref(a), ctypes.byref(b)), "pic_batch_info")
+        return int(a.value), int(b.value)
+
+    def sync(self):
+        _check(load_library().pic_batch_sync(self.h), "pic_batch_sync")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().pic_batch_destroy(self.h)
+            self.h = None
+            self.mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pic_last_gpp_ms(ctx):

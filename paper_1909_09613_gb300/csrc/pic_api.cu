@@ -98,7 +98,13 @@ void refresh_species_ptrs(pic_ctx *c)
         }
         sp.cell = (int32_t *)c->bufA[s][6];
         sp.tile_start = c->tile_start[s];
+        for (int a = 0; a < 3; ++a) {
+            sp.pos_alt[a] = c->bufB[s][a];
+            sp.mom_alt[a] = c->bufB[s][3 + a];
+        }
+        sp.cell_alt = (int32_t *)c->bufB[s][6];
     }
+    c->rd.sc = c->sc;
 }
 
 int latched_status(pic_ctx *c)
@@ -118,7 +124,7 @@ int sort_species(pic_ctx *c, int s)
     RunDev rd = c->rd;
     refresh_species_ptrs(c);
     rd = c->rd;
-    cudaError_t e = launch_sort(rd, s, c->sc, c->tile_start[s], c->bufB[s], c->bufB[s] + 3,
+    cudaError_t e = launch_sort(rd, s, c->tile_start[s], c->bufB[s], c->bufB[s] + 3,
                                 (int32_t *)c->bufB[s][6], c->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
     c->kernel_launches += rd.sp[s].n > 0 ? 5 : 3;
@@ -616,17 +622,6 @@ int pic_diag(pic_ctx *c, pic_diag_t *out)
     return PIC_OK;
 }
 
-int pic_batch_step(pic_ctx **runs, int n, int nsteps)
-{
-    if (!runs || n < 0 || nsteps < 0) return PIC_EINVAL;
-    for (int it = 0; it < nsteps; ++it)
-        for (int r = 0; r < n; ++r) {
-            const int st = pic_step(runs[r], 1);
-            if (st != PIC_OK) return st;
-        }
-    return PIC_OK;
-}
-
 void pic_destroy(pic_ctx *c)
 {
     if (!c) return;
@@ -656,3 +651,36 @@ int pic_axis_weights(int spline_order, int scheme, double dtt, double delta, dou
 }
 
 }  // extern "C"
+
+namespace pic {
+
+RunDev *ctx_rundev(pic_ctx *c)
+{
+    refresh_species_ptrs(c);
+    return &c->rd;
+}
+
+void ctx_after_batch(pic_ctx *c, const RunDev &d, int age, int64_t steps)
+{
+    for (int s = 0; s < c->rd.nsp; ++s) {
+        for (int a = 0; a < 3; ++a) {
+            c->bufA[s][a] = d.sp[s].pos[a];
+            c->bufB[s][a] = d.sp[s].pos_alt[a];
+            c->bufA[s][3 + a] = d.sp[s].mom[a];
+            c->bufB[s][3 + a] = d.sp[s].mom_alt[a];
+        }
+        c->bufA[s][6] = d.sp[s].cell;
+        c->bufB[s][6] = d.sp[s].cell_alt;
+    }
+    refresh_species_ptrs(c);
+    c->age = age;
+    c->step += steps;
+}
+
+int ctx_kt(const pic_ctx *c) { return c->kt; }
+int ctx_sort_interval(const pic_ctx *c) { return c->sort_interval; }
+int ctx_age(const pic_ctx *c) { return c->age; }
+cudaStream_t ctx_stream(const pic_ctx *c) { return c->stream; }
+bool ctx_bound(const pic_ctx *c) { return c->base != nullptr; }
+
+}  // namespace pic

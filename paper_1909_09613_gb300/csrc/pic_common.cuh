@@ -31,6 +31,16 @@ struct TTable {
     float Rfrac_f, phib_f;
 };
 
+// Scratch of the tile sort (one set per run; the species are sorted one after the other).
+struct SortScratch {
+    int32_t *cnt;         // ntiles * TC
+    int32_t *cell_first;  // ntiles * TC
+    int32_t *slot;        // n_max
+    int32_t *key;         // n_max
+    int32_t *pos;         // n_max (slot-major order only)
+    int64_t *tile_count;  // ntiles + 1 (scan workspace)
+};
+
 struct SpeciesDev {
     double q, m, w;
     double qmdt_half;     // q dt / (2 m)
@@ -42,7 +52,11 @@ struct SpeciesDev {
     void *pos[3];
     void *mom[3];
     int32_t *cell;
-    const int64_t *tile_start;  // ntiles + 1
+    int64_t *tile_start;  // ntiles + 1
+    // the other buffer of the ping-pong pair (target of the next sort)
+    void *pos_alt[3];
+    void *mom_alt[3];
+    int32_t *cell_alt;
 };
 
 struct RunDev {
@@ -66,6 +80,7 @@ struct RunDev {
     TTable tt[3];
     int nsp;
     SpeciesDev sp[PIC_NSP_MAX];
+    SortScratch sc;
     int32_t *err;
 };
 

@@ -28,16 +28,7 @@ cudaError_t launch_unpack(const RunDev &rd, int s, double *x, double *u, int64_t
 cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t st);
 
 // tile sort of one species
-struct SortScratch {
-    int32_t *cnt;         // ntiles * TC
-    int32_t *cell_first;  // ntiles * TC
-    int32_t *slot;        // n_max
-    int32_t *key;         // n_max
-    int32_t *pos;         // n_max (slot-major order only)
-    int64_t *tile_count;  // ntiles + 1 (scan workspace)
-};
-cudaError_t launch_sort(const RunDev &rd, int s, const SortScratch &sc, int64_t *tile_start,
-                        void *const *dst_pos, void *const *dst_mom, int32_t *dst_cell,
-                        cudaStream_t st);
+cudaError_t launch_sort(const RunDev &rd, int s, int64_t *tile_start, void *const *dst_pos,
+                        void *const *dst_mom, int32_t *dst_cell, cudaStream_t st);
 
 }  // namespace pic

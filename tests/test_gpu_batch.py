@@ -1,0 +1,108 @@
+"""Batched form (pic_batch_*): many uneven 2D FP32 runs in one persistent particle kernel per
+step, replayed from a CUDA graph.  Every run must evolve as it does alone (pic_step) and, for
+one step, as the FP64 oracle does within the FP32 tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1909_09613_gb300 as pic  # noqa: E402
+
+FP32_TOL = 2e-6
+
+# (grid, cdt, l, ppc, gamma, seed): uneven sizes, both spline orders, narrow and wide T
+RUNS = [((64, 32), 0.35, 2, 4, 10.0, 1), ((96, 48), 0.6, 3, 8, 30.0, 2), ((40, 24), 0.12, 2, 16, 80.0, 3),
+        ((128, 64), 0.25, 3, 6, 15.0, 4), ((33, 21), 0.5, 3, 4, 50.0, 5)]
+
+
+def rel(a, b):
+    den = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / den) if den > 0 else float(np.max(np.abs(a)))
+
+
+def make(spec):
+    grid, cdt, l, ppc, gamma, seed = spec
+    wl = workloads.pair_plasma(grid, (1.0, 1.0), cdt, l, 1, gamma, 0.01, ppc, seed=seed)
+    caps = [int(s.x.shape[1]) for s in wl.species]
+    run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=pic.PIC_FP32_MIXED, capacity=caps)
+    for i, s in enumerate(wl.species):
+        run.load(i, s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
+    rng = np.random.default_rng(seed)
+    f = [0.02 * rng.standard_normal((1, grid[1], grid[0])) for _ in range(6)]
+    for c in range(6):
+        run.set_field(c, f[c])
+    return wl, run, f
+
+
+def test_batch_matches_runs_alone():
+    nsteps = 12  # crosses the sort interval of every run
+    alone, batched = [], []
+    for spec in RUNS:
+        _, r, _ = make(spec)
+        r.step(nsteps)
+        alone.append(r)
+    for spec in RUNS:
+        _, r, _ = make(spec)
+        batched.append(r)
+    b = pic.Batch(batched)
+    b.step(nsteps)
+    b.sync()
+    for ra, rb in zip(alone, batched):
+        for c in range(9):
+            assert rel(rb.field(c), ra.field(c)) < 1e-4, c
+        da, db = ra.diag(), rb.diag()
+        assert db["error_flags"] == 0
+        assert abs(db["kinetic_energy"] - da["kinetic_energy"]) < 1e-5 * da["kinetic_energy"]
+        for s in range(2):
+            xa, ua, ca = ra.particles(s)
+            xb, ub, cb = rb.particles(s)
+            assert np.array_equal(np.sort(ca), np.sort(cb)) or rel(np.sort(xb, axis=1), np.sort(xa, axis=1)) < 1e-5
+    b.close()
+    for r in alone + batched:
+        r.close()
+
+
+def test_batch_one_step_matches_oracle():
+    runs, orcs = [], []
+    for spec in RUNS[:3]:
+        wl, r, f = make(spec)
+        o = oracle.Sim(wl.grid[:2], wl.dx[:2], wl.dt, wl.l, wl.scheme)
+        for i, s in enumerate(wl.species):
+            x, u, _ = r.particles(i)
+            o.add_species(s.q, s.m, s.w, x, u)
+        for c in range(6):
+            o.set_field(c, f[c])
+        runs.append(r)
+        orcs.append(o)
+    b = pic.Batch(runs)
+    b.step(1)
+    b.sync()
+    for r, o in zip(runs, orcs):
+        o.step(1)
+        for c in range(9):
+            assert rel(r.field(c), o.field(c)) < FP32_TOL, c
+        for s in range(2):
+            _, ug, _ = r.particles(s)
+            _, uo = o.particles(s)
+            assert rel(ug, uo) < FP32_TOL
+    b.close()
+    for r in runs:
+        r.close()
+
+
+def test_batch_graph_replay_and_timing():
+    runs = [make(spec)[1] for spec in RUNS]
+    b = pic.Batch(runs)
+    items, launches = b.info()
+    assert items == sum(r.ntiles for r in runs)
+    b.step(3)
+    ms = b.time_gpp()
+    assert ms > 0.0
+    b.sync()
+    for r in runs:
+        assert r.diag()["error_flags"] == 0
+    b.close()
