@@ -241,6 +241,139 @@ def cpu_baseline(wl, budget_s=12.0):
         reps, 2 * S, S, "x".join(str(g) for g in wl.grid[:dim]))
 
 
+def batched_form(steps, warmup, n_runs=256):
+    """Config 4: 256 uneven 2D runs (FP32 form, WT, autotuned tiles) in one persistent particle
+    kernel per step, replayed from a CUDA graph; against the same runs stepped one after another
+    through pic_step (FP32 form, and the plain FP64 form)."""
+    import torch
+    import workloads
+    import paper_1909_09613_gb300 as pic
+    from paper_1909_09613_gb300 import engine
+    specs = workloads.batched_runs(n_runs)
+    reqs = [engine.Request(rid=i, grid=sp["grid"], dt=sp["dt"], l=sp["l"], gamma=sp["gamma"],
+                           u_th=sp["u_th"], ppc=sp["ppc"], steps=sp["steps"], seed=workloads.BASE_SEED)
+            for i, sp in enumerate(specs)]
+    tuner = engine.Autotuner()
+    t0 = time.perf_counter()
+    runs = [engine.make_run(r, tuner=tuner) for r in reqs]
+    setup_s = time.perf_counter() - t0
+    n_part = sum(r.particles for r in reqs)
+    b = pic.Batch(runs)
+    b.step(warmup)
+    gpp_ms = b.time_gpp()
+    torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    b.step(steps)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t1) * 1e3
+    b.sync()
+    items, launches = b.info()
+    b.close()
+    flags = sum(r.diag()["error_flags"] for r in runs)
+    # the same runs one after another, each through pic_step (FP32 form)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for r in runs:
+        r.step(1)
+    torch.cuda.synchronize()
+    seq32_ms = (time.perf_counter() - t1) * 1e3
+    for r in runs:
+        r.close()
+    del runs
+    torch.cuda.empty_cache()
+    # plain FP64 form, one after another (a step of each run)
+    seq64 = []
+    t64 = 0.0
+    for r in reqs:
+        run = engine.make_run(r, precision=pic.PIC_FP64)
+        run.step(1)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        run.step(1)
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - ta
+        run.close()
+    torch.cuda.empty_cache()
+    return {"value": n_part * steps / (ms * 1e-3), "unit": UNIT, "runs": n_runs,
+            "particles": n_part, "steps": steps, "ms_per_step": ms / steps,
+            "gpp_ms_per_step": gpp_ms, "work_items": items, "launches_per_step": launches,
+            "graph": "one CUDA graph per batch step, replayed",
+            "sequential_fp32_particle_steps_per_s": n_part / (seq32_ms * 1e-3),
+            "sequential_fp64_plain_particle_steps_per_s": n_part / t64,
+            "speedup_vs_sequential_fp32": (n_part * steps / (ms * 1e-3)) / (n_part / (seq32_ms * 1e-3)),
+            "speedup_vs_sequential_fp64_plain": (n_part * steps / (ms * 1e-3)) / (n_part / t64),
+            "autotuned": {"%d_%d" % k: {"tile": v[0], "sort_interval_factor": v[1]}
+                          for k, v in tuner.cache.items()},
+            "setup_s": setup_s, "error_flags": flags}
+
+
+def served_form(n_req=48, steps=100, budget=150e9, seed=None):
+    """Config 5: Poisson stream of NCI-scan requests (90% from the batched distribution, 10%
+    3D up to 256x64x64, 8 particles per cell), admitted under a 150 GB budget, served by
+    continuous batching.  Arrival rate 0.8 x the measured service capacity."""
+    import random
+    import torch
+    import workloads
+    import paper_1909_09613_gb300 as pic
+    from paper_1909_09613_gb300 import engine
+    rng = random.Random(workloads.BASE_SEED if seed is None else seed)
+    specs = workloads.batched_runs(n_req, seed=workloads.BASE_SEED + 5)
+    reqs = []
+    for i, sp in enumerate(specs):
+        if rng.random() < 0.1:
+            g = rng.choice([(128, 32, 32), (256, 64, 64)])
+            reqs.append(engine.Request(rid=i, grid=g, dt=0.4, l=2, gamma=sp["gamma"], u_th=0.01,
+                                       ppc=8, steps=steps, seed=workloads.BASE_SEED))
+        else:
+            reqs.append(engine.Request(rid=i, grid=sp["grid"], dt=sp["dt"], l=sp["l"],
+                                       gamma=sp["gamma"], u_th=0.01, ppc=sp["ppc"], steps=steps,
+                                       seed=workloads.BASE_SEED))
+    tuner = engine.Autotuner()
+    # service capacity: a batch of the 2D requests, steps timed
+    probe = [engine.make_run(r, tuner=tuner) for r in reqs if r.dim == 2][:16]
+    b = pic.Batch(probe)
+    b.step(2)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    b.step(10)
+    torch.cuda.synchronize()
+    cap = sum(p.counts[0] + p.counts[1] for p in probe) * 10 / (time.perf_counter() - t1)
+    b.close()
+    for p in probe:
+        p.close()
+    mean_work = sum(r.particles * r.steps for r in reqs) / len(reqs)
+    lam = 0.8 * cap / mean_work
+    t = 0.0
+    for r in reqs:
+        t += rng.expovariate(lam)
+        r.arrival = t
+    srv = engine.Server(budget_bytes=budget, chunk=10, tuner=tuner)
+    t0 = time.perf_counter()
+    res = srv.serve(reqs)
+    makespan = time.perf_counter() - t0
+    lat = [r.latency for r in res]
+    work = sum(r.particles * r.steps for r in res)
+    # plain single-run baseline latency: a sample of requests run alone, one after another
+    alone = []
+    for r in reqs[:6]:
+        run = engine.make_run(r)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        run.step(r.steps)
+        torch.cuda.synchronize()
+        alone.append(time.perf_counter() - ta)
+        run.close()
+    return {"value": work / makespan, "unit": UNIT, "requests": len(res),
+            "p50_latency_s": engine.percentile(lat, 50), "p99_latency_s": engine.percentile(lat, 99),
+            "arrival_rate_per_s": lam, "service_capacity_particle_steps_per_s": cap,
+            "makespan_s": makespan, "max_concurrent_runs": srv.max_active,
+            "peak_admitted_bytes": srv.peak_bytes, "budget_bytes": budget,
+            "steps_per_request": steps, "requests_3d": sum(1 for r in reqs if r.dim == 3),
+            "alone_latency_s_sample": alone,
+            "error_flags": sum(r.diag.get("error_flags", 0) for r in res)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -251,8 +384,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
-    ap.add_argument("--form", default="both", choices=["both", "fp64", "fp32"],
-                    help="fp32: time only the precision form (for profiling runs)")
+    ap.add_argument("--form", default="both", choices=["both", "fp64", "fp32", "batched", "served"],
+                    help="fp32/batched/served: time only that form (profiling runs)")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     rank, world, local = _rank_env()
 
@@ -297,6 +432,11 @@ def main():
 
     wl = workloads.config_large(scheme=1, device="cuda", seed=workloads.BASE_SEED + rank,
                                 scale=args.scale)
+    if args.form in ("batched", "served"):
+        out = batched_form(args.steps, args.warmup) if args.form == "batched" else served_form()
+        if rank == 0:
+            print(json.dumps({"form": args.form, **out}))
+        return
     if args.form == "fp32":
         r32 = time_form(wl, pic.PIC_FP32_MIXED, args.steps, args.warmup, dist_on, clocks=False)
         r32.pop("run").close()
@@ -376,6 +516,11 @@ def main():
             line["fp32_fma_peak_tflops"] = pic.pic_probe_fma_peak(1)
         except Exception:
             pass
+
+    if args.form == "both" and not args.no_batched:
+        line["batched_form"] = batched_form(max(args.steps, 10), args.warmup)
+    if args.form == "both" and not args.no_served:
+        line["served_form"] = served_form()
 
     if rank == 0 and not args.no_cpu:
         rate, sample = cpu_baseline(wl)

@@ -129,8 +129,12 @@ int pic_read_particles(pic_ctx *ctx, int species, double *x, double *u, int64_t 
 /* Copy the tile offsets of the species' current order (ntiles + 1 int64 values). Syncs. */
 int pic_read_tile_offsets(pic_ctx *ctx, int species, int64_t *offsets, int64_t count);
 
-/* Number of tiles and the tile extent actually used. */
-int pic_tile_info(const pic_ctx *ctx, int32_t tile[3], int64_t *ntiles, int32_t *sort_interval);
+/* Tile extent, number of tiles and sort interval actually used, and the tile order:
+ * *slot_major = 1 for (tile, slot, cell) -- one particle of every cell in turn, chosen for the
+ * FP64 form and for sparse runs -- or 0 for (tile, cell, slot), chosen for dense FP32 runs.
+ * Any out pointer may be NULL.                                                              */
+int pic_tile_info(const pic_ctx *ctx, int32_t tile[3], int64_t *ntiles, int32_t *sort_interval,
+                  int32_t *slot_major);
 
 /* Re-sort all species by tile now (also done automatically every sort_interval steps). */
 int pic_sort(pic_ctx *ctx);

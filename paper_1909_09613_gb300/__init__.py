@@ -70,7 +70,7 @@ _SIGS = [
     ("pic_read_particles", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dp, _c_dp, _c_lp,
                                           ctypes.c_int64]),
     ("pic_read_tile_offsets", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_lp, ctypes.c_int64]),
-    ("pic_tile_info", ctypes.c_int, [ctypes.c_void_p, _c_ip, _c_lp, _c_ip]),
+    ("pic_tile_info", ctypes.c_int, [ctypes.c_void_p, _c_ip, _c_lp, _c_ip, _c_ip]),
     ("pic_sort", ctypes.c_int, [ctypes.c_void_p]),
     ("pic_diag", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_diag_t)]),
     ("pic_sync", ctypes.c_int, [ctypes.c_void_p]),
@@ -203,11 +203,14 @@ def pic_read_tile_offsets(ctx, species, ntiles) -> np.ndarray:
 
 
 def pic_tile_info(ctx):
+    """(tile extent, number of tiles, sort interval, slot-major order flag)"""
     t = (ctypes.c_int32 * 3)()
     nt = ctypes.c_int64()
     si = ctypes.c_int32()
-    _check(load_library().pic_tile_info(ctx, t, ctypes.byref(nt), ctypes.byref(si)), "pic_tile_info")
-    return tuple(t), int(nt.value), int(si.value)
+    sm = ctypes.c_int32()
+    _check(load_library().pic_tile_info(ctx, t, ctypes.byref(nt), ctypes.byref(si),
+                                        ctypes.byref(sm)), "pic_tile_info")
+    return tuple(t), int(nt.value), int(si.value), int(sm.value)
 
 
 def pic_sort(ctx):
@@ -364,7 +367,7 @@ class Run:
         self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
         pic_bind_memory(self.ctx, self.mem.data_ptr(), self.nbytes)
         self.counts = [0] * len(capacity)
-        self.tile, self.ntiles, self.sort_interval = pic_tile_info(self.ctx)
+        self.tile, self.ntiles, self.sort_interval, self.slot_major = pic_tile_info(self.ctx)
 
     def load(self, species, q, m, w, x, u):
         import torch

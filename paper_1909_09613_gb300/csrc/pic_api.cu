@@ -303,7 +303,16 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
         nodes *= rd.reg[a];
     }
     rd.reg_nodes = nodes;
-    rd.slot_major = rd.prec == PIC_FP32_MIXED ? 0 : 1;
+    // Tile order.  The FP32 form sums a warp's currents in registers when the warp's particles
+    // sit in at most three neighbouring cells: cell-major order gives that when a cell holds
+    // about a warp of particles of a species or more.  Otherwise (and in the FP64 form, which
+    // deposits per lane) the slot-major order puts the lanes of a warp in different cells.
+    {
+        int64_t capmax = 0;
+        for (int s = 0; s < o.n_species; ++s) capmax = std::max(capmax, (int64_t)o.capacity[s]);
+        const bool dense = rd.ncell > 0 && capmax >= 24 * rd.ncell;
+        rd.slot_major = (rd.prec == PIC_FP32_MIXED && dense) ? 0 : 1;
+    }
     rd.nsp = o.n_species;
     for (int s = 0; s < o.n_species; ++s) {
         if (o.capacity[s] < 0 || o.capacity[s] >= ((int64_t)1 << 31)) { delete c; return PIC_EINVAL; }
@@ -585,8 +594,10 @@ int pic_read_tile_offsets(pic_ctx *c, int species, int64_t *offsets, int64_t cou
     return latched_status(c);
 }
 
-int pic_tile_info(const pic_ctx *c, int32_t tile[3], int64_t *ntiles, int32_t *sort_interval)
+int pic_tile_info(const pic_ctx *c, int32_t tile[3], int64_t *ntiles, int32_t *sort_interval,
+                  int32_t *slot_major)
 {
+    if (c && slot_major) *slot_major = c->rd.slot_major;
     if (!c) return PIC_EINVAL;
     if (tile)
         for (int a = 0; a < 3; ++a) tile[a] = c->rd.tile[a];

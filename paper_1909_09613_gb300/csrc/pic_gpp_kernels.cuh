@@ -287,53 +287,84 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
     const int jx0 = sx + Sx.wb, jy0 = sy + Sy.wb;
 
     if constexpr (sizeof(R) == 4) {
-        // Warp-collective path (cell-major order): when all lanes' windows start within one
-        // node of each other in both axes (lanes of one cell or of two neighbouring cells),
-        // place every lane's window in a common (L+3) x (L+3) block, sum the block over the
-        // warp with one reduce-scatter and add each node once.  Otherwise every lane adds its
-        // own window with shared atomics.
-        const int mnx = __reduce_min_sync(0xffffffffu, act ? jx0 : 0x7fffffff);
-        const int mxx = __reduce_max_sync(0xffffffffu, act ? jx0 : -0x7fffffff);
-        const int mny = __reduce_min_sync(0xffffffffu, act ? jy0 : 0x7fffffff);
-        const int mxy = __reduce_max_sync(0xffffffffu, act ? jy0 : -0x7fffffff);
-        if (mxx < mnx) return;  // no active lane in this warp
-        if (mxx - mnx <= 1 && mxy - mny <= 1) {
-            const bool ox = act && jx0 > mnx, oy = act && jy0 > mny;
+        // Warp-collective path (cell-major order): when the lanes' windows start at most SXM
+        // nodes apart in x and SYM in y (lanes of up to three neighbouring cells along a row),
+        // place every lane's window in a common (L+2+SXM) x (L+2+SYM) block, sum the block over
+        // the warp with one reduce-scatter and add each node once.  Otherwise every lane adds
+        // its own window with shared atomics (the slot-major order, lanes in different cells).
+        constexpr int SXM = 2, SYM = 1;
+        if (rd.slot_major) {  // lanes in different cells: per-lane atomics do not collide
+            if (act) deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+        } else {
+        // passes over groups of lanes that fit one common block (usually one pass; a warp that
+        // straddles the end of a tile row takes two or three)
+        bool todo = act;
+        while (__any_sync(0xffffffffu, todo)) {
+        const int mny = __reduce_min_sync(0xffffffffu, todo ? jy0 : 0x7fffffff);
+        const bool rowok = todo && jy0 <= mny + SYM;
+        const int mnx = __reduce_min_sync(0xffffffffu, rowok ? jx0 : 0x7fffffff);
+        const bool in = rowok && jx0 <= mnx + SXM;
+        todo = todo && !in;
+        {
+            const int ox = in ? jx0 - mnx : 0, oy = in ? jy0 - mny : 0;
+            const R gin = in ? R(1) : R(0);
+            constexpr int NX = L + 2 + SXM, NY = L + 2 + SYM;
             // lane vectors shifted into the common block, constants folded in
-            R pxs[L + 3], Axs[L + 3], Bxs[L + 3], Ays[L + 3], pys[L + 3], S0ys[L + 3], DSys[L + 3];
+            R pxs[NX], Axs[NX], Bxs[NX], Ays[NY], pys[NY], S0ys[NY], DSys[NY];
 #pragma unroll
-            for (int A = 0; A < L + 3; ++A) {
-                const R px0 = (A <= L) ? px[A] : R(0), px1 = (A >= 1 && A - 1 <= L) ? px[A - 1] : R(0);
-                const R ax0 = (A <= L + 1) ? Ax[A] : R(0), ax1 = (A >= 1) ? Ax[A - 1] : R(0);
-                const R bx0 = (A <= L + 1) ? Bx[A] : R(0), bx1 = (A >= 1) ? Bx[A - 1] : R(0);
-                pxs[A] = kx * (ox ? px1 : px0);
-                Axs[A] = ox ? ax1 : ax0;
-                Bxs[A] = ox ? bx1 : bx0;
-                const R ay0 = (A <= L + 1) ? Ay[A] : R(0), ay1 = (A >= 1) ? Ay[A - 1] : R(0);
-                const R py0 = (A <= L) ? py[A] : R(0), py1 = (A >= 1 && A - 1 <= L) ? py[A - 1] : R(0);
-                const R s00 = (A <= L + 1) ? Sy.s0[A] : R(0), s01 = (A >= 1) ? Sy.s0[A - 1] : R(0);
-                const R d00 = (A <= L + 1) ? Sy.ds[A] : R(0), d01 = (A >= 1) ? Sy.ds[A - 1] : R(0);
-                Ays[A] = oy ? ay1 : ay0;
-                pys[A] = ky * (oy ? py1 : py0);
-                S0ys[A] = kz * (oy ? s01 : s00);
-                DSys[A] = kz * (oy ? d01 : d00);
+            for (int A = 0; A < NX; ++A) {
+                R p3[SXM + 1], a3[SXM + 1], b3[SXM + 1];
+#pragma unroll
+                for (int o = 0; o <= SXM; ++o) {
+                    const int k = A - o;
+                    p3[o] = (k >= 0 && k <= L) ? px[k] : R(0);
+                    a3[o] = (k >= 0 && k <= L + 1) ? Ax[k] : R(0);
+                    b3[o] = (k >= 0 && k <= L + 1) ? Bx[k] : R(0);
+                }
+                R pv = p3[0], av = a3[0], bv = b3[0];
+#pragma unroll
+                for (int o = 1; o <= SXM; ++o) {
+                    pv = (ox == o) ? p3[o] : pv;
+                    av = (ox == o) ? a3[o] : av;
+                    bv = (ox == o) ? b3[o] : bv;
+                }
+                pxs[A] = gin * kx * pv;
+                Axs[A] = gin * av;
+                Bxs[A] = gin * bv;
             }
-            // one block of all three components: J1 (L+2)x(L+3), J2 (L+3)x(L+2), J3 (L+3)^2;
+#pragma unroll
+            for (int B = 0; B < NY; ++B) {
+                R ay = (B <= L + 1) ? Ay[B] : R(0), pyv = (B <= L) ? py[B] : R(0);
+                R s0 = (B <= L + 1) ? Sy.s0[B] : R(0), d0 = (B <= L + 1) ? Sy.ds[B] : R(0);
+#pragma unroll
+                for (int o = 1; o <= SYM; ++o) {
+                    const int k = B - o;
+                    ay = (oy == o) ? ((k >= 0 && k <= L + 1) ? Ay[k] : R(0)) : ay;
+                    pyv = (oy == o) ? ((k >= 0 && k <= L) ? py[k] : R(0)) : pyv;
+                    s0 = (oy == o) ? ((k >= 0 && k <= L + 1) ? Sy.s0[k] : R(0)) : s0;
+                    d0 = (oy == o) ? ((k >= 0 && k <= L + 1) ? Sy.ds[k] : R(0)) : d0;
+                }
+                Ays[B] = ay;
+                pys[B] = ky * pyv;
+                S0ys[B] = kz * s0;
+                DSys[B] = kz * d0;
+            }
+            // one block of all three components: J1 (NX-1) x NY, J2 NX x (NY-1), J3 NX x NY;
             // the first butterfly level is fused with forming the block so that only half of
             // it is ever held in registers
-            constexpr int V1 = (L + 2) * (L + 3), V2 = (L + 3) * (L + 2), V3 = (L + 3) * (L + 3);
+            constexpr int V1 = (NX - 1) * NY, V2 = NX * (NY - 1), V3 = NX * NY;
             constexpr int V = V1 + V2 + V3, NP = pad32(V), PER = NP / 32;
             auto jv = [&](int idx) -> R {  // idx is a compile-time constant after unrolling
                 if (idx < V1) {
-                    const int A = idx / (L + 3), Bn = idx % (L + 3);
+                    const int A = idx / NY, Bn = idx % NY;
                     return pxs[A] * Ays[Bn];
                 }
                 if (idx < V1 + V2) {
-                    const int A = (idx - V1) / (L + 2), Bn = (idx - V1) % (L + 2);
+                    const int A = (idx - V1) / (NY - 1), Bn = (idx - V1) % (NY - 1);
                     return Axs[A] * pys[Bn];
                 }
                 if (idx < V) {
-                    const int A = (idx - V1 - V2) / (L + 3), Bn = (idx - V1 - V2) % (L + 3);
+                    const int A = (idx - V1 - V2) / NY, Bn = (idx - V1 - V2) % NY;
                     return S0ys[Bn] * Axs[A] + DSys[Bn] * Bxs[A];
                 }
                 return R(0);
@@ -357,20 +388,19 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
                     R *j;
                     int A, Bn;
                     if (idx < V1) {
-                        j = st.j1; A = idx / (L + 3); Bn = idx - A * (L + 3);
+                        j = st.j1; A = idx / NY; Bn = idx - A * NY;
                     } else if (idx < V1 + V2) {
                         const int r = idx - V1;
-                        j = st.j2; A = r / (L + 2); Bn = r - A * (L + 2);
+                        j = st.j2; A = r / (NY - 1); Bn = r - A * (NY - 1);
                     } else {
                         const int r = idx - V1 - V2;
-                        j = st.j3; A = r / (L + 3); Bn = r - A * (L + 3);
+                        j = st.j3; A = r / NY; Bn = r - A * NY;
                     }
                     atomicAdd(j + (mny + Bn) * RX + mnx + A, v[q]);
                 }
             }
-            if (!act) return;
-        } else if (act) {
-            deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+        }
+        }
         }
     } else if (act) {
         deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);

@@ -78,7 +78,7 @@ def test_footprint_is_about_two_stores_plus_fields(lib, grid, prec):
         low = 2 * 2 * n * per + 9 * 8 * ncell
         staging = min(n, 1 << 22) * (dim + 4) * 8
         assert low <= b <= 1.3 * low + 64 * ncell + staging + (1 << 22)
-        tile, ntiles, si = pic.pic_tile_info(ctx)
+        tile, ntiles, si, sm = pic.pic_tile_info(ctx)
         assert si >= 1 and ntiles >= 1
     finally:
         pic.pic_destroy(ctx)

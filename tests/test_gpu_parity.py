@@ -196,7 +196,7 @@ def test_tile_sort_bit_exact(prec, grid, tile):
                 cells_in += c * stride
                 stride *= wl.grid[a]
         perm, ts = oracle.tile_sort(wl.grid, run.tile, cells_in,
-                                    oracle.CELL_MAJOR if prec == pic.PIC_FP32_MIXED else oracle.SLOT_MAJOR)
+                                    oracle.SLOT_MAJOR if run.slot_major else oracle.CELL_MAJOR)
         xg, ug, cg = run.particles(i)
         assert np.array_equal(cg, cells_in[perm])
         assert np.array_equal(run.tile_offsets(i), ts)

@@ -21,12 +21,13 @@ def test_noalloc_tile_sort_matches_context_sort_twice():
     _build.build()
     import paper_1909_09613_gb300 as pic
 
-    wl = workloads.pair_plasma((96, 40), (1.0, 1.0), 0.3, 3, 1, 4.0, 0.1, 6, omega_p=0.2, seed=77)
+    wl = workloads.pair_plasma((96, 40), (1.0, 1.0), 0.3, 3, 1, 4.0, 0.1, 64, omega_p=0.2, seed=77)
     caps = [int(s.x.shape[1]) for s in wl.species]
     run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=pic.PIC_FP32_MIXED,
                   capacity=caps, tile=(16, 8, 1))
     for i, s in enumerate(wl.species):
         run.load(i, s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
+    assert run.slot_major == 0  # a dense FP32 run is kept in the cell-major order
     _, _, cells_sorted = run.particles(0)
     ts_ctx = run.tile_offsets(0)
     rng = np.random.default_rng(5)
