@@ -54,14 +54,15 @@ def _default_interval(dt: float, dim: int) -> int:
 class Autotuner:
     """Chooses (tile, sort interval) per (spline order, particles per cell) by timing probe runs.
 
-    The probe is a 128x64 run (2D, FP32 form) of the same order and density at c dt = 0.4;
-    candidates are the tile extents below crossed with the default sort interval and half of it
-    (a smaller shared-memory halo, more frequent sorts).  The measured quantity is the time of a
-    whole step averaged over two sort intervals, divided by the particles."""
+    The probe is a 512x256 run (2D, FP32 form) of the same order and density at c dt = 0.4,
+    large enough that launch latency does not decide; candidates are the tile extents below
+    crossed with the default sort interval and half of it (a smaller shared-memory halo, more
+    frequent sorts).  The measured quantity is the time of whole steps (particle kernel, Yee
+    and the amortised sort) over two sort intervals, per particle."""
 
-    TILES = ((32, 8), (16, 8), (32, 16), (16, 16), (64, 4))
+    TILES = ((16, 8), (32, 8), (32, 16), (64, 8), (64, 16), (32, 32))
 
-    def __init__(self, probe_grid=(128, 64), probe_dt=0.4):
+    def __init__(self, probe_grid=(512, 256), probe_dt=0.4):
         self.probe_grid = probe_grid
         self.probe_dt = probe_dt
         self.cache: Dict[Tuple[int, int], Tuple[Tuple[int, int], float]] = {}
