@@ -1,0 +1,90 @@
+"""Numerical Cherenkov instability growth rates (the observable of the paper's Sec. 4 and Fig. 1):
+trajectories diverge chaotically, so long runs are compared by the growth rate of the field
+energy instead of element by element.
+
+Gamma = least-squares slope of ln U_EM(t) (t in 1/omega_p) over the second half of the run.
+Agreement: |Gamma_a - Gamma_b| <= 0.05 * max(|Gamma_b|, Gamma_MC), Gamma_MC being the growth
+rate of the same configuration under the momentum-conserving scheme (the floor keeps the
+criterion meaningful where the WT run barely grows).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1909_09613_gb300 as pic  # noqa: E402
+
+
+def growth_rate(ts, us):
+    ts = np.asarray(ts)
+    lu = np.log(np.asarray(us))
+    h = len(ts) // 2
+    return float(np.polyfit(ts[h:], lu[h:], 1)[0])
+
+
+def gpu_history(wl, prec, nsteps, every):
+    caps = [int(s.x.shape[1]) for s in wl.species]
+    run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps)
+    for i, s in enumerate(wl.species):
+        run.load(i, s.q, s.m, s.w, s.x, s.u)
+    ts, us = [], []
+    for k in range(0, nsteps, every):
+        run.step(every)
+        d = run.diag()
+        assert d["error_flags"] == 0
+        ts.append((k + every) * wl.dt * wl.omega_p)
+        us.append(d["field_energy"])
+    run.close()
+    return ts, us
+
+
+def oracle_history(wl, nsteps, every):
+    o = oracle.Sim(wl.grid[:2], wl.dx[:2], wl.dt, wl.l, wl.scheme)
+    for s in wl.species:
+        o.add_species(s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
+    ts, us = [], []
+    for k in range(0, nsteps, every):
+        o.step(every)
+        ts.append((k + every) * wl.dt * wl.omega_p)
+        us.append(o.diag()["field_energy"])
+    o.close()
+    return ts, us
+
+
+def test_nci_growth_gpu_fp64_vs_oracle_small_config():
+    """64x32, quadratic, cold pair plasma at gamma 20, c dt = 0.35, 200 steps, WT and MC."""
+    rates = {}
+    for scheme in (pic.PIC_SCHEME_MC, pic.PIC_SCHEME_WT):
+        wl = workloads.config_small(scheme=scheme)
+        tg, ug = gpu_history(wl, pic.PIC_FP64, wl.steps, 5)
+        to, uo = oracle_history(wl, wl.steps, 5)
+        rates[scheme] = (growth_rate(tg, ug), growth_rate(to, uo))
+        print("scheme", scheme, "Gamma gpu %.5f oracle %.5f" % rates[scheme])
+    g_mc = abs(rates[pic.PIC_SCHEME_MC][1])
+    for scheme, (gg, go) in rates.items():
+        assert abs(gg - go) <= 0.05 * max(abs(go), g_mc), (scheme, gg, go)
+    # the WT scheme suppresses the instability at a time step where MC does not (Sec. 2, 4)
+    assert rates[pic.PIC_SCHEME_WT][1] < rates[pic.PIC_SCHEME_MC][1]
+
+
+def test_nci_growth_fp32_vs_fp64():
+    """The precision form against the FP64 form on the drifting thermal plasma at gamma 50,
+    cubic, c dt = 0.25, 64 particles per cell (a 256x128 section of the large configuration),
+    500 steps."""
+    res = {}
+    for scheme in (pic.PIC_SCHEME_MC, pic.PIC_SCHEME_WT):
+        wl = workloads.config_large(scheme=scheme, device="cuda", scale=8)
+        t64, u64 = gpu_history(wl, pic.PIC_FP64, 500, 10)
+        t32, u32 = gpu_history(wl, pic.PIC_FP32_MIXED, 500, 10)
+        res[scheme] = (growth_rate(t32, u32), growth_rate(t64, u64))
+        print("scheme", scheme, "Gamma fp32 %.5f fp64 %.5f" % res[scheme])
+    g_mc = abs(res[pic.PIC_SCHEME_MC][1])
+    for scheme, (g32, g64) in res.items():
+        assert abs(g32 - g64) <= 0.05 * max(abs(g64), g_mc), (scheme, g32, g64)
+    assert res[pic.PIC_SCHEME_WT][1] < res[pic.PIC_SCHEME_MC][1]
