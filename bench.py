@@ -41,9 +41,11 @@ WORKLOAD = "pair_2048x1024_l3_WT_g50_uth0.01_ppc64_cdt0.25"
 #              grid: FP32 shadow of E, B (6 x 4 B) + FP64 J (3 x 8 B) = 48 B per cell.
 BYTES = {"fp64": (80.0, 72.0), "fp32": (48.0, 48.0)}
 # FP64 operations of the fused kernel per particle-step (l = 3, WT, 2D), from the ncu
-# instruction counts in profiles/gpp_fp64_pair2048x1024.txt (DADD + DMUL + 2 x DFMA, divided by
-# the particles of the launch).  Used for the FP64 arithmetic roofline of the plain form.
-FP64_FLOPS_PER_PARTICLE = None
+# instruction counts in profiles/gpp2d_fp64_l3_pair512x256.md (DADD + DMUL + 2 x DFMA divided by
+# the particles of the launch), and the FP64 instructions (DADD + DMUL + DFMA).  Used for the
+# FP64 arithmetic roofline of the plain form.
+FP64_FLOPS_PER_PARTICLE = 815.3
+FP64_INSTR_PER_PARTICLE = 561.3
 
 
 def _rank_env():
@@ -462,7 +464,12 @@ def main():
         ach = res["n"] * FP64_FLOPS_PER_PARTICLE / gpp_avg_s / 1e12
         roofline = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                     "frac": ach / fp64_peak, "traffic": _profile_traffic("gpp2d_fp64"),
-                    "peak_source": "measured FP64 FMA probe (pic_probe_fma_peak)"}
+                    "peak_source": "measured FP64 FMA rate (pic_probe_fma_peak, all SMs)",
+                    "flops_per_particle": FP64_FLOPS_PER_PARTICLE,
+                    "fp64_instr_frac": (res["n"] * FP64_INSTR_PER_PARTICLE / gpp_avg_s)
+                                       / (fp64_peak * 1e12 / 2.0),
+                    "hbm_view": {"achieved_gbs": alg_bytes / gpp_avg_s / 1e9,
+                                 "frac_of_measured_hbm": alg_bytes / gpp_avg_s / 1e9 / peaks["hbm_gbs"]}}
     else:
         ach = alg_bytes / gpp_avg_s / 1e9
         roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
