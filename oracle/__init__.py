@@ -91,6 +91,7 @@ def _load():
         lib.orc_yee_b.argtypes = [ctypes.c_void_p, ctypes.c_double]
         lib.orc_yee_e.argtypes = [ctypes.c_void_p]
         lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.orc_push_particle.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dp, _dp]
         lib.orc_particle_pass.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_long]
         lib.orc_diag.argtypes = [ctypes.c_void_p, _dp]
         lib.orc_gauss_residual.argtypes = [ctypes.c_void_p, _dp]
@@ -231,6 +232,14 @@ class Sim:
         out = np.zeros(6)
         self._lib.orc_gather_brute(self._h, _d(p), _d(out))
         return out
+
+    def push_particle(self, q, m, x, u):
+        """Gather + Boris + move of one particle against the current fields (no deposit)."""
+        xx = np.zeros(3)
+        xx[:self.dim] = x[:self.dim]
+        uu = np.array(u, dtype=np.float64)
+        self._lib.orc_push_particle(self._h, float(q), float(m), _d(xx), _d(uu))
+        return xx[:self.dim], uu
 
     def deposit(self, qw, xo, xn, v):
         a = np.zeros(3); a[:self.dim] = xo[:self.dim]

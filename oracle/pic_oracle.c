@@ -522,6 +522,25 @@ static void push_species(orc_sim *s, orc_species *p, long first, long count)
     }
 }
 
+/* Gather at x^n, Boris u^{n-1/2} -> u^{n+1/2}, move x^{n+1} = x^n + dt u/gamma (wrapped) for
+ * one particle of charge q and mass m, without depositing: the particle half of a step for a
+ * sampled particle.  x: dim physical coordinates (updated), u: 3 (updated).               */
+void orc_push_particle(const orc_sim *s, double q, double m, double *x, double *u)
+{
+    double xo[3] = {0, 0, 0}, eb[6];
+    for (int a = 0; a < s->dim; ++a) xo[a] = x[a];
+    orc_gather(s, xo, eb);
+    orc_boris(q * s->dt / m, eb, eb + 3, u);
+    const double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int a = 0; a < s->dim; ++a) {
+        const double L = s->n[a] * s->dx[a];
+        double xn = xo[a] + s->dt * (u[a] / g);
+        if (xn >= L) xn -= L;
+        else if (xn < 0.0) xn += L;
+        x[a] = xn;
+    }
+}
+
 /* Advance nsteps full PIC steps: particles, then B half, E full, B half. */
 void orc_step(orc_sim *s, int nsteps)
 {
