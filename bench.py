@@ -243,7 +243,7 @@ def cpu_baseline(wl, budget_s=12.0):
         reps, 2 * S, S, "x".join(str(g) for g in wl.grid[:dim]))
 
 
-def batched_form(steps, warmup, n_runs=256):
+def batched_form(steps, warmup, n_runs=256, max_nx=512, baselines=True):
     """Config 4: 256 uneven 2D runs (FP32 form, WT, autotuned tiles) in one persistent particle
     kernel per step, replayed from a CUDA graph; against the same runs stepped one after another
     through pic_step (FP32 form, and the plain FP64 form)."""
@@ -251,7 +251,7 @@ def batched_form(steps, warmup, n_runs=256):
     import workloads
     import paper_1909_09613_gb300 as pic
     from paper_1909_09613_gb300 import engine
-    specs = workloads.batched_runs(n_runs)
+    specs = workloads.batched_runs(n_runs, max_nx=max_nx)
     reqs = [engine.Request(rid=i, grid=sp["grid"], dt=sp["dt"], l=sp["l"], gamma=sp["gamma"],
                            u_th=sp["u_th"], ppc=sp["ppc"], steps=sp["steps"], seed=workloads.BASE_SEED)
             for i, sp in enumerate(specs)]
@@ -273,6 +273,12 @@ def batched_form(steps, warmup, n_runs=256):
     items, launches = b.info()
     b.close()
     flags = sum(r.diag()["error_flags"] for r in runs)
+    if not baselines:
+        for r in runs:
+            r.close()
+        return {"value": n_part * steps / (ms * 1e-3), "unit": UNIT, "runs": n_runs,
+                "particles": n_part, "ms_per_step": ms / steps, "gpp_ms_per_step": gpp_ms,
+                "error_flags": flags}
     # the same runs one after another, each through pic_step (FP32 form)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -389,6 +395,8 @@ def main():
     ap.add_argument("--form", default="both", choices=["both", "fp64", "fp32", "batched", "served"],
                     help="fp32/batched/served: time only that form (profiling runs)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--runs", type=int, default=256, help="batched form: number of runs")
+    ap.add_argument("--max-nx", type=int, default=512, help="batched form: largest grid x")
     ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     rank, world, local = _rank_env()
@@ -435,7 +443,9 @@ def main():
     wl = workloads.config_large(scheme=1, device="cuda", seed=workloads.BASE_SEED + rank,
                                 scale=args.scale)
     if args.form in ("batched", "served"):
-        out = batched_form(args.steps, args.warmup) if args.form == "batched" else served_form()
+        out = (batched_form(args.steps, args.warmup, args.runs, args.max_nx,
+                            baselines=args.runs == 256 and args.max_nx == 512)
+               if args.form == "batched" else served_form())
         if rank == 0:
             print(json.dumps({"form": args.form, **out}))
         return

@@ -155,7 +155,8 @@ int pic_diag(pic_ctx *ctx, pic_diag_t *out);
 int pic_sync(pic_ctx *ctx);
 
 /* ---- batched form ----
- * Many independent runs (2D, PIC_FP32_MIXED, same species count, same stream; each created,
+ * Many independent runs (2D, PIC_FP32_MIXED, spline order 2 or 3, same species count, same
+ * stream; each created,
  * bound and loaded as usual) advanced together.  One batch step = device-side choice of the runs
  * due for a tile sort, the batched sort of those runs, ONE persistent gather-push-deposit
  * launch over the tiles of every run (heaviest tiles first, pulled from a device counter), and

@@ -71,8 +71,6 @@ int particle_bytes(const pic_ctx *c)
     return c->rd.prec == PIC_FP32_MIXED ? 4 + 4 * d + 12 : 8 * d + 24;
 }
 
-int status_of(cudaError_t e) { return e == cudaSuccess ? PIC_OK : PIC_ECUDA; }
-
 // Node offsets (relative to a particle's cell) that the stencils of one axis can touch.
 void axis_reach(int l, const TTable &tt, int kt, int *lo, int *hi)
 {
@@ -294,7 +292,9 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     for (int a = 0; a < 3; ++a) {
         if (a >= dim) { rd.pre[a] = 0; rd.post[a] = 0; rd.reg[a] = 1; rd.drift[a] = 0; continue; }
         int lo, hi;
-        axis_reach(spline_order, rd.tt[a], c->kt, &lo, &hi);
+        // the halo covers the wide integer-node stencil (l + 2 nodes) so that the run can
+        // also be advanced by the batched kernel, which uses that stencil for every run
+        axis_reach(spline_order, rd.tt[a], std::max(c->kt, spline_order + 2), &lo, &hi);
         const int D = (int)std::ceil((c->sort_interval - 1) * rd.dtt[a] - 1e-12);
         rd.drift[a] = std::max(D, 0);
         rd.pre[a] = rd.drift[a] + lo;

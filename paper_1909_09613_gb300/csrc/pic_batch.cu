@@ -164,7 +164,7 @@ __device__ __forceinline__ bool try_tile(const RunDev &rd, int kt, char *smem, i
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_b_gpp(const RunDev *runs, const RunState *st,
+__global__ void __launch_bounds__(256, 2) k_b_gpp(const RunDev *runs, const RunState *st,
                                               const int2 *items, int nitems, int *counter)
 {
     extern __shared__ __align__(16) char smem_all[];
@@ -185,10 +185,9 @@ __global__ void __launch_bounds__(256) k_b_gpp(const RunDev *runs, const RunStat
             ((int *)rds)[i] = ((const int *)(runs + w.x))[i];
         __syncthreads();
         const RunDev &rd = *rds;
-        if (!(try_tile<2, 3>(rd, kt, smem, w.y) || try_tile<2, 4>(rd, kt, smem, w.y)
-              || try_tile<3, 4>(rd, kt, smem, w.y) || try_tile<3, 5>(rd, kt, smem, w.y)
-              || try_tile<1, 2>(rd, kt, smem, w.y) || try_tile<1, 3>(rd, kt, smem, w.y)
-              || try_tile<4, 5>(rd, kt, smem, w.y) || try_tile<4, 6>(rd, kt, smem, w.y)))
+        // every run in a batch uses the wide integer-node stencil (l + 2 nodes; the extra
+        // weight is zero when c dt <= dx/2), so two instances cover the batch
+        if (!(try_tile<2, 4>(rd, kt, smem, w.y) || try_tile<3, 5>(rd, kt, smem, w.y)))
             set_err(rd.err, 1);
     }
 }
@@ -322,7 +321,7 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
         pic_ctx *c = runs[r];
         if (!c || !ctx_bound(c)) { delete b; return PIC_ESTATE; }
         const RunDev &rd = *ctx_rundev(c);
-        if (rd.dim != 2 || rd.prec != PIC_FP32_MIXED || rd.nsp != b->nsp
+        if (rd.dim != 2 || rd.prec != PIC_FP32_MIXED || rd.nsp != b->nsp || rd.l < 2 || rd.l > 3
             || ctx_stream(c) != b->stream) {
             delete b;
             return PIC_EINVAL;
@@ -396,7 +395,7 @@ int pic_batch_bind_memory(pic_batch *b, void *dev, size_t bytes)
         sts[r].age = ctx_age(b->ctx[r]);
         sts[r].interval = ctx_sort_interval(b->ctx[r]);
         sts[r].due = 0;
-        sts[r].kt = ctx_kt(b->ctx[r]);
+        sts[r].kt = ctx_rundev(b->ctx[r])->l + 2;
     }
     cudaStream_t st = b->stream;
     auto up = [&](void *dst, const void *src, size_t nb) {

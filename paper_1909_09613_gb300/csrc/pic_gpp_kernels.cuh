@@ -153,10 +153,51 @@ __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int j
     }
 }
 
+// Scalars the particle loop uses, held in registers for the whole tile (a run descriptor in
+// shared or global memory would be re-read for every particle).
+struct Hot2D {
+    int n0, n1, tile0, tile1, drift0, drift1, pre0, pre1, RX, slot_major;
+    double dtt0, dtt1;
+    int32_t *err;
+};
+
+template <typename R>
+struct HotSp {
+    void *pos0, *pos1, *mom0, *mom1, *mom2;
+    int32_t *cell;
+    double qmdt_half, kx0, kx1, kz;
+};
+
+__device__ __forceinline__ Hot2D make_hot2d(const RunDev &rd)
+{
+    Hot2D h;
+    h.n0 = rd.n[0]; h.n1 = rd.n[1];
+    h.tile0 = rd.tile[0]; h.tile1 = rd.tile[1];
+    h.drift0 = rd.drift[0]; h.drift1 = rd.drift[1];
+    h.pre0 = rd.pre[0]; h.pre1 = rd.pre[1];
+    h.RX = rd.reg[0];
+    h.slot_major = rd.slot_major;
+    h.dtt0 = rd.dtt[0]; h.dtt1 = rd.dtt[1];
+    h.err = rd.err;
+    return h;
+}
+
+template <typename R>
+__device__ __forceinline__ HotSp<R> make_hotsp(const SpeciesDev &sp)
+{
+    HotSp<R> h;
+    h.pos0 = sp.pos[0]; h.pos1 = sp.pos[1];
+    h.mom0 = sp.mom[0]; h.mom1 = sp.mom[1]; h.mom2 = sp.mom[2];
+    h.cell = sp.cell;
+    h.qmdt_half = sp.qmdt_half;
+    h.kx0 = sp.kx[0]; h.kx1 = sp.kx[1]; h.kz = sp.kz;
+    return h;
+}
+
 // One particle per lane, 2D, staged tile.  Called by all 32 lanes of a warp together (the
 // deposit is warp-collective); lanes with act == false carry no particle.
 template <int L, int KT, typename R>
-__device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &sp,
+__device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
                                             const Stage2D<R> &st, int64_t p, bool act, int x0,
                                             int y0)
 {
@@ -164,11 +205,29 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
     PState<R> s;
     int lx = 0, ly = 0;
     if (act) {
-        load_particle<2, R>(rd, sp, p, s);
-        const bool okx = local_coord(s.c[0], x0, rd.tile[0], rd.drift[0], rd.n[0], lx);
-        const bool oky = local_coord(s.c[1], y0, rd.tile[1], rd.drift[1], rd.n[1], ly);
+        if constexpr (sizeof(R) == 4) {
+            const int c = __ldg(hs.cell + p);
+            s.c[1] = c / h.n0;
+            s.c[0] = c - s.c[1] * h.n0;
+            s.d[0] = __ldg((const float *)hs.pos0 + p);
+            s.d[1] = __ldg((const float *)hs.pos1 + p);
+        } else {
+            const double x0v = __ldg((const double *)hs.pos0 + p);
+            const double x1v = __ldg((const double *)hs.pos1 + p);
+            const double f0 = floor(x0v), f1 = floor(x1v);
+            s.c[0] = (int)f0;
+            s.c[1] = (int)f1;
+            s.d[0] = x0v - f0;
+            s.d[1] = x1v - f1;
+        }
+        s.c[2] = 0;
+        s.u[0] = __ldg((const R *)hs.mom0 + p);
+        s.u[1] = __ldg((const R *)hs.mom1 + p);
+        s.u[2] = __ldg((const R *)hs.mom2 + p);
+        const bool okx = local_coord(s.c[0], x0, h.tile0, h.drift0, h.n0, lx);
+        const bool oky = local_coord(s.c[1], y0, h.tile1, h.drift1, h.n1, ly);
         if (!(okx && oky)) {
-            set_err(rd.err, 1);
+            set_err(h.err, 1);
             act = false;
         }
     }
@@ -179,8 +238,8 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
         s.u[0] = s.u[1] = s.u[2] = R(0);
         lx = 0; ly = 0;
     }
-    const int RX = rd.reg[0];
-    const int sx = lx + rd.pre[0], sy = ly + rd.pre[1];
+    const int RX = h.RX;
+    const int sx = lx + h.pre0, sy = ly + h.pre1;
 
     AxisW<L, KT, R> wx, wy;
     axis_weights<L, KT, R>(st.tt[0], s.d[0], wx);
@@ -244,7 +303,7 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
     }
 
     // ---- Boris push ----
-    boris<R>(R(sp.qmdt_half), E, B, s.u);
+    boris<R>(R(hs.qmdt_half), E, B, s.u);
     const R g = sqrt(R(1) + s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
     const R ig = R(1) / g;
 
@@ -253,8 +312,8 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
     int cn[2], shv[2];
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
-        dl[a] = R(rd.dtt[a]) * s.u[a] * ig;
-        shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], rd.n[a], o[a], cn[a]);
+        dl[a] = R(a == 0 ? h.dtt0 : h.dtt1) * s.u[a] * ig;
+        shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], a == 0 ? h.n0 : h.n1, o[a], cn[a]);
     }
 
     // ---- Esirkepov deposit ----
@@ -267,8 +326,8 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
         axis_shapes<L, R>(s.d[1], shv[1], o[1], Sy);
     }
     const R wgt = act ? R(1) : R(0);
-    const R kx = wgt * R(sp.kx[0]), ky = wgt * R(sp.kx[1]);
-    const R kz = wgt * R(sp.kz) * s.u[2] * ig;
+    const R kx = wgt * R(hs.kx0), ky = wgt * R(hs.kx1);
+    const R kz = wgt * R(hs.kz) * s.u[2] * ig;
     const R third = R(1) / R(3);
     // W_x = DSx (S0y + DSy/2), prefix along x; W_y = DSy (S0x + DSx/2), prefix along y;
     // W_z = S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3 = S0y Ax + DSy Bx.
@@ -293,7 +352,7 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
         // the warp with one reduce-scatter and add each node once.  Otherwise every lane adds
         // its own window with shared atomics (the slot-major order, lanes in different cells).
         constexpr int SXM = 2, SYM = 1;
-        if (rd.slot_major) {  // lanes in different cells: per-lane atomics do not collide
+        if (h.slot_major) {  // lanes in different cells: per-lane atomics do not collide
             if (act) deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
         } else {
         // passes over groups of lanes that fit one common block (usually one pass; a warp that
@@ -408,15 +467,16 @@ __device__ __forceinline__ void particle_2d(const RunDev &rd, const SpeciesDev &
     if (!act) return;
 
     // ---- store ----
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ((R *)sp.mom[a])[p] = s.u[a];
+    ((R *)hs.mom0)[p] = s.u[0];
+    ((R *)hs.mom1)[p] = s.u[1];
+    ((R *)hs.mom2)[p] = s.u[2];
     if constexpr (sizeof(R) == 4) {
-        sp.cell[p] = cn[1] * rd.n[0] + cn[0];
-        ((float *)sp.pos[0])[p] = o[0];
-        ((float *)sp.pos[1])[p] = o[1];
+        hs.cell[p] = cn[1] * h.n0 + cn[0];
+        ((float *)hs.pos0)[p] = o[0];
+        ((float *)hs.pos1)[p] = o[1];
     } else {
-        ((double *)sp.pos[0])[p] = (double)cn[0] + o[0];
-        ((double *)sp.pos[1])[p] = (double)cn[1] + o[1];
+        ((double *)hs.pos0)[p] = (double)cn[0] + o[0];
+        ((double *)hs.pos1)[p] = (double)cn[1] + o[1];
     }
 }
 
@@ -429,15 +489,17 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile)
     const int ty = (int)(tile / rd.ntile[0]);
     const int x0 = tx * rd.tile[0], y0 = ty * rd.tile[1];
     stage2d_load<R>(rd, st, x0, y0);
+    const Hot2D h = make_hot2d(rd);
     __syncthreads();
     for (int s = 0; s < rd.nsp; ++s) {
         const SpeciesDev &sp = rd.sp[s];
+        const HotSp<R> hs = make_hotsp<R>(sp);
         const int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
         // warp-uniform trip count: a warp's lanes take 32 consecutive particles
         const int64_t wbase = a + (threadIdx.x & ~31);
         for (int64_t q = wbase; q < b; q += blockDim.x) {
             const int64_t p = q + (threadIdx.x & 31);
-            particle_2d<L, KT, R>(rd, sp, st, p, p < b, x0, y0);
+            particle_2d<L, KT, R>(h, hs, st, p, p < b, x0, y0);
         }
         __syncthreads();
         stage2d_flush<R>(rd, st, x0, y0);
