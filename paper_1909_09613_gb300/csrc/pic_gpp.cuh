@@ -194,17 +194,22 @@ __device__ __forceinline__ void axis_shapes_dd(float d_old, float delta, AxisS<L
 
 // ---- Boris push and move --------------------------------------------------------------------
 
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_r(float x) { return __frcp_rn(x); }
+
+// Relativistic Boris rotation u^{n-1/2} -> u^{n+1/2}; h = q dt / (2 m).  Returns 1/gamma^{n+1/2}.
 template <typename R>
-__device__ __forceinline__ void boris(R h, const R *E, const R *B, R *u)
+__device__ __forceinline__ R boris(R h, const R *E, const R *B, R *u)
 {
     R um[3], t[3], sv[3], up[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) um[a] = u[a] + h * E[a];
-    const R gm = sqrt(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-    const R hg = h / gm;
+    const R hg = h * rsqrt_r(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) t[a] = hg * B[a];
-    const R f = R(2) / (R(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    const R f = R(2) * rcp_r(R(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) sv[a] = f * t[a];
     up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
@@ -216,6 +221,7 @@ __device__ __forceinline__ void boris(R h, const R *E, const R *B, R *u)
     q[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) u[a] = q[a] + h * E[a];
+    return rsqrt_r(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 }
 
 // Move one axis in cell units: returns the cell shift sh in {-1,0,1} and the new offset o in

@@ -303,9 +303,7 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
     }
 
     // ---- Boris push ----
-    boris<R>(R(hs.qmdt_half), E, B, s.u);
-    const R g = sqrt(R(1) + s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
-    const R ig = R(1) / g;
+    const R ig = boris<R>(R(hs.qmdt_half), E, B, s.u);
 
     // ---- move ----
     R o[2], dl[2];
@@ -635,9 +633,7 @@ __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &
         B[2] = acc;
     }
 
-    boris<R>(R(sp.qmdt_half), E, B, s.u);
-    const R g = sqrt(R(1) + s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]);
-    const R ig = R(1) / g;
+    const R ig = boris<R>(R(sp.qmdt_half), E, B, s.u);
     R o[3], dl[3];
     int cn[3], shv[3];
 #pragma unroll
