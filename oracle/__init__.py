@@ -17,7 +17,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
                component (Eq. shapeEB); App. B self-force with transverse T
   boris        gyration angle and |u| conservation; E x B drift
   deposit      discrete continuity on every node; 1-D motion; static J_z closed form
-  yee          vacuum dispersion relation (App. C, A_i = 1); Gauss's law conservation
+  yee, M4      vacuum dispersion relation of App. C (A_i = 1 and the M4 A_i); fourth-order
+               phase error of M4; Gauss's law conservation
   tile_sort    brute-force order check on small inputs
   step         composition of the above, brute-force tiny runs (whole-step parity has no
                printed worked example in the paper)
@@ -39,6 +40,7 @@ _lock = threading.Lock()
 _lib = None
 
 MC, WT = 0, 1
+YEE, M4 = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _lp = ctypes.POINTER(ctypes.c_long)
@@ -89,6 +91,7 @@ def _load():
         lib.orc_deposit.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, _dp]
         lib.orc_rho.argtypes = [ctypes.c_void_p, _dp]
         lib.orc_yee_b.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        lib.orc_set_solver.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.orc_yee_e.argtypes = [ctypes.c_void_p]
         lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.orc_push_particle.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dp, _dp]
@@ -155,7 +158,7 @@ class Sim:
     Fields: comps 0..5 = E1 E2 E3 B1 B2 B3, 6..8 = J1 J2 J3, arrays shaped (nz, ny, nx).
     """
 
-    def __init__(self, grid, dx, dt, l, scheme):
+    def __init__(self, grid, dx, dt, l, scheme, solver=0):
         grid = list(grid) + [1] * (3 - len(grid))
         dx = list(dx) + [1.0] * (3 - len(dx))
         self.grid = tuple(int(g) for g in grid)
@@ -168,6 +171,8 @@ class Sim:
         self._h = self._lib.orc_create(*self.grid, *self.dx, self.dt, self.l, self.scheme)
         if not self._h:
             raise ValueError("oracle: bad arguments")
+        self.solver = int(solver)
+        self._lib.orc_set_solver(self._h, self.solver)
         self.nsp = 0
         self.counts = []
 

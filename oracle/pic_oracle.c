@@ -167,6 +167,9 @@ typedef struct {
     int nsp;
     orc_species sp[ORC_MAX_SPECIES];
     long step;
+    int m4;             /* 0: Yee Faraday stencil; 1: M4 (App. C) */
+    double beta[3][3];  /* beta_ij of Eq. Maxwell-A */
+    double delta[3];    /* delta_i of Eq. Maxwell-A */
 } orc_sim;
 
 static long wrapi(long i, long n)
@@ -452,23 +455,77 @@ void orc_rho(const orc_sim *s, double *rho)
 /* Yee FDTD (Sec. 1; "Yee solver", all beta = delta = 0 in Eq. Maxwell-A), periodic        */
 /* ------------------------------------------------------------------------------------- */
 
-/* B <- B - h * curl E  (h = dt/2 for each half push). */
+/* Select the Faraday stencil: Yee (all beta = delta = 0) or M4, the fourth-order-dispersion
+ * choice of App. C: beta_ij = (c dt/dx_j)^2 / 12, delta_i = ((c dt/dx_i)^2 - 1) / 12 (the last
+ * equation of App. C).  Ampere's stencil is never modified. */
+void orc_set_solver(orc_sim *s, int m4)
+{
+    s->m4 = m4;
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            const double r = s->dt / s->dx[j];
+            s->beta[i][j] = (m4 && i != j) ? r * r / 12.0 : 0.0;
+        }
+        const double r = s->dt / s->dx[i];
+        s->delta[i] = m4 ? (r * r - 1.0) / 12.0 : 0.0;
+    }
+}
+
+/* Forward difference of E component c along axis a at node (i, j, k):
+ * (E_c(node + e_a) - E_c(node)) / dx_a. */
+static double fdiff(const orc_sim *s, int c, int a, long i, long j, long k)
+{
+    long ii = i, jj = j, kk = k;
+    if (a == 0) ii++;
+    else if (a == 1) jj++;
+    else kk++;
+    return (s->F[c][cidx(s, ii, jj, kk)] - s->F[c][cidx(s, i, j, k)]) / s->dx[a];
+}
+
+/* Faraday's derivative of E component c along axis a at node (i, j, k).  Its Fourier symbol is
+ * A_a times that of the Yee difference (Eq. Maxwell-A):
+ *   A_a = 1 - 2 sum_{b != a} beta_ab [1 - cos(k_b dx_b)] - 2 delta_a [1 - cos(k_a dx_a)],
+ * and -2 [1 - cos(k dx)] is the symbol of the second difference f(+1) - 2 f + f(-1), so the
+ * derivative is the Yee difference plus beta_ab times its second difference along b and
+ * delta_a times its second difference along a. */
+static double fdiff_faraday(const orc_sim *s, int c, int a, long i, long j, long k)
+{
+    const double d0 = fdiff(s, c, a, i, j, k);
+    if (!s->m4) return d0;
+    double r = d0;
+    for (int b = 0; b < 3; ++b) {
+        const double coef = (b == a) ? s->delta[a] : s->beta[a][b];
+        if (coef == 0.0) continue;
+        const long di = (b == 0), dj = (b == 1), dk = (b == 2);
+        const double dp = fdiff(s, c, a, i + di, j + dj, k + dk);
+        const double dm = fdiff(s, c, a, i - di, j - dj, k - dk);
+        r += coef * (dp - 2.0 * d0 + dm);
+    }
+    return r;
+}
+
+/* B <- B - h * curl E  (h = dt/2 for each half push), curl with Faraday's stencil. */
 void orc_yee_b(orc_sim *s, double h)
 {
-    double *E1 = s->F[0], *E2 = s->F[1], *E3 = s->F[2];
     double *B1 = s->F[3], *B2 = s->F[4], *B3 = s->F[5];
-    const double dx = s->dx[0], dy = s->dx[1], dz = s->dx[2];
+    const long nc = s->ncell;
+    double *c1 = (double *)malloc((size_t)nc * sizeof(double));
+    double *c2 = (double *)malloc((size_t)nc * sizeof(double));
+    double *c3 = (double *)malloc((size_t)nc * sizeof(double));
     for (long k = 0; k < s->n[2]; ++k)
         for (long j = 0; j < s->n[1]; ++j)
             for (long i = 0; i < s->n[0]; ++i) {
                 const long c = cidx(s, i, j, k);
-                const double c1 = (E3[cidx(s, i, j + 1, k)] - E3[c]) / dy - (E2[cidx(s, i, j, k + 1)] - E2[c]) / dz;
-                const double c2 = (E1[cidx(s, i, j, k + 1)] - E1[c]) / dz - (E3[cidx(s, i + 1, j, k)] - E3[c]) / dx;
-                const double c3 = (E2[cidx(s, i + 1, j, k)] - E2[c]) / dx - (E1[cidx(s, i, j + 1, k)] - E1[c]) / dy;
-                B1[c] -= h * c1;
-                B2[c] -= h * c2;
-                B3[c] -= h * c3;
+                c1[c] = fdiff_faraday(s, 2, 1, i, j, k) - fdiff_faraday(s, 1, 2, i, j, k);
+                c2[c] = fdiff_faraday(s, 0, 2, i, j, k) - fdiff_faraday(s, 2, 0, i, j, k);
+                c3[c] = fdiff_faraday(s, 1, 0, i, j, k) - fdiff_faraday(s, 0, 1, i, j, k);
             }
+    for (long c = 0; c < nc; ++c) {
+        B1[c] -= h * c1[c];
+        B2[c] -= h * c2[c];
+        B3[c] -= h * c3[c];
+    }
+    free(c1); free(c2); free(c3);
 }
 
 /* E <- E + dt curl B - dt J. */

@@ -370,11 +370,82 @@ def test_yee_vacuum_dispersion(grid, dx, cdt, comp, m):
     assert np.max(np.abs(e - math.cos(nsteps * w * cdt) * e0)) < 1e-12
 
 
-def test_gauss_law_conserved_over_run():
-    """The charge-conserving deposit keeps D.E - rho unchanged (App. B, Eq. gauss)."""
+def _m4_A(k, dx, cdt):
+    """A_i of Eq. Maxwell-A with the M4 coefficients of App. C."""
+    dim = len(k)
+    out = []
+    for i in range(dim):
+        a = 1.0
+        for j in range(dim):
+            if j == i:
+                delta = ((cdt / dx[i]) ** 2 - 1.0) / 12.0
+                a -= 2 * delta * (1 - math.cos(k[i] * dx[i]))
+            else:
+                beta = (cdt / dx[j]) ** 2 / 12.0
+                a -= 2 * beta * (1 - math.cos(k[j] * dx[j]))
+        out.append(a)
+    return out
+
+
+@pytest.mark.parametrize("grid,dx,cdt,comp,m", [((32, 16), (1.0, 1.0), 0.5, 2, (3, 2, 0)),
+                                                 ((24, 20), (0.8, 1.1), 0.4, 2, (3, 2, 0)),
+                                                 ((12, 10, 8), (1.0, 0.9, 1.2), 0.45, 0, (0, 2, 1))])
+def test_m4_vacuum_dispersion(grid, dx, cdt, comp, m):
+    """M4 solver: a transverse standing mode follows sin^2(w dt/2)/(c dt)^2 = sum s_i^2 A_i
+    with A_i of Eq. Maxwell-A and the M4 beta, delta of App. C."""
+    s = oracle.Sim(grid, dx, cdt, 2, MC, solver=oracle.M4)
+    sh = s.shape
+    kk, jj, ii = np.meshgrid(np.arange(sh[0]), np.arange(sh[1]), np.arange(sh[2]), indexing="ij")
+    dim = len(grid)
+    k = [2 * math.pi * m[a] / (grid[a] * dx[a]) for a in range(dim)]
+    node = [ii + 0.0, jj + 0.0, kk + 0.0]
+    node[comp] = node[comp] + 0.5
+    ph = sum(k[a] * node[a] * dx[a] for a in range(dim))
+    e0 = np.sin(ph + 0.3)
+    s.set_field(comp, e0)
+    A = _m4_A(k, dx, cdt)
+    sw2 = sum(math.sin(k[a] * dx[a] / 2) ** 2 / dx[a] ** 2 * A[a] for a in range(dim))
+    w = 2.0 / cdt * math.asin(cdt * math.sqrt(sw2))
+    for _ in range(60):
+        s.yee_b(0.5 * cdt)
+        s.yee_e()
+        s.yee_b(0.5 * cdt)
+    assert np.max(np.abs(s.field(comp) - math.cos(60 * w * cdt) * e0)) < 1e-12
+
+
+def _measured_phase_error(solver, m, n=512, cdt=0.5, steps=40):
+    """w/(c k) - 1 measured from a simulated x-directed E3 standing wave."""
+    s = oracle.Sim((n, 2), (1.0, 1.0), cdt, 2, MC, solver=solver)
+    k = 2 * math.pi * m / n
+    ii = np.arange(n)[None, None, :] + 0 * np.arange(2)[None, :, None]
+    e0 = np.sin(k * ii + 0.2)
+    s.set_field(2, e0)
+    for _ in range(steps):
+        s.yee_b(0.5 * cdt)
+        s.yee_e()
+        s.yee_b(0.5 * cdt)
+    ratio = np.sum(s.field(2) * e0) / np.sum(e0 * e0)
+    w = math.acos(ratio) / (steps * cdt)
+    return w / k - 1.0
+
+
+def test_m4_phase_error_is_fourth_order():
+    """App. C: the M4 choice cancels the O((k dx)^2) phase-velocity error: halving k divides
+    the error by ~16 (Yee: ~4)."""
+    e_m4 = [_measured_phase_error(oracle.M4, m) for m in (8, 4)]
+    e_yee = [_measured_phase_error(oracle.YEE, m) for m in (8, 4)]
+    assert 12 < e_m4[0] / e_m4[1] < 20
+    assert 3.5 < e_yee[0] / e_yee[1] < 4.5
+    assert abs(e_m4[0]) < 0.05 * abs(e_yee[0])
+
+
+@pytest.mark.parametrize("solver", [oracle.YEE, oracle.M4])
+def test_gauss_law_conserved_over_run(solver):
+    """The charge-conserving deposit keeps D.E - rho unchanged (App. B, Eq. gauss); the M4
+    solver modifies only Faraday's stencil, so this still holds (Sec. 3)."""
     import workloads
     wl = workloads.pair_plasma((16, 8), (1.0, 1.0), 0.3, 3, WT, 5.0, 0.05, 4, omega_p=0.3)
-    s = oracle.Sim(wl.grid[:2], wl.dx[:2], wl.dt, wl.l, WT)
+    s = oracle.Sim(wl.grid[:2], wl.dx[:2], wl.dt, wl.l, WT, solver=solver)
     for sp in wl.species:
         s.add_species(sp.q, sp.m, sp.w, sp.x.numpy(), sp.u.numpy())
     r0 = s.gauss_residual()
