@@ -59,6 +59,7 @@ typedef enum {
 
 enum { PIC_SCHEME_MC = 0, PIC_SCHEME_WT = 1 };
 enum { PIC_FP64 = 0, PIC_FP32_MIXED = 1 };
+enum { PIC_SOLVER_YEE = 0, PIC_SOLVER_M4 = 1 };
 
 /* Error bits of pic_diag_t.error_flags. */
 enum { PIC_ERR_OUTSIDE_TILE = 1, PIC_ERR_NONFINITE = 2, PIC_ERR_TIMEOUT = 4 };
@@ -73,14 +74,20 @@ typedef struct {
     int32_t n_species;      /* species this context will hold (1..PIC_MAX_SPECIES)          */
     int64_t capacity[PIC_MAX_SPECIES]; /* max particles per species                         */
     uint64_t stream;        /* cudaStream_t to issue work on (0 = legacy default stream)    */
+    int32_t solver;         /* PIC_SOLVER_YEE: Yee curl in Faraday's law; PIC_SOLVER_M4: the
+                               modified Faraday stencil with fourth-order dispersion error of
+                               App. C (beta_ij = (c dt/dx_j)^2/12, delta_i = ((c dt/dx_i)^2-1)/12,
+                               Eq. Maxwell-A); Ampere's stencil is the Yee one in both        */
+    int32_t reserved;
 } pic_options;
 
 /* pic_create -- validate a run and build its host-side context (no device memory yet).
  *   grid[3]      cells per axis; grid[2] == 1 selects 2D (x3-independent fields, 2D3V).
  *   dx[3]        cell sizes (dx[2] ignored in 2D).
- *   dt           time step; requires c dt sqrt(sum 1/dx_i^2) < 1 (Yee Courant limit,
- *                App. C with A_i = 1) and c dt / dx_i < 1 so a particle crosses at most
- *                one cell face per axis per step.
+ *   dt           time step; requires sin^2(w dt/2) = (c dt)^2 sum_i A_i sin^2(k_i dx_i/2)/dx_i^2
+ *                < 1 at every grid wavenumber (the Courant limit of App. C: for Yee, A_i = 1,
+ *                c dt sqrt(sum 1/dx_i^2) < 1) and c dt / dx_i < 1 so a particle crosses at
+ *                most one cell face per axis per step.
  *   spline_order l in 1..4: B-spline order of W_l (Sec. 2).
  *   scheme       PIC_SCHEME_WT: gather with Eq. interpolation-EB-real-mod (W along the
  *                component's half-offset axes, T_l along its integer-node axes), valid for any

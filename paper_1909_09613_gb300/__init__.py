@@ -24,6 +24,7 @@ PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECFL, PIC_ECUDA = 0, -1, -2, -3, -4
 PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_ENAN, PIC_ESTATE = -5, -6, -7, -8
 PIC_SCHEME_MC, PIC_SCHEME_WT = 0, 1
 PIC_FP64, PIC_FP32_MIXED = 0, 1
+PIC_SOLVER_YEE, PIC_SOLVER_M4 = 0, 1
 PIC_MAX_SPECIES = 4
 
 _c_dp = ctypes.POINTER(ctypes.c_double)
@@ -34,7 +35,8 @@ _c_ip = ctypes.POINTER(ctypes.c_int32)
 class pic_options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32 * 3), ("sort_interval", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("n_species", ctypes.c_int32),
-                ("capacity", ctypes.c_int64 * PIC_MAX_SPECIES), ("stream", ctypes.c_uint64)]
+                ("capacity", ctypes.c_int64 * PIC_MAX_SPECIES), ("stream", ctypes.c_uint64),
+                ("solver", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pic_diag_t(ctypes.Structure):
@@ -340,7 +342,7 @@ class Run:
     """One PIC run: a libpic context plus the torch-allocated device buffer bound to it."""
 
     def __init__(self, grid, dx, dt, l, scheme, precision=PIC_FP64, capacity=(0, 0),
-                 tile=None, sort_interval=0, stream=None, device=None):
+                 tile=None, sort_interval=0, stream=None, device=None, solver=PIC_SOLVER_YEE):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libpic needs a CUDA device")
@@ -362,6 +364,7 @@ class Run:
         for s, c in enumerate(capacity):
             opt.capacity[s] = int(c)
         opt.stream = int(self.stream.cuda_stream)
+        opt.solver = int(solver)
         self.ctx = pic_create(self.grid, self.dx, dt, l, scheme, opt)
         self.nbytes = pic_footprint(self.ctx)
         self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)

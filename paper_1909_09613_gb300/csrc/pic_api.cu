@@ -241,11 +241,33 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
         s2 += 1.0 / (dx[a] * dx[a]);
         if (dt / dx[a] >= 1.0) return PIC_ECFL;
     }
-    if (dt * std::sqrt(s2) >= 1.0) return PIC_ECFL;
-
     pic_options o;
     std::memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
+    if (o.solver != PIC_SOLVER_YEE && o.solver != PIC_SOLVER_M4) return PIC_EINVAL;
+    // Courant limit of App. C: (c dt)^2 sum_i A_i sin^2(k_i dx_i/2)/dx_i^2 < 1 for every k; the
+    // maximum over k sits at a corner of the Brillouin zone (each k_i dx_i in {0, pi}).
+    {
+        double worst = 0.0;
+        for (int mask = 1; mask < (1 << dim); ++mask) {
+            double sum = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                if (!(mask >> a & 1)) continue;
+                double A = 1.0;
+                if (o.solver == PIC_SOLVER_M4) {
+                    for (int b = 0; b < dim; ++b) {
+                        const double r = dt / dx[b];
+                        const double coef = (b == a) ? (r * r - 1.0) / 12.0 : r * r / 12.0;
+                        if (mask >> b & 1) A -= 4.0 * coef;  // 1 - cos(pi) = 2
+                    }
+                }
+                sum += A / (dx[a] * dx[a]);
+            }
+            worst = std::max(worst, dt * dt * sum);
+        }
+        if (!(worst < 1.0)) return PIC_ECFL;
+    }
+    (void)s2;
     if (o.n_species <= 0) o.n_species = 2;
     if (o.n_species > PIC_MAX_SPECIES) return PIC_EINVAL;
     if (o.precision != PIC_FP64 && o.precision != PIC_FP32_MIXED) return PIC_EINVAL;
@@ -265,6 +287,15 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
         rd.dtt[a] = (a < dim) ? dt / rd.dx[a] : 0.0;
     }
     rd.dt = dt;
+    rd.m4 = o.solver == PIC_SOLVER_M4 ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) {
+            const double r = (b < dim) ? dt / rd.dx[b] : 0.0;
+            rd.beta[a][b] = (rd.m4 && a != b && a < dim && b < dim) ? r * r / 12.0 : 0.0;
+        }
+        const double r = (a < dim) ? dt / rd.dx[a] : 0.0;
+        rd.delta[a] = (rd.m4 && a < dim) ? (r * r - 1.0) / 12.0 : 0.0;
+    }
     // tiles
     const int deft[2][3] = {{32, 8, 1}, {8, 4, 4}};
     for (int a = 0; a < 3; ++a) {

@@ -73,6 +73,8 @@ struct RunDev {
     int pre[3], post[3], reg[3];
     int drift[3];      // max cells a particle can be away from its sorted tile (per axis)
     int slot_major;    // tile order: 1 = (tile, slot, cell), 0 = (tile, cell, slot)
+    int m4;            // Faraday stencil: 0 = Yee, 1 = M4 (beta, delta below)
+    double beta[3][3], delta[3];
     int64_t reg_nodes;
     // fields (FP64, index (k*ny + j)*nx + i) and FP32 shadows of E, B (precision form)
     double *F[9];

@@ -10,28 +10,57 @@ __device__ __forceinline__ int64_t gidx(const RunDev &rd, int i, int j, int k)
     return ((int64_t)k * rd.n[1] + j) * rd.n[0] + i;
 }
 
+// Forward difference of E component ec along axis a at node (i, j, k), periodic.
+__device__ __forceinline__ double fdiff_e(const RunDev &rd, int ec, int a, int i, int j, int k)
+{
+    int ip = i, jp = j, kp = k;
+    if (a == 0) ip = (i + 1 == rd.n[0]) ? 0 : i + 1;
+    else if (a == 1) jp = (j + 1 == rd.n[1]) ? 0 : j + 1;
+    else kp = (k + 1 == rd.n[2]) ? 0 : k + 1;
+    return (rd.F[ec][gidx(rd, ip, jp, kp)] - rd.F[ec][gidx(rd, i, j, k)]) / rd.dx[a];
+}
+
+// Faraday's derivative of E component ec along axis a at node (i, j, k).  Yee: the forward
+// difference.  M4 (App. C): its Fourier symbol is A_a times the Yee one (Eq. Maxwell-A), i.e. the
+// Yee difference plus beta_ab times its second difference along each other axis b and delta_a
+// times its second difference along a.
+__device__ __forceinline__ double faraday_d(const RunDev &rd, int ec, int a, int i, int j, int k)
+{
+    const double d0 = fdiff_e(rd, ec, a, i, j, k);
+    if (!rd.m4) return d0;
+    double r = d0;
+    for (int b = 0; b < 3; ++b) {
+        const double coef = (b == a) ? rd.delta[a] : rd.beta[a][b];
+        if (coef == 0.0 || rd.n[b] == 1) continue;
+        int ip = i, jp = j, kp = k, im = i, jm = j, km = k;
+        if (b == 0) { ip = (i + 1 == rd.n[0]) ? 0 : i + 1; im = (i == 0) ? rd.n[0] - 1 : i - 1; }
+        else if (b == 1) { jp = (j + 1 == rd.n[1]) ? 0 : j + 1; jm = (j == 0) ? rd.n[1] - 1 : j - 1; }
+        else { kp = (k + 1 == rd.n[2]) ? 0 : k + 1; km = (k == 0) ? rd.n[2] - 1 : k - 1; }
+        r += coef * (fdiff_e(rd, ec, a, ip, jp, kp) - 2.0 * d0 + fdiff_e(rd, ec, a, im, jm, km));
+    }
+    return r;
+}
+
 // B <- B - h curl E at cell c (FP32 shadow of B written when `shadow`).
 __device__ __forceinline__ void yee_b_cell(const RunDev &rd, int64_t c, double h, int shadow)
 {
-    const int nx = rd.n[0], ny = rd.n[1], nz = rd.n[2];
+    const int nx = rd.n[0], ny = rd.n[1];
     const int i = (int)(c % nx);
     const int j = (int)((c / nx) % ny);
     const int k = (int)(c / ((int64_t)nx * ny));
-    const int ip = (i + 1 == nx) ? 0 : i + 1;
-    const int jp = (j + 1 == ny) ? 0 : j + 1;
-    const int kp = (k + 1 == nz) ? 0 : k + 1;
-    const double *E1 = rd.F[0], *E2 = rd.F[1], *E3 = rd.F[2];
-    const double e1 = E1[c], e2 = E2[c], e3 = E3[c];
-    const double idx = 1.0 / rd.dx[0], idy = 1.0 / rd.dx[1], idz = 1.0 / rd.dx[2];
-    const double dE3dy = (E3[gidx(rd, i, jp, k)] - e3) * idy;
-    const double dE2dz = (E2[gidx(rd, i, j, kp)] - e2) * idz;
-    const double dE1dz = (E1[gidx(rd, i, j, kp)] - e1) * idz;
-    const double dE3dx = (E3[gidx(rd, ip, j, k)] - e3) * idx;
-    const double dE2dx = (E2[gidx(rd, ip, j, k)] - e2) * idx;
-    const double dE1dy = (E1[gidx(rd, i, jp, k)] - e1) * idy;
-    const double b1 = rd.F[3][c] - h * (dE3dy - dE2dz);
-    const double b2 = rd.F[4][c] - h * (dE1dz - dE3dx);
-    const double b3 = rd.F[5][c] - h * (dE2dx - dE1dy);
+    double c1, c2, c3;
+    if (rd.m4) {
+        c1 = faraday_d(rd, 2, 1, i, j, k) - faraday_d(rd, 1, 2, i, j, k);
+        c2 = faraday_d(rd, 0, 2, i, j, k) - faraday_d(rd, 2, 0, i, j, k);
+        c3 = faraday_d(rd, 1, 0, i, j, k) - faraday_d(rd, 0, 1, i, j, k);
+    } else {
+        c1 = fdiff_e(rd, 2, 1, i, j, k) - fdiff_e(rd, 1, 2, i, j, k);
+        c2 = fdiff_e(rd, 0, 2, i, j, k) - fdiff_e(rd, 2, 0, i, j, k);
+        c3 = fdiff_e(rd, 1, 0, i, j, k) - fdiff_e(rd, 0, 1, i, j, k);
+    }
+    const double b1 = rd.F[3][c] - h * c1;
+    const double b2 = rd.F[4][c] - h * c2;
+    const double b3 = rd.F[5][c] - h * c3;
     rd.F[3][c] = b1;
     rd.F[4][c] = b2;
     rd.F[5][c] = b3;

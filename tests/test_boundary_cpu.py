@@ -65,6 +65,21 @@ def test_create_validates_courant_and_order(lib):
     assert e.value.status == pic.PIC_ECFL
 
 
+def test_create_m4_courant_limit(lib):
+    """Courant limit with the M4 stencil (App. C): on these grids the worst wavenumber is a
+    corner of the Brillouin zone and the limit coincides with Yee's (1/sqrt(2) for dx = dy,
+    1/sqrt(1 + 1/4) for dy = 2 dx)."""
+    for grid, dx, ok, bad in (((64, 32, 1), (1.0, 1.0, 1.0), 0.70, 0.71),
+                              ((64, 32, 1), (1.0, 2.0, 1.0), 0.89, 0.90)):
+        o = _opt()
+        o.solver = pic.PIC_SOLVER_M4
+        ctx = pic.pic_create(grid, dx, ok, 2, pic.PIC_SCHEME_WT, o)
+        pic.pic_destroy(ctx)
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_create(grid, dx, bad, 2, pic.PIC_SCHEME_WT, o)
+        assert e.value.status == pic.PIC_ECFL
+
+
 @pytest.mark.parametrize("grid,prec", [((2048, 1024, 1), pic.PIC_FP64), ((2048, 1024, 1), pic.PIC_FP32_MIXED),
                                        ((64, 32, 1), pic.PIC_FP64), ((128, 32, 32), pic.PIC_FP32_MIXED)])
 def test_footprint_is_about_two_stores_plus_fields(lib, grid, prec):

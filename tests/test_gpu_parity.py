@@ -56,17 +56,17 @@ def smooth_fields(shape, amp, seed):
     return out
 
 
-def make_pair(wl, prec, fields=None, tile=None, sort_interval=0):
+def make_pair(wl, prec, fields=None, tile=None, sort_interval=0, solver=0):
     """Same initial state on the GPU (libpic) and in the oracle.  The GPU's load packs and sorts
     the particles; the oracle is then given the GPU's read-back (sorted, and in the FP32 form
     already rounded) so both start from identical particle arrays in identical order."""
     caps = [int(s.x.shape[1]) for s in wl.species]
     run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps,
-                  tile=tile, sort_interval=sort_interval)
+                  tile=tile, sort_interval=sort_interval, solver=solver)
     for i, s in enumerate(wl.species):
         run.load(i, s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
     dim = wl.dim
-    orc = oracle.Sim(wl.grid[:dim], wl.dx[:dim], wl.dt, wl.l, wl.scheme)
+    orc = oracle.Sim(wl.grid[:dim], wl.dx[:dim], wl.dt, wl.l, wl.scheme, solver=solver)
     for i, s in enumerate(wl.species):
         x, u, _ = run.particles(i)
         orc.add_species(s.q, s.m, s.w, x, u)
@@ -133,6 +133,29 @@ def test_one_step_3d(case, prec):
     run.step(1)
     orc.step(1)
     compare_state(run, orc, 2, FP64_TOL if prec == pic.PIC_FP64 else FP32_TOL, case)
+    run.close()
+
+
+@pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", [((40, 24), (1.0, 1.0), 0.3), ((37, 21), (0.9, 1.1), 0.25),
+                                  ((12, 10, 8), (1.0, 1.0, 1.0), 0.3)],
+                         ids=["2d", "2d_aniso", "3d"])
+def test_one_step_m4_solver(case, prec):
+    """The M4 Faraday stencil (App. C) on the GPU against the oracle, one step from the same
+    state, and a few more steps (fields only) in FP64."""
+    grid, dx, cdt = case
+    wl = workloads.pair_plasma(grid, dx, cdt, 3, 1, 4.0, 0.05, 4, omega_p=0.2, seed=13)
+    shape = (grid[2] if len(grid) == 3 else 1, grid[1], grid[0])
+    f = smooth_fields(shape, 0.05, seed=8)
+    run, orc = make_pair(wl, prec, f, solver=pic.PIC_SOLVER_M4)
+    run.step(1)
+    orc.step(1)
+    compare_state(run, orc, 2, FP64_TOL if prec == pic.PIC_FP64 else FP32_TOL, case)
+    if prec == pic.PIC_FP64:
+        run.step(4)
+        orc.step(4)
+        for c in range(6):
+            assert rel(run.field(c), orc.field(c)) < 1e-11, c
     run.close()
 
 
