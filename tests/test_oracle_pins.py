@@ -532,3 +532,45 @@ def test_loader_drift_moment():
     err = ux.std() / math.sqrt(len(ux))
     assert abs(ux.mean() - expect) < 5 * err
     assert abs(no_flip - expect) > 20 * err
+
+
+# ------------------------------------------------------------------------------------------
+# App. A: the lowest-order NCI growth rate of Eq. NCI-Xu2013 vanishes for WT at any dt
+# ------------------------------------------------------------------------------------------
+
+def _nci_factor(scheme, k1, nu1, k2, l, dx, cdt):
+    """S_B3 xi_0 - S_E2 [k]_B1 on the beam resonance omega' = c k1' (App. A), 2D (k3 = 0, the
+    x3 factors are 1), with the interpolation tensors of Eq. shapeEB (WT) / shapeEB-org (MC)
+    and tau_l of Eq. tau_l, for aliasing order nu1 along x1 (nu2 = 0)."""
+    def sinc(x):
+        return 1.0 if x == 0 else math.sin(x) / x
+    k1p = k1 + nu1 * 2 * math.pi / dx
+    s1 = sinc(k1p * dx / 2) ** (l + 1)
+    s2 = sinc(k2 * dx / 2) ** (l + 1)
+    tau1 = sinc(k1p * dx / 2) ** l * sinc(k1p * cdt)
+    eta1 = (-1) ** nu1
+    wdt2 = k1p * cdt / 2                       # omega' dt / 2 on the resonance
+    if scheme == WT:
+        s_b3 = math.cos(wdt2) * s1 * s2 * eta1  # s_{l,1} s_{l,2} tau_{l,3}(=1) eta1 eta2
+        s_e2 = tau1 * s2
+    else:
+        s_b3 = math.cos(wdt2) * s1 * s2 * eta1
+        s_e2 = s1 * s2
+    xi0 = math.sin(k1p * cdt / 2) / (cdt / 2)  # dt = cdt with c = 1
+    kb1 = math.sin(k1 * dx / 2) / (dx / 2)
+    return s_b3 * xi0 - s_e2 * kb1
+
+
+@pytest.mark.parametrize("l", [2, 3, 4])
+def test_wt_removes_lowest_order_nci_any_dt(l):
+    rng = np.random.default_rng(l)
+    for cdt in (0.1, 0.25, 0.35, 0.6):
+        for _ in range(20):
+            k1 = rng.uniform(-math.pi, math.pi)
+            k2 = rng.uniform(-math.pi, math.pi)
+            for nu1 in (-2, -1, 0, 1, 2):
+                assert abs(_nci_factor(WT, k1, nu1, k2, l, 1.0, cdt)) < 1e-12
+    # MC cancels it only at c dt = dx/2
+    k1, k2 = 1.1, 0.7
+    assert abs(_nci_factor(MC, k1, 1, k2, l, 1.0, 0.5)) < 1e-12
+    assert abs(_nci_factor(MC, k1, 1, k2, l, 1.0, 0.35)) > 1e-4
