@@ -328,7 +328,7 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
         }
         const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
         b->max_tc = std::max(b->max_tc, TC);
-        b->smem = std::max(b->smem, stage2d_bytes<float>(rd.reg_nodes));
+        b->smem = std::max(b->smem, stage2d_bytes<float>(rd.reg_nodes, rd.l));
         for (int s = 0; s < b->nsp; ++s) push_blocks(b->bm_part[s], r, rd.sp[s].n, kBlock);
         push_blocks(b->bm_cell, r, rd.ncell, kBlock);
         push_blocks(b->bm_key, r, rd.ntiles * TC, kBlock);

@@ -59,6 +59,30 @@ struct SpeciesDev {
     int32_t *cell_alt;
 };
 
+// Exact quotient n / d for 0 <= n < 2^31 and 1 <= d < 2^31 by one multiply and a shift:
+// with s = ceil(log2 d) and m = ceil(2^(32+s) / d), floor(n m / 2^(32+s)) = floor(n / d).
+// m d exceeds 2^(32+s) by e < d, so n m / 2^(32+s) exceeds n / d by n e / (d 2^(32+s)), which
+// is below 2^-(s+1) <= 1/d and so never reaches the next integer; n m < 2^31 2^33 fits 64 bits.
+struct FastDiv {
+    uint64_t m;
+    int s;
+};
+
+inline FastDiv make_fastdiv(int d)
+{
+    FastDiv f;
+    f.s = 0;
+    while (((int64_t)1 << f.s) < (int64_t)d) ++f.s;
+    const uint64_t num = (uint64_t)1 << (32 + f.s);
+    f.m = num / (uint64_t)d + (num % (uint64_t)d ? 1 : 0);
+    return f;
+}
+
+__device__ __forceinline__ int fast_div(int n, uint64_t m, int s)
+{
+    return (int)(__umul64hi((uint64_t)(uint32_t)n << 32, m) >> s);
+}
+
 struct RunDev {
     int dim, l, scheme, prec;
     int n[3];
@@ -76,6 +100,7 @@ struct RunDev {
     int m4;            // Faraday stencil: 0 = Yee, 1 = M4 (beta, delta below)
     double beta[3][3], delta[3];
     int64_t reg_nodes;
+    FastDiv div_n0, div_n01;  // division by n[0] and by n[0] n[1] (cell index decode)
     // fields (FP64, index (k*ny + j)*nx + i) and FP32 shadows of E, B (precision form)
     double *F[9];
     float *Fs[6];

@@ -33,14 +33,14 @@ __device__ __forceinline__ void load_particle(const RunDev &rd, const SpeciesDev
     if constexpr (sizeof(R) == 4) {
         const int c = __ldg(sp.cell + p);
         if constexpr (DIM == 2) {
-            s.c[1] = c / rd.n[0];
+            s.c[1] = fast_div(c, rd.div_n0.m, rd.div_n0.s);
             s.c[0] = c - s.c[1] * rd.n[0];
             s.c[2] = 0;
         } else {
             const int nxy = rd.n[0] * rd.n[1];
-            s.c[2] = c / nxy;
+            s.c[2] = fast_div(c, rd.div_n01.m, rd.div_n01.s);
             const int r = c - s.c[2] * nxy;
-            s.c[1] = r / rd.n[0];
+            s.c[1] = fast_div(r, rd.div_n0.m, rd.div_n0.s);
             s.c[0] = r - s.c[1] * rd.n[0];
         }
 #pragma unroll

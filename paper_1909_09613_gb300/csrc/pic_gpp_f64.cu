@@ -23,7 +23,7 @@ template <int L, int KT>
 cudaError_t go(const RunDev &rd, cudaStream_t st)
 {
     if (rd.dim == 2) {
-        const size_t smem = stage2d_bytes<double>(rd.reg_nodes);
+        const size_t smem = stage2d_bytes<double>(rd.reg_nodes, rd.l);
         cudaError_t e = cudaFuncSetAttribute(k_gpp2d<L, KT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -50,7 +50,7 @@ cudaError_t launch_gpp_f64(const RunDev &rd, int kt, cudaStream_t st)
 
 size_t gpp_smem_bytes_f64(const RunDev &rd)
 {
-    return rd.dim == 2 ? stage2d_bytes<double>(rd.reg_nodes) : 0;
+    return rd.dim == 2 ? stage2d_bytes<double>(rd.reg_nodes, rd.l) : 0;
 }
 
 }  // namespace pic

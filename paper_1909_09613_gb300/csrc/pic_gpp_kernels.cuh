@@ -13,19 +13,67 @@ template <typename R> struct AccT { typedef R T; };
 //   pa = (E1, B2) pairs  [both sit at (i+1/2, j): W along x, T along y]
 //   pb = (E2, B1) pairs  [both sit at (i, j+1/2): T along x, W along y]
 //   e3 = E3 [(i, j): T T],  b3 = B3 [(i+1/2, j+1/2): W W],  j1, j2, j3.
+//   rec = per-warp factor records of the FP32 deposit (see DepFrame), FP32 form only.
 template <typename R>
 struct Stage2D {
     typename Vec2<R>::T *pa, *pb;
     R *e3, *b3;
     R *j1, *j2, *j3;
     TTable *tt;
+    float *rec;
 };
 
+// Warps of a 2D tile block (the kernels launch 256 threads).
+constexpr int kTileWarps = 8;
+
+// Frame of the FP32 warp deposit.  The Esirkepov current of a group of lanes whose windows
+// start at most SXM nodes apart along x and SYM along y is a sum over lanes of outer products
+// (J1 = sum px (x) Ay, J2 = sum Ax (x) py, J3 = sum Ax (x) S0y + Bx (x) DSy, in the notation of
+// particle_2d) on a common NX x NY block of nodes.  Every lane writes its factor vectors,
+// shifted into the block, as a record of float4 pairs; lane t then sums a 2 x 2 node block of
+// J1 and J2 (the first PX*PY lanes) or of J3 (the next PX*PY) over the 32 records.
+//   x part of a record, per x pair p (nodes 2p, 2p+1):
+//     (px, px, Ax, Ax) then (Ax, Ax, Bx, Bx)
+//   y part, per y pair q (nodes 2q, 2q+1):
+//     (Ay, Ay, py, py) then (S0y, S0y, DSy, DSy)
+// RS (floats per record) is a multiple of 4 with RS / 4 odd, so that the float4 stores of 8
+// consecutive lanes fall in distinct banks.
+template <int L>
+struct DepFrame {
+    static constexpr int PX = (L + 2 + 2 + 1) / 2, PY = (L + 2 + 1 + 1) / 2;
+    static constexpr int NX = 2 * PX, NY = 2 * PY;
+    static constexpr int SXM = NX - (L + 2), SYM = NY - (L + 2);
+    static constexpr int RS0 = 8 * (PX + PY);
+    static constexpr int RS = ((RS0 / 4) % 2 == 0) ? RS0 + 4 : RS0;
+    static_assert(2 * PX * PY <= 32, "one lane per 2 x 2 node block and component group");
+};
+
+// Floats of one warp's deposit records for spline order l (host-side sizing).
+__host__ __device__ inline int dep_record_floats(int l)
+{
+    switch (l) {
+    case 1: return 32 * DepFrame<1>::RS;
+    case 2: return 32 * DepFrame<2>::RS;
+    case 3: return 32 * DepFrame<3>::RS;
+    default: return 32 * DepFrame<4>::RS;
+    }
+}
+
 template <typename R>
-__host__ __device__ inline size_t stage2d_bytes(int64_t nodes)
+__host__ __device__ inline size_t stage2d_fields_bytes(int64_t nodes)
 {
     size_t b = 2 * sizeof(TTable);
     b += (size_t)nodes * (2 * sizeof(typename Vec2<R>::T) + 5 * sizeof(R));
+    return (b + 15) / 16 * 16;
+}
+
+// Dynamic shared memory of a 2D tile block: staged fields and current, plus (FP32 form) the
+// deposit records of its warps.
+template <typename R>
+__host__ __device__ inline size_t stage2d_bytes(int64_t nodes, int l)
+{
+    size_t b = stage2d_fields_bytes<R>(nodes);
+    if (sizeof(R) == 4) b += (size_t)kTileWarps * dep_record_floats(l) * sizeof(float);
     return b;
 }
 
@@ -42,6 +90,7 @@ __device__ __forceinline__ Stage2D<R> stage2d_carve(char *smem, int64_t nodes)
     s.j1 = (R *)p; p += nodes * sizeof(R);
     s.j2 = (R *)p; p += nodes * sizeof(R);
     s.j3 = (R *)p;
+    s.rec = (float *)(smem + stage2d_fields_bytes<R>(nodes));
     return s;
 }
 
@@ -111,27 +160,6 @@ __device__ __forceinline__ bool local_coord(int c, int origin, int tile, int dri
     return l >= -drift && l < tile + drift;
 }
 
-// Butterfly reduce-scatter across the 32 lanes of a warp, levels OFF, OFF/2, .., 1: on entry
-// every lane holds N values; after the level with offset OFF the lanes whose OFF bit is set
-// keep the upper half of the array.  After the last level lane l holds in v[0 .. N/(2 OFF))
-// the warp sums of the values with indices l*N/(2 OFF) + q (for OFF = 16 entry: N/32 values).
-template <int N, int OFF, typename R>
-__device__ __forceinline__ void rs_levels(R *v, int lane)
-{
-    if constexpr (OFF >= 1) {
-        const bool upper = (lane & OFF) != 0;
-#pragma unroll
-        for (int i = 0; i < N / 2; ++i) {
-            const R send = upper ? v[i] : v[i + N / 2];
-            const R keep = upper ? v[i + N / 2] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
-        }
-        rs_levels<N / 2, OFF / 2, R>(v, lane);
-    }
-}
-
-constexpr int pad32(int v) { return (v + 31) / 32 * 32; }
-
 // One lane's Esirkepov window added to the shared current tile with atomics.
 template <int L, typename R>
 __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int jx0, int jy0, R kx,
@@ -156,8 +184,10 @@ __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int j
 // Scalars the particle loop uses, held in registers for the whole tile (a run descriptor in
 // shared or global memory would be re-read for every particle).
 struct Hot2D {
-    int n0, n1, tile0, tile1, drift0, drift1, pre0, pre1, RX, slot_major;
+    int n0, n1, tile0, tile1, drift0, drift1, pre0, pre1, RX, RY, slot_major;
     double dtt0, dtt1;
+    uint64_t dm;  // division by n0 (FastDiv)
+    int ds;
     int32_t *err;
 };
 
@@ -176,8 +206,10 @@ __device__ __forceinline__ Hot2D make_hot2d(const RunDev &rd)
     h.drift0 = rd.drift[0]; h.drift1 = rd.drift[1];
     h.pre0 = rd.pre[0]; h.pre1 = rd.pre[1];
     h.RX = rd.reg[0];
+    h.RY = rd.reg[1];
     h.slot_major = rd.slot_major;
     h.dtt0 = rd.dtt[0]; h.dtt1 = rd.dtt[1];
+    h.dm = rd.div_n0.m; h.ds = rd.div_n0.s;
     h.err = rd.err;
     return h;
 }
@@ -194,6 +226,20 @@ __device__ __forceinline__ HotSp<R> make_hotsp(const SpeciesDev &sp)
     return h;
 }
 
+// Ask the memory system for the particle stream of a later iteration (lines land in L1 while
+// the current particle is processed; the particle loop is otherwise stalled on these loads).
+template <typename R>
+__device__ __forceinline__ void prefetch_particle(const HotSp<R> &hs, int64_t p)
+{
+    const void *ptrs[6] = {hs.pos0, hs.pos1, hs.mom0, hs.mom1, hs.mom2, hs.cell};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (i == 5 && sizeof(R) == 8) break;  // the FP64 form has no cell array
+        const char *a = (const char *)ptrs[i] + p * (i == 5 ? 4 : (int64_t)sizeof(R));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+    }
+}
+
 // One particle per lane, 2D, staged tile.  Called by all 32 lanes of a warp together (the
 // deposit is warp-collective); lanes with act == false carry no particle.
 template <int L, int KT, typename R>
@@ -207,7 +253,7 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
     if (act) {
         if constexpr (sizeof(R) == 4) {
             const int c = __ldg(hs.cell + p);
-            s.c[1] = c / h.n0;
+            s.c[1] = fast_div(c, h.dm, h.ds);
             s.c[0] = c - s.c[1] * h.n0;
             s.d[0] = __ldg((const float *)hs.pos0 + p);
             s.d[1] = __ldg((const float *)hs.pos1 + p);
@@ -344,116 +390,122 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
     const int jx0 = sx + Sx.wb, jy0 = sy + Sy.wb;
 
     if constexpr (sizeof(R) == 4) {
-        // Warp-collective path (cell-major order): when the lanes' windows start at most SXM
-        // nodes apart in x and SYM in y (lanes of up to three neighbouring cells along a row),
-        // place every lane's window in a common (L+2+SXM) x (L+2+SYM) block, sum the block over
-        // the warp with one reduce-scatter and add each node once.  Otherwise every lane adds
-        // its own window with shared atomics (the slot-major order, lanes in different cells).
-        constexpr int SXM = 2, SYM = 1;
+        // Warp-collective path (cell-major order): lanes whose windows start at most SXM nodes
+        // apart in x and SYM in y (up to three or four neighbouring cells along a row) form a
+        // group; the group's current is a sum of per-lane outer products on a common block
+        // (DepFrame), which the warp sums through shared memory and adds node by node.
+        // Otherwise every lane adds its own window with shared atomics (the slot-major order,
+        // lanes in different cells).
+        using FR = DepFrame<L>;
         if (h.slot_major) {  // lanes in different cells: per-lane atomics do not collide
             if (act) deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
         } else {
+        float *rec = st.rec + (threadIdx.x >> 5) * (32 * FR::RS);
+        float4 *mine = (float4 *)(rec + lane * FR::RS);
+        // this lane's output block: role 0 sums J1 and J2, role 1 sums J3, role 2 idles
+        constexpr int NB = FR::PX * FR::PY;
+        const int role = lane < NB ? 0 : (lane < 2 * NB ? 1 : 2);
+        const int rl = lane - (role == 1 ? NB : 0);
+        const int bp = role == 2 ? 0 : rl % FR::PX, bq = role == 2 ? 0 : rl / FR::PX;
+        const int xo = 8 * bp + (role == 1 ? 4 : 0);
+        const int yo = 8 * FR::PX + 8 * bq + (role == 1 ? 4 : 0);
         // passes over groups of lanes that fit one common block (usually one pass; a warp that
-        // straddles the end of a tile row takes two or three)
+        // straddles the end of a tile row takes two)
         bool todo = act;
         while (__any_sync(0xffffffffu, todo)) {
         const int mny = __reduce_min_sync(0xffffffffu, todo ? jy0 : 0x7fffffff);
-        const bool rowok = todo && jy0 <= mny + SYM;
+        const bool rowok = todo && jy0 <= mny + FR::SYM;
         const int mnx = __reduce_min_sync(0xffffffffu, rowok ? jx0 : 0x7fffffff);
-        const bool in = rowok && jx0 <= mnx + SXM;
+        const bool in = rowok && jx0 <= mnx + FR::SXM;
         todo = todo && !in;
         {
             const int ox = in ? jx0 - mnx : 0, oy = in ? jy0 - mny : 0;
             const R gin = in ? R(1) : R(0);
-            constexpr int NX = L + 2 + SXM, NY = L + 2 + SYM;
-            // lane vectors shifted into the common block, constants folded in
-            R pxs[NX], Axs[NX], Bxs[NX], Ays[NY], pys[NY], S0ys[NY], DSys[NY];
+            const R gkx = gin * kx;
+            __syncwarp();  // the previous pass has read every record
+            // x part: block node A holds this lane's window node A - ox (zero outside it)
 #pragma unroll
-            for (int A = 0; A < NX; ++A) {
-                R p3[SXM + 1], a3[SXM + 1], b3[SXM + 1];
+            for (int pp = 0; pp < FR::PX; ++pp) {
+                R pv[2], av[2], bv[2];
 #pragma unroll
-                for (int o = 0; o <= SXM; ++o) {
-                    const int k = A - o;
-                    p3[o] = (k >= 0 && k <= L) ? px[k] : R(0);
-                    a3[o] = (k >= 0 && k <= L + 1) ? Ax[k] : R(0);
-                    b3[o] = (k >= 0 && k <= L + 1) ? Bx[k] : R(0);
-                }
-                R pv = p3[0], av = a3[0], bv = b3[0];
+                for (int i = 0; i < 2; ++i) {
+                    const int A = 2 * pp + i;
+                    R p1 = R(0), a1 = R(0), b1 = R(0);
 #pragma unroll
-                for (int o = 1; o <= SXM; ++o) {
-                    pv = (ox == o) ? p3[o] : pv;
-                    av = (ox == o) ? a3[o] : av;
-                    bv = (ox == o) ? b3[o] : bv;
-                }
-                pxs[A] = gin * kx * pv;
-                Axs[A] = gin * av;
-                Bxs[A] = gin * bv;
-            }
-#pragma unroll
-            for (int B = 0; B < NY; ++B) {
-                R ay = (B <= L + 1) ? Ay[B] : R(0), pyv = (B <= L) ? py[B] : R(0);
-                R s0 = (B <= L + 1) ? Sy.s0[B] : R(0), d0 = (B <= L + 1) ? Sy.ds[B] : R(0);
-#pragma unroll
-                for (int o = 1; o <= SYM; ++o) {
-                    const int k = B - o;
-                    ay = (oy == o) ? ((k >= 0 && k <= L + 1) ? Ay[k] : R(0)) : ay;
-                    pyv = (oy == o) ? ((k >= 0 && k <= L) ? py[k] : R(0)) : pyv;
-                    s0 = (oy == o) ? ((k >= 0 && k <= L + 1) ? Sy.s0[k] : R(0)) : s0;
-                    d0 = (oy == o) ? ((k >= 0 && k <= L + 1) ? Sy.ds[k] : R(0)) : d0;
-                }
-                Ays[B] = ay;
-                pys[B] = ky * pyv;
-                S0ys[B] = kz * s0;
-                DSys[B] = kz * d0;
-            }
-            // one block of all three components: J1 (NX-1) x NY, J2 NX x (NY-1), J3 NX x NY;
-            // the first butterfly level is fused with forming the block so that only half of
-            // it is ever held in registers
-            constexpr int V1 = (NX - 1) * NY, V2 = NX * (NY - 1), V3 = NX * NY;
-            constexpr int V = V1 + V2 + V3, NP = pad32(V), PER = NP / 32;
-            auto jv = [&](int idx) -> R {  // idx is a compile-time constant after unrolling
-                if (idx < V1) {
-                    const int A = idx / NY, Bn = idx % NY;
-                    return pxs[A] * Ays[Bn];
-                }
-                if (idx < V1 + V2) {
-                    const int A = (idx - V1) / (NY - 1), Bn = (idx - V1) % (NY - 1);
-                    return Axs[A] * pys[Bn];
-                }
-                if (idx < V) {
-                    const int A = (idx - V1 - V2) / NY, Bn = (idx - V1 - V2) % NY;
-                    return S0ys[Bn] * Axs[A] + DSys[Bn] * Bxs[A];
-                }
-                return R(0);
-            };
-            R v[NP / 2];
-            {
-                const bool upper = (lane & 16) != 0;
-#pragma unroll
-                for (int i = 0; i < NP / 2; ++i) {
-                    const R lo = jv(i), hi = jv(i + NP / 2);
-                    const R send = upper ? lo : hi;
-                    const R keep = upper ? hi : lo;
-                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                }
-            }
-            rs_levels<NP / 2, 8, R>(v, lane);
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int idx = lane * PER + q;
-                if (idx < V && v[q] != R(0)) {
-                    R *j;
-                    int A, Bn;
-                    if (idx < V1) {
-                        j = st.j1; A = idx / NY; Bn = idx - A * NY;
-                    } else if (idx < V1 + V2) {
-                        const int r = idx - V1;
-                        j = st.j2; A = r / (NY - 1); Bn = r - A * (NY - 1);
-                    } else {
-                        const int r = idx - V1 - V2;
-                        j = st.j3; A = r / NY; Bn = r - A * NY;
+                    for (int o = 0; o <= FR::SXM; ++o) {
+                        const int k = A - o;
+                        if (k < 0 || k > L + 1) continue;
+                        const bool sel = ox == o;
+                        if (k <= L) p1 = sel ? px[k] : p1;
+                        a1 = sel ? Ax[k] : a1;
+                        b1 = sel ? Bx[k] : b1;
                     }
-                    atomicAdd(j + (mny + Bn) * RX + mnx + A, v[q]);
+                    pv[i] = gkx * p1;
+                    av[i] = gin * a1;
+                    bv[i] = gin * b1;
+                }
+                mine[2 * pp] = make_float4(pv[0], pv[1], av[0], av[1]);
+                mine[2 * pp + 1] = make_float4(av[0], av[1], bv[0], bv[1]);
+            }
+            // y part: block node B holds window node B - oy
+#pragma unroll
+            for (int qq = 0; qq < FR::PY; ++qq) {
+                R ay[2], pyv[2], s0[2], d0[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int Bn = 2 * qq + i;
+                    R a1 = R(0), p1 = R(0), s1 = R(0), e1 = R(0);
+#pragma unroll
+                    for (int o = 0; o <= FR::SYM; ++o) {
+                        const int k = Bn - o;
+                        if (k < 0 || k > L + 1) continue;
+                        const bool sel = oy == o;
+                        a1 = sel ? Ay[k] : a1;
+                        if (k <= L) p1 = sel ? py[k] : p1;
+                        s1 = sel ? Sy.s0[k] : s1;
+                        e1 = sel ? Sy.ds[k] : e1;
+                    }
+                    ay[i] = a1;
+                    pyv[i] = ky * p1;
+                    s0[i] = kz * s1;
+                    d0[i] = kz * e1;
+                }
+                mine[2 * FR::PX + 2 * qq] = make_float4(ay[0], ay[1], pyv[0], pyv[1]);
+                mine[2 * FR::PX + 2 * qq + 1] = make_float4(s0[0], s0[1], d0[0], d0[1]);
+            }
+            __syncwarp();
+            // sum this lane's 2 x 2 node block over the 32 records
+            R o1[4] = {R(0), R(0), R(0), R(0)}, o2[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const float4 xv = *(const float4 *)(rec + q * FR::RS + xo);
+                const float4 yv = *(const float4 *)(rec + q * FR::RS + yo);
+                o1[0] += xv.x * yv.x;
+                o1[1] += xv.x * yv.y;
+                o1[2] += xv.y * yv.x;
+                o1[3] += xv.y * yv.y;
+                o2[0] += xv.z * yv.z;
+                o2[1] += xv.z * yv.w;
+                o2[2] += xv.w * yv.z;
+                o2[3] += xv.w * yv.w;
+            }
+            if (role != 2) {
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int gx = mnx + 2 * bp + i, gy = mny + 2 * bq + j;
+                        if (gx >= RX || gy >= h.RY) continue;
+                        const int node = gy * RX + gx;
+                        const R a = o1[2 * i + j], b = o2[2 * i + j];
+                        if (role == 0) {
+                            if (a != R(0)) atomicAdd(st.j1 + node, a);
+                            if (b != R(0)) atomicAdd(st.j2 + node, b);
+                        } else {
+                            const R c = a + b;
+                            if (c != R(0)) atomicAdd(st.j3 + node, c);
+                        }
+                    }
                 }
             }
         }
@@ -497,6 +549,7 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile)
         const int64_t wbase = a + (threadIdx.x & ~31);
         for (int64_t q = wbase; q < b; q += blockDim.x) {
             const int64_t p = q + (threadIdx.x & 31);
+            if (p + blockDim.x < b) prefetch_particle<R>(hs, p + blockDim.x);
             particle_2d<L, KT, R>(h, hs, st, p, p < b, x0, y0);
         }
         __syncthreads();
