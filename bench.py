@@ -316,6 +316,60 @@ def batched_form(steps, warmup, n_runs=256, max_nx=512, baselines=True):
             "setup_s": setup_s, "error_flags": flags}
 
 
+def table1_form(t_end=300.0, record_dt=1.0, history_path=None, precision="fp32", only=None,
+                colocated=True):
+    """The Table 1 NCI scan (MC4 / WT4 x Yee / M4 x five time steps, 256x128, 64 particles per
+    cell, gamma0 = 1000) served as 20 concurrent NCI-scan requests in the FP32 form, each
+    recording E/E0 (field energy over the initial kinetic energy) every record_dt / omega_pe."""
+    import numpy as np
+    import paper_1909_09613_gb300 as pic
+    from paper_1909_09613_gb300 import engine
+    prec = pic.PIC_FP64 if precision == "fp64" else pic.PIC_FP32_MIXED
+    sel = None
+    if only:
+        # "WT4:Yee:0,MC4:M4:4": scheme, solver, index into the Table 1 time steps
+        sel = set()
+        for item in only.split(","):
+            sc, so, ri = item.split(":")
+            sel.add((pic.PIC_SCHEME_WT if sc == "WT4" else pic.PIC_SCHEME_MC,
+                     pic.PIC_SOLVER_M4 if so == "M4" else pic.PIC_SOLVER_YEE, int(ri)))
+    reqs = engine.table1_requests(t_end, record_dt, precision=prec, only=sel, colocated=colocated)
+    srv = engine.Server(budget_bytes=150e9, chunk=64)
+    t0 = time.perf_counter()
+    res = srv.serve(reqs)
+    wall = time.perf_counter() - t0
+    byid = {r.rid: r for r in res}
+    runs = []
+    for q in reqs:
+        h = np.array(byid[q.rid].history)          # step, t, U_EM, K
+        e0 = h[0, 3]
+        ratio = h[:, 2] / e0
+        t = h[:, 1]
+        half = t >= t[-1] / 2
+        slope = float(np.polyfit(t[half], np.log(np.maximum(ratio[half], 1e-300)), 1)[0])
+        above = np.nonzero(ratio > 1e-3)[0]
+        runs.append({"scheme": "WT4" if q.scheme == pic.PIC_SCHEME_WT else "MC4",
+                     "solver": "M4" if q.solver == pic.PIC_SOLVER_M4 else "Yee",
+                     "dt_over_dt_cfl": round(q.dt * math.sqrt(2.0), 4), "c_dt_over_dx": q.dt,
+                     "steps": q.steps, "E_over_E0_max": float(ratio.max()),
+                     "E_over_E0_end": float(ratio[-1]),
+                     "E_over_E0_at": {str(int(x)): float(np.interp(x, t, ratio))
+                                      for x in (10, 30, 100, 300, 1000) if x <= t[-1]},
+                     "growth_rate_second_half": slope,
+                     "t_first_above_1e-3": float(t[above[0]]) if len(above) else None,
+                     "error_flags": byid[q.rid].diag.get("error_flags")})
+        if history_path:
+            q_tag = "%s_%s_%.4f" % (runs[-1]["scheme"], runs[-1]["solver"], runs[-1]["dt_over_dt_cfl"])
+            np.savetxt("%s_%s.txt" % (history_path, q_tag), np.column_stack([t, ratio]),
+                       header="t_omega_pe E_over_E0", fmt="%.6g")
+    work = sum(q.particles * q.steps for q in reqs)
+    return {"form": "table1", "t_end_omega_pe": t_end, "runs": runs, "wall_s": wall,
+            "particle_steps_per_s": work / wall, "max_concurrent_runs": srv.max_active,
+            "dtype": "f64" if precision == "fp64" else "f32 (FP64 fields)",
+            "workload": "pair_256x128_l4_g1000_kT0.01_ppc64 (Table 1)",
+            "start": "neutral (e+ at the e- positions)" if colocated else "independent positions"}
+
+
 def served_form(n_req=48, steps=100, budget=150e9, seed=None):
     """Config 5: Poisson stream of NCI-scan requests (90% from the batched distribution, 10%
     3D up to 256x64x64, 8 particles per cell), admitted under a 150 GB budget, served by
@@ -392,7 +446,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
-    ap.add_argument("--form", default="both", choices=["both", "fp64", "fp32", "batched", "served"],
+    ap.add_argument("--t-end", type=float, default=300.0, help="table1 form: run length, 1/omega_pe")
+    ap.add_argument("--history", default=None, help="table1 form: prefix of E/E0 history files")
+    ap.add_argument("--t1-precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--t1-only", default=None, help="table1 form: e.g. WT4:Yee:0,MC4:M4:4")
+    ap.add_argument("--t1-independent", action="store_true",
+                    help="table1 form: species at independent positions (non-neutral start)")
+    ap.add_argument("--form", default="both", choices=["both", "fp64", "fp32", "batched", "served",
+                                                       "table1"],
                     help="fp32/batched/served: time only that form (profiling runs)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--runs", type=int, default=256, help="batched form: number of runs")
@@ -440,6 +501,12 @@ def main():
     _build.build()
     pic.load_library()
 
+    if args.form == "table1":
+        out = table1_form(args.t_end, history_path=args.history, precision=args.t1_precision,
+                          only=args.t1_only, colocated=not args.t1_independent)
+        if rank == 0:
+            print(json.dumps(out))
+        return
     wl = workloads.config_large(scheme=1, device="cuda", seed=workloads.BASE_SEED + rank,
                                 scale=args.scale)
     if args.form in ("batched", "served"):

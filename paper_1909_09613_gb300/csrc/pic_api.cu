@@ -296,6 +296,7 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
         const double r = (a < dim) ? dt / rd.dx[a] : 0.0;
         rd.delta[a] = (rd.m4 && a < dim) ? (r * r - 1.0) / 12.0 : 0.0;
     }
+    for (int a = 0; a < 3; ++a) rd.idx[a] = 1.0 / rd.dx[a];
     rd.div_n0 = make_fastdiv(rd.n[0]);
     rd.div_n01 = make_fastdiv(rd.n[0] * rd.n[1]);
     // tiles

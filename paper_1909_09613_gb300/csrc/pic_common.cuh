@@ -91,6 +91,7 @@ struct RunDev {
     int64_t ntiles;
     int64_t ncell;
     double dx[3];
+    double idx[3];  // 1 / dx
     double dt;
     double dtt[3];  // c dt / dx_a
     // staged region around a tile: node local index = cell - tile_origin + pre

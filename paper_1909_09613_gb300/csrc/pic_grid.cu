@@ -204,21 +204,23 @@ __global__ void __launch_bounds__(kBlock) k_kinetic(const __grid_constant__ RunD
     if (threadIdx.x == 0) atomicAdd(out, acc * sp.w * sp.m);
 }
 
-// rho = sum q w W_l / V_c at integer nodes (FP64 atomics).
+// rho = sum q w W_l / V_c at integer nodes (FP64 atomics): the l + 1 non-zero B-spline
+// weights per axis from the basis polynomials, the same S0 the Esirkepov deposit starts from.
+template <int L>
 __global__ void __launch_bounds__(kBlock) k_rho(const __grid_constant__ RunDev rd, int s,
                                                 double *rho)
 {
     const SpeciesDev &sp = rd.sp[s];
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= sp.n) return;
-    const int l = rd.l;
     int c[3] = {0, 0, 0};
     double d[3] = {0, 0, 0};
     if (rd.prec == 1) {
         const int cc = sp.cell[p];
-        c[0] = cc % rd.n[0];
-        c[1] = (cc / rd.n[0]) % rd.n[1];
-        c[2] = cc / (rd.n[0] * rd.n[1]);
+        c[2] = fast_div(cc, rd.div_n01.m, rd.div_n01.s);
+        const int r = cc - c[2] * rd.n[0] * rd.n[1];
+        c[1] = fast_div(r, rd.div_n0.m, rd.div_n0.s);
+        c[0] = r - c[1] * rd.n[0];
         for (int a = 0; a < rd.dim; ++a) d[a] = ((const float *)sp.pos[a])[p];
     } else {
         for (int a = 0; a < rd.dim; ++a) {
@@ -228,40 +230,31 @@ __global__ void __launch_bounds__(kBlock) k_rho(const __grid_constant__ RunDev r
             d[a] = xi - f;
         }
     }
-    // W_l at the integer nodes cell-3 .. cell+3 (evaluated from |x - node|; covers l <= 4)
-    double w[3][7];
+    double w[3][L + 1];
     int b[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        for (int k = 0; k < 7; ++k) w[a][k] = 0.0;
-        b[a] = 0;
-        if (a >= rd.dim) { w[a][0] = 1.0; continue; }
-        b[a] = -3;
-        for (int k = 0; k < 7; ++k) {
-            const double y = fabs(d[a] - (double)(b[a] + k));
-            double v = 0.0;
-            if (l == 1) v = y < 1.0 ? 1.0 - y : 0.0;
-            else if (l == 2) v = y <= 0.5 ? 0.75 - y * y : (y < 1.5 ? 0.5 * (1.5 - y) * (1.5 - y) : 0.0);
-            else if (l == 3) v = y <= 1.0 ? 2.0 / 3.0 - y * y + 0.5 * y * y * y
-                                          : (y < 2.0 ? (2.0 - y) * (2.0 - y) * (2.0 - y) / 6.0 : 0.0);
-            else v = y <= 0.5 ? 115.0 / 192.0 - 5.0 * y * y / 8.0 + y * y * y * y / 4.0
-                     : (y <= 1.5 ? (55.0 + 20.0 * y - 120.0 * y * y + 80.0 * y * y * y - 16.0 * y * y * y * y) / 96.0
-                        : (y < 2.5 ? (2.5 - y) * (2.5 - y) * (2.5 - y) * (2.5 - y) / 24.0 : 0.0));
-            w[a][k] = v;
-        }
+        double psi;
+        b[a] = spline_base<L, double>(d[a], false, psi);
+        bspline<L, double>(psi, w[a]);
     }
     const double vc = rd.dx[0] * rd.dx[1] * (rd.dim == 3 ? rd.dx[2] : 1.0);
     const double qw = sp.q * sp.w / vc;
-    const int nk = rd.dim == 3 ? 7 : 1;
-    for (int kk = 0; kk < nk; ++kk)
-        for (int jj = 0; jj < 7; ++jj)
-            for (int ii = 0; ii < 7; ++ii) {
-                const double v = w[0][ii] * w[1][jj] * w[2][kk];
-                if (v == 0.0) continue;
+    const int nk = rd.dim == 3 ? L + 1 : 1;
+    for (int kk = 0; kk < nk; ++kk) {
+        const int gk = rd.dim == 3 ? wrap_idx(c[2] + b[2] + kk, rd.n[2]) : 0;
+        const double wk = rd.dim == 3 ? qw * w[2][kk] : qw;
+#pragma unroll
+        for (int jj = 0; jj <= L; ++jj) {
+            const int gj = wrap_idx(c[1] + b[1] + jj, rd.n[1]);
+            const double wjk = wk * w[1][jj];
+#pragma unroll
+            for (int ii = 0; ii <= L; ++ii) {
                 const int gi = wrap_idx(c[0] + b[0] + ii, rd.n[0]);
-                const int gj = wrap_idx(c[1] + b[1] + jj, rd.n[1]);
-                const int gk = rd.dim == 3 ? wrap_idx(c[2] + b[2] + kk, rd.n[2]) : 0;
-                atomicAdd(rho + gidx(rd, gi, gj, gk), qw * v);
+                atomicAdd(rho + gidx(rd, gi, gj, gk), wjk * w[0][ii]);
             }
+        }
+    }
 }
 
 // max |D.E - rho| (App. B, Eq. gauss)
@@ -277,11 +270,11 @@ __global__ void __launch_bounds__(kBlock) k_gauss(const __grid_constant__ RunDev
         const int k = (int)(c / ((int64_t)nx * ny));
         const int im = (i == 0) ? nx - 1 : i - 1;
         const int jm = (j == 0) ? ny - 1 : j - 1;
-        double dv = (rd.F[0][c] - rd.F[0][gidx(rd, im, j, k)]) / rd.dx[0]
-                    + (rd.F[1][c] - rd.F[1][gidx(rd, i, jm, k)]) / rd.dx[1];
+        double dv = (rd.F[0][c] - rd.F[0][gidx(rd, im, j, k)]) * rd.idx[0]
+                    + (rd.F[1][c] - rd.F[1][gidx(rd, i, jm, k)]) * rd.idx[1];
         if (rd.dim == 3) {
             const int km = (k == 0) ? nz - 1 : k - 1;
-            dv += (rd.F[2][c] - rd.F[2][gidx(rd, i, j, km)]) / rd.dx[2];
+            dv += (rd.F[2][c] - rd.F[2][gidx(rd, i, j, km)]) * rd.idx[2];
         }
         m = fmax(m, fabs(dv - rho[c]));
     }
@@ -340,7 +333,14 @@ cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t
     k_field_energy<<<gr, kBlock, 0, st>>>(rd, out + 0);
     for (int s = 0; s < rd.nsp; ++s) {
         k_kinetic<<<gr, kBlock, 0, st>>>(rd, s, out + 1);
-        if (rd.sp[s].n > 0) k_rho<<<grid_for(rd.sp[s].n), kBlock, 0, st>>>(rd, s, rho);
+        if (rd.sp[s].n == 0) continue;
+        const unsigned g = grid_for(rd.sp[s].n);
+        switch (rd.l) {
+        case 1: k_rho<1><<<g, kBlock, 0, st>>>(rd, s, rho); break;
+        case 2: k_rho<2><<<g, kBlock, 0, st>>>(rd, s, rho); break;
+        case 3: k_rho<3><<<g, kBlock, 0, st>>>(rd, s, rho); break;
+        default: k_rho<4><<<g, kBlock, 0, st>>>(rd, s, rho); break;
+        }
     }
     k_gauss<<<gr, kBlock, 0, st>>>(rd, rho, out + 2);
     return cudaGetLastError();

@@ -17,7 +17,17 @@ __device__ __forceinline__ double fdiff_e(const RunDev &rd, int ec, int a, int i
     if (a == 0) ip = (i + 1 == rd.n[0]) ? 0 : i + 1;
     else if (a == 1) jp = (j + 1 == rd.n[1]) ? 0 : j + 1;
     else kp = (k + 1 == rd.n[2]) ? 0 : k + 1;
-    return (rd.F[ec][gidx(rd, ip, jp, kp)] - rd.F[ec][gidx(rd, i, j, k)]) / rd.dx[a];
+    return (rd.F[ec][gidx(rd, ip, jp, kp)] - rd.F[ec][gidx(rd, i, j, k)]) * rd.idx[a];
+}
+
+// Cell (i, j, k) of linear cell index c (c < 2^30).
+__device__ __forceinline__ void cell_ijk(const RunDev &rd, int64_t c, int &i, int &j, int &k)
+{
+    const int ci = (int)c;
+    k = fast_div(ci, rd.div_n01.m, rd.div_n01.s);
+    const int r = ci - k * rd.n[0] * rd.n[1];
+    j = fast_div(r, rd.div_n0.m, rd.div_n0.s);
+    i = r - j * rd.n[0];
 }
 
 // Faraday's derivative of E component ec along axis a at node (i, j, k).  Yee: the forward
@@ -44,19 +54,23 @@ __device__ __forceinline__ double faraday_d(const RunDev &rd, int ec, int a, int
 // B <- B - h curl E at cell c (FP32 shadow of B written when `shadow`).
 __device__ __forceinline__ void yee_b_cell(const RunDev &rd, int64_t c, double h, int shadow)
 {
-    const int nx = rd.n[0], ny = rd.n[1];
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const int k = (int)(c / ((int64_t)nx * ny));
+    int i, j, k;
+    cell_ijk(rd, c, i, j, k);
     double c1, c2, c3;
     if (rd.m4) {
         c1 = faraday_d(rd, 2, 1, i, j, k) - faraday_d(rd, 1, 2, i, j, k);
         c2 = faraday_d(rd, 0, 2, i, j, k) - faraday_d(rd, 2, 0, i, j, k);
         c3 = faraday_d(rd, 1, 0, i, j, k) - faraday_d(rd, 0, 1, i, j, k);
     } else {
-        c1 = fdiff_e(rd, 2, 1, i, j, k) - fdiff_e(rd, 1, 2, i, j, k);
-        c2 = fdiff_e(rd, 0, 2, i, j, k) - fdiff_e(rd, 2, 0, i, j, k);
-        c3 = fdiff_e(rd, 1, 0, i, j, k) - fdiff_e(rd, 0, 1, i, j, k);
+        const int ip = (i + 1 == rd.n[0]) ? 0 : i + 1;
+        const int jp = (j + 1 == rd.n[1]) ? 0 : j + 1;
+        const int kp = (k + 1 == rd.n[2]) ? 0 : k + 1;
+        const double *E1 = rd.F[0], *E2 = rd.F[1], *E3 = rd.F[2];
+        const double e1 = E1[c], e2 = E2[c], e3 = E3[c];
+        const double idx = rd.idx[0], idy = rd.idx[1], idz = rd.idx[2];
+        c1 = (E3[gidx(rd, i, jp, k)] - e3) * idy - (E2[gidx(rd, i, j, kp)] - e2) * idz;
+        c2 = (E1[gidx(rd, i, j, kp)] - e1) * idz - (E3[gidx(rd, ip, j, k)] - e3) * idx;
+        c3 = (E2[gidx(rd, ip, j, k)] - e2) * idx - (E1[gidx(rd, i, jp, k)] - e1) * idy;
     }
     const double b1 = rd.F[3][c] - h * c1;
     const double b2 = rd.F[4][c] - h * c2;
@@ -75,15 +89,14 @@ __device__ __forceinline__ void yee_b_cell(const RunDev &rd, int64_t c, double h
 __device__ __forceinline__ void yee_e_cell(const RunDev &rd, int64_t c, int shadow)
 {
     const int nx = rd.n[0], ny = rd.n[1], nz = rd.n[2];
-    const int i = (int)(c % nx);
-    const int j = (int)((c / nx) % ny);
-    const int k = (int)(c / ((int64_t)nx * ny));
+    int i, j, k;
+    cell_ijk(rd, c, i, j, k);
     const int im = (i == 0) ? nx - 1 : i - 1;
     const int jm = (j == 0) ? ny - 1 : j - 1;
     const int km = (k == 0) ? nz - 1 : k - 1;
     const double *B1 = rd.F[3], *B2 = rd.F[4], *B3 = rd.F[5];
     const double b1 = B1[c], b2 = B2[c], b3 = B3[c];
-    const double idx = 1.0 / rd.dx[0], idy = 1.0 / rd.dx[1], idz = 1.0 / rd.dx[2];
+    const double idx = rd.idx[0], idy = rd.idx[1], idz = rd.idx[2];
     const double dt = rd.dt;
     const double dB3dy = (b3 - B3[gidx(rd, i, jm, k)]) * idy;
     const double dB2dz = (b2 - B2[gidx(rd, i, j, km)]) * idz;

@@ -37,6 +37,17 @@ class Request:
     arrival: float = 0.0          # seconds after the serving clock starts
     scheme: int = pic.PIC_SCHEME_WT
     seed: int = 0
+    solver: int = pic.PIC_SOLVER_YEE
+    record_every: int = 0         # steps between field-energy samples (0: none)
+    rng_run: int = -1             # random stream of the initial plasma (-1: the request id)
+    precision: int = pic.PIC_FP32_MIXED
+    colocated: bool = False       # positrons start at the electrons' positions (neutral start)
+
+    @property
+    def batchable(self):
+        """Runs the batched kernel serves (2D FP32 form, quadratic or cubic); others step on
+        their own streams."""
+        return self.dim == 2 and self.l in (2, 3) and self.precision == pic.PIC_FP32_MIXED
 
     @property
     def dim(self):
@@ -112,32 +123,37 @@ class Autotuner:
         return best[1], best[2]
 
 
-def make_run(req: Request, precision=pic.PIC_FP32_MIXED, tuner: Optional[Autotuner] = None,
+def make_run(req: Request, precision=None, tuner: Optional[Autotuner] = None,
              stream=None, device="cuda"):
     """Create, bind and load one run for a request (seeded drifting pair plasma)."""
     import workloads
+    if precision is None:
+        precision = req.precision
     dx = (1.0, 1.0, 1.0)
     wl = workloads.pair_plasma(req.grid if req.dim == 3 else req.grid[:2], dx[:req.dim], req.dt,
                                req.l, req.scheme, req.gamma, req.u_th, req.ppc, seed=req.seed,
-                               run=req.rid, device=device)
+                               run=req.rid if req.rng_run < 0 else req.rng_run, device=device,
+                               colocated=req.colocated)
     tile, si = (None, 0)
-    if tuner is not None and req.dim == 2 and precision == pic.PIC_FP32_MIXED:
+    if tuner is not None and req.batchable and precision == pic.PIC_FP32_MIXED:
         tile, si = tuner.choose(req.l, req.ppc, req.dt)
         tile = (min(tile[0], req.grid[0]), min(tile[1], req.grid[1]), 1)
     caps = [int(s.x.shape[1]) for s in wl.species]
     run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=precision, capacity=caps,
-                  tile=tile, sort_interval=si, stream=stream)
+                  tile=tile, sort_interval=si, stream=stream, solver=req.solver)
     for i, s in enumerate(wl.species):
         run.load(i, s.q, s.m, s.w, s.x, s.u)
     del wl
     return run
 
 
-def footprint_estimate(req: Request, precision=pic.PIC_FP32_MIXED) -> int:
+def footprint_estimate(req: Request, precision=None) -> int:
     """Device bytes a request will hold (libpic's own footprint query, without device work)."""
     dim = req.dim
     grid = req.grid
     n = grid[0] * grid[1] * grid[2] * req.ppc // 2
+    if precision is None:
+        precision = req.precision
     opt = pic.pic_options()
     opt.precision = precision
     opt.n_species = 2
@@ -162,6 +178,8 @@ class Served:
     particles: int
     dim: int
     diag: dict = field(default_factory=dict)
+    # (step, t omega_p, field energy, kinetic energy) every record_every steps, from step 0
+    history: list = field(default_factory=list)
 
     @property
     def latency(self):
@@ -201,17 +219,19 @@ class Server:
                 if used + need > self.budget and active:
                     break
                 pending.pop(0)
-                stream = s3d[req.rid % len(s3d)] if req.dim == 3 else None
+                stream = None if req.batchable else s3d[req.rid % len(s3d)]
                 run = make_run(req, tuner=self.tuner, stream=stream)
                 active[req.rid] = {"run": run, "req": req, "done": 0, "bytes": need,
-                                   "admitted": time.perf_counter() - t0}
+                                   "admitted": time.perf_counter() - t0, "history": []}
+                if req.record_every > 0:
+                    self._record(active[req.rid])
                 used += need
                 self.peak_bytes = max(self.peak_bytes, used)
             if not active:
                 time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
                 continue
-            # the 2D runs form the batch; rebuild it when the set changed
-            ids2d = tuple(sorted(r for r, a in active.items() if a["req"].dim == 2))
+            # the batchable runs form the batch; rebuild it when the set changed
+            ids2d = tuple(sorted(r for r, a in active.items() if a["req"].batchable))
             if ids2d != batch_ids:
                 if batch is not None:
                     batch.sync()
@@ -222,14 +242,21 @@ class Server:
             self.chunks += 1
             # one chunk: as many steps as the nearest-finishing active run still needs
             k = min(self.chunk, min(a["req"].steps - a["done"] for a in active.values()))
+            for a in active.values():  # stop at the next field-energy sample
+                ev = a["req"].record_every
+                if ev > 0:
+                    k = min(k, ev - a["done"] % ev)
             if batch is not None:
                 batch.step(k)
             for rid, a in active.items():
-                if a["req"].dim == 3:
+                if not a["req"].batchable:
                     a["run"].step(k)
             torch.cuda.synchronize()
             for a in active.values():
                 a["done"] += k
+                ev = a["req"].record_every
+                if ev > 0 and a["done"] % ev == 0:
+                    self._record(a)
             finished = [r for r, a in active.items() if a["done"] >= a["req"].steps]
             if finished:
                 if batch is not None:
@@ -243,7 +270,8 @@ class Server:
                     d = a["run"].diag()
                     done_t = time.perf_counter() - t0
                     self.results.append(Served(rid, a["req"].arrival, a["admitted"], done_t,
-                                               a["req"].steps, a["req"].particles, a["req"].dim, d))
+                                               a["req"].steps, a["req"].particles, a["req"].dim, d,
+                                               a["history"]))
                     used -= a["bytes"]
                     if self.keep_runs:
                         self.finished_runs[rid] = a["run"]
@@ -252,6 +280,51 @@ class Server:
         if batch is not None:
             batch.close()
         return self.results
+
+    @staticmethod
+    def _record(a):
+        req = a["req"]
+        d = a["run"].diag()
+        wp = 1.0 / 16.0  # omega_p of the drifting plasma (16 cells per skin depth, dx = 1)
+        a["history"].append((a["done"], a["done"] * req.dt * wp, d["field_energy"],
+                             d["kinetic_energy"]))
+
+
+# The drifting pair-plasma NCI test of Table 1: 256 x 128 cells (16 x 8 skin depths), 64
+# particles per cell, gamma0 = 1000, k T = 0.01 m c^2 in the co-moving frame (Gaussian momenta
+# of spread sqrt(kT / m c^2) = 0.1, boosted with the App. D flip), l = 4, and
+# dt / dt_CFL in {0.1, 0.3, 0.5, 0.7, 1/sqrt(2)} with dt_CFL = dx / (sqrt(2) c).
+TABLE1_RATIOS = (0.1, 0.3, 0.5, 0.7, 1.0 / math.sqrt(2.0))
+
+
+def table1_requests(t_end: float, record_dt: float = 1.0, schemes=(pic.PIC_SCHEME_MC, pic.PIC_SCHEME_WT),
+                    solvers=(pic.PIC_SOLVER_YEE, pic.PIC_SOLVER_M4), ratios=TABLE1_RATIOS,
+                    grid=(256, 128, 1), ppc=64, seed=1909096130, precision=pic.PIC_FP32_MIXED,
+                    only=None, colocated=True):
+    """One request per (scheme, solver, dt) of Table 1, run to t_end (in 1/omega_pe), sampling
+    the field energy every record_dt; every run starts from the same seeded plasma.  `only`
+    keeps the (scheme, solver, ratio index) triples listed.
+
+    The start is neutral by default (positrons at the electrons' positions): with independent
+    positions the initial charge noise, with zero fields, stays in the system as a frozen
+    background (D.E - rho is conserved) through which the plasma streams at ~c, and that
+    drives field growth unrelated to the interpolation scheme."""
+    reqs = []
+    for scheme in schemes:
+        for solver in solvers:
+            for ri, ratio in enumerate(ratios):
+                if only is not None and (scheme, solver, ri) not in only:
+                    continue
+                # c dt / dx = ratio / sqrt(2); the last ratio is exactly dx / 2 (WT = MC there)
+                dt = 0.5 if abs(ratio * math.sqrt(2.0) - 1.0) < 1e-12 else ratio / math.sqrt(2.0)
+                steps = int(math.ceil(t_end * 16.0 / dt))
+                every = max(1, int(round(record_dt * 16.0 / dt)))
+                steps = (steps + every - 1) // every * every
+                reqs.append(Request(rid=len(reqs), grid=grid, dt=dt, l=4, gamma=1000.0, u_th=0.1,
+                                    ppc=ppc, steps=steps, scheme=scheme, seed=seed, solver=solver,
+                                    record_every=every, rng_run=0, precision=precision,
+                                    colocated=colocated))
+    return reqs
 
 
 def percentile(values, q):

@@ -121,3 +121,38 @@ def test_axis_weight_tables_mc_are_bsplines(lib, l):
         for k in range(-4, 6):
             got = w[k] if 0 <= k < len(w) else 0.0
             assert abs(got - oracle.W(l, delta - (base + k))) < 1e-14
+
+
+def test_table1_requests_follow_table_1():
+    """The Table 1 scan: 2 schemes x 2 solvers x 5 time steps, dt / dt_CFL as printed
+    (dt_CFL = dx / (sqrt 2 c)), c dt = dx / 2 exactly for the last one, 256x128 cells, 64 per
+    cell, gamma0 = 1000, quartic, samples aligned with the end of the run."""
+    import math
+    from paper_1909_09613_gb300 import engine
+    reqs = engine.table1_requests(50.0, 1.0)
+    assert len(reqs) == 20
+    ratios = sorted({round(r.dt * math.sqrt(2.0), 12) for r in reqs})
+    assert ratios == [0.1, 0.3, 0.5, 0.7, round(1 / math.sqrt(2.0), 12)]
+    assert any(r.dt == 0.5 for r in reqs)
+    for r in reqs:
+        assert r.grid == (256, 128, 1) and r.ppc == 64 and r.l == 4 and r.gamma == 1000.0
+        assert r.steps % r.record_every == 0
+        assert r.steps * r.dt / 16.0 >= 50.0           # t in 1/omega_pe, 16 cells per d_e
+        assert abs(r.record_every * r.dt / 16.0 - 1.0) < 0.6
+        assert not r.batchable                          # quartic runs step on their own
+    only = {(pic.PIC_SCHEME_WT, pic.PIC_SOLVER_M4, 0)}
+    sub = engine.table1_requests(50.0, 1.0, only=only)
+    assert len(sub) == 1 and sub[0].solver == pic.PIC_SOLVER_M4
+    assert abs(sub[0].dt - 0.1 / math.sqrt(2.0)) < 1e-15
+
+
+def test_neutral_start_colocates_species():
+    """colocated=True: positrons at the electrons' positions (rho = 0 at the start), momenta
+    independent; the default keeps independent positions."""
+    import workloads
+    a = workloads.pair_plasma((8, 4), (1.0, 1.0), 0.3, 2, 1, 50.0, 0.1, 4, colocated=True)
+    assert np.array_equal(a.species[0].x.numpy(), a.species[1].x.numpy())
+    assert not np.array_equal(a.species[0].u.numpy(), a.species[1].u.numpy())
+    b = workloads.pair_plasma((8, 4), (1.0, 1.0), 0.3, 2, 1, 50.0, 0.1, 4)
+    assert not np.array_equal(b.species[0].x.numpy(), b.species[1].x.numpy())
+    assert np.array_equal(a.species[0].x.numpy(), b.species[0].x.numpy())

@@ -120,12 +120,16 @@ class Workload:
 def pair_plasma(grid: Sequence[int], dx: Sequence[float], dt: float, l: int, scheme: int,
                 gamma: float, u_th: float, ppc: int, omega_p: Optional[float] = None,
                 seed: int = BASE_SEED, run: int = 0, device="cpu", steps: int = 0,
-                name: str = "pair_plasma") -> Workload:
+                name: str = "pair_plasma", colocated: bool = False) -> Workload:
     """Drifting e-/e+ pair plasma along x1 (Table 1 set-up), ppc particles per cell in total.
 
     omega_p is the relativistic plasma frequency of each species, omega_p^2 = n q^2/(gamma m)
     with n = (ppc/2) w / V_c (Sec. 4 normalisation); when omitted the grid resolves the skin
     depth with 16 cells, c/omega_p = 16 dx, as in Table 1 (16 d_e over 256 cells).
+
+    colocated: the positrons start at the electrons' positions (a neutral start: rho = 0, so
+    zero initial fields satisfy Gauss's law); momenta stay independent.  Otherwise every
+    species draws its own positions.
     """
     grid = tuple(int(g) for g in grid) + (1,) * (3 - len(grid))
     dx = tuple(float(d) for d in dx) + (1.0,) * (3 - len(dx))
@@ -147,7 +151,7 @@ def pair_plasma(grid: Sequence[int], dx: Sequence[float], dt: float, l: int, sch
     for s, q in enumerate((-1.0, 1.0)):
         xs = []
         for a in range(dim):
-            off = uniform(stream_key(seed, run, s, 10 + a), idx)
+            off = uniform(stream_key(seed, run, 0 if colocated else s, 10 + a), idx)
             L = grid[a] * dx[a]
             xa = (ci[a].to(torch.float64) + off) * dx[a]
             xa = torch.where(xa >= L, xa - L, xa)
