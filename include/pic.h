@@ -120,6 +120,26 @@ int pic_load_particles(pic_ctx *ctx, int species, double q, double m, double w, 
 int pic_load_particles_device(pic_ctx *ctx, int species, double q, double m, double w, int64_t n,
                               const double *x_dev, const double *u_dev);
 
+/* Load species `species` as a drifting plasma generated on the device (App. D): per_cell
+ * particles in every cell (n = ncell * per_cell <= capacity) at uniform in-cell offsets, and
+ * momenta drawn in the co-moving frame, u' ~ N(0, u_th^2) per component (Box-Muller), the x1
+ * component flipped to account for the volume transform (flip when an extra uniform X1 exceeds
+ * (1 + beta u'_1 / E') / 2, E' = sqrt(1 + u'^2)), then boosted along x1 with gamma:
+ * u_1 = gamma (u'_1 + beta E').  u_th = 0 gives the cold beam u = (sqrt(gamma^2 - 1), 0, 0).
+ * Particle p sits in cell p / per_cell (x1 fastest).
+ * Random numbers: SplitMix64 (Steele, Lea, Flood 2014), U[0,1) = 53 high bits of
+ * mix(p * G + key), G = 0x9E3779B97F4A7C15, for stream keys
+ *   key(ids) = mix(... mix(mix(seed + G) ^ ((id_0 + 1) G)) ^ ((id_1 + 1) G) ...)
+ * with ids (run, pos_species, 10 + a) for the offset along axis a, (run, species, 20 + 2a) and
+ * (run, species, 21 + 2a) for the two Box-Muller uniforms of u'_a (the first enters as
+ * 1 - U), and (run, species, 30) for X1.  pos_species = species gives every species its own
+ * positions; another species' index places this one on that species' positions.
+ * gamma >= 1, u_th >= 0, per_cell >= 0.  Tile-sorts like pic_load_particles.  Syncs.
+ * (The paper loads on the host; this is the same distribution generated in HBM.)            */
+int pic_load_drifting_plasma(pic_ctx *ctx, int species, double q, double m, double w,
+                             int64_t per_cell, double gamma, double u_th, uint64_t seed,
+                             uint64_t run, int pos_species);
+
 /* Set field component comp (0..5 = E1 E2 E3 B1 B2 B3) from count = ncell FP64 host values. */
 int pic_set_fields(pic_ctx *ctx, int comp, const double *host, size_t count);
 

@@ -66,6 +66,10 @@ _SIGS = [
     ("pic_load_particles_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                                  ctypes.c_void_p, ctypes.c_void_p]),
+    ("pic_load_drifting_plasma", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                                ctypes.c_uint64, ctypes.c_int]),
     ("pic_set_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dp, ctypes.c_size_t]),
     ("pic_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("pic_read_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dp, ctypes.c_size_t]),
@@ -171,6 +175,15 @@ def pic_load_particles_device(ctx, species, q, m, w, x_ptr: int, u_ptr: int, n: 
                                                     float(w), int(n), ctypes.c_void_p(x_ptr),
                                                     ctypes.c_void_p(u_ptr)),
            "pic_load_particles_device")
+
+
+def pic_load_drifting_plasma(ctx, species, q, m, w, per_cell, gamma, u_th, seed, run,
+                             pos_species):
+    _check(load_library().pic_load_drifting_plasma(ctx, int(species), float(q), float(m),
+                                                   float(w), int(per_cell), float(gamma),
+                                                   float(u_th), int(seed) & (2**64 - 1),
+                                                   int(run) & (2**64 - 1), int(pos_species)),
+           "pic_load_drifting_plasma")
 
 
 def pic_set_fields(ctx, comp, a: np.ndarray):
@@ -385,6 +398,13 @@ class Run:
             n = int(np.asarray(u).shape[-1])
             pic_load_particles(self.ctx, species, q, m, w, x, u)
         self.counts[species] = n
+
+    def load_drifting_plasma(self, species, q, m, w, per_cell, gamma, u_th, seed, run=0,
+                             pos_species=None):
+        """Generate species `species` on the device (App. D drifting plasma, pic.h)."""
+        pic_load_drifting_plasma(self.ctx, species, q, m, w, per_cell, gamma, u_th, seed, run,
+                                 species if pos_species is None else pos_species)
+        self.counts[species] = int(np.prod(self.grid)) * int(per_cell)
 
     def set_field(self, comp, a):
         pic_set_fields(self.ctx, comp, a)

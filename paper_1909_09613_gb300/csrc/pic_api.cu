@@ -154,12 +154,9 @@ int sort_all(pic_ctx *c)
     return PIC_OK;
 }
 
-int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n,
-                const double *x, const double *u, bool on_device)
+// Species constants of a load (charge, mass, weight and the derived per-step factors).
+void set_species(pic_ctx *c, int species, double q, double m, double w, int64_t n)
 {
-    if (!c || !c->base) return c ? PIC_ESTATE : PIC_EINVAL;
-    if (species < 0 || species >= c->rd.nsp || n < 0 || n > c->cap[species]) return PIC_EINVAL;
-    if (!(m > 0.0) || !(w >= 0.0) || (n > 0 && (!x || !u))) return PIC_EINVAL;
     SpeciesDev &sp = c->rd.sp[species];
     const RunDev &rd = c->rd;
     const double vc = rd.dx[0] * rd.dx[1] * (rd.dim == 3 ? rd.dx[2] : 1.0);
@@ -170,8 +167,46 @@ int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n
     for (int a = 0; a < 3; ++a) sp.kx[a] = -q * w * rd.dx[a] / (vc * rd.dt);
     sp.kz = q * w / vc;
     sp.n = n;
-    const int d = rd.dim;
     refresh_species_ptrs(c);
+}
+
+// After the particle store of a species is written: tile-sort it and mark it loaded.
+int finish_load(pic_ctx *c, int species)
+{
+    const int r = sort_species(c, species);
+    if (r != PIC_OK) return r;
+    c->loaded[species] = true;
+    c->age = 0;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+    return PIC_OK;
+}
+
+uint64_t sm64_mix_host(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Key of the SplitMix64 stream named by (seed, ids...), the schedule documented in pic.h.
+uint64_t stream_key(uint64_t seed, uint64_t a, uint64_t b, uint64_t d)
+{
+    const uint64_t G = 0x9E3779B97F4A7C15ull;
+    uint64_t k = sm64_mix_host(seed + G);
+    k = sm64_mix_host(k ^ ((a + 1) * G));
+    k = sm64_mix_host(k ^ ((b + 1) * G));
+    k = sm64_mix_host(k ^ ((d + 1) * G));
+    return k;
+}
+
+int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n,
+                const double *x, const double *u, bool on_device)
+{
+    if (!c || !c->base) return c ? PIC_ESTATE : PIC_EINVAL;
+    if (species < 0 || species >= c->rd.nsp || n < 0 || n > c->cap[species]) return PIC_EINVAL;
+    if (!(m > 0.0) || !(w >= 0.0) || (n > 0 && (!x || !u))) return PIC_EINVAL;
+    set_species(c, species, q, m, w, n);
+    const int d = c->rd.dim;
     if (on_device) {
         if (launch_pack(c->rd, species, x, n, u, n, n, 0, c->stream) != cudaSuccess) return PIC_ECUDA;
         if (n > 0) c->kernel_launches += 1;
@@ -194,12 +229,7 @@ int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n
             c->kernel_launches += 1;
         }
     }
-    const int r = sort_species(c, species);
-    if (r != PIC_OK) return r;
-    c->loaded[species] = true;
-    c->age = 0;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
-    return PIC_OK;
+    return finish_load(c, species);
 }
 
 }  // namespace
@@ -488,6 +518,31 @@ int pic_load_particles_device(pic_ctx *c, int species, double q, double m, doubl
                               const double *x, const double *u)
 {
     return load_common(c, species, q, m, w, n, x, u, true);
+}
+
+int pic_load_drifting_plasma(pic_ctx *c, int species, double q, double m, double w,
+                             int64_t per_cell, double gamma, double u_th, uint64_t seed,
+                             uint64_t run, int pos_species)
+{
+    if (!c || !c->base) return c ? PIC_ESTATE : PIC_EINVAL;
+    if (species < 0 || species >= c->rd.nsp || pos_species < 0 || per_cell < 0) return PIC_EINVAL;
+    if (!(m > 0.0) || !(w >= 0.0) || !(gamma >= 1.0) || !(u_th >= 0.0) || !std::isfinite(gamma)
+        || !std::isfinite(u_th))
+        return PIC_EINVAL;
+    if (per_cell > 0 && c->rd.ncell > c->cap[species] / per_cell) return PIC_EINVAL;
+    const int64_t n = c->rd.ncell * per_cell;
+    set_species(c, species, q, m, w, n);
+    LoadKeys k;
+    for (int a = 0; a < 3; ++a) {
+        k.pos[a] = stream_key(seed, run, (uint64_t)pos_species, 10 + a);
+        k.mom[2 * a] = stream_key(seed, run, (uint64_t)species, 20 + 2 * a);
+        k.mom[2 * a + 1] = stream_key(seed, run, (uint64_t)species, 21 + 2 * a);
+    }
+    k.flip = stream_key(seed, run, (uint64_t)species, 30);
+    if (launch_load_plasma(c->rd, species, k, per_cell, gamma, u_th, n, c->stream) != cudaSuccess)
+        return PIC_ECUDA;
+    if (n > 0) c->kernel_launches += 1;
+    return finish_load(c, species);
 }
 
 int pic_set_fields(pic_ctx *c, int comp, const double *host, size_t count)

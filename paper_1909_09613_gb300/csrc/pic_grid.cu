@@ -38,18 +38,13 @@ __global__ void __launch_bounds__(kBlock) k_shadow(const __grid_constant__ RunDe
 // x[a * xs + i], u[a * us + i] hold particle p0 + i.  Positions are divided by dx (IEEE
 // division, so the cell index floor(x/dx) matches a plain FP64 evaluation) and wrapped into
 // [0, n).
-__global__ void __launch_bounds__(kBlock) k_pack(const __grid_constant__ RunDev rd, int s,
-                                                 const double *x, int64_t xs, const double *u,
-                                                 int64_t us, int64_t m, int64_t p0)
+__device__ __forceinline__ void pack_one(const RunDev &rd, const SpeciesDev &sp, int64_t p,
+                                         const double *xp, const double *up)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const int64_t p = p0 + i;
-    const SpeciesDev &sp = rd.sp[s];
     int cell[3] = {0, 0, 0};
     double off[3] = {0, 0, 0};
     for (int a = 0; a < rd.dim; ++a) {
-        double xi = x[a * xs + i] / rd.dx[a];
+        double xi = xp[a] / rd.dx[a];
         const double N = (double)rd.n[a];
         if (xi >= N) xi -= N;
         if (xi < 0.0) xi += N;
@@ -71,11 +66,81 @@ __global__ void __launch_bounds__(kBlock) k_pack(const __grid_constant__ RunDev 
             ((float *)sp.pos[a])[p] = o[a];
         }
         sp.cell[p] = (int32_t)gidx(rd, c[0], c[1], rd.dim == 3 ? c[2] : 0);
-        for (int a = 0; a < 3; ++a) ((float *)sp.mom[a])[p] = (float)u[a * us + i];
+        for (int a = 0; a < 3; ++a) ((float *)sp.mom[a])[p] = (float)up[a];
     } else {
         for (int a = 0; a < rd.dim; ++a) ((double *)sp.pos[a])[p] = (double)cell[a] + off[a];
-        for (int a = 0; a < 3; ++a) ((double *)sp.mom[a])[p] = u[a * us + i];
+        for (int a = 0; a < 3; ++a) ((double *)sp.mom[a])[p] = up[a];
     }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pack(const __grid_constant__ RunDev rd, int s,
+                                                 const double *x, int64_t xs, const double *u,
+                                                 int64_t us, int64_t m, int64_t p0)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double xp[3] = {0, 0, 0}, up[3];
+    for (int a = 0; a < rd.dim; ++a) xp[a] = x[a * xs + i];
+    for (int a = 0; a < 3; ++a) up[a] = u[a * us + i];
+    pack_one(rd, rd.sp[s], p0 + i, xp, up);
+}
+
+// ---- drifting plasma generated on the device (App. D) ------------------------------------
+// SplitMix64 finaliser (Steele, Lea, Flood 2014) and U[0,1) from its 53 high bits.
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t ctr)
+{
+    return (double)(sm64_mix(ctr * 0x9E3779B97F4A7C15ull + key) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void __launch_bounds__(kBlock) k_load_plasma(const __grid_constant__ RunDev rd, int s,
+                                                        LoadKeys keys, int64_t per_cell,
+                                                        double gamma, double u_th, int64_t n)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t cell = p / per_cell;
+    int64_t ci[3];
+    ci[0] = cell % rd.n[0];
+    ci[1] = (cell / rd.n[0]) % rd.n[1];
+    ci[2] = cell / ((int64_t)rd.n[0] * rd.n[1]);
+    double xp[3] = {0, 0, 0}, up[3] = {0, 0, 0};
+    // every operation rounded on its own (no fused multiply-add), as a plain evaluation does
+    for (int a = 0; a < rd.dim; ++a) {
+        const double L = __dmul_rn((double)rd.n[a], rd.dx[a]);
+        const double off = sm64_uniform(keys.pos[a], (uint64_t)p);
+        double xa = __dmul_rn(__dadd_rn((double)ci[a], off), rd.dx[a]);
+        if (xa >= L) xa = __dsub_rn(xa, L);
+        xp[a] = xa;
+    }
+    const double beta = sqrt(__dsub_rn(1.0, __ddiv_rn(1.0, __dmul_rn(gamma, gamma))));
+    if (u_th > 0.0) {
+        double v[3];
+        for (int a = 0; a < 3; ++a) {
+            const double u1 = __dsub_rn(1.0, sm64_uniform(keys.mom[2 * a], (uint64_t)p));  // (0, 1]
+            const double u2 = sm64_uniform(keys.mom[2 * a + 1], (uint64_t)p);
+            const double r = sqrt(__dmul_rn(-2.0, log(u1)));
+            v[a] = __dmul_rn(u_th, __dmul_rn(r, cos(__dmul_rn(6.283185307179586, u2))));
+        }
+        const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(v[0], v[0]), __dmul_rn(v[1], v[1])),
+                                    __dmul_rn(v[2], v[2]));
+        const double ep = sqrt(__dadd_rn(1.0, s2));
+        const double x1 = sm64_uniform(keys.flip, (uint64_t)p);
+        const double thr = __dmul_rn(0.5, __dadd_rn(1.0, __ddiv_rn(__dmul_rn(beta, v[0]), ep)));
+        const double vx = (x1 > thr) ? -v[0] : v[0];
+        up[0] = __dmul_rn(gamma, __dadd_rn(vx, __dmul_rn(beta, ep)));
+        up[1] = v[1];
+        up[2] = v[2];
+    } else {
+        up[0] = sqrt(__dsub_rn(__dmul_rn(gamma, gamma), 1.0));
+    }
+    pack_one(rd, rd.sp[s], p, xp, up);
 }
 
 // Particles p0 .. p0 + m - 1 -> FP64 physical x[a * m + i], u[a * m + i], cell[i].
@@ -345,5 +410,14 @@ cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t
     k_gauss<<<gr, kBlock, 0, st>>>(rd, rho, out + 2);
     return cudaGetLastError();
 }
+
+cudaError_t launch_load_plasma(const RunDev &rd, int s, const LoadKeys &keys, int64_t per_cell,
+                               double gamma, double u_th, int64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_load_plasma<<<grid_for(n), kBlock, 0, st>>>(rd, s, keys, per_cell, gamma, u_th, n);
+    return cudaGetLastError();
+}
+
 
 }  // namespace pic

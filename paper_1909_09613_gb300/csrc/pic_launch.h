@@ -20,6 +20,15 @@ cudaError_t launch_shadow(const RunDev &rd, cudaStream_t st);
 // particles p0 .. p0 + m - 1; x[a * xs + i], u[a * us + i] hold particle p0 + i
 cudaError_t launch_pack(const RunDev &rd, int s, const double *x, int64_t xs, const double *u,
                         int64_t us, int64_t m, int64_t p0, cudaStream_t st);
+// drifting plasma generated on the device: SplitMix64 stream keys of the offsets (per axis),
+// the two Box-Muller uniforms of each momentum component and the flip uniform
+struct LoadKeys {
+    uint64_t pos[3];
+    uint64_t mom[6];
+    uint64_t flip;
+};
+cudaError_t launch_load_plasma(const RunDev &rd, int s, const LoadKeys &keys, int64_t per_cell,
+                               double gamma, double u_th, int64_t n, cudaStream_t st);
 // particles p0 .. p0 + m - 1 -> x[a * m + i], u[a * m + i], cell[i]
 cudaError_t launch_unpack(const RunDev &rd, int s, double *x, double *u, int64_t *cell,
                           int64_t m, int64_t p0, cudaStream_t st);

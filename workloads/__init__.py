@@ -5,8 +5,9 @@ This module holds no arithmetic of the PIC step.  It draws counter-based random 
 (SplitMix64, Steele/Lea/Flood 2014: state += 0x9E3779B97F4A7C15, then the xor-shift-multiply
 finaliser) and turns them into an initial particle state:
 
-* positions: ppc/2 particles of each species per cell at independent uniform in-cell offsets
-  (stratified per cell; independent per species so that the e-/e+ currents do not cancel);
+* positions: ppc/2 particles of each species per cell at uniform in-cell offsets (stratified
+  per cell; independent per species, or with colocated=True the positrons on the electrons'
+  positions, a neutral start);
 * momenta: cold beam u = (sqrt(gamma^2 - 1), 0, 0), or a drifting Maxwellian loaded as in the
   paper's App. D -- Gaussian u' ~ N(0, u_th^2) per component in the co-moving frame
   (Box-Muller), the flip of u'_x that accounts for the volume transform (flip when the extra
