@@ -60,6 +60,7 @@ typedef enum {
 enum { PIC_SCHEME_MC = 0, PIC_SCHEME_WT = 1 };
 enum { PIC_FP64 = 0, PIC_FP32_MIXED = 1 };
 enum { PIC_SOLVER_YEE = 0, PIC_SOLVER_M4 = 1 };
+enum { PIC_ORDER_AUTO = 0, PIC_ORDER_CELL = 1, PIC_ORDER_SLOT = 2 };
 
 /* Error bits of pic_diag_t.error_flags. */
 enum { PIC_ERR_OUTSIDE_TILE = 1, PIC_ERR_NONFINITE = 2, PIC_ERR_TIMEOUT = 4 };
@@ -78,7 +79,13 @@ typedef struct {
                                modified Faraday stencil with fourth-order dispersion error of
                                App. C (beta_ij = (c dt/dx_j)^2/12, delta_i = ((c dt/dx_i)^2-1)/12,
                                Eq. Maxwell-A); Ampere's stencil is the Yee one in both        */
-    int32_t reserved;
+    int32_t tile_order;     /* order of the particles of a tile in the FP32 form:
+                               PIC_ORDER_AUTO (0): cell-major when a species holds >= 6
+                               particles per cell, else slot-major; PIC_ORDER_CELL (1):
+                               (tile, cell, slot), the warp deposits of neighbouring lanes are
+                               summed through shared memory; PIC_ORDER_SLOT (2): (tile, slot,
+                               cell), every lane adds its own window with shared atomics.
+                               The FP64 form always uses PIC_ORDER_SLOT.                     */
 } pic_options;
 
 /* pic_create -- validate a run and build its host-side context (no device memory yet).

@@ -25,6 +25,7 @@ PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_ENAN, PIC_ESTATE = -5, -6, -7, -8
 PIC_SCHEME_MC, PIC_SCHEME_WT = 0, 1
 PIC_FP64, PIC_FP32_MIXED = 0, 1
 PIC_SOLVER_YEE, PIC_SOLVER_M4 = 0, 1
+PIC_ORDER_AUTO, PIC_ORDER_CELL, PIC_ORDER_SLOT = 0, 1, 2
 PIC_MAX_SPECIES = 4
 
 _c_dp = ctypes.POINTER(ctypes.c_double)
@@ -36,7 +37,7 @@ class pic_options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32 * 3), ("sort_interval", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("n_species", ctypes.c_int32),
                 ("capacity", ctypes.c_int64 * PIC_MAX_SPECIES), ("stream", ctypes.c_uint64),
-                ("solver", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("solver", ctypes.c_int32), ("tile_order", ctypes.c_int32)]
 
 
 class pic_diag_t(ctypes.Structure):
@@ -355,7 +356,8 @@ class Run:
     """One PIC run: a libpic context plus the torch-allocated device buffer bound to it."""
 
     def __init__(self, grid, dx, dt, l, scheme, precision=PIC_FP64, capacity=(0, 0),
-                 tile=None, sort_interval=0, stream=None, device=None, solver=PIC_SOLVER_YEE):
+                 tile=None, sort_interval=0, stream=None, device=None, solver=PIC_SOLVER_YEE,
+                 tile_order=PIC_ORDER_AUTO):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libpic needs a CUDA device")
@@ -378,6 +380,7 @@ class Run:
             opt.capacity[s] = int(c)
         opt.stream = int(self.stream.cuda_stream)
         opt.solver = int(solver)
+        opt.tile_order = int(tile_order)
         self.ctx = pic_create(self.grid, self.dx, dt, l, scheme, opt)
         self.nbytes = pic_footprint(self.ctx)
         self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)

@@ -367,15 +367,19 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
         nodes *= rd.reg[a];
     }
     rd.reg_nodes = nodes;
-    // Tile order.  The FP32 form sums a warp's currents in registers when the warp's particles
-    // sit in at most three neighbouring cells: cell-major order gives that when a cell holds
-    // about a warp of particles of a species or more.  Otherwise (and in the FP64 form, which
-    // deposits per lane) the slot-major order puts the lanes of a warp in different cells.
+    // Tile order.  The FP32 form sums the currents of a warp's lanes through shared memory when
+    // their windows lie in a few neighbouring cells of a row: cell-major order gives that, and
+    // measured on a GB300 it is the faster one from about 6 particles of a species per cell up
+    // (1024x512, cubic: 16 per cell 9.0 vs 7.7, 64 per cell 14.9 vs 8.9 G particle-steps/s);
+    // below that (and in the FP64 form, which deposits per lane) the slot-major order puts the
+    // lanes of a warp in different cells for per-lane shared atomics.
     {
         int64_t capmax = 0;
         for (int s = 0; s < o.n_species; ++s) capmax = std::max(capmax, (int64_t)o.capacity[s]);
-        const bool dense = rd.ncell > 0 && capmax >= 24 * rd.ncell;
-        rd.slot_major = (rd.prec == PIC_FP32_MIXED && dense) ? 0 : 1;
+        const bool dense = rd.ncell > 0 && capmax >= 6 * rd.ncell;
+        if (o.tile_order < PIC_ORDER_AUTO || o.tile_order > PIC_ORDER_SLOT) { delete c; return PIC_EINVAL; }
+        const bool cell = o.tile_order == PIC_ORDER_AUTO ? dense : o.tile_order == PIC_ORDER_CELL;
+        rd.slot_major = (rd.prec == PIC_FP32_MIXED && cell) ? 0 : 1;
     }
     rd.nsp = o.n_species;
     for (int s = 0; s < o.n_species; ++s) {
