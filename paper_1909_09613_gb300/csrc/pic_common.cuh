@@ -212,6 +212,15 @@ __device__ __forceinline__ int wrap_idx(int i, int n)
     return i < 0 ? i + n : i;
 }
 
+// wrap_idx for indices usually within one period of [0, n) (a compare and an add; the
+// remainder only when that is not enough).
+__device__ __forceinline__ int wrap_near(int i, int n)
+{
+    if (i < 0) i += n;
+    else if (i >= n) i -= n;
+    return (i < 0 || i >= n) ? wrap_idx(i, n) : i;
+}
+
 __device__ __forceinline__ void set_err(int32_t *err, int bit)
 {
     if (err) atomicOr(err, bit);

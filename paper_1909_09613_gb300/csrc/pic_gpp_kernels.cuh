@@ -181,10 +181,44 @@ __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int j
     }
 }
 
+// One lane's Esirkepov window added straight to the global FP64 current (FP64 form).  The
+// reductions (red.global.add.f64) are performed by L2, so unlike shared-memory FP64 atomics
+// (compare-and-swap loops around a DADD) they take no issue slots of the SM's FP64 pipe, which
+// bounds this form.  gx0, gy0: global node of the window's first column and row (unwrapped).
+template <int L, typename Hot>
+__device__ __forceinline__ void deposit_lane_global(const Hot &h, int gx0, int gy0, double kx,
+                                                    double ky, double kz, const double *px,
+                                                    const double *py, const double *Ax,
+                                                    const double *Ay, const double *Bx,
+                                                    const AxisS<L, double> &Sy)
+{
+    int gx[L + 2];
+    int64_t gy[L + 2];
+#pragma unroll
+    for (int k = 0; k < L + 2; ++k) {
+        gx[k] = wrap_near(gx0 + k, h.n0);
+        gy[k] = (int64_t)wrap_near(gy0 + k, h.n1) * h.n0;
+    }
+#pragma unroll
+    for (int b = 0; b < L + 2; ++b) {
+        const double ayk = kx * Ay[b];
+        const double pyk = (b <= L) ? ky * py[b] : 0.0;
+        const double zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
+#pragma unroll
+        for (int a = 0; a < L + 2; ++a) {
+            const int64_t g = gy[b] + gx[a];
+            if (a <= L) atomicAdd(h.J0 + g, ayk * px[a]);
+            if (b <= L) atomicAdd(h.J1 + g, pyk * Ax[a]);
+            atomicAdd(h.J2 + g, zs * Ax[a] + zd * Bx[a]);
+        }
+    }
+}
+
 // Scalars the particle loop uses, held in registers for the whole tile (a run descriptor in
 // shared or global memory would be re-read for every particle).
 struct Hot2D {
     int n0, n1, tile0, tile1, drift0, drift1, pre0, pre1, RX, RY, slot_major;
+    double *J0, *J1, *J2;  // global FP64 current
     double dtt0, dtt1;
     uint64_t dm;  // division by n0 (FastDiv)
     int ds;
@@ -207,6 +241,7 @@ __device__ __forceinline__ Hot2D make_hot2d(const RunDev &rd)
     h.pre0 = rd.pre[0]; h.pre1 = rd.pre[1];
     h.RX = rd.reg[0];
     h.RY = rd.reg[1];
+    h.J0 = rd.F[6]; h.J1 = rd.F[7]; h.J2 = rd.F[8];
     h.slot_major = rd.slot_major;
     h.dtt0 = rd.dtt[0]; h.dtt1 = rd.dtt[1];
     h.dm = rd.div_n0.m; h.ds = rd.div_n0.s;
@@ -512,7 +547,8 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         }
         }
     } else if (act) {
-        deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+        deposit_lane_global<L>(h, x0 - h.pre0 + jx0, y0 - h.pre1 + jy0, kx, ky, kz, px, py, Ax,
+                               Ay, Bx, Sy);
     }
     if (!act) return;
 
@@ -552,9 +588,11 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile)
             if (p + blockDim.x < b) prefetch_particle<R>(hs, p + blockDim.x);
             particle_2d<L, KT, R>(h, hs, st, p, p < b, x0, y0);
         }
-        __syncthreads();
-        stage2d_flush<R>(rd, st, x0, y0);
-        __syncthreads();
+        if constexpr (sizeof(R) == 4) {  // the FP64 form deposits to global memory directly
+            __syncthreads();
+            stage2d_flush<R>(rd, st, x0, y0);
+            __syncthreads();
+        }
     }
 }
 
