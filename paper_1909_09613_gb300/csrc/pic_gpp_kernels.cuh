@@ -185,12 +185,11 @@ __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int j
 // reductions (red.global.add.f64) are performed by L2, so unlike shared-memory FP64 atomics
 // (compare-and-swap loops around a DADD) they take no issue slots of the SM's FP64 pipe, which
 // bounds this form.  gx0, gy0: global node of the window's first column and row (unwrapped).
-template <int L, typename Hot>
-__device__ __forceinline__ void deposit_lane_global(const Hot &h, int gx0, int gy0, double kx,
-                                                    double ky, double kz, const double *px,
-                                                    const double *py, const double *Ax,
-                                                    const double *Ay, const double *Bx,
-                                                    const AxisS<L, double> &Sy)
+template <int L, typename R, typename Hot>
+__device__ __forceinline__ void deposit_lane_global(const Hot &h, int gx0, int gy0, R kx, R ky,
+                                                    R kz, const R *px, const R *py, const R *Ax,
+                                                    const R *Ay, const R *Bx,
+                                                    const AxisS<L, R> &Sy)
 {
     int gx[L + 2];
     int64_t gy[L + 2];
@@ -201,15 +200,15 @@ __device__ __forceinline__ void deposit_lane_global(const Hot &h, int gx0, int g
     }
 #pragma unroll
     for (int b = 0; b < L + 2; ++b) {
-        const double ayk = kx * Ay[b];
-        const double pyk = (b <= L) ? ky * py[b] : 0.0;
-        const double zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
+        const R ayk = kx * Ay[b];
+        const R pyk = (b <= L) ? ky * py[b] : R(0);
+        const R zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
 #pragma unroll
         for (int a = 0; a < L + 2; ++a) {
             const int64_t g = gy[b] + gx[a];
-            if (a <= L) atomicAdd(h.J0 + g, ayk * px[a]);
-            if (b <= L) atomicAdd(h.J1 + g, pyk * Ax[a]);
-            atomicAdd(h.J2 + g, zs * Ax[a] + zd * Bx[a]);
+            if (a <= L) atomicAdd(h.J0 + g, (double)(ayk * px[a]));
+            if (b <= L) atomicAdd(h.J1 + g, (double)(pyk * Ax[a]));
+            atomicAdd(h.J2 + g, (double)(zs * Ax[a] + zd * Bx[a]));
         }
     }
 }
@@ -433,6 +432,8 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         // lanes in different cells).
         using FR = DepFrame<L>;
         if (h.slot_major) {  // lanes in different cells: per-lane atomics do not collide
+            // (shared-memory CAS atomics: measured faster here than global FP64 reductions,
+            // which would need an FP32 -> FP64 conversion per node)
             if (act) deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
         } else {
         float *rec = st.rec + (threadIdx.x >> 5) * (32 * FR::RS);
@@ -547,8 +548,8 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         }
         }
     } else if (act) {
-        deposit_lane_global<L>(h, x0 - h.pre0 + jx0, y0 - h.pre1 + jy0, kx, ky, kz, px, py, Ax,
-                               Ay, Bx, Sy);
+        deposit_lane_global<L, R>(h, x0 - h.pre0 + jx0, y0 - h.pre1 + jy0, kx, ky, kz, px, py,
+                                  Ax, Ay, Bx, Sy);
     }
     if (!act) return;
 
