@@ -144,13 +144,22 @@ def _barrier(dist_on):
 
 
 def _max_over_ranks(v, dist_on):
+    """Largest value over the ranks (the slowest replica's time); NCCL on the GPUs, or gloo on
+    the host."""
     if not dist_on:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rate(particles_per_rank, world, steps, ms_max):
+    """Whole-job particle-steps/s of `world` independent replicas that each advance
+    `particles_per_rank` particles `steps` steps, the slowest taking ms_max milliseconds."""
+    return particles_per_rank * world * steps / (ms_max * 1e-3)
 
 
 def time_form(wl, prec, steps, warmup, dist_on, clocks=True):
@@ -527,7 +536,7 @@ def main():
     res = time_form(wl, pic.PIC_FP64, args.steps, args.warmup, dist_on)
     run64 = res.pop("run")
     n_all = res["n"] * world
-    value = n_all * args.steps / (res["ms"] * 1e-3)
+    value = replica_rate(res["n"], world, args.steps, res["ms"])
     gpp_avg_s = res["gpp_ms"] / max(res["gpp_launches"], 1) * 1e-3
     peaks, peak_kind = _peaks()
     pb, gb = BYTES["fp64"]
@@ -588,7 +597,7 @@ def main():
         ab = r32["n"] * pb + r32["ncell"] * gb
         ach = ab / g32 / 1e9
         line["precision_form"] = {
-            "value": r32["n"] * world * args.steps / (r32["ms"] * 1e-3), "unit": UNIT,
+            "value": replica_rate(r32["n"], world, args.steps, r32["ms"]), "unit": UNIT,
             "ms_per_step": r32["ms"] / args.steps, "dtype": "f32 (FP64 fields)",
             "gpp_particle_steps_per_s": r32["n"] / g32,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -265,6 +265,38 @@ def test_empty_and_single_particle():
     run.close()
 
 
+@pytest.mark.parametrize("l", [1, 2, 3, 4])
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("grid", [(8, 8), (6, 6, 6)])
+def test_tiny_runs_ten_steps(grid, scheme, l):
+    """Brute-force-sized whole runs: 1-4 particles per species on an 8x8 (or 6x6x6) periodic grid
+    whose staged region wraps onto itself, 10 full steps of the FP64 form against the oracle."""
+    rng = np.random.default_rng(1000 + 10 * l + scheme + len(grid))
+    dim = len(grid)
+    dt = 0.35 if dim == 2 else 0.3
+    run = pic.Run(grid, (1.0,) * dim, dt, l, scheme, capacity=(4, 3))
+    orc = oracle.Sim(grid, (1.0,) * dim, dt, l, scheme)
+    for sp, (q, n) in enumerate(((-1.0, 4), (1.0, 3))):
+        x = rng.uniform(0, 1, (dim, n)) * np.array(grid, dtype=float)[:, None]
+        u = rng.normal(0, 1.5, (3, n))
+        run.load(sp, q, 1.0, 0.5, x, u)
+        orc.add_species(q, 1.0, 0.5, x, u)
+    for _ in range(10):
+        run.step(1)
+        orc.step(1)
+    for c in range(9):
+        assert rel(run.field(c), orc.field(c)) < 1e-11, c
+    for sp in range(2):
+        xg, ug, _ = run.particles(sp)
+        xo, uo = orc.particles(sp)
+        # both are in the store order of their own sort: compare as sets
+        kg, ko = np.lexsort(xg[::-1]), np.lexsort(xo[::-1])
+        assert np.max(np.abs(xg[:, kg] - xo[:, ko])) < 1e-12
+        assert rel(ug[:, kg], uo[:, ko]) < 1e-11
+    assert run.diag()["error_flags"] == 0
+    run.close()
+
+
 def test_wt_equals_mc_at_half_step_gpu():
     """c dt = dx/2: the WT tables reduce to W_l, so WT and MC steps agree (Sec. 2)."""
     outs = []

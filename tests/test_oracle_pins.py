@@ -270,6 +270,29 @@ def test_boris_exb_drift():
     assert abs(vmean[1]) < 2e-3 * ey / bz
 
 
+def test_boris_rotation_is_second_order():
+    """Pure B: the Boris rotation per step is 2 atan(q B dt / (2 m gamma)) (tan half-angle
+    form), so over a fixed time T the phase error against the exact (q B / (m gamma)) T
+    shrinks 4x when dt halves (second order), and |u| is kept exactly."""
+    qm, bz, T = -1.0, 2.0, 3.0
+    u0 = np.array([0.8, 0.0, 0.3])
+    g = math.sqrt(1 + (u0 ** 2).sum())
+    exact = abs(qm) * bz / g * T
+    errs = []
+    for n in (40, 80, 160):
+        dt = T / n
+        u = u0.copy()
+        ang = 0.0
+        for _ in range(n):
+            un = oracle.boris(qm * dt, [0, 0, 0], [0, 0, bz], u)
+            d = math.atan2(un[1], un[0]) - math.atan2(u[1], u[0])
+            ang += (d + math.pi) % (2 * math.pi) - math.pi
+            u = un
+        assert abs(np.linalg.norm(u) - np.linalg.norm(u0)) < 1e-13
+        errs.append(abs(abs(ang) - exact))
+    assert 3.8 < errs[0] / errs[1] < 4.2 and 3.8 < errs[1] / errs[2] < 4.2
+
+
 # ------------------------------------------------------------------------------------------
 # Esirkepov deposit
 # ------------------------------------------------------------------------------------------
@@ -368,6 +391,26 @@ def test_yee_vacuum_dispersion(grid, dx, cdt, comp, m):
         s.yee_b(0.5 * cdt)
     e = s.field(comp)
     assert np.max(np.abs(e - math.cos(nsteps * w * cdt) * e0)) < 1e-12
+
+
+@pytest.mark.parametrize("solver", [oracle.YEE, oracle.M4])
+def test_vacuum_field_energy_stays_bounded(solver):
+    """No particles, random initial E and B: the leapfrog conserves a discrete energy, so the
+    field energy 1/2 sum (E^2 + B^2) V_c only oscillates -- no growth over 3000 steps at
+    c dt = 0.6 dx (below the Courant limit of App. C for both stencils)."""
+    grid = (24, 20)
+    s = oracle.Sim(grid, (1.0, 1.0), 0.6, 2, MC, solver=solver)
+    rng = np.random.default_rng(11)
+    for c in range(6):
+        s.set_field(c, rng.standard_normal((1, grid[1], grid[0])))
+    u = []
+    for _ in range(30):
+        s.step(100)
+        u.append(s.diag()["field_energy"])
+    u = np.array(u)
+    assert u.max() < 1.2 * u[0] and u.min() > 0.8 * u[0]
+    # no trend: the last third averages like the first
+    assert abs(u[20:].mean() / u[:10].mean() - 1.0) < 0.05
 
 
 def _m4_A(k, dx, cdt):
