@@ -47,3 +47,22 @@ def test_table1_short_scan_wt_suppresses_nci():
     _, a = out[(MC, 0.5)]
     _, b = out[(WT, 0.5)]
     assert np.max(np.abs(a[1:] - b[1:]) / b[1:]) < 1e-3
+
+
+def test_table1_fp32_matches_fp64_at_gamma_1000():
+    """The precision form in the Table 1 regime (gamma0 = 1000, kT = 0.01, quartic): E/E0 of
+    the FP32 form against the plain FP64 form over 40 / omega_pe on a 128x64 section (32 per
+    cell), for the unstable MC4 run and the suppressed WT4 run (same seeded plasma)."""
+    only = {(MC, YEE, 1), (WT, YEE, 1)}
+    out = {}
+    for prec in (pic.PIC_FP64, pic.PIC_FP32_MIXED):
+        reqs = engine.table1_requests(40.0, 2.0, only=only, grid=(128, 64, 1), ppc=32,
+                                      precision=prec)
+        for s, q in zip(sorted(engine.Server(chunk=64).serve(reqs), key=lambda r: r.rid), reqs):
+            out[(prec, q.scheme)] = _ratio(s)[1]
+    for scheme in (MC, WT):
+        a, b = out[(pic.PIC_FP32_MIXED, scheme)], out[(pic.PIC_FP64, scheme)]
+        err = np.max(np.abs(a[1:] - b[1:]) / b[1:])
+        print("scheme", scheme, "max relative E/E0 difference FP32 vs FP64: %.2e" % err)
+        assert err < 1e-2
+    assert out[(pic.PIC_FP64, MC)][-1] > 1e2 * out[(pic.PIC_FP64, WT)][-1]
