@@ -106,3 +106,66 @@ def test_batch_graph_replay_and_timing():
     for r in runs:
         assert r.diag()["error_flags"] == 0
     b.close()
+
+
+def test_batch_full_scale_sampled_particles():
+    """The batched configuration at its benchmark size (256 uneven runs, 184,721,408 particles,
+    one persistent kernel per step): after 3 batched steps, one more; sampled particles of 12
+    runs (no sort due in that step) checked one by one against the oracle push from the run's
+    fields, and on every run the charge is unchanged and D.E - rho conserved."""
+    import workloads
+    from paper_1909_09613_gb300 import engine
+    specs = workloads.batched_runs(256)
+    reqs = [engine.Request(rid=i, grid=sp["grid"], dt=sp["dt"], l=sp["l"], gamma=sp["gamma"],
+                           u_th=sp["u_th"], ppc=sp["ppc"], steps=sp["steps"],
+                           seed=workloads.BASE_SEED) for i, sp in enumerate(specs)]
+    runs = [engine.make_run(r) for r in reqs]
+    assert sum(r.counts[0] + r.counts[1] for r in runs) == 184721408
+    b = pic.Batch(runs)
+    b.step(3)
+    b.sync()
+    d0 = [r.diag() for r in runs]
+    rng = np.random.default_rng(44)
+    # runs whose 4th step does not sort (their particle order is unchanged by it)
+    cand = [i for i, r in enumerate(runs) if r.sort_interval >= 5]
+    pick = sorted(rng.choice(cand, 12, replace=False).tolist())
+    snap = {}
+    for i in pick:
+        r, q = runs[i], reqs[i]
+        orc = oracle.Sim(r.grid[:2], (1.0, 1.0), q.dt, q.l, q.scheme)
+        for c in range(6):
+            orc.set_field(c, r.field(c))
+        parts = []
+        for s in range(2):
+            x, u, _ = r.particles(s)
+            idx = rng.choice(x.shape[1], 40, replace=False)
+            parts.append((idx, x[:, idx].copy(), u[:, idx].copy()))
+        snap[i] = (orc, parts)
+    b.step(1)
+    b.sync()
+    for i in pick:
+        r = runs[i]
+        orc, parts = snap[i]
+        L = np.array([r.grid[0], r.grid[1]], dtype=float)
+        for s, (q, m) in enumerate(((-1.0, 1.0), (1.0, 1.0))):
+            idx, xb, ub = parts[s]
+            x, u, _ = r.particles(s)
+            xg, ug = x[:, idx], u[:, idx]
+            umax = np.max(np.abs(ug))
+            for k in range(len(idx)):
+                xo, uo = orc.push_particle(q, m, xb[:, k], ub[:, k])
+                assert np.max(np.abs(ug[:, k] - uo)) <= FP32_TOL * umax, (i, s, k)
+                dxy = xg[:, k] - xo
+                dxy -= L * np.round(dxy / L)
+                assert np.max(np.abs(dxy)) <= FP32_TOL * L.max(), (i, s, k)
+        orc.close()
+    for r, q, a in zip(runs, reqs, d0):
+        d = r.diag()
+        assert d["error_flags"] == 0
+        assert d["total_charge"] == a["total_charge"]
+        # charge density of one species: w ppc/2 / V_c = omega_p^2 gamma (omega_p = 1/16)
+        rho_scale = q.gamma / 256.0
+        assert abs(d["max_gauss_residual"] - a["max_gauss_residual"]) <= 1e-4 * rho_scale
+    b.close()
+    for r in runs:
+        r.close()
