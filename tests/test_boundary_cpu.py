@@ -123,19 +123,38 @@ def test_axis_weight_tables_mc_are_bsplines(lib, l):
             assert abs(got - oracle.W(l, delta - (base + k))) < 1e-14
 
 
+def _golden(name):
+    out = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            out[line[0]] = [float(v) for v in line[1:]]
+    return out
+
+
 def test_table1_requests_follow_table_1():
-    """The Table 1 scan: 2 schemes x 2 solvers x 5 time steps, dt / dt_CFL as printed
-    (dt_CFL = dx / (sqrt 2 c)), c dt = dx / 2 exactly for the last one, 256x128 cells, 64 per
-    cell, gamma0 = 1000, quartic, samples aligned with the end of the run."""
+    """The Table 1 scan against the printed parameters (tests/golden/table1_parameters.txt):
+    2 schemes x 2 solvers x 5 time steps, dt / dt_CFL as printed (dt_CFL = dx / (sqrt 2 c)),
+    c dt = dx / 2 exactly for the last one, the printed cells, particles per cell, drift gamma
+    and temperature (Gaussian co-moving spread sqrt(kT/mc^2)), a skin depth of 16 cells (the
+    printed domain over the printed cells), quartic, samples aligned with the end of the run."""
     import math
     from paper_1909_09613_gb300 import engine
+    g = _golden("table1_parameters.txt")
     reqs = engine.table1_requests(50.0, 1.0)
     assert len(reqs) == 20
     ratios = sorted({round(r.dt * math.sqrt(2.0), 12) for r in reqs})
-    assert ratios == [0.1, 0.3, 0.5, 0.7, round(1 / math.sqrt(2.0), 12)]
+    assert ratios == [round(v, 12) for v in g["dt_over_dt_cfl"]]
     assert any(r.dt == 0.5 for r in reqs)
+    cells = tuple(int(v) for v in g["cells"])
+    de_cells = cells[0] / g["domain_skin_depths"][0]
+    assert de_cells == cells[1] / g["domain_skin_depths"][1] == 16.0
+    assert int(g["particles_per_cell"][0]) == 2 * int(g["particles_per_cell_per_species"][0])
     for r in reqs:
-        assert r.grid == (256, 128, 1) and r.ppc == 64 and r.l == 4 and r.gamma == 1000.0
+        assert r.grid == cells + (1,) and r.ppc == int(g["particles_per_cell"][0]) and r.l == 4
+        assert r.gamma == g["drift_lorentz_factor"][0]
+        assert abs(r.u_th - math.sqrt(g["temperature_kT_over_mc2"][0])) < 1e-15
         assert r.steps % r.record_every == 0
         assert r.steps * r.dt / 16.0 >= 50.0           # t in 1/omega_pe, 16 cells per d_e
         assert abs(r.record_every * r.dt / 16.0 - 1.0) < 0.6
