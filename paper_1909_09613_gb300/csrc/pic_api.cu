@@ -330,7 +330,9 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     rd.div_n0 = make_fastdiv(rd.n[0]);
     rd.div_n01 = make_fastdiv(rd.n[0] * rd.n[1]);
     // tiles
-    const int deft[2][3] = {{32, 8, 1}, {8, 4, 4}};
+    // default tiles (measured on the 2048x1024 cubic workload: the FP32 form is 2% faster with
+    // 64x8 than with 32x8, the FP64 form the same with both)
+    const int deft[2][3] = {{rd.prec == PIC_FP32_MIXED ? 64 : 32, 8, 1}, {8, 4, 4}};
     for (int a = 0; a < 3; ++a) {
         int t = o.tile[a] > 0 ? o.tile[a] : deft[dim - 2][a];
         if (a >= dim) t = 1;

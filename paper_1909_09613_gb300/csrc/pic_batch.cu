@@ -34,6 +34,9 @@ bool ctx_bound(const pic_ctx *c);
 namespace {
 
 constexpr int kBlock = 256;
+// elements per thread of the per-particle, per-key and per-cell stages: fewer, fuller blocks
+// (the blocks of runs that are not due for a sort exit at once, and there are many of them)
+constexpr int kPartPer = 8, kKeyPer = 8, kCellPer = 4;
 
 struct RunState {
     int age, interval, due, kt;
@@ -64,8 +67,12 @@ __global__ void __launch_bounds__(kBlock) k_b_zero_cnt(const RunDev *runs, const
     const BlockMap m = bm[blockIdx.x];
     if (!st[m.run].due) return;
     const RunDev &rd = runs[m.run];
-    const int64_t i = (int64_t)m.block * blockDim.x + threadIdx.x;
-    if (i < rd.ntiles * rd.tile[0] * rd.tile[1] * rd.tile[2]) rd.sc.cnt[i] = 0;
+    const int64_t nk = rd.ntiles * rd.tile[0] * rd.tile[1] * rd.tile[2];
+    int32_t *cnt = rd.sc.cnt;
+    for (int k = 0; k < kKeyPer; ++k) {
+        const int64_t i = ((int64_t)m.block * kKeyPer + k) * blockDim.x + threadIdx.x;
+        if (i < nk) cnt[i] = 0;
+    }
 }
 
 __global__ void __launch_bounds__(kBlock) k_b_count(const RunDev *runs, const RunState *st,
@@ -74,8 +81,11 @@ __global__ void __launch_bounds__(kBlock) k_b_count(const RunDev *runs, const Ru
     const BlockMap m = bm[blockIdx.x];
     if (!st[m.run].due) return;
     const RunDev &rd = runs[m.run];
-    const int64_t p = (int64_t)m.block * blockDim.x + threadIdx.x;
-    if (p < rd.sp[s].n) sort_count_one(rd, s, p);
+    const int64_t n = rd.sp[s].n;
+    for (int k = 0; k < kPartPer; ++k) {
+        const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
+        if (p < n) sort_count_one(rd, s, p);
+    }
 }
 
 __global__ void k_b_tile_sum(const RunDev *runs, const RunState *st, const BlockMap *bm)
@@ -107,9 +117,11 @@ __global__ void __launch_bounds__(kBlock) k_b_scatter(const RunDev *runs, const 
     const BlockMap m = bm[blockIdx.x];
     if (!st[m.run].due) return;
     const RunDev &rd = runs[m.run];
-    const int64_t p = (int64_t)m.block * blockDim.x + threadIdx.x;
     const SpeciesDev &sp = rd.sp[s];
-    if (p < sp.n) sort_scatter_one(rd, s, p, sp.pos_alt, sp.mom_alt, sp.cell_alt);
+    for (int k = 0; k < kPartPer; ++k) {
+        const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
+        if (p < sp.n) sort_scatter_one(rd, s, p, sp.pos_alt, sp.mom_alt, sp.cell_alt);
+    }
 }
 
 // the sorted buffers become the current ones
@@ -130,11 +142,14 @@ __global__ void __launch_bounds__(kBlock) k_b_zero_j(const RunDev *runs, const B
 {
     const BlockMap m = bm[blockIdx.x];
     const RunDev &rd = runs[m.run];
-    const int64_t c = (int64_t)m.block * blockDim.x + threadIdx.x;
-    if (c < rd.ncell) {
-        rd.F[6][c] = 0.0;
-        rd.F[7][c] = 0.0;
-        rd.F[8][c] = 0.0;
+    double *j0 = rd.F[6], *j1 = rd.F[7], *j2 = rd.F[8];
+    for (int k = 0; k < kCellPer; ++k) {
+        const int64_t c = ((int64_t)m.block * kCellPer + k) * blockDim.x + threadIdx.x;
+        if (c < rd.ncell) {
+            j0[c] = 0.0;
+            j1[c] = 0.0;
+            j2[c] = 0.0;
+        }
     }
 }
 
@@ -143,16 +158,20 @@ __global__ void __launch_bounds__(kBlock) k_b_yee_b(const RunDev *runs, const Bl
 {
     const BlockMap m = bm[blockIdx.x];
     const RunDev &rd = runs[m.run];
-    const int64_t c = (int64_t)m.block * blockDim.x + threadIdx.x;
-    if (c < rd.ncell) yee_b_cell(rd, c, 0.5 * rd.dt, shadow);
+    for (int k = 0; k < kCellPer; ++k) {
+        const int64_t c = ((int64_t)m.block * kCellPer + k) * blockDim.x + threadIdx.x;
+        if (c < rd.ncell) yee_b_cell(rd, c, 0.5 * rd.dt, shadow);
+    }
 }
 
 __global__ void __launch_bounds__(kBlock) k_b_yee_e(const RunDev *runs, const BlockMap *bm)
 {
     const BlockMap m = bm[blockIdx.x];
     const RunDev &rd = runs[m.run];
-    const int64_t c = (int64_t)m.block * blockDim.x + threadIdx.x;
-    if (c < rd.ncell) yee_e_cell(rd, c, 1);
+    for (int k = 0; k < kCellPer; ++k) {
+        const int64_t c = ((int64_t)m.block * kCellPer + k) * blockDim.x + threadIdx.x;
+        if (c < rd.ncell) yee_e_cell(rd, c, 1);
+    }
 }
 
 // ---- the persistent gather-push-deposit kernel over all runs' tiles ----
@@ -329,9 +348,9 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
         const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
         b->max_tc = std::max(b->max_tc, TC);
         b->smem = std::max(b->smem, stage2d_bytes<float>(rd.reg_nodes, rd.l));
-        for (int s = 0; s < b->nsp; ++s) push_blocks(b->bm_part[s], r, rd.sp[s].n, kBlock);
-        push_blocks(b->bm_cell, r, rd.ncell, kBlock);
-        push_blocks(b->bm_key, r, rd.ntiles * TC, kBlock);
+        for (int s = 0; s < b->nsp; ++s) push_blocks(b->bm_part[s], r, rd.sp[s].n, kBlock * kPartPer);
+        push_blocks(b->bm_cell, r, rd.ncell, kBlock * kCellPer);
+        push_blocks(b->bm_key, r, rd.ntiles * TC, kBlock * kKeyPer);
         for (int64_t t = 0; t < rd.ntiles; ++t) b->bm_tile.push_back({r, (int)t});
         int64_t np = 0;
         for (int s = 0; s < b->nsp; ++s) np += rd.sp[s].n;
