@@ -50,7 +50,7 @@ __device__ __forceinline__ void load_particle(const RunDev &rd, const SpeciesDev
         for (int a = 0; a < DIM; ++a) {
             const double x = __ldg((const double *)sp.pos[a] + p);
             const double f = floor(x);
-            s.c[a] = (int)f;
+            s.c[a] = min(max((int)f, 0), rd.n[a] - 1);  // a non-finite position stays in range
             s.d[a] = x - f;
         }
         if (DIM == 2) s.c[2] = 0;

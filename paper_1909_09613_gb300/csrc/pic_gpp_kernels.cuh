@@ -295,8 +295,9 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
             const double x0v = __ldg((const double *)hs.pos0 + p);
             const double x1v = __ldg((const double *)hs.pos1 + p);
             const double f0 = floor(x0v), f1 = floor(x1v);
-            s.c[0] = (int)f0;
-            s.c[1] = (int)f1;
+            // in [0, n) by construction; the clamp keeps a non-finite position's index valid
+            s.c[0] = min(max((int)f0, 0), h.n0 - 1);
+            s.c[1] = min(max((int)f1, 0), h.n1 - 1);
             s.d[0] = x0v - f0;
             s.d[1] = x1v - f1;
         }

@@ -45,6 +45,10 @@ __device__ __forceinline__ void pack_one(const RunDev &rd, const SpeciesDev &sp,
     double off[3] = {0, 0, 0};
     for (int a = 0; a < rd.dim; ++a) {
         double xi = xp[a] / rd.dx[a];
+        if (!isfinite(xi)) {  // a non-finite input position: flag it, keep the index in range
+            set_err(rd.err, 2);  // PIC_ERR_NONFINITE
+            xi = 0.0;
+        }
         const double N = (double)rd.n[a];
         if (xi >= N) xi -= N;
         if (xi < 0.0) xi += N;
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(kBlock) k_rho(const __grid_constant__ RunDev r
         for (int a = 0; a < rd.dim; ++a) {
             const double xi = ((const double *)sp.pos[a])[p];
             const double f = floor(xi);
-            c[a] = (int)f;
+            c[a] = min(max((int)f, 0), rd.n[a] - 1);  // a non-finite position stays in range
             d[a] = xi - f;
         }
     }

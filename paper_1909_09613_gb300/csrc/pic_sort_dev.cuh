@@ -15,7 +15,9 @@ __device__ __forceinline__ void sort_cell_coords(const RunDev &rd, const Species
         c[2] = cc / (rd.n[0] * rd.n[1]);
     } else {
         c[2] = 0;
-        for (int a = 0; a < rd.dim; ++a) c[a] = (int)floor(((const double *)sp.pos[a])[p]);
+        // positions are kept in [0, n); the clamp only keeps a non-finite one inside the grid
+        for (int a = 0; a < rd.dim; ++a)
+            c[a] = min(max((int)floor(((const double *)sp.pos[a])[p]), 0), rd.n[a] - 1);
     }
 }
 

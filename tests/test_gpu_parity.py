@@ -297,6 +297,26 @@ def test_tiny_runs_ten_steps(grid, scheme, l):
     run.close()
 
 
+@pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
+def test_nonfinite_particle_is_reported(prec):
+    """A particle whose momentum is not finite (made on the host) spreads NaN through its
+    current into the fields; the kernels keep every index in range, pic_diag reports it in
+    error_flags and the next syncing call returns PIC_ENAN."""
+    grid = (16, 8)
+    run = pic.Run(grid, (1.0, 1.0), 0.3, 2, 1, precision=prec, capacity=(8, 1))
+    rng = np.random.default_rng(5)
+    run.load(0, -1.0, 1.0, 0.5, rng.uniform(0, 8, (2, 8)), rng.normal(0, 1, (3, 8)))
+    run.load(1, 1.0, 1.0, 0.5, np.array([[3.5], [2.5]]), np.array([[np.nan], [0.0], [0.0]]))
+    run.step(3)
+    d = run.diag()
+    assert d["status"] == pic.PIC_ENAN
+    assert d["error_flags"] & 2
+    with pytest.raises(pic.PicError) as e:
+        run.sync()
+    assert e.value.status == pic.PIC_ENAN
+    run.close()
+
+
 def test_wt_equals_mc_at_half_step_gpu():
     """c dt = dx/2: the WT tables reduce to W_l, so WT and MC steps agree (Sec. 2)."""
     outs = []
