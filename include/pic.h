@@ -9,7 +9,8 @@
  * relativistic Boris push u^{n-1/2} -> u^{n+1/2} (Sec. 1; equations of motion App. E) -> move
  * x^{n+1} = x^n + dt u/gamma -> Esirkepov charge-conserving current deposit J^{n+1/2} with the
  * B-spline form factor W_l (Sec. 1, Sec. 2 Eq. shape-real) -> periodic Yee update
- * B^{n+1/2}, E^{n+1}, B^{n+1} (Sec. 1 "staggered Yee grid"; App. C with A_i = 1).
+ * B^{n+1/2}, E^{n+1}, B^{n+1} (Sec. 1 "staggered Yee grid"; App. C with A_i = 1, or the M4
+ * modified-Faraday stencil of App. C selected by pic_options.solver).
  *
  * Units are the paper's dimensionless ones (App. E): c = 1, 4 pi absorbed, u = gamma v in units
  * of c, so du/dt = (q/m)(E + v x B), dE/dt = curl B - J, dB/dt = -curl E.
