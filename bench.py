@@ -379,6 +379,36 @@ def table1_form(t_end=300.0, record_dt=1.0, history_path=None, precision="fp32",
             "start": "neutral (e+ at the e- positions)" if colocated else "independent positions"}
 
 
+def form_3d(steps=10, warmup=3):
+    """The 3D path (the served form's 3D requests): a 256x64x64 drifting pair plasma, 8 particles
+    per cell (8,388,608 particles), quadratic WT, c dt = 0.4, gamma 20, in both forms; device-
+    resident inputs, CUDA events around whole steps."""
+    import torch
+    import workloads
+    import paper_1909_09613_gb300 as pic
+    wl = workloads.pair_plasma((256, 64, 64), (1.0, 1.0, 1.0), 0.4, 2, 1, 20.0, 0.01, 8,
+                               device="cuda")
+    caps = [int(s.x.shape[1]) for s in wl.species]
+    out = {"workload": "pair_256x64x64_l2_WT_g20_ppc8_cdt0.4", "particles": sum(caps)}
+    for name, prec in (("fp32", pic.PIC_FP32_MIXED), ("fp64", pic.PIC_FP64)):
+        r = pic.Run(wl.grid, wl.dx, wl.dt, 2, 1, precision=prec, capacity=caps)
+        for i, sp in enumerate(wl.species):
+            r.load(i, sp.q, sp.m, sp.w, sp.x, sp.u)
+        r.step(warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(r.stream)
+        r.step(steps)
+        e1.record(r.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"value": sum(caps) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "tile": list(r.tile), "error_flags": r.diag()["error_flags"]}
+        r.close()
+    return out
+
+
 def served_form(n_req=48, steps=100, budget=150e9, seed=None):
     """Config 5: Poisson stream of NCI-scan requests (90% from the batched distribution, 10%
     3D up to 256x64x64, 8 particles per cell), admitted under a 150 GB budget, served by
@@ -468,6 +498,7 @@ def main():
     ap.add_argument("--runs", type=int, default=256, help="batched form: number of runs")
     ap.add_argument("--max-nx", type=int, default=512, help="batched form: largest grid x")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
     args = ap.parse_args()
     rank, world, local = _rank_env()
 
@@ -614,6 +645,8 @@ def main():
         line["batched_form"] = batched_form(max(args.steps, 10), args.warmup)
     if args.form == "both" and not args.no_served:
         line["served_form"] = served_form()
+    if args.form == "both" and not args.no_3d:
+        line["form_3d"] = form_3d()
 
     if rank == 0 and not args.no_cpu:
         rate, sample = cpu_baseline(wl)
