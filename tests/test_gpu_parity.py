@@ -317,6 +317,45 @@ def test_nonfinite_particle_is_reported(prec):
     run.close()
 
 
+def test_diagnostics_match_oracle_and_keep_total_energy():
+    """pic_diag on the Langmuir oscillation of the oracle's energy pin (quiet neutral pair
+    plasma, dx = 0.5): field energy, kinetic energy, charge and the Gauss residual follow the
+    oracle's (FP64 form; 1e-9 over the 440 steps: round-off grows about linearly in this
+    non-chaotic oscillation, 2e-12 after 40 steps), and in both forms the total energy stays
+    within 5% of the energy the oscillation exchanges."""
+    import test_oracle_pins as pins
+    grid, dx, dt = (32, 2), (0.5, 0.5), 0.1
+    x, ue, up, w = pins._langmuir(grid, dx, dt, 0.2, 0.01)
+    orc = oracle.Sim(grid, dx, dt, 2, 0)
+    orc.add_species(-1.0, 1.0, w, x, ue)
+    orc.add_species(1.0, 1.0, w, x, up)
+    runs = {}
+    for prec in (pic.PIC_FP64, pic.PIC_FP32_MIXED):
+        r = pic.Run(grid, dx, dt, 2, 0, precision=prec, capacity=(x.shape[1], x.shape[1]))
+        r.load(0, -1.0, 1.0, w, x, ue)
+        r.load(1, 1.0, 1.0, w, x, up)
+        runs[prec] = (r, [], [])
+    for it in range(110):
+        orc.step(4)
+        do = orc.diag()
+        for prec, (r, ke, fe) in runs.items():
+            r.step(4)
+            d = r.diag()
+            assert d["error_flags"] == 0
+            ke.append(d["kinetic_energy"])
+            fe.append(d["field_energy"])
+            if prec == pic.PIC_FP64 and it % 10 == 9:
+                for key in ("field_energy", "kinetic_energy", "total_charge"):
+                    assert abs(d[key] - do[key]) <= 1e-9 * max(abs(do[key]), 1e-300), key
+                assert abs(d["max_gauss_residual"] - do["max_gauss_residual"]) <= 1e-9 * abs(w) / 0.25
+    for prec, (r, ke, fe) in runs.items():
+        ke, fe = np.array(ke), np.array(fe)
+        total = ke + fe
+        assert np.max(np.abs(total - total[0])) < 0.05 * (ke.max() - ke.min()), prec
+        r.close()
+    orc.close()
+
+
 def test_wt_equals_mc_at_half_step_gpu():
     """c dt = dx/2: the WT tables reduce to W_l, so WT and MC steps agree (Sec. 2)."""
     outs = []

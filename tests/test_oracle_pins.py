@@ -617,3 +617,47 @@ def test_wt_removes_lowest_order_nci_any_dt(l):
     k1, k2 = 1.1, 0.7
     assert abs(_nci_factor(MC, k1, 1, k2, l, 1.0, 0.5)) < 1e-12
     assert abs(_nci_factor(MC, k1, 1, k2, l, 1.0, 0.35)) > 1e-4
+
+
+# ------------------------------------------------------------------------------------------
+# Diagnostics: the energy normalisations agree with the equations of motion (App. E units)
+# ------------------------------------------------------------------------------------------
+
+def _langmuir(grid, dx, dt, wp, delta):
+    """Neutral cold pair plasma on a quiet lattice (4 x 4 per cell and species); the electrons
+    carry a velocity perturbation u_x = delta sin(k x) of the longest mode along x."""
+    per = 16
+    vc = dx[0] * dx[1]
+    w = wp * wp * vc / per
+    sub = (np.arange(4) + 0.5) / 4.0
+    cx, cy, ox, oy = np.meshgrid(np.arange(grid[0]), np.arange(grid[1]), sub, sub, indexing="ij")
+    x = np.vstack([((cx + ox) * dx[0]).ravel(), ((cy + oy) * dx[1]).ravel()])
+    k = 2.0 * math.pi / (grid[0] * dx[0])
+    ue = np.zeros((3, x.shape[1]))
+    ue[0] = delta * np.sin(k * x[0])
+    return x, ue, np.zeros_like(ue), w
+
+
+def test_energy_exchange_keeps_total_energy():
+    """A Langmuir oscillation moves energy between the particles, sum w m (gamma - 1), and the
+    field, 1/2 sum (E^2 + B^2) V_c; with both normalised as the equations of motion imply, their
+    sum stays constant to the leapfrog's phase offset (kinetic energy at t^(n-1/2), fields at
+    t^n: O(omega dt) of the exchanged amount).  dx != 1 so that a missing cell volume shows."""
+    grid, dx = (32, 2), (0.5, 0.5)
+    wp, dt = 0.2, 0.1                      # omega_p dt = 0.02 per species
+    x, ue, up, w = _langmuir(grid, dx, dt, wp, 0.01)
+    s = oracle.Sim(grid, dx, dt, 2, MC)
+    s.add_species(-1.0, 1.0, w, x, ue)
+    s.add_species(1.0, 1.0, w, x, up)
+    ke, fe = [], []
+    for _ in range(220):                  # about two periods of sqrt(2) omega_p
+        s.step(2)
+        d = s.diag()
+        ke.append(d["kinetic_energy"])
+        fe.append(d["field_energy"])
+    ke, fe = np.array(ke), np.array(fe)
+    total = ke + fe
+    swing = ke.max() - ke.min()
+    assert fe.max() > 0.5 * ke.max()       # the energy does go into the field and back
+    assert np.max(np.abs(total - total[0])) < 0.05 * swing
+    s.close()
