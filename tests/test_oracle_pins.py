@@ -661,3 +661,29 @@ def test_energy_exchange_keeps_total_energy():
     assert fe.max() > 0.5 * ke.max()       # the energy does go into the field and back
     assert np.max(np.abs(total - total[0])) < 0.05 * swing
     s.close()
+
+
+def test_langmuir_frequency_is_pair_plasma_frequency():
+    """The same cold Langmuir mode oscillates at omega = sqrt(omega_pe^2 + omega_pp^2) =
+    sqrt(2) omega_p (cold-fluid result, independent of k): the kinetic energy oscillates at twice
+    that.  Measured from the zero crossings over about five periods; within 2% (the B-spline
+    smoothing of the k dx = 0.2 mode and the leapfrog shift it by less than 1%).  A wrong charge,
+    weight or cell-volume factor in the deposit or the gather moves it by sqrt of that factor."""
+    grid, dx, dt, wp = (32, 2), (0.5, 0.5), 0.1, 0.2
+    x, ue, up, w = _langmuir(grid, dx, dt, wp, 0.01)
+    s = oracle.Sim(grid, dx, dt, 2, MC)
+    s.add_species(-1.0, 1.0, w, x, ue)
+    s.add_species(1.0, 1.0, w, x, up)
+    ke = []
+    for _ in range(560):
+        s.step(2)
+        ke.append(s.diag()["kinetic_energy"])
+    s.close()
+    ke = np.array(ke) - np.mean(ke)
+    t = 2 * dt * (np.arange(len(ke)) + 1)
+    idx = np.nonzero(np.diff(np.sign(ke)) != 0)[0]
+    # linear interpolation of the crossings; consecutive crossings are half a period of ke apart
+    tc = t[idx] - ke[idx] * (t[idx + 1] - t[idx]) / (ke[idx + 1] - ke[idx])
+    half = np.mean(np.diff(tc))
+    omega = 2 * math.pi / (2 * half) / 2      # ke oscillates at 2 omega
+    assert abs(omega / (math.sqrt(2.0) * wp) - 1.0) < 0.02, omega
