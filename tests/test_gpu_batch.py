@@ -24,11 +24,12 @@ def rel(a, b):
     return float(np.max(np.abs(a - b)) / den) if den > 0 else float(np.max(np.abs(a)))
 
 
-def make(spec):
+def make(spec, solver=pic.PIC_SOLVER_YEE):
     grid, cdt, l, ppc, gamma, seed = spec
     wl = workloads.pair_plasma(grid, (1.0, 1.0), cdt, l, 1, gamma, 0.01, ppc, seed=seed)
     caps = [int(s.x.shape[1]) for s in wl.species]
-    run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=pic.PIC_FP32_MIXED, capacity=caps)
+    run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=pic.PIC_FP32_MIXED, capacity=caps,
+                  solver=solver)
     for i, s in enumerate(wl.species):
         run.load(i, s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
     rng = np.random.default_rng(seed)
@@ -63,6 +64,31 @@ def test_batch_matches_runs_alone():
             assert np.array_equal(np.sort(ca), np.sort(cb)) or rel(np.sort(xb, axis=1), np.sort(xa, axis=1)) < 1e-5
     b.close()
     for r in alone + batched:
+        r.close()
+
+
+def test_batch_mixed_solvers_match_runs_alone():
+    """Runs with the M4 modified-Faraday stencil (App. C) and with Yee in one batch: the
+    batched Yee launches take each run's stencil from its descriptor, so every run evolves as
+    it does alone, and the M4 runs differ from the same runs under Yee."""
+    specs = RUNS[:4]
+    solvers = [pic.PIC_SOLVER_M4, pic.PIC_SOLVER_YEE, pic.PIC_SOLVER_M4, pic.PIC_SOLVER_YEE]
+    alone = [make(sp, so)[1] for sp, so in zip(specs, solvers)]
+    for r in alone:
+        r.step(12)
+    batched = [make(sp, so)[1] for sp, so in zip(specs, solvers)]
+    b = pic.Batch(batched)
+    b.step(12)
+    b.sync()
+    yee0 = make(specs[0])[1]
+    yee0.step(12)
+    for ra, rb in zip(alone, batched):
+        for c in range(9):
+            assert rel(rb.field(c), ra.field(c)) < 1e-4, c
+        assert rb.diag()["error_flags"] == 0
+    assert rel(batched[0].field(5), yee0.field(5)) > 1e-3   # the stencil really differs
+    b.close()
+    for r in alone + batched + [yee0]:
         r.close()
 
 
