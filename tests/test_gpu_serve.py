@@ -24,9 +24,20 @@ def _requests():
     specs = [((64, 32, 1), 0.35, 2, 8, 10.0, 24, 0.00), ((96, 48, 1), 0.6, 3, 4, 40.0, 18, 0.00),
              ((48, 32, 1), 0.15, 3, 16, 20.0, 30, 0.05), ((24, 16, 16), 0.4, 2, 8, 5.0, 12, 0.05),
              ((128, 64, 1), 0.25, 2, 4, 70.0, 20, 0.10), ((40, 40, 1), 0.5, 3, 8, 15.0, 16, 0.15)]
-    return [engine.Request(rid=i, grid=g, dt=dt, l=l, gamma=gm, u_th=0.01, ppc=ppc, steps=st,
+    reqs = [engine.Request(rid=i, grid=g, dt=dt, l=l, gamma=gm, u_th=0.01, ppc=ppc, steps=st,
                            arrival=arr, seed=100 + i)
             for i, (g, dt, l, ppc, gm, st, arr) in enumerate(specs)]
+    # requests the batch does not take (quartic; the plain FP64 form) step on their own streams;
+    # one batched request uses the M4 solver; two record their field-energy history
+    n = len(reqs)
+    reqs.append(engine.Request(rid=n, grid=(64, 32, 1), dt=0.3, l=4, gamma=20.0, u_th=0.01, ppc=8,
+                               steps=20, arrival=0.02, seed=200, record_every=5))
+    reqs.append(engine.Request(rid=n + 1, grid=(48, 24, 1), dt=0.35, l=3, gamma=30.0, u_th=0.01,
+                               ppc=8, steps=15, arrival=0.05, seed=201,
+                               precision=pic.PIC_FP64, record_every=3))
+    reqs.append(engine.Request(rid=n + 2, grid=(64, 32, 1), dt=0.4, l=2, gamma=25.0, u_th=0.01,
+                               ppc=8, steps=18, arrival=0.0, seed=202, solver=pic.PIC_SOLVER_M4))
+    return reqs
 
 
 def test_served_results_equal_alone():
@@ -41,6 +52,10 @@ def test_served_results_equal_alone():
     assert srv.peak_bytes <= budget
     for r in res:
         assert r.latency >= 0.0 and r.diag["error_flags"] == 0
+        q = reqs[r.rid]
+        if q.record_every:
+            assert [h[0] for h in r.history] == list(range(0, q.steps + 1, q.record_every))
+            assert all(h[3] > 0.0 for h in r.history)
     for req in reqs:
         alone = engine.make_run(req)
         alone.step(req.steps)
