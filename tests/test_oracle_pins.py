@@ -687,3 +687,34 @@ def test_langmuir_frequency_is_pair_plasma_frequency():
     half = np.mean(np.diff(tc))
     omega = 2 * math.pi / (2 * half) / 2      # ke oscillates at 2 omega
     assert abs(omega / (math.sqrt(2.0) * wp) - 1.0) < 0.02, omega
+
+
+@pytest.mark.parametrize("scheme", [MC, WT])
+@pytest.mark.parametrize("grid,dx", [((12, 10), (1.0, 0.8)), ((6, 7, 5), (1.0, 1.2, 0.9))])
+def test_push_particle_in_uniform_fields(grid, dx, scheme):
+    """Uniform E and B on every component's nodes: the interpolation weights sum to one (W_l and
+    T_l alike), so the particle push sees exactly those fields -- the push equals the Boris
+    rotation of the pinned routine followed by x += dt u/gamma, wrapped into the box."""
+    dim = len(grid)
+    dt, q, m = 0.3, -1.0, 1.0
+    s = oracle.Sim(grid, dx, dt, 3, scheme)
+    E = np.array([0.02, -0.05, 0.03])
+    B = np.array([0.4, 0.1, -0.7])
+    shape = (1,) + tuple(grid[::-1]) if dim == 2 else tuple(grid[::-1])
+    for c in range(3):
+        s.set_field(c, np.full(shape, E[c]))
+        s.set_field(3 + c, np.full(shape, B[c]))
+    rng = np.random.default_rng(9)
+    L = np.array(grid, dtype=float) * np.array(dx)
+    for _ in range(20):
+        x = rng.uniform(0, 1, dim) * L
+        u = rng.normal(0, 2, 3)
+        xn, un = s.push_particle(q, m, x, u)
+        ub = oracle.boris(q / m * dt, E, B, u)
+        g = math.sqrt(1 + (ub ** 2).sum())
+        xb = np.mod(x + dt * ub[:dim] / g, L)
+        assert np.max(np.abs(un - ub)) < 1e-13 * max(1.0, np.max(np.abs(ub)))
+        d = xn - xb
+        d -= L * np.round(d / L)
+        assert np.max(np.abs(d)) < 1e-12 * L.max()
+    s.close()
