@@ -88,3 +88,38 @@ def test_nci_growth_fp32_vs_fp64():
     for scheme, (g32, g64) in res.items():
         assert abs(g32 - g64) <= 0.05 * max(abs(g64), g_mc), (scheme, g32, g64)
     assert res[pic.PIC_SCHEME_WT][1] < res[pic.PIC_SCHEME_MC][1]
+
+
+def test_precision_form_error_growth_steps_1_10_100():
+    """Error of the precision form against the plain FP64 form from the same state, on a
+    256x128 section of the large workload (64 per cell, gamma 50, cubic WT, c dt = 0.25): the
+    fields after 1, 10 and 100 steps (max |FP32 - FP64| / max |FP64| per component, worst
+    component).  Step 1 is the parity bar (2e-6); later steps show how the FP32 rounding of
+    the particle state grows (measured on a GB300: 1.6e-6, 1.7e-6, 3.8e-6)."""
+    wl = workloads.config_large(scheme=pic.PIC_SCHEME_WT, device="cuda", scale=8)
+    caps = [int(s.x.shape[1]) for s in wl.species]
+    runs = {}
+    for prec in (pic.PIC_FP64, pic.PIC_FP32_MIXED):
+        r = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps)
+        for i, s in enumerate(wl.species):
+            r.load(i, s.q, s.m, s.w, s.x, s.u)
+        runs[prec] = r
+    errs = {}
+    done = 0
+    for n in (1, 10, 100):
+        for r in runs.values():
+            r.step(n - done)
+        done = n
+        worst = 0.0
+        for c in range(9):
+            a, b = runs[pic.PIC_FP32_MIXED].field(c), runs[pic.PIC_FP64].field(c)
+            worst = max(worst, float(np.max(np.abs(a - b)) / np.max(np.abs(b))))
+        errs[n] = worst
+    print("precision form field error vs FP64: step 1 %.2e, step 10 %.2e, step 100 %.2e"
+          % (errs[1], errs[10], errs[100]))
+    assert errs[1] < 2e-6
+    assert errs[10] < 1e-5
+    assert errs[100] < 1e-4
+    for r in runs.values():
+        assert r.diag()["error_flags"] == 0
+        r.close()
