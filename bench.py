@@ -610,7 +610,11 @@ def main():
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "fp64_fma_peak_tflops": fp64_peak,
-            "gpp_particle_steps_per_s": res["n"] / gpp_avg_s}
+            "gpp_particle_steps_per_s": res["n"] / gpp_avg_s,
+            # per step: the particle kernel (gather + push + deposit) and the rest (Yee, the
+            # tile sort amortised over its interval, clearing the current)
+            "split_ms_per_step": {"gather_push_deposit": gpp_avg_s * 1e3,
+                                  "yee_sort_other": res["ms"] / args.steps - gpp_avg_s * 1e3}}
     if not args.no_e2e:
         try:
             line["e2e"] = e2e_form(run64, wl, args.steps)
@@ -631,6 +635,8 @@ def main():
             "value": replica_rate(r32["n"], world, args.steps, r32["ms"]), "unit": UNIT,
             "ms_per_step": r32["ms"] / args.steps, "dtype": "f32 (FP64 fields)",
             "gpp_particle_steps_per_s": r32["n"] / g32,
+            "split_ms_per_step": {"gather_push_deposit": g32 * 1e3,
+                                  "yee_sort_other": r32["ms"] / args.steps - g32 * 1e3},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": ach / peaks["hbm_gbs"], "traffic": _profile_traffic("gpp2d_fp32"),
                          "kernel": "k_gpp2d<3,4> (float)", "kernel_ms": g32 * 1e3,
