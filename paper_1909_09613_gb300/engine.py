@@ -10,9 +10,12 @@ libpic's kernels (pic_step for a run on its own, pic_batch_step for a batch).
 * `Server` is a continuous-batching request loop: requests (NCI-scan runs: grid, c dt, drift
   gamma, particles per cell) arrive over time, are admitted when the device-memory budget has
   room, stay resident until their last step, and are advanced in chunks of steps -- every 2D
-  run of the FP32 form in one batch (one persistent particle kernel per step), every 3D run on
-  its own stream, all concurrently.  When runs finish or arrive, the batch is rebuilt at the
-  next chunk boundary.  It reports the latency (completion - arrival) of every request.
+  quadratic or cubic run of the FP32 form in one batch (one persistent particle kernel per
+  step), every other run (3D, quartic, plain FP64) on a side stream, all concurrently.  When
+  runs finish or arrive, the batch is rebuilt at the next chunk boundary.  It reports the
+  latency (completion - arrival) of every request and, for requests that ask for it, the
+  field-energy history (E/E0 of the Table 1 scan).
+* `table1_requests` builds the requests of the paper's Table 1 NCI scan.
 """
 from __future__ import annotations
 
@@ -209,7 +212,7 @@ class Server:
         batch = None
         batch_ids: Tuple[int, ...] = ()
         t0 = time.perf_counter()
-        s3d = [torch.cuda.Stream() for _ in range(4)]
+        side = [torch.cuda.Stream() for _ in range(4)]  # runs the batch does not take
         while pending or active:
             now = time.perf_counter() - t0
             # admit arrived requests while the budget has room (arrival order)
@@ -219,7 +222,7 @@ class Server:
                 if used + need > self.budget and active:
                     break
                 pending.pop(0)
-                stream = None if req.batchable else s3d[req.rid % len(s3d)]
+                stream = None if req.batchable else side[req.rid % len(side)]
                 run = make_run(req, tuner=self.tuner, stream=stream)
                 active[req.rid] = {"run": run, "req": req, "done": 0, "bytes": need,
                                    "admitted": time.perf_counter() - t0, "history": []}
