@@ -40,9 +40,14 @@ constexpr int kTileWarps = 8;
 // consecutive lanes fall in distinct banks.
 template <int L>
 struct DepFrame {
-    static constexpr int PX = (L + 2 + 2 + 1) / 2, PY = (L + 2 + 1 + 1) / 2;
+    // Along y the windows of a group start at most SYM rows apart: for odd l a particle's
+    // integer-node window starts at a fixed offset from its cell, so the lanes of one cell row
+    // share it (SYM = 0; a warp straddling the end of a tile row takes a second pass); for even
+    // l the start moves by one with the in-cell offset (SYM = 1).  Along x, up to SXM nodes.
+    static constexpr int SYM = (L % 2 == 0) ? 1 : 0;
+    static constexpr int PX = (L + 2 + 2 + 1) / 2, PY = (L + 2 + SYM + 1) / 2;
     static constexpr int NX = 2 * PX, NY = 2 * PY;
-    static constexpr int SXM = NX - (L + 2), SYM = NY - (L + 2);
+    static constexpr int SXM = NX - (L + 2);
     static constexpr int RS0 = 8 * (PX + PY);
     static constexpr int RS = ((RS0 / 4) % 2 == 0) ? RS0 + 4 : RS0;
     static_assert(2 * PX * PY <= 32, "one lane per 2 x 2 node block and component group");
@@ -458,55 +463,71 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         {
             const int ox = in ? jx0 - mnx : 0, oy = in ? jy0 - mny : 0;
             const R gin = in ? R(1) : R(0);
-            const R gkx = gin * kx;
             __syncwarp();  // the previous pass has read every record
-            // x part: block node A holds this lane's window node A - ox (zero outside it)
+            // x part: block node A holds this lane's window node A - ox (zero outside it); the
+            // factors are scaled first, then shifted by ox = 0..SXM in two steps (ox & 1, ox & 2)
+            R sp[L + 2], sa[L + 2], sb[L + 2];
+            const R gkx = gin * kx;
+#pragma unroll
+            for (int k = 0; k < L + 2; ++k) {
+                sp[k] = (k <= L) ? gkx * px[k] : R(0);
+                sa[k] = gin * Ax[k];
+                sb[k] = gin * Bx[k];
+            }
+            const bool sh1 = (ox & 1) != 0, sh2 = (ox & 2) != 0;
+            R tp[L + 3], ta[L + 3], tb[L + 3];
+#pragma unroll
+            for (int k = 0; k < L + 3; ++k) {
+                const R p0 = (k < L + 2) ? sp[k] : R(0), p1 = (k >= 1) ? sp[k - 1] : R(0);
+                const R a0 = (k < L + 2) ? sa[k] : R(0), a1 = (k >= 1) ? sa[k - 1] : R(0);
+                const R b0 = (k < L + 2) ? sb[k] : R(0), b1 = (k >= 1) ? sb[k - 1] : R(0);
+                tp[k] = sh1 ? p1 : p0;
+                ta[k] = sh1 ? a1 : a0;
+                tb[k] = sh1 ? b1 : b0;
+            }
 #pragma unroll
             for (int pp = 0; pp < FR::PX; ++pp) {
                 R pv[2], av[2], bv[2];
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     const int A = 2 * pp + i;
-                    R p1 = R(0), a1 = R(0), b1 = R(0);
-#pragma unroll
-                    for (int o = 0; o <= FR::SXM; ++o) {
-                        const int k = A - o;
-                        if (k < 0 || k > L + 1) continue;
-                        const bool sel = ox == o;
-                        if (k <= L) p1 = sel ? px[k] : p1;
-                        a1 = sel ? Ax[k] : a1;
-                        b1 = sel ? Bx[k] : b1;
-                    }
-                    pv[i] = gkx * p1;
-                    av[i] = gin * a1;
-                    bv[i] = gin * b1;
+                    const R p0 = (A < L + 3) ? tp[A] : R(0), p2 = (A >= 2 && A - 2 < L + 3) ? tp[A - 2] : R(0);
+                    const R a0 = (A < L + 3) ? ta[A] : R(0), a2 = (A >= 2 && A - 2 < L + 3) ? ta[A - 2] : R(0);
+                    const R b0 = (A < L + 3) ? tb[A] : R(0), b2 = (A >= 2 && A - 2 < L + 3) ? tb[A - 2] : R(0);
+                    pv[i] = sh2 ? p2 : p0;
+                    av[i] = sh2 ? a2 : a0;
+                    bv[i] = sh2 ? b2 : b0;
                 }
                 mine[2 * pp] = make_float4(pv[0], pv[1], av[0], av[1]);
                 mine[2 * pp + 1] = make_float4(av[0], av[1], bv[0], bv[1]);
             }
-            // y part: block node B holds window node B - oy
+            // y part: block node B holds window node B - oy (oy = 0 when SYM = 0)
+            R ty[4][L + 2];  // Ay, ky py, kz S0y, kz DSy
+#pragma unroll
+            for (int k = 0; k < L + 2; ++k) {
+                ty[0][k] = Ay[k];
+                ty[1][k] = (k <= L) ? ky * py[k] : R(0);
+                ty[2][k] = kz * Sy.s0[k];
+                ty[3][k] = kz * Sy.ds[k];
+            }
 #pragma unroll
             for (int qq = 0; qq < FR::PY; ++qq) {
-                R ay[2], pyv[2], s0[2], d0[2];
+                R yv[4][2];
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
                     const int Bn = 2 * qq + i;
-                    R a1 = R(0), p1 = R(0), s1 = R(0), e1 = R(0);
 #pragma unroll
-                    for (int o = 0; o <= FR::SYM; ++o) {
-                        const int k = Bn - o;
-                        if (k < 0 || k > L + 1) continue;
-                        const bool sel = oy == o;
-                        a1 = sel ? Ay[k] : a1;
-                        if (k <= L) p1 = sel ? py[k] : p1;
-                        s1 = sel ? Sy.s0[k] : s1;
-                        e1 = sel ? Sy.ds[k] : e1;
+                    for (int f = 0; f < 4; ++f) {
+                        const R v0 = (Bn <= L + 1) ? ty[f][Bn] : R(0);
+                        if constexpr (FR::SYM == 0) {
+                            yv[f][i] = v0;
+                        } else {
+                            const R v1 = (Bn >= 1 && Bn - 1 <= L + 1) ? ty[f][Bn - 1] : R(0);
+                            yv[f][i] = (oy == 1) ? v1 : v0;
+                        }
                     }
-                    ay[i] = a1;
-                    pyv[i] = ky * p1;
-                    s0[i] = kz * s1;
-                    d0[i] = kz * e1;
                 }
+                R *ay = yv[0], *pyv = yv[1], *s0 = yv[2], *d0 = yv[3];
                 mine[2 * FR::PX + 2 * qq] = make_float4(ay[0], ay[1], pyv[0], pyv[1]);
                 mine[2 * FR::PX + 2 * qq + 1] = make_float4(s0[0], s0[1], d0[0], d0[1]);
             }
