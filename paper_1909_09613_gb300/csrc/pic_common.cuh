@@ -130,12 +130,13 @@ __device__ __forceinline__ void bspline(R p, R *w)
         w[1] = R(0.5) + p * q;
         w[2] = R(0.5) * p * p;
     } else if constexpr (L == 3) {
-        const R s6 = R(1) / R(6);
-        const R p2 = p * p, p3 = p2 * p;
-        w[0] = s6 * q * q * q;
-        w[1] = s6 * (R(3) * p3 - R(6) * p2 + R(4));
-        w[2] = s6 * (R(-3) * p3 + R(3) * p2 + R(3) * p + one);
-        w[3] = s6 * p3;
+        // Horner forms; the third weight from the partition of unity (it is >= 1/6, so the
+        // subtraction loses no relative precision) -- fewer FP64 operations than expanding all
+        const R p2 = p * p;
+        w[0] = (q * q) * (q * R(1.0 / 6.0));
+        w[1] = (R(0.5) * p - one) * p2 + R(2.0 / 3.0);
+        w[3] = p2 * (p * R(1.0 / 6.0));
+        w[2] = one - ((w[0] + w[1]) + w[3]);
     } else {
         const R s24 = R(1) / R(24);
         const R p2 = p * p;
