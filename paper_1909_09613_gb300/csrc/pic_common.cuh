@@ -138,14 +138,16 @@ __device__ __forceinline__ void bspline(R p, R *w)
         w[3] = p2 * (p * R(1.0 / 6.0));
         w[2] = one - ((w[0] + w[1]) + w[3]);
     } else {
-        const R s24 = R(1) / R(24);
+        // Horner forms with the 1/24 folded into the coefficients; the middle weight from the
+        // partition of unity (it is >= 11/24)
         const R p2 = p * p;
         const R q2 = q * q;
-        w[0] = s24 * q2 * q2;
-        w[1] = s24 * ((((R(-4) * p + R(12)) * p - R(6)) * p - R(12)) * p + R(11));
-        w[2] = s24 * ((((R(6) * p - R(12)) * p - R(6)) * p + R(12)) * p + R(11));
-        w[3] = s24 * ((((R(-4) * p + R(4)) * p + R(6)) * p + R(4)) * p + one);
-        w[4] = s24 * p2 * p2;
+        w[0] = q2 * (q2 * R(1.0 / 24.0));
+        w[1] = (((R(-1.0 / 6.0) * p + R(0.5)) * p - R(0.25)) * p - R(0.5)) * p + R(11.0 / 24.0);
+        w[3] = (((R(-1.0 / 6.0) * p + R(1.0 / 6.0)) * p + R(0.25)) * p + R(1.0 / 6.0)) * p
+               + R(1.0 / 24.0);
+        w[4] = p2 * (p2 * R(1.0 / 24.0));
+        w[2] = one - (((w[0] + w[1]) + w[3]) + w[4]);
     }
 }
 

@@ -70,7 +70,16 @@ __device__ __forceinline__ void sort_count_one(const RunDev &rd, int s, int64_t 
     sort_cell_coords(rd, sp, p, c);
     const int key = sort_tile_major_key(rd, c);
     rd.sc.key[p] = key;
-    rd.sc.slot[p] = atomicAdd(rd.sc.cnt + key, 1);
+    // lanes with the same key (neighbours in a sorted store) take consecutive slots from one
+    // atomic of their leader instead of contending for the counter one by one
+    const unsigned act = __activemask();
+    const unsigned same = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(same) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(rd.sc.cnt + key, __popc(same));
+    base = __shfl_sync(same, base, leader);
+    rd.sc.slot[p] = base + __popc(same & ((1u << lane) - 1u));
 }
 
 // 2. particles of tile t (block-wide, one thread per cell of the tile)
