@@ -148,6 +148,23 @@ int pic_load_drifting_plasma(pic_ctx *ctx, int species, double q, double m, doub
                              int64_t per_cell, double gamma, double u_th, uint64_t seed,
                              uint64_t run, int pos_species);
 
+/* Same as pic_load_drifting_plasma with the co-moving momenta drawn from the Juttner-Synge
+ * distribution of temperature theta = kT / (m c^2) (the App. D set-up for relativistically hot
+ * plasmas), by Sobol's method: attempt a of particle p draws X1..X4 uniform on (0, 1] (1 - U
+ * at counter p * 128 + a, stream ids (run, species, 40 + j) for X_{j+1}), sets
+ * u = -theta ln(X1 X2 X3), eta = -theta ln(X1 X2 X3 X4), and accepts the first attempt with
+ * eta^2 - u^2 > 1.  The direction is isotropic: cos = 2 X5 - 1, azimuth 2 pi X6, with X5, X6 at
+ * counter p on ids (run, species, 44) and (run, species, 45).  The flip and boost along x1
+ * follow as in pic_load_drifting_plasma; positions likewise.
+ * theta >= PIC_JUTTNER_MIN_THETA (at 0.3 an attempt is accepted with probability 0.22, so
+ * 128 attempts leave a particle unsampled with probability about 1e-14); else PIC_EINVAL.
+ * A particle with no accepted attempt is loaded at rest in the co-moving frame, sets
+ * PIC_ERR_TIMEOUT and the call returns PIC_ETIMEOUT.  Syncs.                                  */
+#define PIC_JUTTNER_MIN_THETA 0.3
+int pic_load_drifting_juttner(pic_ctx *ctx, int species, double q, double m, double w,
+                              int64_t per_cell, double gamma, double theta, uint64_t seed,
+                              uint64_t run, int pos_species);
+
 /* Set field component comp (0..5 = E1 E2 E3 B1 B2 B3) from count = ncell FP64 host values. */
 int pic_set_fields(pic_ctx *ctx, int comp, const double *host, size_t count);
 

@@ -26,7 +26,9 @@ PIC_SCHEME_MC, PIC_SCHEME_WT = 0, 1
 PIC_FP64, PIC_FP32_MIXED = 0, 1
 PIC_SOLVER_YEE, PIC_SOLVER_M4 = 0, 1
 PIC_ORDER_AUTO, PIC_ORDER_CELL, PIC_ORDER_SLOT = 0, 1, 2
+PIC_ERR_OUTSIDE_TILE, PIC_ERR_NONFINITE, PIC_ERR_TIMEOUT = 1, 2, 4  # diag()["error_flags"] bits
 PIC_MAX_SPECIES = 4
+PIC_JUTTNER_MIN_THETA = 0.3
 
 _c_dp = ctypes.POINTER(ctypes.c_double)
 _c_lp = ctypes.POINTER(ctypes.c_int64)
@@ -71,6 +73,10 @@ _SIGS = [
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                                 ctypes.c_uint64, ctypes.c_int]),
+    ("pic_load_drifting_juttner", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                                 ctypes.c_uint64, ctypes.c_int]),
     ("pic_set_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dp, ctypes.c_size_t]),
     ("pic_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("pic_read_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_dp, ctypes.c_size_t]),
@@ -185,6 +191,15 @@ def pic_load_drifting_plasma(ctx, species, q, m, w, per_cell, gamma, u_th, seed,
                                                    float(u_th), int(seed) & (2**64 - 1),
                                                    int(run) & (2**64 - 1), int(pos_species)),
            "pic_load_drifting_plasma")
+
+
+def pic_load_drifting_juttner(ctx, species, q, m, w, per_cell, gamma, theta, seed, run,
+                              pos_species):
+    _check(load_library().pic_load_drifting_juttner(ctx, int(species), float(q), float(m),
+                                                    float(w), int(per_cell), float(gamma),
+                                                    float(theta), int(seed) & (2**64 - 1),
+                                                    int(run) & (2**64 - 1), int(pos_species)),
+           "pic_load_drifting_juttner")
 
 
 def pic_set_fields(ctx, comp, a: np.ndarray):
@@ -407,6 +422,13 @@ class Run:
         """Generate species `species` on the device (App. D drifting plasma, pic.h)."""
         pic_load_drifting_plasma(self.ctx, species, q, m, w, per_cell, gamma, u_th, seed, run,
                                  species if pos_species is None else pos_species)
+        self.counts[species] = int(np.prod(self.grid)) * int(per_cell)
+
+    def load_drifting_juttner(self, species, q, m, w, per_cell, gamma, theta, seed, run=0,
+                              pos_species=None):
+        """Same with Juttner-Synge co-moving momenta of temperature theta (Sobol's method)."""
+        pic_load_drifting_juttner(self.ctx, species, q, m, w, per_cell, gamma, theta, seed, run,
+                                  species if pos_species is None else pos_species)
         self.counts[species] = int(np.prod(self.grid)) * int(per_cell)
 
     def set_field(self, comp, a):

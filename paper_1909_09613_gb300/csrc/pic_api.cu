@@ -526,14 +526,16 @@ int pic_load_particles_device(pic_ctx *c, int species, double q, double m, doubl
     return load_common(c, species, q, m, w, n, x, u, true);
 }
 
-int pic_load_drifting_plasma(pic_ctx *c, int species, double q, double m, double w,
-                             int64_t per_cell, double gamma, double u_th, uint64_t seed,
-                             uint64_t run, int pos_species)
+// Both drifting-plasma loaders: theta > 0 draws the co-moving momenta from the Juttner-Synge
+// distribution (Sobol's method), else from N(0, u_th^2) per component.
+static int load_drifting(pic_ctx *c, int species, double q, double m, double w, int64_t per_cell,
+                         double gamma, double u_th, double theta, uint64_t seed, uint64_t run,
+                         int pos_species)
 {
     if (!c || !c->base) return c ? PIC_ESTATE : PIC_EINVAL;
     if (species < 0 || species >= c->rd.nsp || pos_species < 0 || per_cell < 0) return PIC_EINVAL;
     if (!(m > 0.0) || !(w >= 0.0) || !(gamma >= 1.0) || !(u_th >= 0.0) || !std::isfinite(gamma)
-        || !std::isfinite(u_th))
+        || !std::isfinite(u_th) || !(theta >= 0.0) || !std::isfinite(theta))
         return PIC_EINVAL;
     if (per_cell > 0 && c->rd.ncell > c->cap[species] / per_cell) return PIC_EINVAL;
     const int64_t n = c->rd.ncell * per_cell;
@@ -545,10 +547,30 @@ int pic_load_drifting_plasma(pic_ctx *c, int species, double q, double m, double
         k.mom[2 * a + 1] = stream_key(seed, run, (uint64_t)species, 21 + 2 * a);
     }
     k.flip = stream_key(seed, run, (uint64_t)species, 30);
-    if (launch_load_plasma(c->rd, species, k, per_cell, gamma, u_th, n, c->stream) != cudaSuccess)
+    for (int j = 0; j < 4; ++j) k.jut[j] = stream_key(seed, run, (uint64_t)species, 40 + j);
+    k.dir[0] = stream_key(seed, run, (uint64_t)species, 44);
+    k.dir[1] = stream_key(seed, run, (uint64_t)species, 45);
+    if (launch_load_plasma(c->rd, species, k, per_cell, gamma, u_th, theta, n, c->stream)
+        != cudaSuccess)
         return PIC_ECUDA;
     if (n > 0) c->kernel_launches += 1;
-    return finish_load(c, species);
+    const int r = finish_load(c, species);
+    return r != PIC_OK ? r : latched_status(c);
+}
+
+int pic_load_drifting_plasma(pic_ctx *c, int species, double q, double m, double w,
+                             int64_t per_cell, double gamma, double u_th, uint64_t seed,
+                             uint64_t run, int pos_species)
+{
+    return load_drifting(c, species, q, m, w, per_cell, gamma, u_th, 0.0, seed, run, pos_species);
+}
+
+int pic_load_drifting_juttner(pic_ctx *c, int species, double q, double m, double w,
+                              int64_t per_cell, double gamma, double theta, uint64_t seed,
+                              uint64_t run, int pos_species)
+{
+    if (!(theta >= PIC_JUTTNER_MIN_THETA)) return PIC_EINVAL;
+    return load_drifting(c, species, q, m, w, per_cell, gamma, 0.0, theta, seed, run, pos_species);
 }
 
 int pic_set_fields(pic_ctx *c, int comp, const double *host, size_t count)

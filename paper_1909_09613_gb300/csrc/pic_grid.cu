@@ -98,6 +98,8 @@ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z)
     return z ^ (z >> 31);
 }
 
+constexpr int kJuttnerAttempts = 128;
+
 __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t ctr)
 {
     return (double)(sm64_mix(ctr * 0x9E3779B97F4A7C15ull + key) >> 11) * (1.0 / 9007199254740992.0);
@@ -105,7 +107,8 @@ __device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t ctr)
 
 __global__ void __launch_bounds__(kBlock) k_load_plasma(const __grid_constant__ RunDev rd, int s,
                                                         LoadKeys keys, int64_t per_cell,
-                                                        double gamma, double u_th, int64_t n)
+                                                        double gamma, double u_th, double theta,
+                                                        int64_t n)
 {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -124,8 +127,38 @@ __global__ void __launch_bounds__(kBlock) k_load_plasma(const __grid_constant__ 
         xp[a] = xa;
     }
     const double beta = sqrt(__dsub_rn(1.0, __ddiv_rn(1.0, __dmul_rn(gamma, gamma))));
-    if (u_th > 0.0) {
+    if (theta > 0.0 || u_th > 0.0) {
         double v[3];
+        if (theta > 0.0) {
+            // Sobol's method: attempt a draws X1..X4 at counter p * kJuttnerAttempts + a;
+            // u = -theta ln(X1 X2 X3), eta = -theta ln(X1 X2 X3 X4), accepted when
+            // eta^2 - u^2 > 1.  The loop is bounded; a particle left without an accepted
+            // attempt (about 1e-14 at theta = 0.3) is flagged and loaded at rest.
+            double um = -1.0;
+            for (int a = 0; a < kJuttnerAttempts && um < 0.0; ++a) {
+                const uint64_t ctr = (uint64_t)p * kJuttnerAttempts + a;
+                const double x1 = __dsub_rn(1.0, sm64_uniform(keys.jut[0], ctr));
+                const double x2 = __dsub_rn(1.0, sm64_uniform(keys.jut[1], ctr));
+                const double x3 = __dsub_rn(1.0, sm64_uniform(keys.jut[2], ctr));
+                const double x4 = __dsub_rn(1.0, sm64_uniform(keys.jut[3], ctr));
+                const double p3 = __dmul_rn(__dmul_rn(x1, x2), x3);
+                const double u = __dmul_rn(-theta, log(p3));
+                const double eta = __dmul_rn(-theta, log(__dmul_rn(p3, x4)));
+                if (__dsub_rn(__dmul_rn(eta, eta), __dmul_rn(u, u)) > 1.0) um = u;
+            }
+            if (um < 0.0) {
+                set_err(rd.err, 4);  // PIC_ERR_TIMEOUT: a bounded device loop gave up
+                um = 0.0;
+            }
+            const double x5 = sm64_uniform(keys.dir[0], (uint64_t)p);
+            const double x6 = sm64_uniform(keys.dir[1], (uint64_t)p);
+            const double ct = __dsub_rn(__dmul_rn(2.0, x5), 1.0);
+            const double st = __dmul_rn(2.0, sqrt(__dmul_rn(x5, __dsub_rn(1.0, x5))));
+            const double ph = __dmul_rn(6.283185307179586, x6);
+            v[0] = __dmul_rn(um, ct);
+            v[1] = __dmul_rn(__dmul_rn(um, st), cos(ph));
+            v[2] = __dmul_rn(__dmul_rn(um, st), sin(ph));
+        } else
         for (int a = 0; a < 3; ++a) {
             const double u1 = __dsub_rn(1.0, sm64_uniform(keys.mom[2 * a], (uint64_t)p));  // (0, 1]
             const double u2 = sm64_uniform(keys.mom[2 * a + 1], (uint64_t)p);
@@ -416,10 +449,10 @@ cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t
 }
 
 cudaError_t launch_load_plasma(const RunDev &rd, int s, const LoadKeys &keys, int64_t per_cell,
-                               double gamma, double u_th, int64_t n, cudaStream_t st)
+                               double gamma, double u_th, double theta, int64_t n, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_load_plasma<<<grid_for(n), kBlock, 0, st>>>(rd, s, keys, per_cell, gamma, u_th, n);
+    k_load_plasma<<<grid_for(n), kBlock, 0, st>>>(rd, s, keys, per_cell, gamma, u_th, theta, n);
     return cudaGetLastError();
 }
 

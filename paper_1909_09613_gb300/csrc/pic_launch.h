@@ -26,9 +26,12 @@ struct LoadKeys {
     uint64_t pos[3];
     uint64_t mom[6];
     uint64_t flip;
+    uint64_t jut[4];  // Sobol's method: the four uniforms of an attempt
+    uint64_t dir[2];  // isotropic direction of a Juttner momentum
 };
+// theta > 0: Juttner-Synge co-moving momenta of temperature theta (u_th unused); else Gaussian
 cudaError_t launch_load_plasma(const RunDev &rd, int s, const LoadKeys &keys, int64_t per_cell,
-                               double gamma, double u_th, int64_t n, cudaStream_t st);
+                               double gamma, double u_th, double theta, int64_t n, cudaStream_t st);
 // particles p0 .. p0 + m - 1 -> x[a * m + i], u[a * m + i], cell[i]
 cudaError_t launch_unpack(const RunDev &rd, int s, double *x, double *u, int64_t *cell,
                           int64_t m, int64_t p0, cudaStream_t st);

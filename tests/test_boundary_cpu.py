@@ -39,6 +39,29 @@ def test_every_declared_symbol_is_exported(lib):
     assert declared <= set(pic.exported_names()) | {"pic_strerror"}
 
 
+def test_binding_constants_match_the_header():
+    txt = open(os.path.join(ROOT, "include", "pic.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    found = {}
+    for name, val in re.findall(r"#define\s+(PIC_[A-Z0-9_]+)\s+([-0-9.]+)\s*$", txt, flags=re.M):
+        found[name] = float(val)
+    for body in re.findall(r"enum\s*\w*\s*\{(.*?)\}", txt, flags=re.S):
+        for name, val in re.findall(r"(PIC_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            found[name] = float(val)
+    assert len(found) > 20
+    for name, val in found.items():
+        assert getattr(pic, name) == val, name
+
+
+def test_juttner_loader_rejects_cold_theta(lib):
+    """Sobol's method needs theta >= 0.3 for its bounded attempts; the check precedes any use
+    of the context, so it is exercised here without a device."""
+    f = lib.pic_load_drifting_juttner
+    for theta in (0.0, 0.29, float("nan"), -1.0):
+        assert f(None, 0, -1.0, 1.0, 1.0, 1, 10.0, theta, 1, 0, 0) == pic.PIC_EINVAL
+    assert f(None, 0, -1.0, 1.0, 1.0, 1, 10.0, 0.5, 1, 0, 0) == pic.PIC_EINVAL  # no context
+
+
 def test_strerror(lib):
     assert pic.pic_strerror(0) == "ok"
     assert "Courant" in pic.pic_strerror(pic.PIC_ECFL)

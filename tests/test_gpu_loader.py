@@ -1,7 +1,9 @@
-"""The drifting-plasma loader on the device (pic_load_drifting_plasma, App. D) against the same
-distribution drawn by the seeded input generator and loaded from arrays: the two implement the
-one counter-based generator (SplitMix64) from its published definition, so cells, offsets and
-the flip decisions must agree exactly, and the Box-Muller momenta to the last bits of log/cos."""
+"""The drifting-plasma loaders on the device (pic_load_drifting_plasma and, for Juttner-Synge
+momenta by Sobol's method, pic_load_drifting_juttner; App. D) against the same distribution
+drawn by the seeded input generator and loaded from arrays: the two implement the one
+counter-based generator (SplitMix64) from its published definition, so cells, offsets, the
+accepted Sobol attempts and the flip decisions must agree exactly, and the momenta to the last
+bits of log/cos/sin."""
 import math
 
 import numpy as np
@@ -20,14 +22,17 @@ CASES = [((48, 20), 2, pic.PIC_FP64, 50.0, 0.01, 6),
          ((12, 8, 6), 2, pic.PIC_FP64, 10.0, 0.05, 4)]
 
 
-def _pair(run_loader, grid, l, prec, gamma, u_th, ppc, colocated):
+def _pair(run_loader, grid, l, prec, gamma, u_th, ppc, colocated, theta=None):
     dx = (1.0,) * len(grid)
     wl = workloads.pair_plasma(grid, dx, 0.3, l, pic.PIC_SCHEME_WT, gamma, u_th, ppc,
-                               device="cuda", seed=77, run=3, colocated=colocated)
+                               device="cuda", seed=77, run=3, colocated=colocated, theta=theta)
     caps = [int(s.x.shape[1]) for s in wl.species]
     r = pic.Run(wl.grid, wl.dx, wl.dt, l, pic.PIC_SCHEME_WT, precision=prec, capacity=caps)
     for i, s in enumerate(wl.species):
-        if run_loader:
+        if run_loader and theta is not None:
+            r.load_drifting_juttner(i, s.q, s.m, s.w, ppc // 2, gamma, theta, seed=77, run=3,
+                                    pos_species=0 if colocated else i)
+        elif run_loader:
             r.load_drifting_plasma(i, s.q, s.m, s.w, ppc // 2, gamma, u_th, seed=77, run=3,
                                    pos_species=0 if colocated else i)
         else:
@@ -35,12 +40,7 @@ def _pair(run_loader, grid, l, prec, gamma, u_th, ppc, colocated):
     return r
 
 
-@pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("colocated", [False, True])
-def test_device_loader_matches_generator(case, colocated):
-    grid, l, prec, gamma, u_th, ppc = case
-    a = _pair(True, grid, l, prec, gamma, u_th, ppc, colocated)
-    b = _pair(False, grid, l, prec, gamma, u_th, ppc, colocated)
+def _same_particles(a, b, prec):
     for s in range(2):
         xa, ua, ca = a.particles(s)
         xb, ub, cb = b.particles(s)
@@ -54,6 +54,15 @@ def test_device_loader_matches_generator(case, colocated):
         # log/cos either way)
         tol = 4e-16 if prec == pic.PIC_FP64 else 1.2e-7
         assert np.max(np.abs(ua - ub)) <= tol * max(1.0, np.max(np.abs(ub)))
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("colocated", [False, True])
+def test_device_loader_matches_generator(case, colocated):
+    grid, l, prec, gamma, u_th, ppc = case
+    a = _pair(True, grid, l, prec, gamma, u_th, ppc, colocated)
+    b = _pair(False, grid, l, prec, gamma, u_th, ppc, colocated)
+    _same_particles(a, b, prec)
     a.step(3)
     b.step(3)
     # same particle sets; the summation order of the current (order within a cell) is not
@@ -104,3 +113,36 @@ def test_device_loader_moments_and_cold_beam():
     with pytest.raises(pic.PicError):
         r.load_drifting_plasma(0, -1.0, 1.0, 1e-3, 2, 0.5, u_th, seed=5)       # gamma < 1
     r.close()
+
+
+JCASES = [((48, 20), 2, pic.PIC_FP64, 50.0, 0.3, 6),
+          ((33, 17), 3, pic.PIC_FP32_MIXED, 1000.0, 1.0, 4),
+          ((12, 8, 6), 2, pic.PIC_FP64, 1.0, 4.0, 4)]
+
+
+@pytest.mark.parametrize("case", JCASES)
+def test_device_juttner_loader_matches_generator(case):
+    grid, l, prec, gamma, theta, ppc = case
+    a = _pair(True, grid, l, prec, gamma, 0.0, ppc, False, theta)
+    b = _pair(False, grid, l, prec, gamma, 0.0, ppc, False, theta)
+    _same_particles(a, b, prec)
+    # at gamma = 1 (no boost, no flip) the loaded |u| is the Sobol speed itself: mean gamma of
+    # the Juttner-Synge distribution is 3 theta + K1(1/theta) / K2(1/theta)
+    if gamma == 1.0:
+        from scipy.special import kve
+        u = np.concatenate([a.particles(s)[1] for s in range(2)], axis=1)
+        g = np.sqrt(1.0 + np.sum(u * u, axis=0))
+        expect = 3.0 * theta + kve(1, 1.0 / theta) / kve(2, 1.0 / theta)
+        assert abs(g.mean() - expect) < 5.0 * g.std() / math.sqrt(g.size)
+    a.step(3)
+    b.step(3)
+    ftol = 1e-12 if prec == pic.PIC_FP64 else 2e-6
+    for c in range(9):
+        fa, fb = a.field(c), b.field(c)
+        den = max(np.max(np.abs(fb)), 1e-300)
+        assert np.max(np.abs(fa - fb)) / den < ftol
+    assert a.diag()["error_flags"] == 0
+    with pytest.raises(pic.PicError):   # below the temperature the bounded sampler supports
+        a.load_drifting_juttner(0, -1.0, 1.0, 1e-3, 1, gamma, 0.2, seed=5)
+    a.close()
+    b.close()

@@ -718,3 +718,32 @@ def test_push_particle_in_uniform_fields(grid, dx, scheme):
         d -= L * np.round(d / L)
         assert np.max(np.abs(d)) < 1e-12 * L.max()
     s.close()
+
+
+@pytest.mark.parametrize("theta", [0.3, 1.0, 4.0])
+def test_juttner_loader_matches_the_distribution(theta):
+    """App. D, Eq. Maxwell-dist-relativistic, sampled with Sobol's method by the seeded input
+    generator: the co-moving |u| follows f(u) ~ u^2 exp(-sqrt(1 + u^2)/theta) (CDF at five
+    sample quantiles against numerical integration), the mean Lorentz factor is the closed form
+    3 theta + K1(1/theta)/K2(1/theta), and the directions are isotropic."""
+    import torch
+    import workloads
+    from scipy import integrate
+    from scipy.special import kn
+    n = 400000
+    keys = [workloads.stream_key(11, 0, 0, 40 + j) for j in range(4)]
+    u = workloads.juttner_speeds(theta, keys, torch.arange(n)).numpy()
+    assert not np.isnan(u).any()
+    g = np.sqrt(1.0 + u * u)
+    expect = 3.0 * theta + kn(1, 1.0 / theta) / kn(2, 1.0 / theta)
+    assert abs(g.mean() - expect) < 4.0 * g.std() / math.sqrt(n)
+    f = lambda x: x * x * math.exp(-(math.sqrt(1.0 + x * x) - 1.0) / theta)
+    z = integrate.quad(f, 0, np.inf, limit=200)[0]
+    for q in (0.1, 0.25, 0.5, 0.75, 0.9):
+        x = np.quantile(u, q)
+        assert abs(integrate.quad(f, 0, x, limit=200)[0] / z - q) < 0.004
+    # a full load at rest (gamma0 = 1): isotropic momenta
+    wl = workloads.pair_plasma((32, 16), (1.0, 1.0), 0.3, 2, 1, 1.0, 0.0, 64, theta=theta)
+    up = wl.species[0].u.numpy()
+    m2 = (up ** 2).mean(axis=1)
+    assert np.max(np.abs(m2 / m2.mean() - 1.0)) < 0.03

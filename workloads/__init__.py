@@ -81,6 +81,35 @@ def normal(key_a: int, key_b: int, counter: torch.Tensor) -> torch.Tensor:
     return torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
 
 
+JUTTNER_ATTEMPTS = 128
+
+
+def juttner_speeds(theta: float, key_x: Sequence[int], counter: torch.Tensor) -> torch.Tensor:
+    """|u'| of the Juttner-Synge distribution f(u) ~ u^2 exp(-sqrt(1 + u^2)/theta) (App. D) by
+    Sobol's rejection method: u = -theta ln(X1 X2 X3), eta = -theta ln(X1 X2 X3 X4), accepted
+    when eta^2 - u^2 > 1.  Attempt a of particle p draws its four uniforms at counter
+    p * JUTTNER_ATTEMPTS + a of the streams key_x[0..3]; the first accepted attempt is taken.
+    Particles with no accepted attempt among JUTTNER_ATTEMPTS get NaN (theta >= 0.3 makes that
+    a ~1e-14 event per particle)."""
+    n = counter.numel()
+    out = torch.full((n,), float("nan"), dtype=torch.float64, device=counter.device)
+    todo = torch.ones(n, dtype=torch.bool, device=counter.device)
+    base = counter.to(torch.int64) * JUTTNER_ATTEMPTS
+    for a in range(JUTTNER_ATTEMPTS):
+        idx = torch.nonzero(todo).flatten()
+        if idx.numel() == 0:
+            break
+        c = base[idx] + a
+        x = [1.0 - uniform(key_x[j], c) for j in range(4)]   # (0, 1]
+        p3 = x[0] * x[1] * x[2]
+        u = -theta * torch.log(p3)
+        eta = -theta * torch.log(p3 * x[3])
+        ok = eta * eta - u * u > 1.0
+        out[idx[ok]] = u[ok]
+        todo[idx[ok]] = False
+    return out
+
+
 @dataclass
 class Species:
     q: float
@@ -121,7 +150,8 @@ class Workload:
 def pair_plasma(grid: Sequence[int], dx: Sequence[float], dt: float, l: int, scheme: int,
                 gamma: float, u_th: float, ppc: int, omega_p: Optional[float] = None,
                 seed: int = BASE_SEED, run: int = 0, device="cpu", steps: int = 0,
-                name: str = "pair_plasma", colocated: bool = False) -> Workload:
+                name: str = "pair_plasma", colocated: bool = False,
+                theta: Optional[float] = None) -> Workload:
     """Drifting e-/e+ pair plasma along x1 (Table 1 set-up), ppc particles per cell in total.
 
     omega_p is the relativistic plasma frequency of each species, omega_p^2 = n q^2/(gamma m)
@@ -131,6 +161,10 @@ def pair_plasma(grid: Sequence[int], dx: Sequence[float], dt: float, l: int, sch
     colocated: the positrons start at the electrons' positions (a neutral start: rho = 0, so
     zero initial fields satisfy Gauss's law); momenta stay independent.  Otherwise every
     species draws its own positions.
+
+    theta: when given, the co-moving momenta follow the Juttner-Synge distribution of
+    temperature theta = kT / mc^2 (App. D, Sobol's method; isotropic directions), instead of
+    the Gaussian of spread u_th.
     """
     grid = tuple(int(g) for g in grid) + (1,) * (3 - len(grid))
     dx = tuple(float(d) for d in dx) + (1.0,) * (3 - len(dx))
@@ -158,10 +192,19 @@ def pair_plasma(grid: Sequence[int], dx: Sequence[float], dt: float, l: int, sch
             xa = torch.where(xa >= L, xa - L, xa)
             xs.append(xa)
         x = torch.stack(xs)
-        if u_th > 0.0:
-            up = torch.stack([u_th * normal(stream_key(seed, run, s, 20 + 2 * a),
-                                            stream_key(seed, run, s, 21 + 2 * a), idx)
-                              for a in range(3)])
+        if theta is not None or u_th > 0.0:
+            if theta is not None:
+                um = juttner_speeds(theta, [stream_key(seed, run, s, 40 + j) for j in range(4)], idx)
+                x5 = uniform(stream_key(seed, run, s, 44), idx)
+                x6 = uniform(stream_key(seed, run, s, 45), idx)
+                ct = 2.0 * x5 - 1.0
+                st = 2.0 * torch.sqrt(x5 * (1.0 - x5))
+                ph = 2.0 * math.pi * x6
+                up = torch.stack([um * ct, um * st * torch.cos(ph), um * st * torch.sin(ph)])
+            else:
+                up = torch.stack([u_th * normal(stream_key(seed, run, s, 20 + 2 * a),
+                                                stream_key(seed, run, s, 21 + 2 * a), idx)
+                                  for a in range(3)])
             e_prime = torch.sqrt(1.0 + (up * up).sum(0))
             x1 = uniform(stream_key(seed, run, s, 30), idx)
             flip = x1 > 0.5 * (1.0 + beta * up[0] / e_prime)
