@@ -151,6 +151,39 @@ __device__ __forceinline__ void bspline(R p, R *w)
     }
 }
 
+// Comparisons of non-negative FP64 values against non-negative constants, taken on the bit
+// pattern: for x >= +0 and c >= +0, x >= c exactly when bits(x) >= bits(c) as integers, and for
+// c = 1/2 or 1 (low word zero) the high words decide.  The FP64 pipe of this GPU completes two
+// lanes per clock per SM, so an integer compare here frees one of its issue slots; R = float
+// keeps the plain compare.  (A NaN offset only selects a branch whose indices stay in range.)
+template <typename R>
+__device__ __forceinline__ bool ge_half(R x)
+{
+    if constexpr (sizeof(R) == 8) return __double2hiint(x) >= 0x3FE00000;
+    else return x >= R(0.5);
+}
+
+template <typename R>
+__device__ __forceinline__ bool ge_one(R x)
+{
+    if constexpr (sizeof(R) == 8) return __double2hiint(x) >= 0x3FF00000;
+    else return x >= R(1);
+}
+
+template <typename R>
+__device__ __forceinline__ bool ge_pos(R x, R c)
+{
+    if constexpr (sizeof(R) == 8) return __double_as_longlong(x) >= __double_as_longlong(c);
+    else return x >= c;
+}
+
+template <typename R>
+__device__ __forceinline__ bool is_neg(R x)  // x < 0 for x != -0 (the callers never see -0)
+{
+    if constexpr (sizeof(R) == 8) return __double2hiint(x) < 0;
+    else return x < R(0);
+}
+
 // Split an offset delta in [0,1) against a node lattice shifted by h = c + (L-1)/2 (c = 0 for
 // integer nodes, 1/2 for half-integer nodes): returns the first node (relative to the cell)
 // and the local coordinate psi in [0,1).
@@ -161,9 +194,9 @@ __device__ __forceinline__ int spline_base(R delta, bool half, R &psi)
     const int h2 = (half ? 1 : 0) + L - 1;
     const int hi = h2 >> 1;            // integer part of h
     if (h2 & 1) {                      // h = hi + 1/2
-        if (delta >= R(0.5)) { psi = delta - R(0.5); return -hi; }
+        if (ge_half(delta)) { psi = delta - R(0.5); return -hi; }
         psi = delta + R(0.5);
-        if (psi >= R(1)) { psi = R(0); return -hi; }  // delta + 1/2 rounded up to 1
+        if (ge_one(psi)) { psi = R(0); return -hi; }  // delta + 1/2 rounded up to 1
         return -hi - 1;
     }
     psi = delta;
@@ -181,16 +214,16 @@ __device__ __forceinline__ int ttable_weights(const TTable &t, R delta, R *w)
     // v in (-1, 1)
     int fl = 0;
     R phi = v;
-    if (v < R(0)) {
+    if (is_neg(v)) {  // v = delta - Rfrac is never -0 (delta = Rfrac gives +0)
         phi = v + R(1);
         fl = -1;
-        if (phi >= R(1)) { phi = R(0); fl = 0; }
+        if (ge_one(phi)) { phi = R(0); fl = 0; }
     }
     const int base = fl - t.Rint + 1;
     R phib;
     if constexpr (sizeof(R) == 8) phib = R(t.phib);
     else phib = R(t.phib_f);
-    const int p = (phi >= phib) ? 1 : 0;
+    const int p = ge_pos(phi, phib) ? 1 : 0;  // phi >= +0, phib >= +0
     const R tl = phi - (p ? phib : R(0));
 #pragma unroll
     for (int k = 0; k < KT; ++k) {

@@ -226,26 +226,38 @@ __device__ __forceinline__ R boris(R h, const R *E, const R *B, R *u)
 
 // Move one axis in cell units: returns the cell shift sh in {-1,0,1} and the new offset o in
 // [0,1).  In the FP64 form o is re-derived from the stored value cell + o so that the next
-// step's old-position weights are bit-identical to this step's new-position weights.
+// step's old-position weights are bit-identical to this step's new-position weights; xs is that
+// stored value (unused for FP32).
 template <typename R>
-__device__ __forceinline__ int move_axis(R d, R delta, int c, int n, R &o, int &cn)
+__device__ __forceinline__ int move_axis(R d, R delta, int c, int n, R &o, int &cn, R &xs)
 {
     const R xn = d + delta;
-    int sh = (xn < R(0)) ? -1 : ((xn >= R(1)) ? 1 : 0);
-    R on = xn - R(sh);
+    int sh;
+    R on;
+    if constexpr (sizeof(R) == 8) {
+        // xn - sh as xn plus a selected constant: the same rounding, without converting sh
+        const bool lo = xn < 0.0, up = xn >= 1.0;
+        sh = lo ? -1 : (up ? 1 : 0);
+        on = xn + (lo ? 1.0 : (up ? -1.0 : 0.0));
+    } else {
+        sh = (xn < R(0)) ? -1 : ((xn >= R(1)) ? 1 : 0);
+        on = xn - R(sh);
+    }
     if (on >= R(1)) { on = R(0); sh += 1; }
     if (on < R(0)) on = R(0);
     int cc = c + sh;
     if (cc < 0) cc += n;
     if (cc >= n) cc -= n;
+    xs = R(0);
     if constexpr (sizeof(R) == 8) {
         const double stored = (double)cc + on;
-        double o2 = stored - (double)cc;
-        if (o2 >= 1.0) {  // cc + on rounded up to the next integer
+        double o2 = stored - (double)cc;  // exact (Sterbenz)
+        xs = stored;
+        if (o2 >= 1.0) {  // cc + on rounded up to the next integer, which is the stored value
             o2 = 0.0;
             sh += 1;
             cc += 1;
-            if (cc >= n) cc -= n;
+            if (cc >= n) { cc -= n; xs = 0.0; }
         }
         on = o2;
     }

@@ -279,6 +279,70 @@ __device__ __forceinline__ void prefetch_particle(const HotSp<R> &hs, int64_t p)
     }
 }
 
+// FP32 gather on packed pairs: __ffma2_rn performs two FP32 fused multiply-adds in one
+// instruction (sm_100 and later), each rounded exactly as the scalar FMA, so the result is the
+// scalar loop's bit for bit.  (E1, B2) and (E2, B1) are staged as pairs that share their
+// weights; E3 (T x T) and B3 (W x W) pair up when the two stencils have the same size.
+template <int L, int KT>
+__device__ __forceinline__ void gather_2d_x2(const Stage2D<float> &st, const AxisW<L, KT, float> &wx,
+                                             const AxisW<L, KT, float> &wy, int sx, int sy,
+                                             int RX, float *E, float *B)
+{
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    float2 e1b2 = z2, e2b1 = z2;
+#pragma unroll
+    for (int b = 0; b < KT; ++b) {  // (E1, B2): W along x (half nodes), T along y
+        const int row = (sy + wy.bt + b) * RX + sx + wx.bh;
+        float2 r = z2;
+#pragma unroll
+        for (int a = 0; a <= L; ++a) r = __ffma2_rn(make_float2(wx.wh[a], wx.wh[a]), st.pa[row + a], r);
+        e1b2 = __ffma2_rn(make_float2(wy.wt[b], wy.wt[b]), r, e1b2);
+    }
+#pragma unroll
+    for (int b = 0; b <= L; ++b) {  // (E2, B1): T along x, W along y
+        const int row = (sy + wy.bh + b) * RX + sx + wx.bt;
+        float2 r = z2;
+#pragma unroll
+        for (int a = 0; a < KT; ++a) r = __ffma2_rn(make_float2(wx.wt[a], wx.wt[a]), st.pb[row + a], r);
+        e2b1 = __ffma2_rn(make_float2(wy.wh[b], wy.wh[b]), r, e2b1);
+    }
+    E[0] = e1b2.x; B[1] = e1b2.y;
+    E[1] = e2b1.x; B[0] = e2b1.y;
+    if constexpr (KT == L + 1) {
+        float2 e3b3 = z2;
+#pragma unroll
+        for (int b = 0; b < KT; ++b) {  // E3: T T, B3: W W
+            const int rt = (sy + wy.bt + b) * RX + sx + wx.bt;
+            const int rw = (sy + wy.bh + b) * RX + sx + wx.bh;
+            float2 r = z2;
+#pragma unroll
+            for (int a = 0; a < KT; ++a)
+                r = __ffma2_rn(make_float2(wx.wt[a], wx.wh[a]), make_float2(st.e3[rt + a], st.b3[rw + a]), r);
+            e3b3 = __ffma2_rn(make_float2(wy.wt[b], wy.wh[b]), r, e3b3);
+        }
+        E[2] = e3b3.x; B[2] = e3b3.y;
+    } else {
+        float e3 = 0.0f, b3 = 0.0f;
+#pragma unroll
+        for (int b = 0; b < KT; ++b) {
+            const int row = (sy + wy.bt + b) * RX + sx + wx.bt;
+            float r = 0.0f;
+#pragma unroll
+            for (int a = 0; a < KT; ++a) r += wx.wt[a] * st.e3[row + a];
+            e3 += wy.wt[b] * r;
+        }
+#pragma unroll
+        for (int b = 0; b <= L; ++b) {
+            const int row = (sy + wy.bh + b) * RX + sx + wx.bh;
+            float r = 0.0f;
+#pragma unroll
+            for (int a = 0; a <= L; ++a) r += wx.wh[a] * st.b3[row + a];
+            b3 += wy.wh[b] * r;
+        }
+        E[2] = e3; B[2] = b3;
+    }
+}
+
 // One particle per lane, 2D, staged tile.  Called by all 32 lanes of a warp together (the
 // deposit is warp-collective); lanes with act == false carry no particle.
 template <int L, int KT, typename R>
@@ -333,7 +397,9 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
 
     // ---- gather (Eq. interpolation-EB-real-mod; MC when the tables hold W_l) ----
     R E[3], B[3];
-    {
+    if constexpr (sizeof(R) == 4) {
+        gather_2d_x2<L, KT>(st, wx, wy, sx, sy, RX, E, B);
+    } else {
         // (E1, B2): W along x (half nodes), T along y (integer nodes)
         R e1 = R(0), b2 = R(0);
 #pragma unroll
@@ -392,12 +458,12 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
     const R ig = boris<R>(R(hs.qmdt_half), E, B, s.u);
 
     // ---- move ----
-    R o[2], dl[2];
+    R o[2], dl[2], xs[2];
     int cn[2], shv[2];
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         dl[a] = R(a == 0 ? h.dtt0 : h.dtt1) * s.u[a] * ig;
-        shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], a == 0 ? h.n0 : h.n1, o[a], cn[a]);
+        shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], a == 0 ? h.n0 : h.n1, o[a], cn[a], xs[a]);
     }
 
     // ---- Esirkepov deposit ----
@@ -409,9 +475,12 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         axis_shapes<L, R>(s.d[0], shv[0], o[0], Sx);
         axis_shapes<L, R>(s.d[1], shv[1], o[1], Sy);
     }
-    const R wgt = act ? R(1) : R(0);
-    const R kx = wgt * R(hs.kx0), ky = wgt * R(hs.kx1);
-    const R kz = wgt * R(hs.kz) * s.u[2] * ig;
+    // the FP32 warp-collective deposit carries idle lanes with zero weight; the FP64 form
+    // deposits active lanes only, and saves the three products
+    const R wgt = (sizeof(R) == 8 || act) ? R(1) : R(0);
+    const R kx = (sizeof(R) == 8) ? R(hs.kx0) : wgt * R(hs.kx0);
+    const R ky = (sizeof(R) == 8) ? R(hs.kx1) : wgt * R(hs.kx1);
+    const R kz = ((sizeof(R) == 8) ? R(hs.kz) : wgt * R(hs.kz)) * s.u[2] * ig;
     const R third = R(1) / R(3);
     // W_x = DSx (S0y + DSy/2), prefix along x; W_y = DSy (S0x + DSx/2), prefix along y;
     // W_z = S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3 = S0y Ax + DSy Bx.
@@ -584,8 +653,8 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         ((float *)hs.pos0)[p] = o[0];
         ((float *)hs.pos1)[p] = o[1];
     } else {
-        ((double *)hs.pos0)[p] = (double)cn[0] + o[0];
-        ((double *)hs.pos1)[p] = (double)cn[1] + o[1];
+        ((double *)hs.pos0)[p] = xs[0];  // = cn + o
+        ((double *)hs.pos1)[p] = xs[1];
     }
 }
 
@@ -748,12 +817,12 @@ __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &
     }
 
     const R ig = boris<R>(R(sp.qmdt_half), E, B, s.u);
-    R o[3], dl[3];
+    R o[3], dl[3], xs[3];
     int cn[3], shv[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         dl[a] = R(rd.dtt[a]) * s.u[a] * ig;
-        shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], rd.n[a], o[a], cn[a]);
+        shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], rd.n[a], o[a], cn[a], xs[a]);
     }
 
     AxisS<L, R> S[3];
@@ -810,7 +879,7 @@ __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &
         for (int a = 0; a < 3; ++a) ((float *)sp.pos[a])[p] = o[a];
     } else {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) ((double *)sp.pos[a])[p] = (double)cn[a] + o[a];
+        for (int a = 0; a < 3; ++a) ((double *)sp.pos[a])[p] = xs[a];  // = cn + o
     }
     (void)nz;
 }
