@@ -44,8 +44,8 @@ BYTES = {"fp64": (80.0, 72.0), "fp32": (48.0, 48.0)}
 # instruction counts in profiles/gpp2d_fp64_l3_pair512x256.md (DADD + DMUL + 2 x DFMA divided by
 # the particles of the launch), and the FP64 instructions (DADD + DMUL + DFMA).  Used for the
 # FP64 arithmetic roofline of the plain form.
-FP64_FLOPS_PER_PARTICLE = 670.5
-FP64_INSTR_PER_PARTICLE = 440.5
+FP64_FLOPS_PER_PARTICLE = 651.5
+FP64_INSTR_PER_PARTICLE = 415.5
 
 
 def _rank_env():

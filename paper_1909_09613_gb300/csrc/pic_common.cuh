@@ -129,14 +129,43 @@ __device__ __forceinline__ void bspline(R p, R *w)
         w[0] = R(0.5) * q * q;
         w[1] = R(0.5) + p * q;
         w[2] = R(0.5) * p * p;
+    } else if constexpr (L == 3 && sizeof(R) == 4) {
+        // node k at psi is node L - k at 1 - psi: (w3, w0) and (w1, w2) are one polynomial
+        // each, evaluated on the pair (psi, 1 - psi) with packed FP32 arithmetic
+        const float2 pq = make_float2(p, q);
+        const float2 s2 = __fmul2_rn(pq, pq);
+        const float2 e = __fmul2_rn(s2, __fmul2_rn(pq, make_float2(1.0f / 6.0f, 1.0f / 6.0f)));
+        const float2 h = __ffma2_rn(make_float2(0.5f, 0.5f), pq, make_float2(-1.0f, -1.0f));
+        const float2 m = __ffma2_rn(h, s2, make_float2(2.0f / 3.0f, 2.0f / 3.0f));
+        w[0] = e.y;
+        w[1] = m.x;
+        w[2] = m.y;
+        w[3] = e.x;
     } else if constexpr (L == 3) {
-        // Horner forms; the third weight from the partition of unity (it is >= 1/6, so the
-        // subtraction loses no relative precision) -- fewer FP64 operations than expanding all
+        // Horner forms of w3 = psi^3/6 and w1 = 2/3 - psi^2 (1 - psi/2); w0 and w2 are the same
+        // polynomials in 1 - psi (node k at psi is node 3 - k at 1 - psi): eleven FP64 operations
         const R p2 = p * p;
-        w[0] = (q * q) * (q * R(1.0 / 6.0));
+        const R q2 = q * q;
+        w[0] = q2 * (q * R(1.0 / 6.0));
         w[1] = (R(0.5) * p - one) * p2 + R(2.0 / 3.0);
+        w[2] = (R(0.5) * q - one) * q2 + R(2.0 / 3.0);
         w[3] = p2 * (p * R(1.0 / 6.0));
-        w[2] = one - ((w[0] + w[1]) + w[3]);
+    } else if constexpr (sizeof(R) == 4) {
+        // L = 4 on the pair (psi, 1 - psi): (w4, w0) = (psi^4, (1-psi)^4) / 24, and (w3, w1) one
+        // Horner polynomial; the middle weight from the partition of unity (>= 11/24)
+        const float2 pq = make_float2(p, q);
+        const float2 s2 = __fmul2_rn(pq, pq);
+        const float2 e = __fmul2_rn(s2, __fmul2_rn(s2, make_float2(1.0f / 24.0f, 1.0f / 24.0f)));
+        float2 t = __ffma2_rn(make_float2(-1.0f / 6.0f, -1.0f / 6.0f), pq,
+                              make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+        t = __ffma2_rn(t, pq, make_float2(0.25f, 0.25f));
+        t = __ffma2_rn(t, pq, make_float2(1.0f / 6.0f, 1.0f / 6.0f));
+        t = __ffma2_rn(t, pq, make_float2(1.0f / 24.0f, 1.0f / 24.0f));
+        w[0] = e.y;
+        w[1] = t.y;
+        w[3] = t.x;
+        w[4] = e.x;
+        w[2] = 1.0f - (((w[0] + w[1]) + w[3]) + w[4]);
     } else {
         // Horner forms with the 1/24 folded into the coefficients; the middle weight from the
         // partition of unity (it is >= 11/24)

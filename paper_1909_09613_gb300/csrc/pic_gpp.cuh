@@ -83,6 +83,7 @@ __device__ __forceinline__ void axis_weights(const TTable &tt, R d, AxisW<L, KT,
 template <int L, typename R>
 struct AxisS {
     int wb;
+    bool wide;  // the window needs all l + 2 nodes (else node l + 1 carries S0 = DS = 0)
     R s0[L + 2];
     R ds[L + 2];
 };
@@ -97,6 +98,7 @@ __device__ __forceinline__ void axis_shapes(R d_old, int sh, R o_new, AxisS<L, R
     bspline<L, R>(p0, w0);
     bspline<L, R>(p1, w1);
     s.wb = min(b0, b1);
+    s.wide = b0 != b1;
     const bool sh0 = b0 > s.wb, sh1 = b1 > s.wb;
 #pragma unroll
     for (int k = 0; k < L + 2; ++k) {
@@ -153,6 +155,7 @@ __device__ __forceinline__ void axis_shapes_dd(float d_old, float delta, AxisS<L
     const int b0 = spline_base<L, float>(d_old, false, p0);
     bspline<L, float>(p0, w0);
     const float p1 = p0 + delta;
+    s.wide = true;
     if (p1 >= 1.0f) {            // base moves up: window starts at b0
         s.wb = b0;
         const float a = 1.0f - p0;     // part of the move before the lattice point
@@ -182,6 +185,7 @@ __device__ __forceinline__ void axis_shapes_dd(float d_old, float delta, AxisS<L
         }
     } else {                     // same base
         s.wb = b0;
+        s.wide = false;
         float D[L + 1];
         bspline_dd<L>(p0, p1, D);
 #pragma unroll

@@ -7,7 +7,7 @@ namespace pic {
 namespace {
 
 template <int L, int KT>
-__global__ void __launch_bounds__(256) k_gpp2d(const __grid_constant__ RunDev rd)
+__global__ void __launch_bounds__(256, 2) k_gpp2d(const __grid_constant__ RunDev rd)
 {
     extern __shared__ __align__(16) char smem[];
     tile_2d<L, KT, double>(rd, smem, blockIdx.x);

@@ -165,14 +165,15 @@ __device__ __forceinline__ bool local_coord(int c, int origin, int tile, int dri
     return l >= -drift && l < tile + drift;
 }
 
-// One lane's Esirkepov window added to the shared current tile with atomics.
-template <int L, typename R>
+// One lane's Esirkepov window added to the shared current tile with atomics (WY as in
+// deposit_lane_global below).
+template <int L, typename R, bool WY = true>
 __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int jx0, int jy0, R kx,
                                              R ky, R kz, const R *px, const R *py, const R *Ax,
                                              const R *Ay, const R *Bx, const AxisS<L, R> &Sy)
 {
 #pragma unroll
-    for (int b = 0; b < L + 2; ++b) {
+    for (int b = 0; b < (WY ? L + 2 : L + 1); ++b) {
         const int row = (jy0 + b) * RX + jx0;
         const R ayk = kx * Ay[b];
         const R pyk = (b <= L) ? ky * py[b] : R(0);
@@ -190,7 +191,9 @@ __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int j
 // reductions (red.global.add.f64) are performed by L2, so unlike shared-memory FP64 atomics
 // (compare-and-swap loops around a DADD) they take no issue slots of the SM's FP64 pipe, which
 // bounds this form.  gx0, gy0: global node of the window's first column and row (unwrapped).
-template <int L, typename R, typename Hot>
+// WY = false when no lane of the warp changed its y window base: row l + 1 then carries exact
+// zeros (S0y = DSy = 0) and is skipped.
+template <int L, typename R, typename Hot, bool WY = true>
 __device__ __forceinline__ void deposit_lane_global(const Hot &h, int gx0, int gy0, R kx, R ky,
                                                     R kz, const R *px, const R *py, const R *Ax,
                                                     const R *Ay, const R *Bx,
@@ -204,7 +207,7 @@ __device__ __forceinline__ void deposit_lane_global(const Hot &h, int gx0, int g
         gy[k] = (int64_t)wrap_near(gy0 + k, h.n1) * h.n0;
     }
 #pragma unroll
-    for (int b = 0; b < L + 2; ++b) {
+    for (int b = 0; b < (WY ? L + 2 : L + 1); ++b) {
         const R ayk = kx * Ay[b];
         const R pyk = (b <= L) ? ky * py[b] : R(0);
         const R zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
@@ -509,7 +512,12 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         if (h.slot_major) {  // lanes in different cells: per-lane atomics do not collide
             // (shared-memory CAS atomics: measured faster here than global FP64 reductions,
             // which would need an FP32 -> FP64 conversion per node)
-            if (act) deposit_lane<L, R>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+            if (__any_sync(0xffffffffu, act && Sy.wide)) {
+                if (act)
+                    deposit_lane<L, R, true>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+            } else if (act) {
+                deposit_lane<L, R, false>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+            }
         } else {
         float *rec = st.rec + (threadIdx.x >> 5) * (32 * FR::RS);
         float4 *mine = (float4 *)(rec + lane * FR::RS);
@@ -638,9 +646,16 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         }
         }
         }
-    } else if (act) {
-        deposit_lane_global<L, R>(h, x0 - h.pre0 + jx0, y0 - h.pre1 + jy0, kx, ky, kz, px, py,
-                                  Ax, Ay, Bx, Sy);
+    } else {
+        // a drift along x1 rarely moves the y window: skip its empty last row warp-uniformly
+        if (__any_sync(0xffffffffu, act && Sy.wide)) {
+            if (act)
+                deposit_lane_global<L, R, Hot2D, true>(h, x0 - h.pre0 + jx0, y0 - h.pre1 + jy0,
+                                                       kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+        } else if (act) {
+            deposit_lane_global<L, R, Hot2D, false>(h, x0 - h.pre0 + jx0, y0 - h.pre1 + jy0,
+                                                    kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+        }
     }
     if (!act) return;
 
