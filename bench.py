@@ -35,17 +35,19 @@ UNIT = "particle-steps/s"
 WORKLOAD = "pair_2048x1024_l3_WT_g50_uth0.01_ppc64_cdt0.25"
 
 # Algorithmic bytes of the fused particle kernel (per particle-step, per cell-step):
-#   FP64 form: particle read + write 2 x (2 x 8 position + 3 x 8 momentum) = 80 B;
+#   FP64 form: particle read + write 2 x (2 x 8 position + 3 x 8 momentum) = 80 B, plus the
+#              cached B-spline weights of the stored positions read and written,
+#              2 x 2 (l + 1) x 8 B = 128 B for l = 3: 208 B;
 #              grid: E, B read once (6 x 8 B) + J written (3 x 8 B) = 72 B per cell.
 #   FP32 form: 2 x (4 cell + 2 x 4 offset + 3 x 4 momentum) = 48 B;
 #              grid: FP32 shadow of E, B (6 x 4 B) + FP64 J (3 x 8 B) = 48 B per cell.
-BYTES = {"fp64": (80.0, 72.0), "fp32": (48.0, 48.0)}
+BYTES = {"fp64": (208.0, 72.0), "fp32": (48.0, 48.0)}
 # FP64 operations of the fused kernel per particle-step (l = 3, WT, 2D), from the ncu
 # instruction counts in profiles/gpp2d_fp64_l3_pair512x256.md (DADD + DMUL + 2 x DFMA divided by
-# the particles of the launch), and the FP64 instructions (DADD + DMUL + DFMA).  Used for the
-# FP64 arithmetic roofline of the plain form.
-FP64_FLOPS_PER_PARTICLE = 651.5
-FP64_INSTR_PER_PARTICLE = 415.5
+# the particles of the launch, a step that reads the weight cache), and the FP64 instructions
+# (DADD + DMUL + DFMA).  Used for the FP64 arithmetic roofline of the plain form.
+FP64_FLOPS_PER_PARTICLE = 621.5
+FP64_INSTR_PER_PARTICLE = 393.5
 
 
 def _rank_env():

@@ -34,6 +34,8 @@ struct pic_ctx {
     void *bufA[PIC_MAX_SPECIES][7];   // current store: pos[3], mom[3], cell
     void *bufB[PIC_MAX_SPECIES][7];   // sort target
     int64_t *tile_start[PIC_MAX_SPECIES];
+    double *wc[PIC_MAX_SPECIES];      // FP64 2D weight cache (see SpeciesDev::wc)
+    bool wc_valid[PIC_MAX_SPECIES];   // the cache holds the weights of the current store
     SortScratch sc;
     char *staging;
     size_t staging_bytes;
@@ -64,6 +66,13 @@ size_t staging_size(const RunDev &rd, int64_t capmax)
 }
 
 int pos_bytes(const pic_ctx *c) { return c->rd.prec == PIC_FP32_MIXED ? 4 : 8; }
+
+// FP64 2D, l <= 3: 2 (l + 1) cached B-spline weights per particle of capacity (SpeciesDev::wc)
+size_t weight_cache_bytes(const pic_ctx *c, int s)
+{
+    if (c->rd.prec != PIC_FP64 || c->rd.dim != 2 || c->rd.l > 3) return 0;
+    return (size_t)c->cap[s] * 2 * (c->rd.l + 1) * sizeof(double);
+}
 
 int particle_bytes(const pic_ctx *c)
 {
@@ -101,6 +110,9 @@ void refresh_species_ptrs(pic_ctx *c)
             sp.mom_alt[a] = c->bufB[s][3 + a];
         }
         sp.cell_alt = (int32_t *)c->bufB[s][6];
+        sp.wc = c->wc[s];
+        sp.wc_stride = c->cap[s];
+        sp.wc_mode = c->wc[s] ? (c->wc_valid[s] ? 2 : 1) : 0;
     }
     c->rd.sc = c->sc;
 }
@@ -127,6 +139,7 @@ int sort_species(pic_ctx *c, int s)
     if (e != cudaSuccess) return PIC_ECUDA;
     c->kernel_launches += rd.sp[s].n > 0 ? 5 : 3;
     for (int i = 0; i < 7; ++i) std::swap(c->bufA[s][i], c->bufB[s][i]);
+    c->wc_valid[s] = false;  // the weight cache follows the old order
     refresh_species_ptrs(c);
     return PIC_OK;
 }
@@ -173,10 +186,11 @@ void set_species(pic_ctx *c, int species, double q, double m, double w, int64_t 
 // After the particle store of a species is written: tile-sort it and mark it loaded.
 int finish_load(pic_ctx *c, int species)
 {
-    const int r = sort_species(c, species);
+    // every species is re-sorted: the sort age is shared, and a species that kept its older
+    // order could otherwise drift past the staged halo before the next automatic sort
+    const int r = sort_all(c);
     if (r != PIC_OK) return r;
     c->loaded[species] = true;
-    c->age = 0;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
     return PIC_OK;
 }
@@ -415,6 +429,7 @@ int pic_footprint(const pic_ctx *c, size_t *bytes)
     const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
     for (int s = 0; s < rd.nsp; ++s) b += align_up((size_t)c->cap[s] * pb + 7 * A, A);  // current stores
     for (int s = 0; s < rd.nsp; ++s) b += align_up((rd.ntiles + 1) * sizeof(int64_t), A);           // tile_start
+    for (int s = 0; s < rd.nsp; ++s) b += align_up(weight_cache_bytes(c, s), A);                  // wc
     // sort targets and sort scratch
     for (int s = 0; s < rd.nsp; ++s) b += align_up((size_t)c->cap[s] * pb + 7 * A, A);
     b += 2 * align_up(rd.ntiles * TC * sizeof(int32_t), A);
@@ -457,6 +472,11 @@ int pic_bind_memory(pic_ctx *c, void *dev, size_t bytes)
         take((size_t)c->cap[s] * pb + 7 * A);
     }
     for (int s = 0; s < rd.nsp; ++s) c->tile_start[s] = (int64_t *)take((rd.ntiles + 1) * sizeof(int64_t));
+    for (int s = 0; s < rd.nsp; ++s) {
+        const size_t wb = weight_cache_bytes(c, s);
+        c->wc[s] = wb ? (double *)take(wb) : nullptr;
+        c->wc_valid[s] = false;
+    }
     int64_t capmax = 0;
     for (int s = 0; s < rd.nsp; ++s) capmax = std::max(capmax, c->cap[s]);
     const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
@@ -615,6 +635,7 @@ int pic_step(pic_ctx *c, int nsteps)
         if (e != cudaSuccess) return PIC_ECUDA;
         if (c->have_events) cudaEventRecord(c->ev1[c->ev_pending++], c->stream);
         c->gpp_launches += 1;
+        for (int s = 0; s < rd.nsp; ++s) c->wc_valid[s] = c->wc[s] != nullptr;
         if (launch_yee_b(rd, 0.5 * rd.dt, false, c->stream) != cudaSuccess) return PIC_ECUDA;
         if (launch_yee_e(rd, shadow, c->stream) != cudaSuccess) return PIC_ECUDA;
         if (launch_yee_b(rd, 0.5 * rd.dt, shadow, c->stream) != cudaSuccess) return PIC_ECUDA;
@@ -799,6 +820,7 @@ void ctx_after_batch(pic_ctx *c, const RunDev &d, int age, int64_t steps)
         }
         c->bufA[s][6] = d.sp[s].cell;
         c->bufB[s][6] = d.sp[s].cell_alt;
+        c->wc_valid[s] = false;
     }
     refresh_species_ptrs(c);
     c->age = age;

@@ -57,6 +57,14 @@ struct SpeciesDev {
     void *pos_alt[3];
     void *mom_alt[3];
     int32_t *cell_alt;
+    // FP64 2D: the B-spline weights of each particle at its stored position, l + 1 per axis at
+    // wc[(a (l + 1) + k) wc_stride + p], written by every step for the next one, whose
+    // old-position deposit weights they are (bit-identical by construction of the move).
+    // wc_mode: 0 no cache, 1 write only (the positions were loaded or re-ordered since the
+    // last step), 2 read and write.
+    double *wc;
+    int64_t wc_stride;
+    int wc_mode;
 };
 
 // Exact quotient n / d for 0 <= n < 2^31 and 1 <= d < 2^31 by one multiply and a shift:

@@ -88,15 +88,29 @@ struct AxisS {
     R ds[L + 2];
 };
 
-// FP64: S1 from the stored new position (cell shift sh, offset o_new), DS = S1 - S0.
+// FP64: S1 from the stored new position (cell shift sh, offset o_new), DS = S1 - S0.  The
+// old-position weights are read from wsrc (l + 1 values wstride apart: what the previous step
+// wrote for this position) when given, else evaluated; the new-position weights are written to
+// wdst when given.
 template <int L, typename R>
-__device__ __forceinline__ void axis_shapes(R d_old, int sh, R o_new, AxisS<L, R> &s)
+__device__ __forceinline__ void axis_shapes(R d_old, int sh, R o_new, AxisS<L, R> &s,
+                                            const R *wsrc = nullptr, R *wdst = nullptr,
+                                            int64_t wstride = 0)
 {
     R p0, p1, w0[L + 1], w1[L + 1];
     const int b0 = spline_base<L, R>(d_old, false, p0);
     const int b1 = sh + spline_base<L, R>(o_new, false, p1);
-    bspline<L, R>(p0, w0);
+    if (wsrc) {
+#pragma unroll
+        for (int k = 0; k <= L; ++k) w0[k] = __ldg(wsrc + (int64_t)k * wstride);
+    } else {
+        bspline<L, R>(p0, w0);
+    }
     bspline<L, R>(p1, w1);
+    if (wdst) {
+#pragma unroll
+        for (int k = 0; k <= L; ++k) wdst[(int64_t)k * wstride] = w1[k];
+    }
     s.wb = min(b0, b1);
     s.wide = b0 != b1;
     const bool sh0 = b0 > s.wb, sh1 = b1 > s.wb;

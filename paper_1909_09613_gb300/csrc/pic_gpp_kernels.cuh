@@ -237,6 +237,9 @@ struct HotSp {
     void *pos0, *pos1, *mom0, *mom1, *mom2;
     int32_t *cell;
     double qmdt_half, kx0, kx1, kz;
+    double *wc;  // FP64 weight cache (SpeciesDev::wc)
+    int64_t wc_stride;
+    int wc_mode;
 };
 
 __device__ __forceinline__ Hot2D make_hot2d(const RunDev &rd)
@@ -265,6 +268,7 @@ __device__ __forceinline__ HotSp<R> make_hotsp(const SpeciesDev &sp)
     h.cell = sp.cell;
     h.qmdt_half = sp.qmdt_half;
     h.kx0 = sp.kx[0]; h.kx1 = sp.kx[1]; h.kz = sp.kz;
+    h.wc = sp.wc; h.wc_stride = sp.wc_stride; h.wc_mode = sp.wc_mode;
     return h;
 }
 
@@ -278,6 +282,17 @@ __device__ __forceinline__ void prefetch_particle(const HotSp<R> &hs, int64_t p)
     for (int i = 0; i < 6; ++i) {
         if (i == 5 && sizeof(R) == 8) break;  // the FP64 form has no cell array
         const char *a = (const char *)ptrs[i] + p * (i == 5 ? 4 : (int64_t)sizeof(R));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+    }
+}
+
+// The cached old-position weights of a later iteration (FP64 form, 2 (l + 1) arrays).
+template <int L>
+__device__ __forceinline__ void prefetch_weights(const HotSp<double> &hs, int64_t p)
+{
+#pragma unroll
+    for (int i = 0; i < 2 * (L + 1); ++i) {
+        const double *a = hs.wc + (int64_t)i * hs.wc_stride + p;
         asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
     }
 }
@@ -475,8 +490,15 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         axis_shapes_dd<L>(s.d[0], dl[0], Sx);
         axis_shapes_dd<L>(s.d[1], dl[1], Sy);
     } else {
-        axis_shapes<L, R>(s.d[0], shv[0], o[0], Sx);
-        axis_shapes<L, R>(s.d[1], shv[1], o[1], Sy);
+        // old-position weights: from the cache the previous step wrote at this particle's
+        // stored position (bit-identical to evaluating them), else evaluated.  (l = 4 keeps
+        // evaluating: its cache would not fit the register budget of two CTAs per SM.)
+        double *wc = (L <= 3 && act && hs.wc_mode != 0) ? hs.wc + p : nullptr;
+        const double *wr = hs.wc_mode == 2 ? wc : nullptr;
+        const int64_t ws = hs.wc_stride;
+        axis_shapes<L, R>(s.d[0], shv[0], o[0], Sx, wr, wc, ws);
+        axis_shapes<L, R>(s.d[1], shv[1], o[1], Sy, wr ? wr + (L + 1) * ws : nullptr,
+                          wc ? wc + (L + 1) * ws : nullptr, ws);
     }
     // the FP32 warp-collective deposit carries idle lanes with zero weight; the FP64 form
     // deposits active lanes only, and saves the three products
@@ -692,7 +714,11 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile)
         const int64_t wbase = a + (threadIdx.x & ~31);
         for (int64_t q = wbase; q < b; q += blockDim.x) {
             const int64_t p = q + (threadIdx.x & 31);
-            if (p + blockDim.x < b) prefetch_particle<R>(hs, p + blockDim.x);
+            if (p + blockDim.x < b) {
+                prefetch_particle<R>(hs, p + blockDim.x);
+                if constexpr (sizeof(R) == 8 && L <= 3)
+                    if (hs.wc_mode == 2) prefetch_weights<L>(hs, p + blockDim.x);
+            }
             particle_2d<L, KT, R>(h, hs, st, p, p < b, x0, y0);
         }
         if constexpr (sizeof(R) == 4) {  // the FP64 form deposits to global memory directly

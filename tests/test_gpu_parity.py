@@ -185,6 +185,37 @@ def test_multi_step_across_sorts_fp64():
     run.close()
 
 
+@pytest.mark.parametrize("l", [2, 3, 4])
+def test_weight_cache_follows_sorts_and_reloads_fp64(l):
+    """The FP64 form keeps each particle's B-spline weights at its stored position for the next
+    step's Esirkepov deposit (l <= 3).  Every re-ordering must invalidate them: 16 steps with the
+    automatic sort every 4 steps, an explicit sort after step 5 and a reload of one species
+    (re-packed and re-sorted) after step 9, against the oracle."""
+    wl = workloads.pair_plasma((40, 24), (1.0, 1.0), 0.3, l, pic.PIC_SCHEME_WT, 5.0, 0.05, 6)
+    run, orc = make_pair(wl, pic.PIC_FP64, sort_interval=4)
+    run.step(5)
+    orc.step(5)
+    run.sort()
+    run.step(4)
+    orc.step(4)
+    s1 = wl.species[1]
+    x, u, _ = run.particles(1)
+    run.load(1, s1.q, s1.m, s1.w, x, u)
+    run.step(7)
+    orc.step(7)
+    for c in range(9):
+        assert rel(run.field(c), orc.field(c)) < 1e-10, c
+    for s in range(2):
+        xg, ug, _ = run.particles(s)
+        xo, uo = orc.particles(s)
+        kg = np.lexsort(xg[::-1])
+        ko = np.lexsort(xo[::-1])
+        assert np.max(np.abs(xg[:, kg] - xo[:, ko])) < 1e-9
+        assert rel(ug[:, kg], uo[:, ko]) < 1e-10
+    assert run.diag()["error_flags"] == 0
+    run.close()
+
+
 @pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("grid,tile", [((64, 32, 1), None), ((37, 21, 1), (8, 4, 1)),
                                        ((12, 10, 8), None), ((5, 3, 1), None)])
