@@ -47,7 +47,7 @@ BYTES = {"fp64": (208.0, 72.0), "fp32": (48.0, 48.0)}
 # the particles of the launch, a step that reads the weight cache), and the FP64 instructions
 # (DADD + DMUL + DFMA).  Used for the FP64 arithmetic roofline of the plain form.
 FP64_FLOPS_PER_PARTICLE = 621.5
-FP64_INSTR_PER_PARTICLE = 393.5
+FP64_INSTR_PER_PARTICLE = 390.5
 
 
 def _rank_env():

@@ -221,22 +221,21 @@ __device__ __forceinline__ float rcp_r(float x) { return __frcp_rn(x); }
 template <typename R>
 __device__ __forceinline__ R boris(R h, const R *E, const R *B, R *u)
 {
-    R um[3], t[3], sv[3], up[3];
+    R um[3], t[3], up[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) um[a] = u[a] + h * E[a];
     const R hg = h * rsqrt_r(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) t[a] = hg * B[a];
     const R f = R(2) * rcp_r(R(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) sv[a] = f * t[a];
     up[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
     up[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
     up[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
+    // u+ = u- + u' x s with s = f t: the scale f applied once to u' x t (three products fewer)
     R q[3];
-    q[0] = um[0] + (up[1] * sv[2] - up[2] * sv[1]);
-    q[1] = um[1] + (up[2] * sv[0] - up[0] * sv[2]);
-    q[2] = um[2] + (up[0] * sv[1] - up[1] * sv[0]);
+    q[0] = um[0] + f * (up[1] * t[2] - up[2] * t[1]);
+    q[1] = um[1] + f * (up[2] * t[0] - up[0] * t[2]);
+    q[2] = um[2] + f * (up[0] * t[1] - up[1] * t[0]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) u[a] = q[a] + h * E[a];
     return rsqrt_r(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -253,16 +252,22 @@ __device__ __forceinline__ int move_axis(R d, R delta, int c, int n, R &o, int &
     int sh;
     R on;
     if constexpr (sizeof(R) == 8) {
-        // xn - sh as xn plus a selected constant: the same rounding, without converting sh
-        const bool lo = xn < 0.0, up = xn >= 1.0;
+        // xn - sh as xn plus a selected constant: the same rounding, without converting sh.
+        // The compares are taken on the bit pattern (is_neg, ge_one): for finite values they
+        // decide as the FP64 compares do (-0 aside, which moves to +0 here); a NaN position,
+        // which only a non-finite momentum makes, leaves with a finite offset and a cell shift
+        // of at most 1, while its current and kinetic energy carry the NaN that reports it.
+        const bool lo = is_neg(xn), up = ge_one(xn);
         sh = lo ? -1 : (up ? 1 : 0);
         on = xn + (lo ? 1.0 : (up ? -1.0 : 0.0));
+        if (ge_one(on)) { on = 0.0; sh = min(sh + 1, 1); }  // finite: only from sh = -1
+        if (is_neg(on)) on = 0.0;
     } else {
         sh = (xn < R(0)) ? -1 : ((xn >= R(1)) ? 1 : 0);
         on = xn - R(sh);
+        if (on >= R(1)) { on = R(0); sh += 1; }
+        if (on < R(0)) on = R(0);
     }
-    if (on >= R(1)) { on = R(0); sh += 1; }
-    if (on < R(0)) on = R(0);
     int cc = c + sh;
     if (cc < 0) cc += n;
     if (cc >= n) cc -= n;
@@ -271,7 +276,7 @@ __device__ __forceinline__ int move_axis(R d, R delta, int c, int n, R &o, int &
         const double stored = (double)cc + on;
         double o2 = stored - (double)cc;  // exact (Sterbenz)
         xs = stored;
-        if (o2 >= 1.0) {  // cc + on rounded up to the next integer, which is the stored value
+        if (ge_one(o2)) {  // cc + on rounded up to the next integer, which is the stored value
             o2 = 0.0;
             sh += 1;
             cc += 1;
