@@ -48,6 +48,13 @@ BYTES = {"fp64": (208.0, 72.0), "fp32": (48.0, 48.0)}
 # (DADD + DMUL + DFMA).  Used for the FP64 arithmetic roofline of the plain form.
 FP64_FLOPS_PER_PARTICLE = 621.5
 FP64_INSTR_PER_PARTICLE = 390.5
+# Warp instructions the FP32 form's fused kernel issues per particle (ncu smsp__inst_executed
+# over the particles of the 512x256 capture in profiles/gpp2d_fp32_l3_pair512x256.md, l = 3).
+# The kernel is bound by instruction issue, not by DRAM: its issue-slot view divides the issued
+# instructions per second by the issue rate, one warp instruction per clock on each of the four
+# schedulers of the 152 SMs.
+FP32_WARP_INSTR_PER_PARTICLE = 40.43
+SMS, SCHEDULERS_PER_SM = 152, 4
 
 
 def _rank_env():
@@ -219,6 +226,7 @@ def e2e_form(run, wl, steps):
             pic.ctypes.cast(pic.ctypes.c_void_p(us[i].data_ptr()), pic._c_dp))
         if st != 0:
             raise pic.PicError(st, "pic_load_particles")
+    tl = time.perf_counter()  # pic_load_particles returns after its sort has completed
     run.step(steps)
     d = run.diag()
     t1 = time.perf_counter()
@@ -226,7 +234,7 @@ def e2e_form(run, wl, steps):
     n = sum(int(s.x.shape[1]) for s in wl.species)
     return {"value": n * steps / (t1 - t0), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(math.ceil(d2h / steps)),
-            "status": d["status"]}
+            "status": d["status"], "load_s": tl - t0, "steps_and_diag_s": t1 - tl}
 
 
 def cpu_baseline(wl, budget_s=12.0):
@@ -644,6 +652,13 @@ def main():
                          "kernel": "k_gpp2d<3,4> (float)", "kernel_ms": g32 * 1e3,
                          "algorithmic_bytes": ab, "peak_source": "%s hbm_gbs" % peak_kind},
             "gpu_launches": r32["launches"], "clocks": r32["clocks"]}
+        mhz = (r32["clocks"] or {}).get("sm_mhz") or 2070.0
+        issue_peak = SMS * SCHEDULERS_PER_SM * mhz * 1e6
+        issued = r32["n"] * FP32_WARP_INSTR_PER_PARTICLE / g32
+        line["precision_form"]["roofline"]["issue_view"] = {
+            "warp_instr_per_particle": FP32_WARP_INSTR_PER_PARTICLE,
+            "achieved_warp_instr_per_s": issued, "peak_warp_instr_per_s": issue_peak,
+            "frac": issued / issue_peak, "sm_mhz": mhz}
         try:
             line["fp32_fma_peak_tflops"] = pic.pic_probe_fma_peak(1)
         except Exception:
