@@ -46,6 +46,11 @@ struct pic_ctx {
     // timing of the particle pass: a ring of event pairs, drained when it fills
     cudaEvent_t ev0[64], ev1[64];
     bool have_events;
+    // host loads: copies of the next chunk (copy_stream) overlap the packing of the previous
+    // one (stream), the two halves of the staging buffer alternating
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_ready, ev_copied[2], ev_packed[2];
+    bool have_copy;
     int ev_pending;
     double gpp_ms;
     int64_t gpp_launches;
@@ -186,9 +191,10 @@ void set_species(pic_ctx *c, int species, double q, double m, double w, int64_t 
 // After the particle store of a species is written: tile-sort it and mark it loaded.
 int finish_load(pic_ctx *c, int species)
 {
-    // every species is re-sorted: the sort age is shared, and a species that kept its older
-    // order could otherwise drift past the staged halo before the next automatic sort
-    const int r = sort_all(c);
+    // the loaded species is sorted now; the shared sort age keeps counting the steps since the
+    // other species were sorted (resetting it could let them drift past the staged halo
+    // before the next automatic sort)
+    const int r = sort_species(c, species);
     if (r != PIC_OK) return r;
     c->loaded[species] = true;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
@@ -224,22 +230,46 @@ int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n
     if (on_device) {
         if (launch_pack(c->rd, species, x, n, u, n, n, 0, c->stream) != cudaSuccess) return PIC_ECUDA;
         if (n > 0) c->kernel_launches += 1;
-    } else {
-        // host arrays go through the staging buffer in chunks of kChunk particles
-        for (int64_t p0 = 0; p0 < n; p0 += kChunk) {
-            const int64_t mc = std::min(kChunk, n - p0);
-            double *sx = (double *)c->staging;
+    } else if (n > 0) {
+        // host arrays go through the two halves of the staging buffer in turn: the copies of
+        // chunk k (copy_stream) overlap the packing of chunk k - 1 (stream)
+        if (!c->have_copy) {
+            bool ok = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+            const unsigned fl = cudaEventDisableTiming;
+            ok = ok && cudaEventCreateWithFlags(&c->ev_ready, fl) == cudaSuccess;
+            for (int b = 0; b < 2; ++b)
+                ok = ok && cudaEventCreateWithFlags(&c->ev_copied[b], fl) == cudaSuccess
+                     && cudaEventCreateWithFlags(&c->ev_packed[b], fl) == cudaSuccess;
+            if (!ok) return PIC_ECUDA;
+            c->have_copy = true;
+        }
+        const int64_t ch = std::min<int64_t>(kChunk / 2, (int64_t)(c->staging_bytes / (2 * (d + 3) * sizeof(double))));
+        if (ch < 1) return PIC_ENOMEM;
+        // the staging buffer may still be in use by earlier work on the context's stream
+        if (cudaEventRecord(c->ev_ready, c->stream) != cudaSuccess
+            || cudaStreamWaitEvent(c->copy_stream, c->ev_ready, 0) != cudaSuccess)
+            return PIC_ECUDA;
+        int k = 0;
+        for (int64_t p0 = 0; p0 < n; p0 += ch, ++k) {
+            const int b = k & 1;
+            const int64_t mc = std::min(ch, n - p0);
+            double *sx = (double *)c->staging + (size_t)b * (d + 3) * ch;
             double *su = sx + (size_t)d * mc;
-            if ((size_t)(d + 3) * mc * sizeof(double) > c->staging_bytes) return PIC_ENOMEM;
+            if (k >= 2 && cudaStreamWaitEvent(c->copy_stream, c->ev_packed[b], 0) != cudaSuccess)
+                return PIC_ECUDA;
             for (int a = 0; a < d; ++a)
                 if (cudaMemcpyAsync(sx + (size_t)a * mc, x + (size_t)a * n + p0, mc * sizeof(double),
-                                    cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+                                    cudaMemcpyHostToDevice, c->copy_stream) != cudaSuccess)
                     return PIC_ECUDA;
             for (int a = 0; a < 3; ++a)
                 if (cudaMemcpyAsync(su + (size_t)a * mc, u + (size_t)a * n + p0, mc * sizeof(double),
-                                    cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+                                    cudaMemcpyHostToDevice, c->copy_stream) != cudaSuccess)
                     return PIC_ECUDA;
+            if (cudaEventRecord(c->ev_copied[b], c->copy_stream) != cudaSuccess
+                || cudaStreamWaitEvent(c->stream, c->ev_copied[b], 0) != cudaSuccess)
+                return PIC_ECUDA;
             if (launch_pack(c->rd, species, sx, mc, su, mc, mc, p0, c->stream) != cudaSuccess) return PIC_ECUDA;
+            if (cudaEventRecord(c->ev_packed[b], c->stream) != cudaSuccess) return PIC_ECUDA;
             c->kernel_launches += 1;
         }
     }
@@ -779,6 +809,15 @@ void pic_destroy(pic_ctx *c)
         for (int i = 0; i < 64; ++i) {
             cudaEventDestroy(c->ev0[i]);
             cudaEventDestroy(c->ev1[i]);
+        }
+    }
+    if (c->have_copy) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+        cudaEventDestroy(c->ev_ready);
+        for (int b = 0; b < 2; ++b) {
+            cudaEventDestroy(c->ev_copied[b]);
+            cudaEventDestroy(c->ev_packed[b]);
         }
     }
     if (c->owns && c->base) cudaFree(c->base);
