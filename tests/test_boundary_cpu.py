@@ -88,6 +88,30 @@ def test_create_validates_courant_and_order(lib):
     assert e.value.status == pic.PIC_ECFL
 
 
+def test_size_limits(lib):
+    """The largest accepted sizes and the first refused ones: 2^30 cells (int32 cell indices and
+    tile keys), 2^31 - 1 particles per species (int32 slot and key scratch of the sort), 1024
+    cells per tile.  Creation and the footprint query only: nothing is allocated."""
+    big = 2 ** 31 - 1
+    ctx = pic.pic_create((1 << 15, 1 << 15, 1), (1.0, 1.0, 1.0), 0.25, 3, pic.PIC_SCHEME_WT,
+                         _opt((big, 1), pic.PIC_FP32_MIXED))
+    try:
+        b = pic.pic_footprint(ctx)
+        assert b >= 2 * big * 24 + (1 << 30) * 9 * 8   # two FP32 stores + the FP64 grid
+    finally:
+        pic.pic_destroy(ctx)
+    for grid, cap, tile in ((((1 << 15) + 1, 1 << 15, 1), (16, 16), None),
+                            ((64, 32, 1), (2 ** 31, 1), None),
+                            ((64, 32, 1), (16, 16), (64, 32, 1))):
+        o = _opt(cap)
+        if tile:
+            for a in range(3):
+                o.tile[a] = tile[a]
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_create(grid, (1.0, 1.0, 1.0), 0.25, 3, pic.PIC_SCHEME_WT, o)
+        assert e.value.status == pic.PIC_EINVAL, (grid, cap, tile)
+
+
 def test_create_m4_courant_limit(lib):
     """Courant limit with the M4 stencil (App. C): on these grids the worst wavenumber is a
     corner of the Brillouin zone and the limit coincides with Yee's (1/sqrt(2) for dx = dy,
