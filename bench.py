@@ -563,15 +563,19 @@ def main():
         wl = workloads.config_large(scheme=1, device="cpu", scale=8)
         # same per-particle work as the full grid (the oracle's cost is per particle)
         wl_full = wl
-        rates = []
+        rates, secs = [], []
         budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
         for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
             r, sample = cpu_baseline(wl_full, budget_s=budget)
             if i >= args.warmup:
                 rates.append(r)
+                secs.append(time.perf_counter() - t0)
         v = statistics.median(rates)
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+        # a step of this arm is one bounded sample of the workload (see cpu_baseline.sample)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * statistics.median(secs),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "grid_sample": "256x128 (same per-particle work)"},
