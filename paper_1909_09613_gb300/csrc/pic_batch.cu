@@ -179,7 +179,7 @@ template <int L, int KT>
 __device__ __forceinline__ bool try_tile(const RunDev &rd, int kt, char *smem, int64_t tile)
 {
     if (rd.l != L || kt != KT) return false;
-    tile_2d<L, KT, float>(rd, smem, tile);
+    tile_2d<L, KT, float>(rd, smem, tile, rd.tt);  // the descriptor copy holds the tables
     return true;
 }
 
@@ -347,7 +347,7 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
         }
         const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
         b->max_tc = std::max(b->max_tc, TC);
-        b->smem = std::max(b->smem, stage2d_bytes<float>(rd.reg_nodes, rd.l));
+        b->smem = std::max(b->smem, stage2d_bytes<float>(rd.reg_nodes, rd.l, false));
         for (int s = 0; s < b->nsp; ++s) push_blocks(b->bm_part[s], r, rd.sp[s].n, kBlock * kPartPer);
         push_blocks(b->bm_cell, r, rd.ncell, kBlock * kCellPer);
         push_blocks(b->bm_key, r, rd.ntiles * TC, kBlock * kKeyPer);

@@ -27,8 +27,9 @@ struct TTable {
     double Rfrac;     // R - floor(R)
     double phib;      // interior breakpoint (0 if none)
     double coef[2][PIC_TK_MAX][5];
-    float coef_f[2][PIC_TK_MAX][5];
     float Rfrac_f, phib_f;
+    // coef in FP32, grouped for vector loads: cf4[p][m][g] = coefficient m of nodes 4g .. 4g + 3
+    float4 cf4[2][5][2];
 };
 
 // Scratch of the tile sort (one set per run; the species are sorted one after the other).
@@ -262,19 +263,33 @@ __device__ __forceinline__ int ttable_weights(const TTable &t, R delta, R *w)
     else phib = R(t.phib_f);
     const int p = ge_pos(phi, phib) ? 1 : 0;  // phi >= +0, phib >= +0
     const R tl = phi - (p ? phib : R(0));
+    if constexpr (sizeof(R) == 8) {
 #pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        R acc;
-        if constexpr (sizeof(R) == 8) {
-            acc = R(t.coef[p][k][L]);
+        for (int k = 0; k < KT; ++k) {
+            R acc = R(t.coef[p][k][L]);
 #pragma unroll
             for (int m = L - 1; m >= 0; --m) acc = acc * tl + R(t.coef[p][k][m]);
-        } else {
-            acc = R(t.coef_f[p][k][L]);
-#pragma unroll
-            for (int m = L - 1; m >= 0; --m) acc = acc * tl + R(t.coef_f[p][k][m]);
+            w[k] = acc;
         }
-        w[k] = acc;
+    } else {
+        // the same Horner steps for four nodes at a time: one 16-byte shared load per
+        // coefficient and two packed FMAs (each rounded as the scalar FMA)
+        const float2 t2 = make_float2(tl, tl);
+#pragma unroll
+        for (int g = 0; g < (KT + 3) / 4; ++g) {
+            float4 c = t.cf4[p][L][g];
+            float2 a01 = make_float2(c.x, c.y), a23 = make_float2(c.z, c.w);
+#pragma unroll
+            for (int m = L - 1; m >= 0; --m) {
+                c = t.cf4[p][m][g];
+                a01 = __ffma2_rn(a01, t2, make_float2(c.x, c.y));
+                a23 = __ffma2_rn(a23, t2, make_float2(c.z, c.w));
+            }
+            const float v[4] = {a01.x, a01.y, a23.x, a23.y};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (4 * g + j < KT) w[4 * g + j] = v[j];
+        }
     }
     return base;
 }

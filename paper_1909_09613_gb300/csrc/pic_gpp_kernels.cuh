@@ -64,10 +64,12 @@ __host__ __device__ inline int dep_record_floats(int l)
     }
 }
 
+// own_tt: the stage holds its own copy of the two T tables (false when the caller already
+// keeps the run descriptor, tables included, in shared memory).
 template <typename R>
-__host__ __device__ inline size_t stage2d_fields_bytes(int64_t nodes)
+__host__ __device__ inline size_t stage2d_fields_bytes(int64_t nodes, bool own_tt = true)
 {
-    size_t b = 2 * sizeof(TTable);
+    size_t b = own_tt ? 2 * sizeof(TTable) : 0;
     b += (size_t)nodes * (2 * sizeof(typename Vec2<R>::T) + 5 * sizeof(R));
     return (b + 15) / 16 * 16;
 }
@@ -75,19 +77,21 @@ __host__ __device__ inline size_t stage2d_fields_bytes(int64_t nodes)
 // Dynamic shared memory of a 2D tile block: staged fields and current, plus (FP32 form) the
 // deposit records of its warps.
 template <typename R>
-__host__ __device__ inline size_t stage2d_bytes(int64_t nodes, int l)
+__host__ __device__ inline size_t stage2d_bytes(int64_t nodes, int l, bool own_tt = true)
 {
-    size_t b = stage2d_fields_bytes<R>(nodes);
+    size_t b = stage2d_fields_bytes<R>(nodes, own_tt);
     if (sizeof(R) == 4) b += (size_t)kTileWarps * dep_record_floats(l) * sizeof(float);
     return b;
 }
 
+// tt_shared: T tables already in shared memory (else the stage carries a copy)
 template <typename R>
-__device__ __forceinline__ Stage2D<R> stage2d_carve(char *smem, int64_t nodes)
+__device__ __forceinline__ Stage2D<R> stage2d_carve(char *smem, int64_t nodes,
+                                                    const TTable *tt_shared = nullptr)
 {
     Stage2D<R> s;
-    s.tt = (TTable *)smem;
-    char *p = smem + 2 * sizeof(TTable);
+    s.tt = tt_shared ? (TTable *)tt_shared : (TTable *)smem;
+    char *p = smem + (tt_shared ? 0 : 2 * sizeof(TTable));
     s.pa = (typename Vec2<R>::T *)p; p += nodes * sizeof(typename Vec2<R>::T);
     s.pb = (typename Vec2<R>::T *)p; p += nodes * sizeof(typename Vec2<R>::T);
     s.e3 = (R *)p; p += nodes * sizeof(R);
@@ -95,7 +99,7 @@ __device__ __forceinline__ Stage2D<R> stage2d_carve(char *smem, int64_t nodes)
     s.j1 = (R *)p; p += nodes * sizeof(R);
     s.j2 = (R *)p; p += nodes * sizeof(R);
     s.j3 = (R *)p;
-    s.rec = (float *)(smem + stage2d_fields_bytes<R>(nodes));
+    s.rec = (float *)(smem + stage2d_fields_bytes<R>(nodes, tt_shared == nullptr));
     return s;
 }
 
@@ -105,8 +109,9 @@ __device__ void stage2d_load(const RunDev &rd, const Stage2D<R> &st, int x0, int
 {
     const int RX = rd.reg[0];
     const int64_t nodes = rd.reg_nodes;
-    for (int i = threadIdx.x; i < (int)(2 * sizeof(TTable) / sizeof(int)); i += blockDim.x)
-        ((int *)st.tt)[i] = ((const int *)rd.tt)[i];
+    if (st.tt != rd.tt)
+        for (int i = threadIdx.x; i < (int)(2 * sizeof(TTable) / sizeof(int)); i += blockDim.x)
+            ((int *)st.tt)[i] = ((const int *)rd.tt)[i];
     for (int64_t n = threadIdx.x; n < nodes; n += blockDim.x) {
         const int rx = (int)(n % RX), ry = (int)(n / RX);
         const int gx = wrap_idx(x0 - rd.pre[0] + rx, rd.n[0]);
@@ -695,11 +700,12 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
     }
 }
 
-// All particles of one tile (both species), 2D.
+// All particles of one tile (both species), 2D.  tt_shared as in stage2d_carve.
 template <int L, int KT, typename R>
-__device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile)
+__device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
+                        const TTable *tt_shared = nullptr)
 {
-    Stage2D<R> st = stage2d_carve<R>(smem, rd.reg_nodes);
+    Stage2D<R> st = stage2d_carve<R>(smem, rd.reg_nodes, tt_shared);
     const int tx = (int)(tile % rd.ntile[0]);
     const int ty = (int)(tile / rd.ntile[0]);
     const int x0 = tx * rd.tile[0], y0 = ty * rd.tile[1];

@@ -142,8 +142,15 @@ bool build_ttable(int l, int scheme, double dtt_d, TTable *t)
         }
     }
     for (int p = 0; p < 2; ++p)
-        for (int k = 0; k < PIC_TK_MAX; ++k)
-            for (int m = 0; m < 5; ++m) t->coef_f[p][k][m] = (float)t->coef[p][k][m];
+        for (int m = 0; m < 5; ++m)
+            for (int g = 0; g < 2; ++g) {
+                float v[4];
+                for (int j = 0; j < 4; ++j) {
+                    const int k = 4 * g + j;
+                    v[j] = k < PIC_TK_MAX ? (float)t->coef[p][k][m] : 0.0f;
+                }
+                t->cf4[p][m][g] = make_float4(v[0], v[1], v[2], v[3]);
+            }
     t->Rfrac_f = (float)t->Rfrac;
     t->phib_f = (float)t->phib;
     // the float split must reproduce the same breakpoint ordering
