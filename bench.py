@@ -53,7 +53,7 @@ FP64_INSTR_PER_PARTICLE = 390.5
 # The kernel is bound by instruction issue, not by DRAM: its issue-slot view divides the issued
 # instructions per second by the issue rate, one warp instruction per clock on each of the four
 # schedulers of the 152 SMs.
-FP32_WARP_INSTR_PER_PARTICLE = 40.43
+FP32_WARP_INSTR_PER_PARTICLE = 40.25
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 
