@@ -516,23 +516,25 @@ def served_form(n_req=48, steps=100, budget=150e9, seed=None):
     makespan = time.perf_counter() - t0
     lat = [r.latency for r in res]
     work = sum(r.particles * r.steps for r in res)
-    # plain single-run baseline latency: a sample of requests run alone, one after another
-    alone = []
+    # single-run baseline latency: a sample of requests run alone, one after another, in their
+    # own (FP32) form and in the plain FP64 form
+    alone, alone64 = [], []
     for r in reqs[:6]:
-        run = engine.make_run(r)
-        torch.cuda.synchronize()
-        ta = time.perf_counter()
-        run.step(r.steps)
-        torch.cuda.synchronize()
-        alone.append(time.perf_counter() - ta)
-        run.close()
+        for prec, dst in ((None, alone), (pic.PIC_FP64, alone64)):
+            run = engine.make_run(r, precision=prec)
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            run.step(r.steps)
+            torch.cuda.synchronize()
+            dst.append(time.perf_counter() - ta)
+            run.close()
     return {"value": work / makespan, "unit": UNIT, "requests": len(res),
             "p50_latency_s": engine.percentile(lat, 50), "p99_latency_s": engine.percentile(lat, 99),
             "arrival_rate_per_s": lam, "service_capacity_particle_steps_per_s": cap,
             "makespan_s": makespan, "max_concurrent_runs": srv.max_active,
             "peak_admitted_bytes": srv.peak_bytes, "budget_bytes": budget,
             "steps_per_request": steps, "requests_3d": sum(1 for r in reqs if r.dim == 3),
-            "alone_latency_s_sample": alone,
+            "alone_latency_s_sample": alone, "alone_fp64_plain_latency_s_sample": alone64,
             "error_flags": sum(r.diag.get("error_flags", 0) for r in res)}
 
 

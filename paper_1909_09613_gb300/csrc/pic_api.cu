@@ -310,11 +310,8 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     for (int a = 0; a < dim; ++a)
         if (!(dx[a] > 0.0) || !std::isfinite(dx[a])) return PIC_EINVAL;
     if (!(dt > 0.0) || !std::isfinite(dt)) return PIC_EINVAL;
-    double s2 = 0.0;
-    for (int a = 0; a < dim; ++a) {
-        s2 += 1.0 / (dx[a] * dx[a]);
-        if (dt / dx[a] >= 1.0) return PIC_ECFL;
-    }
+    for (int a = 0; a < dim; ++a)
+        if (dt / dx[a] >= 1.0) return PIC_ECFL;  // the one-cell-per-step bound of the move
     pic_options o;
     std::memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
@@ -341,7 +338,6 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
         }
         if (!(worst < 1.0)) return PIC_ECFL;
     }
-    (void)s2;
     if (o.n_species <= 0) o.n_species = 2;
     if (o.n_species > PIC_MAX_SPECIES) return PIC_EINVAL;
     if (o.precision != PIC_FP64 && o.precision != PIC_FP32_MIXED) return PIC_EINVAL;
