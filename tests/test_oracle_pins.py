@@ -747,3 +747,30 @@ def test_juttner_loader_matches_the_distribution(theta):
     up = wl.species[0].u.numpy()
     m2 = (up ** 2).mean(axis=1)
     assert np.max(np.abs(m2 / m2.mean() - 1.0)) < 0.03
+
+
+def test_juttner_attempt_bound(monkeypatch):
+    """The bounded Sobol loop: with a single attempt per particle the accepted fraction is the
+    acceptance probability of one attempt, P(eta^2 - u^2 > 1), evaluated by quadrature from the
+    method's own construction (below), and every particle left without an accepted attempt is
+    marked NaN rather than given a biased speed."""
+    import torch
+    import workloads
+    from scipy import integrate
+    theta, n = 0.3, 200000
+    keys = [workloads.stream_key(12, 0, 0, 40 + j) for j in range(4)]
+    monkeypatch.setattr(workloads, "JUTTNER_ATTEMPTS", 1)
+    u = workloads.juttner_speeds(theta, keys, torch.arange(n)).numpy()
+    acc = np.isfinite(u)
+    # one attempt proposes u ~ Gamma(3, theta) (density u^2 e^{-u/theta} / (2 theta^3)) and
+    # accepts it with probability e^{-(sqrt(1+u^2) - u)/theta}; the accepted fraction is the
+    # integral of their product
+    f = lambda x: x * x * math.exp(-x / theta) / (2.0 * theta ** 3) \
+        * math.exp(-(math.sqrt(1.0 + x * x) - x) / theta)
+    p = integrate.quad(f, 0, np.inf, limit=200)[0]
+    assert abs(acc.mean() - p) < 5.0 * math.sqrt(p * (1 - p) / n)
+    assert np.all(u[acc] > 0.0)
+    # with the default bound no particle is left unsampled at the lowest supported theta
+    monkeypatch.setattr(workloads, "JUTTNER_ATTEMPTS", 128)
+    u = workloads.juttner_speeds(theta, keys, torch.arange(n)).numpy()
+    assert np.isfinite(u).all()
