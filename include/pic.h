@@ -188,6 +188,15 @@ int pic_read_tile_offsets(pic_ctx *ctx, int species, int64_t *offsets, int64_t c
 int pic_tile_info(const pic_ctx *ctx, int32_t tile[3], int64_t *ntiles, int32_t *sort_interval,
                   int32_t *slot_major);
 
+/* Dynamic shared memory per CTA of the 2D particle kernel of this context (*own_bytes) and of
+ * this run's work items in the batched kernel (*batched_bytes; 0 for the FP64 form and in 3D),
+ * and the largest per-CTA amount with which two CTAs still share an SM of the current device
+ * (*two_per_sm_bytes; 0 when no device is present).  Host query: no device work.  A batch runs
+ * at the largest *batched_bytes of its runs, so runs that stay within *two_per_sm_bytes keep two
+ * CTAs per SM.  Any out pointer may be NULL.                                                  */
+int pic_smem_info(const pic_ctx *ctx, size_t *own_bytes, size_t *batched_bytes,
+                  size_t *two_per_sm_bytes);
+
 /* Re-sort all species by tile now (also done automatically every sort_interval steps). */
 int pic_sort(pic_ctx *ctx);
 

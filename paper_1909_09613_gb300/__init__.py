@@ -84,6 +84,9 @@ _SIGS = [
                                           ctypes.c_int64]),
     ("pic_read_tile_offsets", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_lp, ctypes.c_int64]),
     ("pic_tile_info", ctypes.c_int, [ctypes.c_void_p, _c_ip, _c_lp, _c_ip, _c_ip]),
+    ("pic_smem_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t)]),
     ("pic_sort", ctypes.c_int, [ctypes.c_void_p]),
     ("pic_diag", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_diag_t)]),
     ("pic_sync", ctypes.c_int, [ctypes.c_void_p]),
@@ -242,6 +245,14 @@ def pic_tile_info(ctx):
     _check(load_library().pic_tile_info(ctx, t, ctypes.byref(nt), ctypes.byref(si),
                                         ctypes.byref(sm)), "pic_tile_info")
     return tuple(t), int(nt.value), int(si.value), int(sm.value)
+
+
+def pic_smem_info(ctx):
+    """(own kernel's shared memory per CTA, batched kernel's for this run, two-per-SM limit)"""
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load_library().pic_smem_info(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "pic_smem_info")
+    return int(a.value), int(b.value), int(c.value)
 
 
 def pic_sort(ctx):

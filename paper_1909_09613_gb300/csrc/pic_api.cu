@@ -15,6 +15,7 @@ namespace pic {
 cudaError_t launch_gpp_f32(const RunDev &rd, int kt, cudaStream_t st);
 cudaError_t launch_gpp_f64(const RunDev &rd, int kt, cudaStream_t st);
 size_t gpp_smem_bytes_f32(const RunDev &rd);
+size_t gpp_batch_smem_bytes_f32(const RunDev &rd);
 size_t gpp_smem_bytes_f64(const RunDev &rd);
 }  // namespace pic
 
@@ -767,6 +768,32 @@ int pic_tile_info(const pic_ctx *c, int32_t tile[3], int64_t *ntiles, int32_t *s
         for (int a = 0; a < 3; ++a) tile[a] = c->rd.tile[a];
     if (ntiles) *ntiles = c->rd.ntiles;
     if (sort_interval) *sort_interval = c->sort_interval;
+    return PIC_OK;
+}
+
+int pic_smem_info(const pic_ctx *c, size_t *own_bytes, size_t *batched_bytes,
+                  size_t *two_per_sm_bytes)
+{
+    if (!c) return PIC_EINVAL;
+    if (own_bytes) *own_bytes = c->smem;
+    if (batched_bytes)
+        *batched_bytes = c->rd.prec == PIC_FP32_MIXED ? gpp_batch_smem_bytes_f32(c->rd) : 0;
+    if (two_per_sm_bytes) {
+        *two_per_sm_bytes = 0;
+        int dev = 0, per_sm = 0, reserved = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess
+            && cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)
+                   == cudaSuccess
+            && cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)
+                   == cudaSuccess) {
+            // two blocks of dynamic + static + reserved shared memory per SM; 64 bytes cover
+            // the kernels' static shared variables
+            const long v = (long)per_sm / 2 - reserved - 64;
+            *two_per_sm_bytes = v > 0 ? (size_t)v : 0;
+        } else {
+            cudaGetLastError();  // no device: leave 0
+        }
+    }
     return PIC_OK;
 }
 

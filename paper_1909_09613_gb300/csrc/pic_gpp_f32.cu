@@ -53,4 +53,12 @@ size_t gpp_smem_bytes_f32(const RunDev &rd)
     return rd.dim == 2 ? stage2d_bytes<float>(rd.reg_nodes, rd.l) : 0;
 }
 
+// Dynamic shared memory a work item of this run needs in the batched kernel: the copy of the
+// run descriptor (tables included) and a stage without its own tables.
+size_t gpp_batch_smem_bytes_f32(const RunDev &rd)
+{
+    if (rd.dim != 2) return 0;
+    return (sizeof(RunDev) + 15) / 16 * 16 + stage2d_bytes<float>(rd.reg_nodes, rd.l, false);
+}
+
 }  // namespace pic

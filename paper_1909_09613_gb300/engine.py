@@ -126,6 +126,43 @@ class Autotuner:
         return best[1], best[2]
 
 
+# Tiles tried, in order, when the tuned tile of a batchable run would give its batched work
+# items more shared memory than two CTAs per SM leave (a batch runs at the largest of its runs)
+BATCH_FALLBACK_TILES = ((32, 16), (32, 8), (16, 16), (16, 8))
+
+
+def fit_batch_tile(req: Request, tile, si):
+    """The tuned (tile, sort interval) of a batchable request, or the first of the fallback
+    tiles (then with half the sort interval, a narrower drift halo) whose stage keeps two CTAs
+    per SM in the batched kernel (pic_smem_info; a host query, no device memory)."""
+    def fits(t, k):
+        opt = pic.pic_options()
+        opt.precision = pic.PIC_FP32_MIXED
+        opt.n_species = 2
+        n = req.grid[0] * req.grid[1] * req.ppc // 2
+        opt.capacity[0] = n
+        opt.capacity[1] = n
+        opt.tile[0], opt.tile[1], opt.tile[2] = t[0], t[1], 1
+        opt.sort_interval = k
+        try:
+            ctx = pic.pic_create(req.grid, (1.0, 1.0, 1.0), req.dt, req.l, req.scheme, opt)
+        except pic.PicError:
+            return False
+        try:
+            _, batched, two = pic.pic_smem_info(ctx)
+        finally:
+            pic.pic_destroy(ctx)
+        return two == 0 or batched <= two
+    if fits(tile, si):
+        return tile, si
+    for k in (si, max(1, si // 2)):
+        for t in BATCH_FALLBACK_TILES:
+            t = (min(t[0], req.grid[0]), min(t[1], req.grid[1]), 1)
+            if fits(t, k):
+                return t, k
+    return tile, si
+
+
 def make_run(req: Request, precision=None, tuner: Optional[Autotuner] = None,
              stream=None, device="cuda"):
     """Create, bind and load one run for a request (seeded drifting pair plasma)."""
@@ -141,6 +178,7 @@ def make_run(req: Request, precision=None, tuner: Optional[Autotuner] = None,
     if tuner is not None and req.batchable and precision == pic.PIC_FP32_MIXED:
         tile, si = tuner.choose(req.l, req.ppc, req.dt)
         tile = (min(tile[0], req.grid[0]), min(tile[1], req.grid[1]), 1)
+        tile, si = fit_batch_tile(req, tile, si)
     caps = [int(s.x.shape[1]) for s in wl.species]
     run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=precision, capacity=caps,
                   tile=tile, sort_interval=si, stream=stream, solver=req.solver)

@@ -112,6 +112,29 @@ def test_size_limits(lib):
         assert e.value.status == pic.PIC_EINVAL, (grid, cap, tile)
 
 
+def test_smem_info(lib):
+    """Shared memory per CTA of the particle kernels (host query): the batched kernel's stage
+    carries no T tables of its own but a copy of the run descriptor; the FP64 form has no
+    batched items; a larger tile needs more; without a device the two-per-SM limit is 0."""
+    sizes = {}
+    for tile in ((16, 8), (64, 8)):
+        o = _opt((1 << 20, 1 << 20), pic.PIC_FP32_MIXED)
+        o.tile[0], o.tile[1], o.tile[2] = tile[0], tile[1], 1
+        ctx = pic.pic_create((512, 256, 1), (1.0, 1.0, 1.0), 0.4, 3, pic.PIC_SCHEME_WT, o)
+        try:
+            sizes[tile] = pic.pic_smem_info(ctx)
+        finally:
+            pic.pic_destroy(ctx)
+    own, batched, two = sizes[(64, 8)]
+    assert own > 64 * 1024 and batched > 0 and abs(batched - own) < 8 * 1024
+    assert sizes[(16, 8)][0] < own and sizes[(16, 8)][1] < batched
+    ctx = pic.pic_create((512, 256, 1), (1.0, 1.0, 1.0), 0.4, 3, pic.PIC_SCHEME_WT, _opt())
+    try:
+        assert pic.pic_smem_info(ctx)[1] == 0
+    finally:
+        pic.pic_destroy(ctx)
+
+
 def test_create_m4_courant_limit(lib):
     """Courant limit with the M4 stencil (App. C): on these grids the worst wavenumber is a
     corner of the Brillouin zone and the limit coincides with Yee's (1/sqrt(2) for dx = dy,
