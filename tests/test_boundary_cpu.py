@@ -247,3 +247,11 @@ def test_neutral_start_colocates_species():
     b = workloads.pair_plasma((8, 4), (1.0, 1.0), 0.3, 2, 1, 50.0, 0.1, 4)
     assert not np.array_equal(b.species[0].x.numpy(), b.species[1].x.numpy())
     assert np.array_equal(a.species[0].x.numpy(), b.species[0].x.numpy())
+
+
+def test_fit_batch_tile_without_device_keeps_the_tuned_tile(lib):
+    """Without a device the two-per-SM limit is unknown (0): the tuned tile stands."""
+    from paper_1909_09613_gb300 import engine
+    req = engine.Request(rid=0, grid=(512, 256, 1), l=3, dt=0.7, gamma=20.0, u_th=0.01, ppc=32,
+                         steps=1)
+    assert engine.fit_batch_tile(req, (64, 16, 1), 4) == ((64, 16, 1), 4)

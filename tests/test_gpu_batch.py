@@ -195,3 +195,31 @@ def test_batch_full_scale_sampled_particles():
     b.close()
     for r in runs:
         r.close()
+
+
+def test_batch_tiles_keep_two_ctas_per_sm():
+    """A batch runs at the largest shared-memory stage of its runs.  For batchable requests whose
+    tuned tile would exceed what two CTAs per SM leave, the engine picks a fallback tile that
+    fits (pic_smem_info on the device), and the fitted tile is unchanged when it already fits."""
+    from paper_1909_09613_gb300 import engine
+    two = None
+    for l, dt, ppc in ((3, 0.7, 32), (2, 0.6, 8), (3, 0.25, 16)):
+        req = engine.Request(rid=0, grid=(512, 256, 1), l=l, dt=dt, gamma=20.0, u_th=0.01,
+                             ppc=ppc, steps=1)
+        for tile in ((64, 16, 1), (32, 32, 1), (64, 8, 1)):
+            t, si = engine.fit_batch_tile(req, tile, 4)
+            opt = pic.pic_options()
+            opt.precision = pic.PIC_FP32_MIXED
+            opt.n_species = 2
+            opt.capacity[0] = opt.capacity[1] = 512 * 256 * ppc // 2
+            opt.tile[0], opt.tile[1], opt.tile[2] = t
+            opt.sort_interval = si
+            ctx = pic.pic_create(req.grid, (1.0, 1.0, 1.0), dt, l, req.scheme, opt)
+            try:
+                own, batched, two = pic.pic_smem_info(ctx)
+            finally:
+                pic.pic_destroy(ctx)
+            assert two > 100 * 1024          # a device is present
+            assert batched <= two, (l, dt, tile, t, batched, two)
+            if t == tile:
+                assert si == 4
