@@ -563,6 +563,9 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-loader", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=None,
+                    help="reference arm: seconds of oracle work per step (default: about a "
+                         "minute over all steps)")
     args = ap.parse_args()
     rank, world, local = _rank_env()
 
@@ -575,7 +578,8 @@ def main():
         # same per-particle work as the full grid (the oracle's cost is per particle)
         wl_full = wl
         rates, secs = [], []
-        budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+        budget = (args.ref_budget if args.ref_budget is not None
+                  else max(2.0, 60.0 / max(1, args.steps + args.warmup)))
         for i in range(args.warmup + args.steps):
             t0 = time.perf_counter()
             r, sample = cpu_baseline(wl_full, budget_s=budget)
