@@ -1,12 +1,15 @@
-// Fused gather -> Boris push -> move -> Esirkepov deposit for one particle tile.
+// Fused gather -> Boris push -> move -> Esirkepov deposit for one particle tile: the WT (or MC)
+// field interpolation of Sec. 2 (Eq. interpolation-EB-real-mod), the relativistic Boris push
+// (Sec. 1, in the dimensionless equations of motion of App. E) and Esirkepov's charge-conserving
+// current with the B-spline form factor W_l, which the WT scheme keeps (Sec. 1, end of Sec. 2).
 //
 // One CTA owns one tile of cells.  In 2D it stages the tile's E and B (plus a halo covering the
 // interpolation stencils and the drift since the last sort) in shared memory, walks the tile's
-// particles (contiguous in the sorted store), gathers with the WT (or MC) weights, pushes,
-// moves, and accumulates the Esirkepov current of every particle in a shared-memory J tile,
-// which is then added to the global FP64 current with one atomic per tile node and component,
-// once per species.  In 3D the halo would not fit, so fields are read through the L1 cache and
-// the current goes straight to global atomics.
+// particles (contiguous in the sorted store), gathers, pushes and moves them.  The FP32 form sums
+// its lanes' currents through shared memory into a J tile that is added to the global FP64
+// current with one atomic per tile node and component, once per species; the FP64 form, bound
+// by its FP64 pipe, adds every contribution to the global current as an L2 reduction.  In 3D
+// fields are read through the L1 cache and the current goes straight to global reductions.
 #pragma once
 #include "pic_common.cuh"
 
@@ -59,7 +62,8 @@ __device__ __forceinline__ void load_particle(const RunDev &rd, const SpeciesDev
     for (int a = 0; a < 3; ++a) s.u[a] = __ldg((const R *)sp.mom[a] + p);
 }
 
-// ---- weights of one axis ------------------------------------------------------------------
+// ---- weights of one axis: W_l at half-integer nodes (Eq. shape-real), T_l of Eq. tau_l (WT) or
+// W_l (MC) at integer nodes -------------------------------------------------------------------
 
 template <int L, int KT, typename R>
 struct AxisW {
@@ -79,7 +83,7 @@ __device__ __forceinline__ void axis_weights(const TTable &tt, R d, AxisW<L, KT,
 }
 
 // Esirkepov window of one axis: S0 (old-position weights) and DS = S1 - S0 on l+2 nodes
-// starting at node wb (relative to the old cell).
+// starting at node wb (relative to the old cell); the charge form factor is W_l (Sec. 1).
 template <int L, typename R>
 struct AxisS {
     int wb;
@@ -217,7 +221,8 @@ __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rcp_r(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp_r(float x) { return __frcp_rn(x); }
 
-// Relativistic Boris rotation u^{n-1/2} -> u^{n+1/2}; h = q dt / (2 m).  Returns 1/gamma^{n+1/2}.
+// Relativistic Boris rotation u^{n-1/2} -> u^{n+1/2} (Sec. 1; units of App. E, u = gamma v,
+// c = 1); h = q dt / (2 m).  Returns 1/gamma^{n+1/2}.
 template <typename R>
 __device__ __forceinline__ R boris(R h, const R *E, const R *B, R *u)
 {
@@ -241,10 +246,10 @@ __device__ __forceinline__ R boris(R h, const R *E, const R *B, R *u)
     return rsqrt_r(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 }
 
-// Move one axis in cell units: returns the cell shift sh in {-1,0,1} and the new offset o in
-// [0,1).  In the FP64 form o is re-derived from the stored value cell + o so that the next
-// step's old-position weights are bit-identical to this step's new-position weights; xs is that
-// stored value (unused for FP32).
+// Move one axis in cell units, x^{n+1} = x^n + dt u^{n+1/2} / gamma^{n+1/2} (App. E): returns
+// the cell shift sh in {-1,0,1} and the new offset o in [0,1).  In the FP64 form o is re-derived
+// from the stored value cell + o so that the next step's old-position weights are bit-identical
+// to this step's new-position weights; xs is that stored value (unused for FP32).
 template <typename R>
 __device__ __forceinline__ int move_axis(R d, R delta, int c, int n, R &o, int &cn, R &xs)
 {

@@ -170,8 +170,9 @@ __device__ __forceinline__ bool local_coord(int c, int origin, int tile, int dri
     return l >= -drift && l < tile + drift;
 }
 
-// One lane's Esirkepov window added to the shared current tile with atomics (WY as in
-// deposit_lane_global below).
+// One lane's Esirkepov window (Sec. 1: W_x = DSx (S0y + DSy/2) summed along x, W_y likewise,
+// W_z = S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3) added to the shared current tile with
+// atomics (WY as in deposit_lane_global below).
 template <int L, typename R, bool WY = true>
 __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int jx0, int jy0, R kx,
                                              R ky, R kz, const R *px, const R *py, const R *Ax,
