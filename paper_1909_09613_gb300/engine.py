@@ -6,7 +6,9 @@ libpic's kernels (pic_step for a run on its own, pic_batch_step for a batch).
 * `Autotuner` picks the particle-tile extent and the sort interval of a run by timing short
   probe runs of the same spline order and particle density and keeping the fastest full step
   (sort cost included).
-* `make_run` builds a run from a request and loads its seeded particles on the device.
+* `make_run` builds a run from a request and loads its seeded particles on the device; for a
+  batchable run `fit_batch_tile` keeps the tuned tile only if its shared-memory stage still
+  lets the batched kernel hold two CTAs per SM (a batch runs at the largest stage of its runs).
 * `Server` is a continuous-batching request loop: requests (NCI-scan runs: grid, c dt, drift
   gamma, particles per cell) arrive over time, are admitted when the device-memory budget has
   room, stay resident until their last step, and are advanced in chunks of steps -- every 2D
