@@ -2,8 +2,9 @@
 """Benchmark of the WT-scheme PIC step on GB300 (one JSON line on rank 0).
 
 Workload (default): the 2048x1024 periodic drifting pair plasma, cubic B-splines, WT gather,
-gamma = 50, u_th = 0.01 (App. D loading), 64 particles per cell = 134,217,728 particles,
-c dt = 0.25 dx, in the plain FP64 single-run form.  A step is one full PIC step through
+gamma = 50, u_th = 0.01 (App. D loading, generated in HBM by the library's device loader),
+64 particles per cell = 134,217,728 particles, c dt = 0.25 dx, in the plain FP64 single-run
+form.  A step is one full PIC step through
 pic_step: gather + Boris + move + Esirkepov deposit (the fused particle kernel), the periodic
 Yee update, and the tile sort every sort_interval steps.  The same workload in the precision
 form (int32 cell + FP32 offset, FP32 push/gather/tile current, FP64 fields) is reported under
@@ -13,7 +14,8 @@ form (int32 cell + FP32 offset, FP32 push/gather/tile current, FP64 fields) is r
 
 Under torchrun (N > 1) every rank advances its own replica of the run (independent runs, no
 collective on the data path); value = particle-steps of all ranks / max-over-ranks time.
---impl reference times the FP64 CPU oracle on the host cores on a bounded sample.
+--impl reference times the FP64 CPU oracle (its OpenMP timing build, all host cores) on a
+bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -35,26 +37,21 @@ UNIT = "particle-steps/s"
 WORKLOAD = "pair_2048x1024_l3_WT_g50_uth0.01_ppc64_cdt0.25"
 
 # Algorithmic bytes of the fused particle kernel (per particle-step, per cell-step):
-#   FP64 form: particle read + write 2 x (2 x 8 position + 3 x 8 momentum) = 80 B, plus the
-#              cached B-spline weights of the stored positions read and written,
-#              2 x 2 (l + 1) x 8 B = 128 B for l = 3: 208 B;
-#              grid: E, B read once (6 x 8 B) + J written (3 x 8 B) = 72 B per cell.
+#   FP64 form: particle read + write 2 x (2 x 8 position + 3 x 8 momentum) = 80 B per
+#              particle-step (the method's bytes); grid: E, B read once (6 x 8 B) + J written
+#              (3 x 8 B) = 72 B per cell.  The kernel also reads and writes the B-spline
+#              weights of the stored positions, 2 x 2 (l + 1) x 8 B = 128 B for l = 3, a cache
+#              that spends HBM bytes to save FP64 instructions (the form is bound by its FP64
+#              pipe), reported beside the roofline as extra traffic.
 #   FP32 form: 2 x (4 cell + 2 x 4 offset + 3 x 4 momentum) = 48 B;
 #              grid: FP32 shadow of E, B (6 x 4 B) + FP64 J (3 x 8 B) = 48 B per cell.
-BYTES = {"fp64": (208.0, 72.0), "fp32": (48.0, 48.0)}
-# FP64 operations of the fused kernel per particle-step (l = 3, WT, 2D), from the ncu
-# instruction counts in profiles/gpp2d_fp64_l3_pair512x256.md (DADD + DMUL + 2 x DFMA divided by
-# the particles of the launch, a step that reads the weight cache), and the FP64 instructions
-# (DADD + DMUL + DFMA).  Used for the FP64 arithmetic roofline of the plain form.
-FP64_FLOPS_PER_PARTICLE = 621.5
-FP64_INSTR_PER_PARTICLE = 390.5
-# Warp instructions the FP32 form's fused kernel issues per particle (ncu smsp__inst_executed
-# over the particles of the 512x256 capture in profiles/gpp2d_fp32_l3_pair512x256.md, l = 3).
-# The kernel is bound by instruction issue, not by DRAM: its issue-slot view divides the issued
-# instructions per second by the issue rate, one warp instruction per clock on each of the four
-# schedulers of the 152 SMs.
-FP32_WARP_INSTR_PER_PARTICLE = 40.25
-SMS, SCHEDULERS_PER_SM = 152, 4
+BYTES = {"fp64": (80.0, 72.0), "fp32": (48.0, 48.0)}
+WEIGHT_CACHE_BYTES_FP64_L3 = 128.0
+SCHEDULERS_PER_SM = 4
+# The particle kernel's sources: the counts of profiles/counts.txt (from one ncu capture) are
+# used only while these files hash to the digest recorded with them.
+KERNEL_SOURCES = ("pic_common.cuh", "pic_gpp.cuh", "pic_gpp_kernels.cuh", "pic_gpp_f32.cu",
+                  "pic_gpp_f64.cu")
 
 
 def _rank_env():
@@ -70,24 +67,30 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _profile_traffic(kernel: str):
-    """DRAM bytes per launch recorded from an ncu capture, if the kernel sources are unchanged."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
+def kernel_digest():
+    """sha256 (16 hex digits) of the particle kernel's source files."""
+    import hashlib
+    from paper_1909_09613_gb300 import _build
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(_build.CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_counts(kernel: str):
+    """The counts recorded from an ncu capture of `kernel` (profiles/counts.txt: kernel, source
+    digest, key=value ...), if the kernel sources still hash to the recorded digest; else {}
+    (the numbers no longer describe the code)."""
+    path = os.path.join(ROOT, "profiles", "counts.txt")
     try:
-        from paper_1909_09613_gb300 import _build
-        import hashlib
-        import glob
-        h = hashlib.sha256()
-        for f in sorted(glob.glob(os.path.join(_build.CSRC, "*"))):
-            h.update(open(f, "rb").read())
-        digest = h.hexdigest()[:16]
+        digest = kernel_digest()
         for line in open(path):
             parts = line.split()
             if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
-                return float(parts[2])
+                return {k: float(v) for k, v in (p.split("=") for p in parts[2:])}
     except Exception:
         pass
-    return None
+    return {}
 
 
 class ClockSampler:
@@ -171,14 +174,25 @@ def replica_rate(particles_per_rank, world, steps, ms_max):
     return particles_per_rank * world * steps / (ms_max * 1e-3)
 
 
+def load_device(run, wl):
+    """Generate the workload's plasma in the run's stores with the device loader (App. D)."""
+    for i, s in enumerate(wl.species):
+        if wl.theta > 0.0:
+            run.load_drifting_juttner(i, s.q, s.m, s.w, s.per_cell, wl.gamma, wl.theta,
+                                      seed=wl.seed, run=wl.run, pos_species=s.pos_species)
+        else:
+            run.load_drifting_plasma(i, s.q, s.m, s.w, s.per_cell, wl.gamma, wl.u_th,
+                                     seed=wl.seed, run=wl.run, pos_species=s.pos_species)
+
+
 def time_form(wl, prec, steps, warmup, dist_on, clocks=True):
-    """Load the workload (device-resident inputs), warm up, time `steps` full steps."""
+    """Load the workload on the device (inputs resident in HBM), warm up, time `steps` full
+    steps with CUDA events on the run's stream."""
     import torch
     import paper_1909_09613_gb300 as pic
-    caps = [int(s.x.shape[1]) for s in wl.species]
+    caps = [wl.ncell * s.per_cell for s in wl.species]
     run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps)
-    for i, s in enumerate(wl.species):
-        run.load(i, s.q, s.m, s.w, s.x, s.u)
+    load_device(run, wl)
     run.step(warmup)
     run.sync()
     stream = run.stream
@@ -202,21 +216,32 @@ def time_form(wl, prec, steps, warmup, dist_on, clocks=True):
     clk = sampler.stop() if sampler else None
     run.sync()
     d = run.diag()
+    run.step(1)
+    d1 = run.diag()  # one step after the previous pic_diag: the continuity residual
     out = {"ms": _max_over_ranks(ms, dist_on), "gpp_ms": gpp_ms, "gpp_launches": gpp_n,
            "launches": launches, "clocks": clk, "n": sum(caps), "ncell": wl.ncell,
            "sort_interval": run.sort_interval, "tile": run.tile, "diag_status": d["status"],
+           "charge_conservation": {
+               "max_continuity_residual": d1["max_continuity_residual"],
+               "max_gauss_residual_drift": d1["max_gauss_residual_drift"],
+               "rho_scale": abs(wl.species[0].q * wl.species[0].w) * wl.species[0].per_cell},
            "run": run}
     return out
 
 
 def e2e_form(run, wl, steps):
-    """Same metric through the public C-ABI from pinned host buffers: load (H2D) + steps +
-    diagnostics read-back (D2H), every byte counted."""
+    """Same metric through the public C-ABI from pinned host buffers: load (H2D, pack, sort) +
+    steps + diagnostics read-back (D2H), every byte counted.  The host arrays are the run's
+    own initial state, read back once before timing (the same plasma the device loader drew)."""
     import torch
-    xs = [s.x.cpu().pin_memory() for s in wl.species]
-    us = [s.u.cpu().pin_memory() for s in wl.species]
-    h2d = sum(x.numel() * 8 + u.numel() * 8 for x, u in zip(xs, us))
     import paper_1909_09613_gb300 as pic
+    xs, us = [], []
+    for i in range(len(wl.species)):
+        x, u, _ = run.particles(i)
+        xs.append(torch.from_numpy(x).pin_memory())
+        us.append(torch.from_numpy(u).pin_memory())
+        del x, u
+    h2d = sum(x.numel() * 8 + u.numel() * 8 for x, u in zip(xs, us))
 
     def load():
         for i, s in enumerate(wl.species):
@@ -247,8 +272,8 @@ def e2e_form(run, wl, steps):
     run.step(steps)
     d = run.diag()
     t1 = time.perf_counter()
-    d2h = 48  # pic_diag_t
-    n = sum(int(s.x.shape[1]) for s in wl.species)
+    d2h = 72  # pic_diag_t
+    n = sum(int(x.shape[1]) for x in xs)
     return {"value": n * steps / (t1 - t0), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(math.ceil(d2h / steps)),
             "status": d["status"], "load_s": tl - t0, "steps_and_diag_s": t1 - tl,
@@ -256,29 +281,50 @@ def e2e_form(run, wl, steps):
             "warmup_load_s": [round(w, 4) for w in warm]}
 
 
-def cpu_baseline(wl, budget_s=12.0):
-    """The FP64 oracle as it stands, single thread, on a bounded sample of the workload:
-    the particle pass (gather + push + deposit) of the first S particles of each species on
-    the full grid.  Returns (particle-steps/s, sample description)."""
+def cpu_baseline(budget_s=8.0, one_core=True):
+    """The FP64 oracle as it stands (its OpenMP timing build: particles split over threads,
+    per-thread current buffers added at the end), on all host cores and on one core, over a
+    bounded sample of the large workload: the particle pass (gather + push + deposit) of the
+    same plasma on a 256x128 section of the grid (64 per cell, the same per-particle work;
+    the oracle's cost is per particle).  Returns a dict for the bench line."""
     import oracle
-    oracle.build()
-    dim = wl.dim
-    S = 2000
-    sim = oracle.Sim(wl.grid[:dim], wl.dx[:dim], wl.dt, wl.l, wl.scheme)
-    for s in wl.species:
-        sim.add_species(s.q, s.m, s.w, s.x[:, :S].cpu().numpy(), s.u[:, :S].cpu().numpy())
-    t0 = time.perf_counter()
-    sim.particle_pass(0, S)
-    one = time.perf_counter() - t0
-    reps = max(1, int(budget_s / max(one, 1e-6)) - 1)
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        sim.particle_pass(0, S)
-    t = time.perf_counter() - t0
+    import workloads
+    oracle.build(timing=True)
+    wl = workloads.config_large(scheme=1, scale=8)
+    ncores = os.cpu_count() or 1
+    try:
+        nproc = int(subprocess.run(["nproc"], capture_output=True, text=True).stdout.strip())
+    except Exception:
+        nproc = ncores
+    sim = oracle.Sim(wl.grid[:2], wl.dx[:2], wl.dt, wl.l, wl.scheme, timing=True)
+    n_per = wl.ncell * wl.species[0].per_cell
+    for i, s in enumerate(wl.species):
+        x, u, _ = oracle.load_drifting(wl.grid, wl.dx, s.per_cell, wl.gamma, wl.u_th, 0.0,
+                                       wl.seed, wl.run, i, s.pos_species)
+        sim.add_species(s.q, s.m, s.w, x, u)
+        del x, u
+    out = {"unit": UNIT, "kind": "oracle", "nproc": nproc}
+    modes = [("all_cores", nproc, n_per)]
+    if one_core:
+        modes.append(("one_core", 1, max(1, n_per // 32)))
+    for name, threads, count in modes:
+        t0 = time.perf_counter()
+        used = sim.particle_pass_threads(0, count, threads)
+        one = time.perf_counter() - t0
+        reps = max(1, int(budget_s / max(one, 1e-6)))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            sim.particle_pass_threads(0, count, threads)
+        t = time.perf_counter() - t0
+        out[name] = {"value": 2 * count * reps / t, "cores": used,
+                     "sample": "%d particle passes over %d particles (%d per species) of the "
+                               "256x128 section (64 per cell) of the large workload"
+                               % (reps, 2 * count, count)}
     sim.close()
-    rate = 2 * S * reps / t
-    return rate, "%d particle passes over %d particles (%d per species) of the %s grid" % (
-        reps, 2 * S, S, "x".join(str(g) for g in wl.grid[:dim]))
+    out["value"] = out["all_cores"]["value"]
+    out["cores"] = out["all_cores"]["cores"]
+    out["sample"] = out["all_cores"]["sample"]
+    return out
 
 
 def batched_form(steps, warmup, n_runs=256, max_nx=512, baselines=True):
@@ -415,14 +461,12 @@ def form_3d(steps=10, warmup=3):
     import torch
     import workloads
     import paper_1909_09613_gb300 as pic
-    wl = workloads.pair_plasma((256, 64, 64), (1.0, 1.0, 1.0), 0.4, 2, 1, 20.0, 0.01, 8,
-                               device="cuda")
-    caps = [int(s.x.shape[1]) for s in wl.species]
+    wl = workloads.pair_plasma((256, 64, 64), (1.0, 1.0, 1.0), 0.4, 2, 1, 20.0, 0.01, 8)
+    caps = [wl.ncell * s.per_cell for s in wl.species]
     out = {"workload": "pair_256x64x64_l2_WT_g20_ppc8_cdt0.4", "particles": sum(caps)}
     for name, prec in (("fp32", pic.PIC_FP32_MIXED), ("fp64", pic.PIC_FP64)):
         r = pic.Run(wl.grid, wl.dx, wl.dt, 2, 1, precision=prec, capacity=caps)
-        for i, sp in enumerate(wl.species):
-            r.load(i, sp.q, sp.m, sp.w, sp.x, sp.u)
+        load_device(r, wl)
         r.step(warmup)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -574,17 +618,14 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        wl = workloads.config_large(scheme=1, device="cpu", scale=8)
-        # same per-particle work as the full grid (the oracle's cost is per particle)
-        wl_full = wl
         rates, secs = [], []
         budget = (args.ref_budget if args.ref_budget is not None
-                  else max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+                  else max(1.0, 30.0 / max(1, args.steps + args.warmup)))
         for i in range(args.warmup + args.steps):
             t0 = time.perf_counter()
-            r, sample = cpu_baseline(wl_full, budget_s=budget)
+            cb = cpu_baseline(budget_s=budget, one_core=False)
             if i >= args.warmup:
-                rates.append(r)
+                rates.append(cb["value"])
                 secs.append(time.perf_counter() - t0)
         v = statistics.median(rates)
         # a step of this arm is one bounded sample of the workload (see cpu_baseline.sample)
@@ -594,8 +635,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "grid_sample": "256x128 (same per-particle work)"},
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": sample},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                                 "nproc": cb["nproc"], "sample": cb["sample"]},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -619,8 +660,7 @@ def main():
         if rank == 0:
             print(json.dumps(out))
         return
-    wl = workloads.config_large(scheme=1, device="cuda", seed=workloads.BASE_SEED + rank,
-                                scale=args.scale)
+    wl = workloads.config_large(scheme=1, seed=workloads.BASE_SEED + rank, scale=args.scale)
     if args.form in ("batched", "served"):
         out = (batched_form(args.steps, args.warmup, args.runs, args.max_nx,
                             baselines=args.runs == 256 and args.max_nx == 512)
@@ -636,42 +676,55 @@ def main():
                               "gpp_ms": r32["gpp_ms"] / max(r32["gpp_launches"], 1),
                               "particles": r32["n"]}))
         return
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    digest = kernel_digest()
     res = time_form(wl, pic.PIC_FP64, args.steps, args.warmup, dist_on)
     run64 = res.pop("run")
-    n_all = res["n"] * world
     value = replica_rate(res["n"], world, args.steps, res["ms"])
     gpp_avg_s = res["gpp_ms"] / max(res["gpp_launches"], 1) * 1e-3
     peaks, peak_kind = _peaks()
     pb, gb = BYTES["fp64"]
     alg_bytes = res["n"] * pb + res["ncell"] * gb
+    c64 = profile_counts("gpp2d_fp64")
+    traffic64 = c64.get("dram_bytes_per_launch")
     fp64_peak = None
     try:
         fp64_peak = pic.pic_probe_fma_peak(0)
     except Exception:
         pass
-    if FP64_FLOPS_PER_PARTICLE and fp64_peak:
-        ach = res["n"] * FP64_FLOPS_PER_PARTICLE / gpp_avg_s / 1e12
+    hbm_view = {"achieved_gbs": alg_bytes / gpp_avg_s / 1e9,
+                "frac_of_measured_hbm": alg_bytes / gpp_avg_s / 1e9 / peaks["hbm_gbs"],
+                "weight_cache_bytes_per_particle": WEIGHT_CACHE_BYTES_FP64_L3,
+                "traffic_over_algorithmic": (traffic64 / alg_bytes) if traffic64 else None,
+                "note": "the DRAM traffic includes the read and write of the cached B-spline "
+                        "weights (128 B per particle-step), bytes spent to save FP64 "
+                        "instructions in a form bound by its FP64 pipe"}
+    flops = c64.get("fp64_flops_per_particle")
+    if flops and fp64_peak:
+        ach = res["n"] * flops / gpp_avg_s / 1e12
         roofline = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp64_peak, "traffic": _profile_traffic("gpp2d_fp64"),
+                    "frac": ach / fp64_peak, "traffic": traffic64,
                     "peak_source": "measured FP64 FMA rate (pic_probe_fma_peak, all SMs)",
-                    "flops_per_particle": FP64_FLOPS_PER_PARTICLE,
-                    "fp64_instr_frac": (res["n"] * FP64_INSTR_PER_PARTICLE / gpp_avg_s)
+                    "flops_per_particle": flops,
+                    "fp64_instr_frac": (res["n"] * c64.get("fp64_instr_per_particle", 0.0) / gpp_avg_s)
                                        / (fp64_peak * 1e12 / 2.0),
-                    "hbm_view": {"achieved_gbs": alg_bytes / gpp_avg_s / 1e9,
-                                 "frac_of_measured_hbm": alg_bytes / gpp_avg_s / 1e9 / peaks["hbm_gbs"]}}
+                    "hbm_view": hbm_view}
     else:
         ach = alg_bytes / gpp_avg_s / 1e9
         roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": _profile_traffic("gpp2d_fp64"),
-                    "peak_source": "%s hbm_gbs" % peak_kind}
+                    "frac": ach / peaks["hbm_gbs"], "traffic": traffic64,
+                    "peak_source": "%s hbm_gbs" % peak_kind,
+                    "note": "no FP64 instruction count recorded for these kernel sources"}
     roofline["kernel"] = "k_gpp2d<3,4> (double): fused gather+push+move+deposit"
     roofline["kernel_ms"] = gpp_avg_s * 1e3
     roofline["algorithmic_bytes"] = alg_bytes
+    roofline["counts_digest"] = digest
+    roofline["counts_from_profile"] = bool(c64)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "data": "synthetic (seeded, generated in HBM by the device loader)",
             "config": {"workload": WORKLOAD, "grid": list(wl.grid[:2]), "particles": res["n"],
                        "form": "plain FP64 single run", "spline_order": wl.l, "scheme": "WT",
                        "c_dt_over_dx": wl.dt, "sort_interval": res["sort_interval"],
@@ -681,8 +734,10 @@ def main():
             "roofline": roofline,
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
+            "sms": sms,
             "fp64_fma_peak_tflops": fp64_peak,
             "gpp_particle_steps_per_s": res["n"] / gpp_avg_s,
+            "charge_conservation": res["charge_conservation"],
             # per step: the particle kernel (gather + push + deposit) and the rest (Yee, the
             # tile sort amortised over its interval, clearing the current)
             "split_ms_per_step": {"gather_push_deposit": gpp_avg_s * 1e3,
@@ -698,11 +753,12 @@ def main():
 
     if not args.no_fp32 and args.form == "both":
         r32 = time_form(wl, pic.PIC_FP32_MIXED, args.steps, args.warmup, dist_on)
-        r32.pop("run").close()
+        run32 = r32.pop("run")
         g32 = r32["gpp_ms"] / max(r32["gpp_launches"], 1) * 1e-3
         pb, gb = BYTES["fp32"]
         ab = r32["n"] * pb + r32["ncell"] * gb
         ach = ab / g32 / 1e9
+        c32 = profile_counts("gpp2d_fp32")
         line["precision_form"] = {
             "value": replica_rate(r32["n"], world, args.steps, r32["ms"]), "unit": UNIT,
             "ms_per_step": r32["ms"] / args.steps, "dtype": "f32 (FP64 fields)",
@@ -710,17 +766,30 @@ def main():
             "split_ms_per_step": {"gather_push_deposit": g32 * 1e3,
                                   "yee_sort_other": r32["ms"] / args.steps - g32 * 1e3},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": ach / peaks["hbm_gbs"], "traffic": _profile_traffic("gpp2d_fp32"),
+                         "frac": ach / peaks["hbm_gbs"],
+                         "traffic": c32.get("dram_bytes_per_launch"),
                          "kernel": "k_gpp2d<3,4> (float)", "kernel_ms": g32 * 1e3,
-                         "algorithmic_bytes": ab, "peak_source": "%s hbm_gbs" % peak_kind},
+                         "algorithmic_bytes": ab, "peak_source": "%s hbm_gbs" % peak_kind,
+                         "counts_digest": digest, "counts_from_profile": bool(c32)},
+            "charge_conservation": r32["charge_conservation"],
             "gpu_launches": r32["launches"], "clocks": r32["clocks"]}
-        mhz = (r32["clocks"] or {}).get("sm_mhz") or 2070.0
-        issue_peak = SMS * SCHEDULERS_PER_SM * mhz * 1e6
-        issued = r32["n"] * FP32_WARP_INSTR_PER_PARTICLE / g32
-        line["precision_form"]["roofline"]["issue_view"] = {
-            "warp_instr_per_particle": FP32_WARP_INSTR_PER_PARTICLE,
-            "achieved_warp_instr_per_s": issued, "peak_warp_instr_per_s": issue_peak,
-            "frac": issued / issue_peak, "sm_mhz": mhz}
+        wip = c32.get("warp_instr_per_particle")
+        if wip:
+            mhz = (r32["clocks"] or {}).get("sm_mhz") or 2070.0
+            issue_peak = sms * SCHEDULERS_PER_SM * mhz * 1e6
+            issued = r32["n"] * wip / g32
+            line["precision_form"]["roofline"]["issue_view"] = {
+                "warp_instr_per_particle": wip,
+                "achieved_warp_instr_per_s": issued, "peak_warp_instr_per_s": issue_peak,
+                "frac": issued / issue_peak, "sm_mhz": mhz}
+        if not args.no_e2e:
+            try:
+                line["precision_form"]["e2e"] = e2e_form(run32, wl, args.steps)
+            except Exception as ex:  # report, do not hide
+                line["precision_form"]["e2e"] = {"error": str(ex)}
+        run32.close()
+        del run32
+        torch.cuda.empty_cache()
         try:
             line["fp32_fma_peak_tflops"] = pic.pic_probe_fma_peak(1)
         except Exception:
@@ -736,9 +805,7 @@ def main():
         line["loader"] = loader_form()
 
     if rank == 0 and not args.no_cpu:
-        rate, sample = cpu_baseline(wl)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": sample}
+        line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line))
     if dist_on:

@@ -87,6 +87,19 @@ typedef struct {
                                summed through shared memory; PIC_ORDER_SLOT (2): (tile, slot,
                                cell), every lane adds its own window with shared atomics.
                                The FP64 form always uses PIC_ORDER_SLOT.                     */
+    int32_t deterministic;  /* 0: the current is summed with floating-point atomics, so its
+                               last bits depend on the order in which the GPU serves them.
+                               1: every current contribution is added as a 64-bit fixed-point
+                               integer (unit = s 2^-40 in the FP32 form; two words, units
+                               s 2^-31 and s 2^-63, in the FP64 form; s = the largest
+                               |q w dx_a / (V_c dt)| or |q w / V_c| of the loaded species, the
+                               bound of one particle's contribution to one node), so the sums
+                               are exact and order-independent and a run gives bit-identical
+                               fields and particles every time; J is converted to FP64 after
+                               the particle pass.  With the stable tile sort this makes pic_step
+                               reproducible.  Costs integer atomics and, in the FP32 form, a
+                               shared-memory current tile twice as large (default tile 32 x 8).
+                               Batches (pic_batch_create) do not take deterministic runs.      */
 } pic_options;
 
 /* pic_create -- validate a run and build its host-side context (no device memory yet).
@@ -205,19 +218,34 @@ typedef struct {
     double field_energy;          /* 1/2 sum over nodes (E^2 + B^2) V_c, FP64               */
     double kinetic_energy;        /* sum w m (gamma - 1), FP64                              */
     double total_charge;          /* sum q w                                                */
-    double max_gauss_residual;    /* max over nodes |D.E - rho| (App. B, Eq. gauss)          */
+    double max_gauss_residual;    /* max over nodes |D.E - rho| (App. B, Eq. gauss), with
+                                     D the backward difference that takes E at its Yee
+                                     position to the integer node of rho                     */
+    double max_continuity_residual; /* max over nodes |(rho^{n+1} - rho^n)/dt + D.J^{n+1/2}|,
+                                     the discrete continuity equation the Esirkepov deposit
+                                     satisfies (Sec. 1; App. B): rho^{n+1} from the current
+                                     particles, rho^n kept by the previous pic_diag, J the
+                                     current of the last step.  Defined only when the previous
+                                     pic_diag came exactly one step earlier with no load in
+                                     between; NaN otherwise                                   */
+    double max_gauss_residual_drift; /* max over nodes |G - G_0|, G = D.E - rho: the change of
+                                     the Gauss residual (App. B: conserved by a
+                                     charge-conserving deposit) since G_0, which the first
+                                     pic_step (or batch) after the last load or field set
+                                     records; 0 before that step                             */
     int32_t error_flags;          /* PIC_ERR_* bits latched since creation                  */
 } pic_diag_t;
 
-/* FP64 diagnostics of the current state. Syncs. */
+/* FP64 diagnostics of the current state (the particle deposit for rho, the reductions and the
+ * residuals all on the device).  Syncs. */
 int pic_diag(pic_ctx *ctx, pic_diag_t *out);
 
 /* Wait for the context's stream; returns the latched error as a status. */
 int pic_sync(pic_ctx *ctx);
 
 /* ---- batched form ----
- * Many independent runs (2D, PIC_FP32_MIXED, spline order 2 or 3, same species count, same
- * stream; each created,
+ * Many independent runs (2D, PIC_FP32_MIXED, spline order 2 or 3, not deterministic, same
+ * species count, same stream; each created,
  * bound and loaded as usual) advanced together.  One batch step = device-side choice of the runs
  * due for a tile sort, the batched sort of those runs, ONE persistent gather-push-deposit
  * launch over the tiles of every run (heaviest tiles first, pulled from a device counter), and
@@ -252,21 +280,25 @@ int pic_probe_fma_peak(int kind, double *tflops);
 /* Tile sort that allocates no device memory.  No counterpart in the paper: it exists for
  * callers that cannot allocate device memory when they need the sort (their device memory is
  * owned by another allocator, or they cannot afford the device-wide synchronisation of
- * cudaMalloc/cudaFree).  Its scratch is a fixed file-scope device array of about 16.5 MB that
+ * cudaMalloc/cudaFree).  Its scratch is a fixed file-scope device array of about 20.5 MB that
  * every GPU loading the library holds until the process exits.
  *   grid[3], tile[3]  grid extent and tile extent in cells (tile <= grid, cells per tile <= 1024)
  *   n                 particles, n <= 1,048,576
  *   cell_dev          device, n int32 linear cell indices (k*ny + j)*nx + i; cells outside the
- *                     grid are left out of the order
+ *                     grid (< 0 or >= nx*ny*nz) are left out of the order
  *   perm_dev          device, n int64 out: perm[p] = input index placed at position p of the
- *                     cell-major tile order (by tile, then cell in tile, then an arbitrary slot)
+ *                     cell-major tile order, sorted by (tile, cell in tile, input index): the
+ *                     same stable order as the context's sort.  Positions from
+ *                     tile_start[ntiles] (the number of particles inside the grid) to n - 1
+ *                     are set to -1.
  *   tile_start_dev    device, ntiles + 1 int64 out: first position of every tile
  *   stream            cudaStream_t (0 = legacy default stream); asynchronous on it
- * Requires ntiles <= 65,536 and ntiles * cells-per-tile <= 1,048,576; larger sizes return
- * PIC_EINVAL.  The first call on a device looks up the scratch array's device address (with
- * that device current); make that first call before any stream capture.  Every call on a
- * device uses the same scratch array, so calls that overlap on the GPU (other streams, other
- * host threads) race: serialise them.                                                       */
+ * The current device must be the device that holds cell_dev, perm_dev and tile_start_dev: the
+ * scratch array of that device is used.  Requires ntiles <= 65,536 and ntiles *
+ * cells-per-tile <= 1,048,576; larger sizes return PIC_EINVAL.  The first call on a device
+ * looks up the scratch array's device address (with that device current); make that first
+ * call before any stream capture.  Every call on a device uses the same scratch array, so
+ * calls that overlap on the GPU (other streams, other host threads) race: serialise them.    */
 int pic_tile_sort_noalloc(const int32_t grid[3], const int32_t tile[3], int64_t n,
                           const int32_t *cell_dev, int64_t *perm_dev, int64_t *tile_start_dev,
                           uint64_t stream);

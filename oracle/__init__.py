@@ -3,7 +3,8 @@
 This package is the slow, plain, obviously-correct reference that the CUDA library is checked
 against.  It is written from the paper (Sec. 2 for W_l, T_l and the WT gather of
 Eq. interpolation-EB-real-mod; Sec. 1 for Boris, Esirkepov and Yee; App. B for Gauss's law;
-App. E for the dimensionless equations) and shares no code with the CUDA path.  Only the tests,
+App. D for loading a drifting plasma; App. E for the dimensionless equations) and shares no
+code with the CUDA path.  Only the tests,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import it.
 
 The arithmetic lives in ``pic_oracle.c`` (plain C99, IEEE binary64, compiled with
@@ -20,6 +21,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   yee, M4      vacuum dispersion relation of App. C (A_i = 1 and the M4 A_i); fourth-order
                phase error of M4; Gauss's law conservation
   tile_sort    brute-force order check on small inputs
+  load_drifting  App. D: the drift moment with and without the flip, the Juttner-Synge
+               distribution (mean gamma, CDF, isotropy), the cold beam, the attempt bound
   step         composition of the above, brute-force tiny runs (whole-step parity has no
                printed worked example in the paper)
 """
@@ -36,8 +39,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic_oracle.c")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
+_LIB_TIMING = os.path.join(_LIBDIR, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_timing = None
 
 MC, WT = 0, 1
 YEE, M4 = 0, 1
@@ -47,26 +52,33 @@ _lp = ctypes.POINTER(ctypes.c_long)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
-def build(force: bool = False) -> str:
-    """Compile pic_oracle.c into oracle/_lib/liboracle.so (plain gcc, no CUDA)."""
+def build(force: bool = False, timing: bool = False) -> str:
+    """Compile pic_oracle.c into oracle/_lib/liboracle.so (plain gcc, no CUDA): the parity build,
+    -O2 with no fused multiply-add, single-threaded.  timing=True builds liboracle_omp.so, the
+    same source at -O3 with OpenMP over particles (orc_particle_pass_threads), for the timed
+    CPU baseline only."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+    out = _LIB_TIMING if timing else _LIB
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
+    opt = ["-O3", "-fopenmp"] if timing else ["-O2"]
+    cmd = ["gcc"] + opt + ["-ffp-contract=off", "-std=c99", "-fPIC", "-shared",
+                           "-o", tmp, _SRC, "-lm"]
     subprocess.check_call(cmd)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, out)
+    return out
 
 
-def _load():
-    global _lib
+def _load(timing: bool = False):
+    global _lib, _lib_timing
     with _lock:
-        if _lib is not None:
+        if not timing and _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
+        if timing and _lib_timing is not None:
+            return _lib_timing
+        lib = ctypes.CDLL(build(timing=timing))
         lib.orc_W.restype = ctypes.c_double
         lib.orc_W.argtypes = [ctypes.c_int, ctypes.c_double]
         lib.orc_T.restype = ctypes.c_double
@@ -100,7 +112,21 @@ def _load():
         lib.orc_gauss_residual.argtypes = [ctypes.c_void_p, _dp]
         lib.orc_tile_sort.restype = ctypes.c_long
         lib.orc_tile_sort.argtypes = [_ip, _ip, ctypes.c_int, ctypes.c_long, _lp, _lp, _lp]
-        _lib = lib
+        lib.orc_load_drifting.restype = ctypes.c_long
+        lib.orc_load_drifting.argtypes = [ctypes.c_int, _ip, _dp, ctypes.c_long, ctypes.c_long,
+                                          ctypes.c_long, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_ulonglong, ctypes.c_ulonglong,
+                                          ctypes.c_int, ctypes.c_int, _dp, _dp]
+        lib.orc_juttner_speeds.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_ulonglong,
+                                           ctypes.c_ulonglong, ctypes.c_int, ctypes.c_long,
+                                           ctypes.c_long, _dp]
+        lib.orc_particle_pass_threads.restype = ctypes.c_int
+        lib.orc_particle_pass_threads.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_long,
+                                                  ctypes.c_int]
+        if timing:
+            _lib_timing = lib
+        else:
+            _lib = lib
         return lib
 
 
@@ -151,6 +177,48 @@ def tile_sort(grid, tile, cells, order=CELL_MAJOR):
     return perm[:len(cells)], ts
 
 
+def load_drifting(grid, dx, per_cell, gamma, u_th=0.0, theta=0.0, seed=0, run=0, species=0,
+                  pos_species=None, first=0, count=None):
+    """Particles first .. first + count - 1 of one species of the App. D drifting plasma along
+    x1 (per_cell per cell, cells x1-fastest; Gaussian co-moving momenta of spread u_th, or
+    Juttner-Synge ones of temperature theta > 0 by Sobol's method; the flip and the boost).
+    Returns (x (dim, count) physical positions, u (3, count), particles without an accepted
+    Sobol attempt)."""
+    grid = list(grid)
+    dim = 3 if len(grid) == 3 and grid[2] > 1 else 2
+    n = np.array(grid + [1] * (3 - len(grid)), dtype=np.int32)
+    d = np.array(list(dx) + [1.0] * (3 - len(dx)), dtype=np.float64)
+    ncell = int(np.prod(n.astype(np.int64)))
+    total = ncell * int(per_cell)
+    if count is None:
+        count = total - first
+    x = np.zeros((dim, count))
+    u = np.zeros((3, count))
+    if count > 0:
+        failed = _load().orc_load_drifting(
+            dim, n.ctypes.data_as(_ip), _d(d), int(per_cell), int(first), int(count),
+            float(gamma), float(u_th), float(theta), int(seed) & (2 ** 64 - 1),
+            int(run) & (2 ** 64 - 1), int(species),
+            int(species if pos_species is None else pos_species), _d(x), _d(u))
+    else:
+        failed = 0
+    return x, u, int(failed)
+
+
+JUTTNER_ATTEMPTS = 128
+
+
+def juttner_speeds(theta, n, seed=0, run=0, species=0, attempts=JUTTNER_ATTEMPTS, first=0):
+    """Co-moving |u'| of n particles drawn from the Juttner-Synge distribution (App. D,
+    Eq. Maxwell-dist-relativistic) by Sobol's method with at most `attempts` attempts each
+    (the streams the loader uses); NaN where no attempt was accepted."""
+    out = np.zeros(n)
+    _load().orc_juttner_speeds(float(theta), int(attempts), int(seed) & (2 ** 64 - 1),
+                               int(run) & (2 ** 64 - 1), int(species), int(first), int(n), _d(out))
+    out[out < 0.0] = np.nan
+    return out
+
+
 class Sim:
     """One periodic 2D (nz = 1) or 3D simulation held by the C oracle.
 
@@ -158,7 +226,7 @@ class Sim:
     Fields: comps 0..5 = E1 E2 E3 B1 B2 B3, 6..8 = J1 J2 J3, arrays shaped (nz, ny, nx).
     """
 
-    def __init__(self, grid, dx, dt, l, scheme, solver=0):
+    def __init__(self, grid, dx, dt, l, scheme, solver=0, timing=False):
         grid = list(grid) + [1] * (3 - len(grid))
         dx = list(dx) + [1.0] * (3 - len(dx))
         self.grid = tuple(int(g) for g in grid)
@@ -167,7 +235,7 @@ class Sim:
         self.dt = float(dt)
         self.l = int(l)
         self.scheme = int(scheme)
-        self._lib = _load()
+        self._lib = _load(timing)
         self._h = self._lib.orc_create(*self.grid, *self.dx, self.dt, self.l, self.scheme)
         if not self._h:
             raise ValueError("oracle: bad arguments")
@@ -268,6 +336,12 @@ class Sim:
 
     def particle_pass(self, first, count):
         self._lib.orc_particle_pass(self._h, int(first), int(count))
+
+    def particle_pass_threads(self, first, count, threads=0):
+        """The particle pass over `threads` host threads (0: all OpenMP threads; the timing build
+        only runs in parallel).  Returns the threads used."""
+        return int(self._lib.orc_particle_pass_threads(self._h, int(first), int(count),
+                                                       int(threads)))
 
     @property
     def step_count(self):

@@ -24,6 +24,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAX_SPECIES 4
 #define ORC_MC 0
@@ -623,6 +626,49 @@ void orc_particle_pass(orc_sim *s, long first, long count)
     }
 }
 
+/* Particle pass of particles first .. first + count - 1 of every species over `threads` host
+ * threads (the timing build, compiled with OpenMP; without it one thread does all): each
+ * thread pushes a contiguous share of the particles and deposits into a private copy of J,
+ * and the copies are then added into J in thread order.  The arithmetic of every particle is
+ * that of push_species.  Returns the number of threads used.                              */
+int orc_particle_pass_threads(orc_sim *s, long first, long count, int threads)
+{
+    for (int c = 6; c < 9; ++c) memset(s->F[c], 0, (size_t)s->ncell * sizeof(double));
+#ifdef _OPENMP
+    if (threads < 1) threads = omp_get_max_threads();
+#else
+    threads = 1;
+#endif
+    double *priv = (double *)calloc((size_t)threads * 3 * (size_t)s->ncell, sizeof(double));
+    if (!priv) return 0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(threads)
+#endif
+    {
+#ifdef _OPENMP
+        const int t = omp_get_thread_num(), nt = omp_get_num_threads();
+#else
+        const int t = 0, nt = 1;
+#endif
+        orc_sim local = *s;
+        for (int c = 0; c < 3; ++c) local.F[6 + c] = priv + ((size_t)t * 3 + c) * (size_t)s->ncell;
+        for (int sp = 0; sp < s->nsp; ++sp) {
+            long n = s->sp[sp].n - first;
+            if (n > count) n = count;
+            if (n <= 0) continue;
+            const long a = first + n * t / nt, b = first + n * (t + 1) / nt;
+            if (b > a) push_species(&local, &local.sp[sp], a, b - a);
+        }
+    }
+    for (int t = 0; t < threads; ++t)
+        for (int c = 0; c < 3; ++c) {
+            const double *src = priv + ((size_t)t * 3 + c) * (size_t)s->ncell;
+            for (long i = 0; i < s->ncell; ++i) s->F[6 + c][i] += src[i];
+        }
+    free(priv);
+    return threads;
+}
+
 /* ------------------------------------------------------------------------------------- */
 /* Diagnostics                                                                            */
 /* ------------------------------------------------------------------------------------- */
@@ -746,4 +792,158 @@ long orc_tile_sort(const int *n, const int *tile, int order, long np, const long
     free(cnt);
     free(r);
     return ntiles;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Particle loading: drifting plasma of App. D                                            */
+/* ------------------------------------------------------------------------------------- */
+
+/* Counter-based random numbers: SplitMix64 (Steele, Lea, Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014): the state advances by the odd constant
+ * 0x9E3779B97F4A7C15 and each output is the state passed through the 64-bit finaliser below.
+ * Value k of a stream with key K is mix(k * 0x9E3779B97F4A7C15 + K); a uniform deviate on
+ * [0, 1) takes its 53 high bits.  Stream keys chain the finaliser over the stream's ids:
+ * K = mix(... mix(mix(seed + G) ^ ((id_0 + 1) G)) ^ ((id_1 + 1) G) ...), G the constant above
+ * (the schedule the library documents for its device loader).                              */
+typedef unsigned long long u64;
+static const u64 SM64_GAMMA = 0x9E3779B97F4A7C15ull;
+
+static u64 sm64_finalise(u64 z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static u64 stream_key3(u64 seed, u64 a, u64 b, u64 c)
+{
+    u64 k = sm64_finalise(seed + SM64_GAMMA);
+    k = sm64_finalise(k ^ ((a + 1) * SM64_GAMMA));
+    k = sm64_finalise(k ^ ((b + 1) * SM64_GAMMA));
+    k = sm64_finalise(k ^ ((c + 1) * SM64_GAMMA));
+    return k;
+}
+
+static double uniform01(u64 key, u64 ctr)
+{
+    return (double)(sm64_finalise(ctr * SM64_GAMMA + key) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+#define ORC_JUTTNER_ATTEMPTS 128
+
+/* |u'| of the Juttner-Synge distribution of Eq. Maxwell-dist-relativistic (temperature
+ * theta = k_B T / (m c^2), u' = p'/(m c)) by Sobol's rejection method: with X1..X4 uniform on
+ * (0, 1], u = -theta ln(X1 X2 X3) and eta = -theta ln(X1 X2 X3 X4); the pair is accepted when
+ * eta^2 - u^2 > 1, and u then has density proportional to u^2 exp(-sqrt(1 + u^2) / theta).
+ * Attempt a (a < attempts <= ORC_JUTTNER_ATTEMPTS) of particle p uses counter
+ * p * ORC_JUTTNER_ATTEMPTS + a.  Returns -1 when every attempt was rejected.              */
+static double juttner_speed(double theta, const u64 *key, u64 p, int attempts)
+{
+    for (int a = 0; a < attempts; ++a) {
+        const u64 ctr = p * ORC_JUTTNER_ATTEMPTS + (u64)a;
+        double X[4];
+        for (int j = 0; j < 4; ++j) X[j] = 1.0 - uniform01(key[j], ctr);
+        const double prod3 = X[0] * X[1] * X[2];
+        const double u = -theta * log(prod3);
+        const double eta = -theta * log(prod3 * X[3]);
+        if (eta * eta - u * u > 1.0) return u;
+    }
+    return -1.0;
+}
+
+/* Particles p0 .. p0 + m - 1 of one species of a plasma drifting along x1 (App. D, n = e_1):
+ *   - particle p sits in cell p / per_cell (cells numbered x1 fastest) at uniform offsets
+ *     U(key(seed, run, pos_species, 10 + a), p) per axis a;
+ *   - co-moving momentum u' = p'/(m c): theta > 0 draws the Juttner-Synge speed above with an
+ *     isotropic direction (cos = 2 X5 - 1, azimuth 2 pi X6, X5 and X6 at counter p of streams
+ *     (run, species, 44) and (run, species, 45)); otherwise each component is u_th times a
+ *     standard normal by Box-Muller, sqrt(-2 ln U1) cos(2 pi U2) with U1 = 1 - U(key(..,
+ *     20 + 2a), p) in (0, 1] and U2 = U(key(.., 21 + 2a), p) (the Maxwell-Boltzmann limit,
+ *     Eq. Maxwell-dist-non-relativistic); u_th = 0 and theta = 0 give u' = 0;
+ *   - the volume transform of App. D by flipping instead of rejecting: with X1 = U(key(..,
+ *     30), p) and E' = sqrt(1 + u'^2), u'_1 -> -u'_1 when X1 > (1 + beta u'_1 / E') / 2 (the
+ *     reading of the flip rule under which the loaded density carries the weight
+ *     1 + beta u'_1 / E' that App. D requires);
+ *   - the Lorentz transform of App. D along n = e_1: u_1 = gamma (u'_1 + beta E'), the
+ *     transverse components unchanged, beta = sqrt(1 - 1 / gamma^2).  For u' = 0 this is the
+ *     cold beam u = (gamma beta, 0, 0), written as sqrt(gamma^2 - 1).
+ * x: dim x m physical positions (SoA), u: 3 x m.  Returns the number of particles for which no
+ * Sobol attempt was accepted (they are loaded at rest in the co-moving frame).              */
+long orc_load_drifting(int dim, const int *n, const double *dx, long per_cell, long p0, long m,
+                       double gamma, double u_th, double theta, u64 seed, u64 run, int species,
+                       int pos_species, double *x, double *u)
+{
+    u64 kpos[3], kmom[6], kjut[4], kdir[2];
+    for (int a = 0; a < 3; ++a) {
+        kpos[a] = stream_key3(seed, run, (u64)pos_species, (u64)(10 + a));
+        kmom[2 * a] = stream_key3(seed, run, (u64)species, (u64)(20 + 2 * a));
+        kmom[2 * a + 1] = stream_key3(seed, run, (u64)species, (u64)(21 + 2 * a));
+    }
+    const u64 kflip = stream_key3(seed, run, (u64)species, 30);
+    for (int j = 0; j < 4; ++j) kjut[j] = stream_key3(seed, run, (u64)species, (u64)(40 + j));
+    kdir[0] = stream_key3(seed, run, (u64)species, 44);
+    kdir[1] = stream_key3(seed, run, (u64)species, 45);
+    const double beta = sqrt(1.0 - 1.0 / (gamma * gamma));
+    const double two_pi = 6.28318530717958647692;  /* 2 pi */
+    long failed = 0;
+    for (long i = 0; i < m; ++i) {
+        const long p = p0 + i;
+        const long cell = p / per_cell;
+        long ci[3];
+        ci[0] = cell % n[0];
+        ci[1] = (cell / n[0]) % n[1];
+        ci[2] = cell / ((long)n[0] * n[1]);
+        for (int a = 0; a < dim; ++a) {
+            const double L = (double)n[a] * dx[a];
+            double xa = ((double)ci[a] + uniform01(kpos[a], (u64)p)) * dx[a];
+            if (xa >= L) xa -= L;
+            x[(long)a * m + i] = xa;
+        }
+        if (theta > 0.0 || u_th > 0.0) {
+            double v[3];
+            if (theta > 0.0) {
+                double um = juttner_speed(theta, kjut, (u64)p, ORC_JUTTNER_ATTEMPTS);
+                if (um < 0.0) {
+                    ++failed;
+                    um = 0.0;
+                }
+                const double x5 = uniform01(kdir[0], (u64)p), x6 = uniform01(kdir[1], (u64)p);
+                const double cos_t = 2.0 * x5 - 1.0;
+                /* sin = sqrt(1 - cos^2) = 2 sqrt(X5 (1 - X5)), the form without cancellation */
+                const double sin_t = 2.0 * sqrt(x5 * (1.0 - x5));
+                const double phi = two_pi * x6;
+                v[0] = um * cos_t;
+                v[1] = um * sin_t * cos(phi);
+                v[2] = um * sin_t * sin(phi);
+            } else {
+                for (int a = 0; a < 3; ++a) {
+                    const double U1 = 1.0 - uniform01(kmom[2 * a], (u64)p);
+                    const double U2 = uniform01(kmom[2 * a + 1], (u64)p);
+                    v[a] = u_th * (sqrt(-2.0 * log(U1)) * cos(two_pi * U2));
+                }
+            }
+            const double e_prime = sqrt(1.0 + (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+            const double X1 = uniform01(kflip, (u64)p);
+            const double v1 = (X1 > 0.5 * (1.0 + beta * v[0] / e_prime)) ? -v[0] : v[0];
+            u[i] = gamma * (v1 + beta * e_prime);
+            u[m + i] = v[1];
+            u[2 * m + i] = v[2];
+        } else {
+            u[i] = sqrt(gamma * gamma - 1.0);
+            u[m + i] = 0.0;
+            u[2 * m + i] = 0.0;
+        }
+    }
+    return failed;
+}
+
+/* The Juttner-Synge speeds alone (the co-moving |u'| of particles p0 .. p0 + m - 1 of one
+ * species' streams) with at most `attempts` Sobol attempts each; -1 where none was accepted. */
+void orc_juttner_speeds(double theta, int attempts, u64 seed, u64 run, int species, long p0,
+                        long m, double *out)
+{
+    u64 kjut[4];
+    for (int j = 0; j < 4; ++j) kjut[j] = stream_key3(seed, run, (u64)species, (u64)(40 + j));
+    if (attempts > ORC_JUTTNER_ATTEMPTS) attempts = ORC_JUTTNER_ATTEMPTS;
+    for (long i = 0; i < m; ++i) out[i] = juttner_speed(theta, kjut, (u64)(p0 + i), attempts);
 }

@@ -39,13 +39,16 @@ class pic_options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32 * 3), ("sort_interval", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("n_species", ctypes.c_int32),
                 ("capacity", ctypes.c_int64 * PIC_MAX_SPECIES), ("stream", ctypes.c_uint64),
-                ("solver", ctypes.c_int32), ("tile_order", ctypes.c_int32)]
+                ("solver", ctypes.c_int32), ("tile_order", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32)]
 
 
 class pic_diag_t(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("field_energy", ctypes.c_double),
                 ("kinetic_energy", ctypes.c_double), ("total_charge", ctypes.c_double),
-                ("max_gauss_residual", ctypes.c_double), ("error_flags", ctypes.c_int32)]
+                ("max_gauss_residual", ctypes.c_double),
+                ("max_continuity_residual", ctypes.c_double),
+                ("max_gauss_residual_drift", ctypes.c_double), ("error_flags", ctypes.c_int32)]
 
 
 class PicError(RuntimeError):
@@ -268,6 +271,8 @@ def pic_diag(ctx) -> dict:
     st = load_library().pic_diag(ctx, ctypes.byref(d))
     out = {"step": d.step, "field_energy": d.field_energy, "kinetic_energy": d.kinetic_energy,
            "total_charge": d.total_charge, "max_gauss_residual": d.max_gauss_residual,
+           "max_continuity_residual": d.max_continuity_residual,
+           "max_gauss_residual_drift": d.max_gauss_residual_drift,
            "error_flags": d.error_flags, "status": st}
     return out
 
@@ -342,7 +347,14 @@ def pic_probe_fma_peak(kind: int) -> float:
 def pic_tile_sort_noalloc(grid, tile, cells, stream=None):
     """Cell-major tile order of `cells` (a CUDA int32 tensor) without any device allocation
     inside the library; returns (perm, tile_start) as CUDA int64 tensors (allocated here by
-    torch, i.e. by the caller of the C entry point)."""
+    torch, i.e. by the caller of the C entry point).  perm positions past tile_start[-1] (cells
+    outside the grid) hold -1.  The call runs with the tensors' device current."""
+    import torch
+    with torch.cuda.device(cells.device):
+        return _tile_sort_noalloc(grid, tile, cells, stream)
+
+
+def _tile_sort_noalloc(grid, tile, cells, stream):
     import torch
     g = (ctypes.c_int32 * 3)(*[int(v) for v in grid])
     t = (ctypes.c_int32 * 3)(*[int(v) for v in tile])
@@ -383,7 +395,7 @@ class Run:
 
     def __init__(self, grid, dx, dt, l, scheme, precision=PIC_FP64, capacity=(0, 0),
                  tile=None, sort_interval=0, stream=None, device=None, solver=PIC_SOLVER_YEE,
-                 tile_order=PIC_ORDER_AUTO):
+                 tile_order=PIC_ORDER_AUTO, deterministic=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libpic needs a CUDA device")
@@ -407,6 +419,7 @@ class Run:
         opt.stream = int(self.stream.cuda_stream)
         opt.solver = int(solver)
         opt.tile_order = int(tile_order)
+        opt.deterministic = 1 if deterministic else 0
         self.ctx = pic_create(self.grid, self.dx, dt, l, scheme, opt)
         self.nbytes = pic_footprint(self.ctx)
         self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)

@@ -42,6 +42,14 @@ struct pic_ctx {
     size_t staging_bytes;
     double *diag_out;
     double *rho;
+    // charge-conservation diagnostics: rho of the previous pic_diag (continuity residual) and
+    // the Gauss residual recorded by the first step after a load or field set (drift)
+    double *rho_prev;
+    double *gref;
+    bool rho_prev_valid;
+    int64_t rho_prev_step;
+    bool gref_valid;
+    unsigned long long *jlo;  // FP64 deterministic run: low fixed-point words of J (3 ncell)
     int32_t *err;
     size_t smem;
     // timing of the particle pass: a ring of event pairs, drained when it fills
@@ -143,7 +151,7 @@ int sort_species(pic_ctx *c, int s)
     cudaError_t e = launch_sort(rd, s, c->tile_start[s], c->bufB[s], c->bufB[s] + 3,
                                 (int32_t *)c->bufB[s][6], c->stream);
     if (e != cudaSuccess) return PIC_ECUDA;
-    c->kernel_launches += rd.sp[s].n > 0 ? 5 : 3;
+    c->kernel_launches += rd.sp[s].n > 0 ? 6 : 3;
     for (int i = 0; i < 7; ++i) std::swap(c->bufA[s][i], c->bufB[s][i]);
     c->wc_valid[s] = false;  // the weight cache follows the old order
     refresh_species_ptrs(c);
@@ -176,6 +184,9 @@ int sort_all(pic_ctx *c)
 // Species constants of a load (charge, mass, weight and the derived per-step factors).
 void set_species(pic_ctx *c, int species, double q, double m, double w, int64_t n)
 {
+    // the particles change: the charge-conservation references no longer apply
+    c->gref_valid = false;
+    c->rho_prev_valid = false;
     SpeciesDev &sp = c->rd.sp[species];
     const RunDev &rd = c->rd;
     const double vc = rd.dx[0] * rd.dx[1] * (rd.dim == 3 ? rd.dx[2] : 1.0);
@@ -218,6 +229,38 @@ uint64_t stream_key(uint64_t seed, uint64_t a, uint64_t b, uint64_t d)
     k = sm64_mix_host(k ^ ((b + 1) * G));
     k = sm64_mix_host(k ^ ((d + 1) * G));
     return k;
+}
+
+// Fixed-point scale of a deterministic run: s = the largest bound of one particle's
+// contribution to one node over the species, |q w dx_a / (V_c dt)| for J_a (the Esirkepov
+// prefix sums and form factors are at most 1 in magnitude) and |q w / V_c| for the
+// out-of-plane current (|v| < 1).
+void set_det_scale(pic_ctx *c)
+{
+    RunDev &rd = c->rd;
+    double sc = 0.0;
+    for (int s = 0; s < rd.nsp; ++s) {
+        const SpeciesDev &sp = rd.sp[s];
+        for (int a = 0; a < 3; ++a) sc = std::max(sc, std::fabs(sp.kx[a]));
+        sc = std::max(sc, std::fabs(sp.kz));
+    }
+    if (!(sc > 0.0) || !std::isfinite(sc)) sc = 1.0;
+    rd.det_scale = sc;
+    rd.det_inv32 = (float)(std::ldexp(1.0, 40) / sc);
+    rd.det_inv64 = std::ldexp(1.0, 31) / sc;
+}
+
+// Record G = D.E - rho of the current state as the reference of the Gauss-residual drift.
+int capture_gauss_ref(pic_ctx *c)
+{
+    if (c->gref_valid) return PIC_OK;
+    refresh_species_ptrs(c);
+    if (launch_gauss_ref(c->rd, c->rho, c->gref, c->diag_out, c->stream) != cudaSuccess)
+        return PIC_ECUDA;
+    c->kernel_launches += 2;
+    for (int s = 0; s < c->rd.nsp; ++s) c->kernel_launches += c->rd.sp[s].n > 0 ? 1 : 0;
+    c->gref_valid = true;
+    return PIC_OK;
 }
 
 int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n,
@@ -342,6 +385,7 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     if (o.n_species <= 0) o.n_species = 2;
     if (o.n_species > PIC_MAX_SPECIES) return PIC_EINVAL;
     if (o.precision != PIC_FP64 && o.precision != PIC_FP32_MIXED) return PIC_EINVAL;
+    if (o.deterministic != 0 && o.deterministic != 1) return PIC_EINVAL;
 
     pic_ctx *c = new (std::nothrow) pic_ctx;
     if (!c) return PIC_ENOMEM;
@@ -352,6 +396,7 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     rd.scheme = scheme;
     rd.prec = o.precision;
     rd.ncell = ncell;
+    rd.det = o.deterministic;
     for (int a = 0; a < 3; ++a) {
         rd.n[a] = grid[a];
         rd.dx[a] = (a < dim) ? dx[a] : 1.0;
@@ -372,8 +417,9 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     rd.div_n01 = make_fastdiv(rd.n[0] * rd.n[1]);
     // tiles
     // default tiles (measured on the 2048x1024 cubic workload: the FP32 form is 2% faster with
-    // 64x8 than with 32x8, the FP64 form the same with both)
-    const int deft[2][3] = {{rd.prec == PIC_FP32_MIXED ? 64 : 32, 8, 1}, {8, 4, 4}};
+    // 64x8 than with 32x8, the FP64 form the same with both); a deterministic FP32 run keeps
+    // 64-bit words in its shared current tile and takes 32x8 so that two CTAs share an SM
+    const int deft[2][3] = {{rd.prec == PIC_FP32_MIXED && !rd.det ? 64 : 32, 8, 1}, {8, 4, 4}};
     for (int a = 0; a < 3; ++a) {
         int t = o.tile[a] > 0 ? o.tile[a] : deft[dim - 2][a];
         if (a >= dim) t = 1;
@@ -460,10 +506,11 @@ int pic_footprint(const pic_ctx *c, size_t *bytes)
     // sort targets and sort scratch
     for (int s = 0; s < rd.nsp; ++s) b += align_up((size_t)c->cap[s] * pb + 7 * A, A);
     b += 2 * align_up(rd.ntiles * TC * sizeof(int32_t), A);
-    b += 3 * align_up((size_t)capmax * sizeof(int32_t), A);
+    b += 4 * align_up((size_t)capmax * sizeof(int32_t), A);
     b += align_up((rd.ntiles + 1) * sizeof(int64_t), A);
     b += staging_size(rd, capmax);                // host<->device staging (chunked)
-    b += align_up(rd.ncell * sizeof(double), A);  // rho
+    b += 3 * align_up(rd.ncell * sizeof(double), A);  // rho, rho_prev, gref
+    if (rd.det && rd.prec == PIC_FP64) b += 3 * align_up(rd.ncell * sizeof(double), A);  // jlo
     b += 2 * A;                                   // diag out, err
     b += A;                                       // base alignment slack
     (void)captot;
@@ -516,12 +563,23 @@ int pic_bind_memory(pic_ctx *c, void *dev, size_t bytes)
     c->sc.cell_first = (int32_t *)take(rd.ntiles * TC * sizeof(int32_t));
     c->sc.slot = (int32_t *)take((size_t)capmax * sizeof(int32_t));
     c->sc.key = (int32_t *)take((size_t)capmax * sizeof(int32_t));
+    c->sc.idx = (int32_t *)take((size_t)capmax * sizeof(int32_t));
     c->sc.pos = (int32_t *)take((size_t)capmax * sizeof(int32_t));
     c->sc.tile_count = (int64_t *)take((rd.ntiles + 1) * sizeof(int64_t));
     c->staging_bytes = staging_size(rd, capmax);
     c->staging = take(c->staging_bytes);
     c->rho = (double *)take(rd.ncell * sizeof(double));
-    c->diag_out = (double *)take(4 * sizeof(double));
+    c->rho_prev = (double *)take(rd.ncell * sizeof(double));
+    c->gref = (double *)take(rd.ncell * sizeof(double));
+    c->jlo = nullptr;
+    for (int a = 0; a < 3; ++a) rd.Jlo[a] = nullptr;
+    if (rd.det && rd.prec == PIC_FP64) {
+        c->jlo = (unsigned long long *)take(3 * rd.ncell * sizeof(double));
+        for (int a = 0; a < 3; ++a) rd.Jlo[a] = c->jlo + a * rd.ncell;
+    }
+    c->rho_prev_valid = false;
+    c->gref_valid = false;
+    c->diag_out = (double *)take(8 * sizeof(double));
     c->err = (int32_t *)take(sizeof(int32_t));
     rd.err = c->err;
     if ((size_t)(p - (char *)dev) > bytes) return PIC_ENOMEM;
@@ -628,6 +686,7 @@ int pic_set_fields(pic_ctx *c, int comp, const double *host, size_t count)
     if (cudaMemcpyAsync(c->rd.F[comp], host, count * sizeof(double), cudaMemcpyHostToDevice,
                         c->stream) != cudaSuccess)
         return PIC_ECUDA;
+    c->gref_valid = false;  // D.E changes: the drift is measured from the next step on
     if (c->rd.prec == PIC_FP32_MIXED) {
         if (launch_shadow(c->rd, c->stream) != cudaSuccess) return PIC_ECUDA;
         c->kernel_launches += 1;
@@ -644,6 +703,11 @@ int pic_step(pic_ctx *c, int nsteps)
     drain_events(c);
     c->gpp_ms = 0.0;
     c->gpp_launches = 0;
+    if (nsteps > 0) {
+        const int r = capture_gauss_ref(c);
+        if (r != PIC_OK) return r;
+    }
+    if (rd.det) set_det_scale(c);
     for (int it = 0; it < nsteps; ++it) {
         if (c->age >= c->sort_interval) {
             const int r = sort_all(c);
@@ -653,6 +717,8 @@ int pic_step(pic_ctx *c, int nsteps)
         if (cudaMemsetAsync(rd.F[6], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess) return PIC_ECUDA;
         if (cudaMemsetAsync(rd.F[7], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess) return PIC_ECUDA;
         if (cudaMemsetAsync(rd.F[8], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess) return PIC_ECUDA;
+        if (c->jlo && cudaMemsetAsync(c->jlo, 0, 3 * rd.ncell * sizeof(double), c->stream) != cudaSuccess)
+            return PIC_ECUDA;
         if (c->have_events) {
             if (c->ev_pending == 64) drain_events(c);
             cudaEventRecord(c->ev0[c->ev_pending], c->stream);
@@ -662,6 +728,10 @@ int pic_step(pic_ctx *c, int nsteps)
         if (e != cudaSuccess) return PIC_ECUDA;
         if (c->have_events) cudaEventRecord(c->ev1[c->ev_pending++], c->stream);
         c->gpp_launches += 1;
+        if (rd.det) {  // the fixed-point sums become the FP64 current
+            if (launch_det_finish(rd, c->stream) != cudaSuccess) return PIC_ECUDA;
+            c->kernel_launches += 1;
+        }
         for (int s = 0; s < rd.nsp; ++s) c->wc_valid[s] = c->wc[s] != nullptr;
         if (launch_yee_b(rd, 0.5 * rd.dt, false, c->stream) != cudaSuccess) return PIC_ECUDA;
         if (launch_yee_e(rd, shadow, c->stream) != cudaSuccess) return PIC_ECUDA;
@@ -803,9 +873,18 @@ int pic_diag(pic_ctx *c, pic_diag_t *out)
     if (!c->base) return PIC_ESTATE;
     refresh_species_ptrs(c);
     const RunDev &rd = c->rd;
-    if (launch_diag(rd, c->diag_out, c->rho, c->stream) != cudaSuccess) return PIC_ECUDA;
+    const bool cont = c->rho_prev_valid && c->step == c->rho_prev_step + 1;
+    if (launch_diag(rd, c->diag_out, c->rho, c->gref_valid ? c->gref : nullptr,
+                    cont ? c->rho_prev : nullptr, c->stream) != cudaSuccess)
+        return PIC_ECUDA;
     c->kernel_launches += 2 + 2 * rd.nsp;
-    double h[4] = {0, 0, 0, 0};
+    // this rho is the reference of the next call's continuity residual
+    if (cudaMemcpyAsync(c->rho_prev, c->rho, rd.ncell * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+        return PIC_ECUDA;
+    c->rho_prev_valid = true;
+    c->rho_prev_step = c->step;
+    double h[6] = {0, 0, 0, 0, 0, 0};
     int32_t e = 0;
     if (cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return PIC_ECUDA;
     if (cudaMemcpyAsync(&e, c->err, sizeof(e), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return PIC_ECUDA;
@@ -818,6 +897,8 @@ int pic_diag(pic_ctx *c, pic_diag_t *out)
     for (int s = 0; s < rd.nsp; ++s) qt += rd.sp[s].q * rd.sp[s].w * (double)rd.sp[s].n;
     out->total_charge = qt;
     out->max_gauss_residual = h[2];
+    out->max_gauss_residual_drift = c->gref_valid ? h[3] : 0.0;
+    out->max_continuity_residual = cont ? h[4] : std::nan("");
     out->error_flags = e;
     if (e & PIC_ERR_NONFINITE) return PIC_ENAN;
     if (e & PIC_ERR_OUTSIDE_TILE) return PIC_EOVERFLOW;
@@ -890,6 +971,14 @@ void ctx_after_batch(pic_ctx *c, const RunDev &d, int age, int64_t steps)
 }
 
 int ctx_kt(const pic_ctx *c) { return c->kt; }
+// before a batch takes the run over: record the Gauss-residual reference if a load or field
+// set left it stale (the batch's steps do not), and wait for it
+int ctx_prepare_batch(pic_ctx *c)
+{
+    const int r = capture_gauss_ref(c);
+    if (r != PIC_OK) return r;
+    return cudaStreamSynchronize(c->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
 int ctx_sort_interval(const pic_ctx *c) { return c->sort_interval; }
 int ctx_age(const pic_ctx *c) { return c->age; }
 cudaStream_t ctx_stream(const pic_ctx *c) { return c->stream; }

@@ -25,6 +25,7 @@ namespace pic {
 RunDev *ctx_rundev(pic_ctx *c);
 void ctx_after_batch(pic_ctx *c, const RunDev &dev_copy, int age, int64_t steps);
 int ctx_kt(const pic_ctx *c);
+int ctx_prepare_batch(pic_ctx *c);
 int ctx_sort_interval(const pic_ctx *c);
 int ctx_age(const pic_ctx *c);
 cudaStream_t ctx_stream(const pic_ctx *c);
@@ -111,6 +112,20 @@ __global__ void k_b_layout(const RunDev *runs, const RunState *st, const BlockMa
     sort_layout_block(rd, rd.sp[s].tile_start, m.block);
 }
 
+__global__ void __launch_bounds__(kBlock) k_b_place(const RunDev *runs, const RunState *st,
+                                                    const BlockMap *bm, int s)
+{
+    const BlockMap m = bm[blockIdx.x];
+    if (!st[m.run].due) return;
+    const RunDev &rd = runs[m.run];
+    const int64_t n = rd.sp[s].n;
+    for (int k = 0; k < kPartPer; ++k) {
+        const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
+        if (p < n) sort_place_one(rd, p);
+    }
+}
+
+// one thread per cell-major position r of the run's species (the same range as its particles)
 __global__ void __launch_bounds__(kBlock) k_b_scatter(const RunDev *runs, const RunState *st,
                                                       const BlockMap *bm, int s)
 {
@@ -119,8 +134,8 @@ __global__ void __launch_bounds__(kBlock) k_b_scatter(const RunDev *runs, const 
     const RunDev &rd = runs[m.run];
     const SpeciesDev &sp = rd.sp[s];
     for (int k = 0; k < kPartPer; ++k) {
-        const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
-        if (p < sp.n) sort_scatter_one(rd, s, p, sp.pos_alt, sp.mom_alt, sp.cell_alt);
+        const int64_t r = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
+        if (r < sp.n) sort_scatter_one(rd, s, r, sp.pos_alt, sp.mom_alt, sp.cell_alt);
     }
 }
 
@@ -277,6 +292,9 @@ cudaError_t enqueue_step(pic_batch *b)
         k_b_layout<<<(unsigned)b->bm_tile.size(), tb, 0, st>>>(b->d_runs, b->d_state, b->d_bm_tile, s);
         nl += 3;
         if (!b->bm_part[s].empty()) {
+            k_b_place<<<(unsigned)b->bm_part[s].size(), kBlock, 0, st>>>(b->d_runs, b->d_state,
+                                                                         b->d_bm_part[s], s);
+            ++nl;
             k_b_scatter<<<(unsigned)b->bm_part[s].size(), kBlock, 0, st>>>(b->d_runs, b->d_state,
                                                                            b->d_bm_part[s], s);
             ++nl;
@@ -341,7 +359,7 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
         if (!c || !ctx_bound(c)) { delete b; return PIC_ESTATE; }
         const RunDev &rd = *ctx_rundev(c);
         if (rd.dim != 2 || rd.prec != PIC_FP32_MIXED || rd.nsp != b->nsp || rd.l < 2 || rd.l > 3
-            || ctx_stream(c) != b->stream) {
+            || rd.det || ctx_stream(c) != b->stream) {
             delete b;
             return PIC_EINVAL;
         }
@@ -406,6 +424,10 @@ int pic_batch_bind_memory(pic_batch *b, void *dev, size_t bytes)
     b->d_bm_tile = (BlockMap *)take(table_bytes(b->bm_tile));
     b->d_items = (int2 *)take(table_bytes(b->items));
     b->d_counter = (int *)take(sizeof(int));
+    for (int r = 0; r < b->n; ++r) {
+        const int e = ctx_prepare_batch(b->ctx[r]);
+        if (e != PIC_OK) return e;
+    }
     // descriptors and tables
     std::vector<RunDev> rds(b->n);
     std::vector<RunState> sts(b->n);

@@ -36,8 +36,9 @@ struct TTable {
 struct SortScratch {
     int32_t *cnt;         // ntiles * TC
     int32_t *cell_first;  // ntiles * TC
-    int32_t *slot;        // n_max
+    int32_t *slot;        // n_max: provisional place in the cell
     int32_t *key;         // n_max
+    int32_t *idx;         // n_max: particle index at every cell-major position
     int32_t *pos;         // n_max (slot-major order only)
     int64_t *tile_count;  // ntiles + 1 (scan workspace)
 };
@@ -119,7 +120,34 @@ struct RunDev {
     SpeciesDev sp[PIC_NSP_MAX];
     SortScratch sc;
     int32_t *err;
+    // deterministic current (pic_options.deterministic): every contribution is added as a
+    // 64-bit fixed-point integer, so the sums do not depend on the order of the atomics.
+    // FP32 form: one word, unit s 2^-40 (det_inv32 = 2^40 / s).  FP64 form: two words, the
+    // high one in units of s 2^-31 (det_inv64 = 2^31 / s) in F[6..8], the low one in units of
+    // s 2^-63 in Jlo.  s (det_scale) bounds one particle's contribution to one node.
+    int det;
+    float det_inv32;
+    double det_inv64;
+    double det_scale;
+    unsigned long long *Jlo[3];
 };
+
+// Fixed-point forms of a current contribution v (see RunDev::det).
+__device__ __forceinline__ unsigned long long det_word32(float v, float inv)
+{
+    return (unsigned long long)__float2ll_rn(v * inv);
+}
+
+// High and low words of v in units of s 2^-31 and s 2^-63: t = v 2^31 / s = hi + lo 2^-32 with
+// hi = floor(t) and lo = round((t - hi) 2^32) in [0, 2^32]; t - hi is exact.
+__device__ __forceinline__ void det_words64(double v, double inv, unsigned long long &hi,
+                                            unsigned long long &lo)
+{
+    const double t = v * inv;
+    const double h = floor(t);
+    hi = (unsigned long long)__double2ll_rn(h);
+    lo = (unsigned long long)__double2ll_rn((t - h) * 4294967296.0);
+}
 
 // ------------------------------------------------------------------------------------------
 // B-spline weights W_l at the l+1 nodes that carry a non-zero weight (Sec. 2, Eq. shape-real).

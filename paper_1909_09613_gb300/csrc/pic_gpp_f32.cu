@@ -23,7 +23,7 @@ template <int L, int KT>
 cudaError_t go(const RunDev &rd, cudaStream_t st)
 {
     if (rd.dim == 2) {
-        const size_t smem = stage2d_bytes<float>(rd.reg_nodes, rd.l);
+        const size_t smem = stage2d_bytes<float>(rd.reg_nodes, rd.l, true, rd.det != 0);
         cudaError_t e = cudaFuncSetAttribute(k_gpp2d<L, KT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -50,7 +50,7 @@ cudaError_t launch_gpp_f32(const RunDev &rd, int kt, cudaStream_t st)
 
 size_t gpp_smem_bytes_f32(const RunDev &rd)
 {
-    return rd.dim == 2 ? stage2d_bytes<float>(rd.reg_nodes, rd.l) : 0;
+    return rd.dim == 2 ? stage2d_bytes<float>(rd.reg_nodes, rd.l, true, rd.det != 0) : 0;
 }
 
 // Dynamic shared memory a work item of this run needs in the batched kernel: the copy of the

@@ -12,13 +12,15 @@ template <typename R> struct AccT { typedef R T; };
 // Shared-memory layout of a staged 2D tile (all arrays reg_nodes long, x fastest):
 //   pa = (E1, B2) pairs  [both sit at (i+1/2, j): W along x, T along y]
 //   pb = (E2, B1) pairs  [both sit at (i, j+1/2): T along x, W along y]
-//   e3 = E3 [(i, j): T T],  b3 = B3 [(i+1/2, j+1/2): W W],  j1, j2, j3.
+//   e3 = E3 [(i, j): T T],  b3 = B3 [(i+1/2, j+1/2): W W],  j1, j2, j3 (R), or, for a
+//   deterministic run, q1, q2, q3 (64-bit fixed point, RunDev::det) in their place.
 //   rec = per-warp factor records of the FP32 deposit (see DepFrame), FP32 form only.
 template <typename R>
 struct Stage2D {
     typename Vec2<R>::T *pa, *pb;
     R *e3, *b3;
     R *j1, *j2, *j3;
+    unsigned long long *q1, *q2, *q3;
     TTable *tt;
     float *rec;
 };
@@ -64,22 +66,33 @@ __host__ __device__ inline int dep_record_floats(int l)
     }
 }
 
+// Bytes per node of the shared current tile: R per component, or (FP32 form of a
+// deterministic run) a 64-bit fixed-point word per component.
+template <typename R>
+__host__ __device__ inline size_t stage2d_j_bytes(bool det)
+{
+    return (sizeof(R) == 4 && det) ? 8 : sizeof(R);
+}
+
 // own_tt: the stage holds its own copy of the two T tables (false when the caller already
 // keeps the run descriptor, tables included, in shared memory).
 template <typename R>
-__host__ __device__ inline size_t stage2d_fields_bytes(int64_t nodes, bool own_tt = true)
+__host__ __device__ inline size_t stage2d_fields_bytes(int64_t nodes, bool own_tt = true,
+                                                       bool det = false)
 {
     size_t b = own_tt ? 2 * sizeof(TTable) : 0;
-    b += (size_t)nodes * (2 * sizeof(typename Vec2<R>::T) + 5 * sizeof(R));
+    b += (size_t)nodes * (2 * sizeof(typename Vec2<R>::T) + 2 * sizeof(R)
+                          + 3 * stage2d_j_bytes<R>(det));
     return (b + 15) / 16 * 16;
 }
 
 // Dynamic shared memory of a 2D tile block: staged fields and current, plus (FP32 form) the
 // deposit records of its warps.
 template <typename R>
-__host__ __device__ inline size_t stage2d_bytes(int64_t nodes, int l, bool own_tt = true)
+__host__ __device__ inline size_t stage2d_bytes(int64_t nodes, int l, bool own_tt = true,
+                                                bool det = false)
 {
-    size_t b = stage2d_fields_bytes<R>(nodes, own_tt);
+    size_t b = stage2d_fields_bytes<R>(nodes, own_tt, det);
     if (sizeof(R) == 4) b += (size_t)kTileWarps * dep_record_floats(l) * sizeof(float);
     return b;
 }
@@ -87,7 +100,8 @@ __host__ __device__ inline size_t stage2d_bytes(int64_t nodes, int l, bool own_t
 // tt_shared: T tables already in shared memory (else the stage carries a copy)
 template <typename R>
 __device__ __forceinline__ Stage2D<R> stage2d_carve(char *smem, int64_t nodes,
-                                                    const TTable *tt_shared = nullptr)
+                                                    const TTable *tt_shared = nullptr,
+                                                    bool det = false)
 {
     Stage2D<R> s;
     s.tt = tt_shared ? (TTable *)tt_shared : (TTable *)smem;
@@ -96,10 +110,18 @@ __device__ __forceinline__ Stage2D<R> stage2d_carve(char *smem, int64_t nodes,
     s.pb = (typename Vec2<R>::T *)p; p += nodes * sizeof(typename Vec2<R>::T);
     s.e3 = (R *)p; p += nodes * sizeof(R);
     s.b3 = (R *)p; p += nodes * sizeof(R);
-    s.j1 = (R *)p; p += nodes * sizeof(R);
-    s.j2 = (R *)p; p += nodes * sizeof(R);
-    s.j3 = (R *)p;
-    s.rec = (float *)(smem + stage2d_fields_bytes<R>(nodes, tt_shared == nullptr));
+    s.j1 = s.j2 = s.j3 = nullptr;
+    s.q1 = s.q2 = s.q3 = nullptr;
+    if (sizeof(R) == 4 && det) {
+        s.q1 = (unsigned long long *)p; p += nodes * 8;
+        s.q2 = (unsigned long long *)p; p += nodes * 8;
+        s.q3 = (unsigned long long *)p;
+    } else {
+        s.j1 = (R *)p; p += nodes * sizeof(R);
+        s.j2 = (R *)p; p += nodes * sizeof(R);
+        s.j3 = (R *)p;
+    }
+    s.rec = (float *)(smem + stage2d_fields_bytes<R>(nodes, tt_shared == nullptr, det));
     return s;
 }
 
@@ -131,9 +153,15 @@ __device__ void stage2d_load(const RunDev &rd, const Stage2D<R> &st, int x0, int
         }
         st.pa[n] = a;
         st.pb[n] = b;
-        st.j1[n] = R(0);
-        st.j2[n] = R(0);
-        st.j3[n] = R(0);
+        if (st.q1) {
+            st.q1[n] = 0ull;
+            st.q2[n] = 0ull;
+            st.q3[n] = 0ull;
+        } else {
+            st.j1[n] = R(0);
+            st.j2[n] = R(0);
+            st.j3[n] = R(0);
+        }
     }
 }
 
@@ -143,6 +171,23 @@ __device__ void stage2d_flush(const RunDev &rd, const Stage2D<R> &st, int x0, in
 {
     const int RX = rd.reg[0];
     const int64_t nodes = rd.reg_nodes;
+    if (st.q1) {  // deterministic run: integer sums, exact in any order
+        for (int64_t n = threadIdx.x; n < nodes; n += blockDim.x) {
+            const unsigned long long a = st.q1[n], b = st.q2[n], c = st.q3[n];
+            if ((a | b | c) == 0ull) continue;
+            const int rx = (int)(n % RX), ry = (int)(n / RX);
+            const int gx = wrap_idx(x0 - rd.pre[0] + rx, rd.n[0]);
+            const int gy = wrap_idx(y0 - rd.pre[1] + ry, rd.n[1]);
+            const int64_t g = (int64_t)gy * rd.n[0] + gx;
+            if (a) atomicAdd((unsigned long long *)(rd.F[6] + g), a);
+            if (b) atomicAdd((unsigned long long *)(rd.F[7] + g), b);
+            if (c) atomicAdd((unsigned long long *)(rd.F[8] + g), c);
+            st.q1[n] = 0ull;
+            st.q2[n] = 0ull;
+            st.q3[n] = 0ull;
+        }
+        return;
+    }
     for (int64_t n = threadIdx.x; n < nodes; n += blockDim.x) {
         const R a = st.j1[n], b = st.j2[n], c = st.j3[n];
         if (a == R(0) && b == R(0) && c == R(0)) continue;
@@ -172,11 +217,12 @@ __device__ __forceinline__ bool local_coord(int c, int origin, int tile, int dri
 
 // One lane's Esirkepov window (Sec. 1: W_x = DSx (S0y + DSy/2) summed along x, W_y likewise,
 // W_z = S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3) added to the shared current tile with
-// atomics (WY as in deposit_lane_global below).
-template <int L, typename R, bool WY = true>
+// atomics (WY as in deposit_lane_global below); DET: as fixed-point words (RunDev::det).
+template <int L, typename R, bool WY = true, bool DET = false>
 __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int jx0, int jy0, R kx,
                                              R ky, R kz, const R *px, const R *py, const R *Ax,
-                                             const R *Ay, const R *Bx, const AxisS<L, R> &Sy)
+                                             const R *Ay, const R *Bx, const AxisS<L, R> &Sy,
+                                             float dinv = 0.0f)
 {
 #pragma unroll
     for (int b = 0; b < (WY ? L + 2 : L + 1); ++b) {
@@ -186,9 +232,15 @@ __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int j
         const R zs = kz * Sy.s0[b], zd = kz * Sy.ds[b];
 #pragma unroll
         for (int a = 0; a < L + 2; ++a) {
-            if (a <= L) atomicAdd(st.j1 + row + a, ayk * px[a]);
-            if (b <= L) atomicAdd(st.j2 + row + a, pyk * Ax[a]);
-            atomicAdd(st.j3 + row + a, zs * Ax[a] + zd * Bx[a]);
+            if constexpr (DET) {
+                if (a <= L) atomicAdd(st.q1 + row + a, det_word32(ayk * px[a], dinv));
+                if (b <= L) atomicAdd(st.q2 + row + a, det_word32(pyk * Ax[a], dinv));
+                atomicAdd(st.q3 + row + a, det_word32(zs * Ax[a] + zd * Bx[a], dinv));
+            } else {
+                if (a <= L) atomicAdd(st.j1 + row + a, ayk * px[a]);
+                if (b <= L) atomicAdd(st.j2 + row + a, pyk * Ax[a]);
+                atomicAdd(st.j3 + row + a, zs * Ax[a] + zd * Bx[a]);
+            }
         }
     }
 }
@@ -199,7 +251,7 @@ __device__ __forceinline__ void deposit_lane(const Stage2D<R> &st, int RX, int j
 // bounds this form.  gx0, gy0: global node of the window's first column and row (unwrapped).
 // WY = false when no lane of the warp changed its y window base: row l + 1 then carries exact
 // zeros (S0y = DSy = 0) and is skipped.
-template <int L, typename R, typename Hot, bool WY = true>
+template <int L, typename R, typename Hot, bool WY = true, bool DET = false>
 __device__ __forceinline__ void deposit_lane_global(const Hot &h, int gx0, int gy0, R kx, R ky,
                                                     R kz, const R *px, const R *py, const R *Ax,
                                                     const R *Ay, const R *Bx,
@@ -220,9 +272,26 @@ __device__ __forceinline__ void deposit_lane_global(const Hot &h, int gx0, int g
 #pragma unroll
         for (int a = 0; a < L + 2; ++a) {
             const int64_t g = gy[b] + gx[a];
-            if (a <= L) atomicAdd(h.J0 + g, (double)(ayk * px[a]));
-            if (b <= L) atomicAdd(h.J1 + g, (double)(pyk * Ax[a]));
-            atomicAdd(h.J2 + g, (double)(zs * Ax[a] + zd * Bx[a]));
+            if constexpr (DET) {
+                unsigned long long hi, lo;
+                if (a <= L) {
+                    det_words64((double)(ayk * px[a]), h.dinv64, hi, lo);
+                    atomicAdd((unsigned long long *)(h.J0 + g), hi);
+                    atomicAdd(h.Jlo0 + g, lo);
+                }
+                if (b <= L) {
+                    det_words64((double)(pyk * Ax[a]), h.dinv64, hi, lo);
+                    atomicAdd((unsigned long long *)(h.J1 + g), hi);
+                    atomicAdd(h.Jlo1 + g, lo);
+                }
+                det_words64((double)(zs * Ax[a] + zd * Bx[a]), h.dinv64, hi, lo);
+                atomicAdd((unsigned long long *)(h.J2 + g), hi);
+                atomicAdd(h.Jlo2 + g, lo);
+            } else {
+                if (a <= L) atomicAdd(h.J0 + g, (double)(ayk * px[a]));
+                if (b <= L) atomicAdd(h.J1 + g, (double)(pyk * Ax[a]));
+                atomicAdd(h.J2 + g, (double)(zs * Ax[a] + zd * Bx[a]));
+            }
         }
     }
 }
@@ -231,11 +300,15 @@ __device__ __forceinline__ void deposit_lane_global(const Hot &h, int gx0, int g
 // shared or global memory would be re-read for every particle).
 struct Hot2D {
     int n0, n1, tile0, tile1, drift0, drift1, pre0, pre1, RX, RY, slot_major;
-    double *J0, *J1, *J2;  // global FP64 current
+    double *J0, *J1, *J2;  // global FP64 current (high fixed-point words of a deterministic run)
     double dtt0, dtt1;
     uint64_t dm;  // division by n0 (FastDiv)
     int ds;
     int32_t *err;
+    int det;  // RunDev::det and its fixed-point scales and low words
+    float dinv32;
+    double dinv64;
+    unsigned long long *Jlo0, *Jlo1, *Jlo2;
 };
 
 template <typename R>
@@ -262,6 +335,10 @@ __device__ __forceinline__ Hot2D make_hot2d(const RunDev &rd)
     h.dtt0 = rd.dtt[0]; h.dtt1 = rd.dtt[1];
     h.dm = rd.div_n0.m; h.ds = rd.div_n0.s;
     h.err = rd.err;
+    h.det = rd.det;
+    h.dinv32 = rd.det_inv32;
+    h.dinv64 = rd.det_inv64;
+    h.Jlo0 = rd.Jlo[0]; h.Jlo1 = rd.Jlo[1]; h.Jlo2 = rd.Jlo[2];
     return h;
 }
 
@@ -540,10 +617,18 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         if (h.slot_major) {  // lanes in different cells: per-lane atomics do not collide
             // (shared-memory CAS atomics: measured faster here than global FP64 reductions,
             // which would need an FP32 -> FP64 conversion per node)
-            if (__any_sync(0xffffffffu, act && Sy.wide)) {
-                if (act)
-                    deposit_lane<L, R, true>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
-            } else if (act) {
+            const bool wide = __any_sync(0xffffffffu, act && Sy.wide);
+            if (!act) {
+            } else if (h.det) {
+                if (wide)
+                    deposit_lane<L, R, true, true>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay,
+                                                   Bx, Sy, h.dinv32);
+                else
+                    deposit_lane<L, R, false, true>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay,
+                                                    Bx, Sy, h.dinv32);
+            } else if (wide) {
+                deposit_lane<L, R, true>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+            } else {
                 deposit_lane<L, R, false>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
             }
         } else {
@@ -661,7 +746,15 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
                         if (gx >= RX || gy >= h.RY) continue;
                         const int node = gy * RX + gx;
                         const R a = o1[2 * i + j], b = o2[2 * i + j];
-                        if (role == 0) {
+                        if (h.det) {  // fixed-point words: the warps' sums commute exactly
+                            if (role == 0) {
+                                if (a != R(0)) atomicAdd(st.q1 + node, det_word32(a, h.dinv32));
+                                if (b != R(0)) atomicAdd(st.q2 + node, det_word32(b, h.dinv32));
+                            } else {
+                                const R c = a + b;
+                                if (c != R(0)) atomicAdd(st.q3 + node, det_word32(c, h.dinv32));
+                            }
+                        } else if (role == 0) {
                             if (a != R(0)) atomicAdd(st.j1 + node, a);
                             if (b != R(0)) atomicAdd(st.j2 + node, b);
                         } else {
@@ -676,13 +769,21 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         }
     } else {
         // a drift along x1 rarely moves the y window: skip its empty last row warp-uniformly
-        if (__any_sync(0xffffffffu, act && Sy.wide)) {
-            if (act)
-                deposit_lane_global<L, R, Hot2D, true>(h, x0 - h.pre0 + jx0, y0 - h.pre1 + jy0,
-                                                       kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
-        } else if (act) {
-            deposit_lane_global<L, R, Hot2D, false>(h, x0 - h.pre0 + jx0, y0 - h.pre1 + jy0,
-                                                    kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+        const bool wide = __any_sync(0xffffffffu, act && Sy.wide);
+        const int gx0 = x0 - h.pre0 + jx0, gy0 = y0 - h.pre1 + jy0;
+        if (!act) {
+        } else if (h.det) {
+            if (wide)
+                deposit_lane_global<L, R, Hot2D, true, true>(h, gx0, gy0, kx, ky, kz, px, py, Ax,
+                                                             Ay, Bx, Sy);
+            else
+                deposit_lane_global<L, R, Hot2D, false, true>(h, gx0, gy0, kx, ky, kz, px, py,
+                                                              Ax, Ay, Bx, Sy);
+        } else if (wide) {
+            deposit_lane_global<L, R, Hot2D, true>(h, gx0, gy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
+        } else {
+            deposit_lane_global<L, R, Hot2D, false>(h, gx0, gy0, kx, ky, kz, px, py, Ax, Ay, Bx,
+                                                    Sy);
         }
     }
     if (!act) return;
@@ -706,7 +807,7 @@ template <int L, int KT, typename R>
 __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
                         const TTable *tt_shared = nullptr)
 {
-    Stage2D<R> st = stage2d_carve<R>(smem, rd.reg_nodes, tt_shared);
+    Stage2D<R> st = stage2d_carve<R>(smem, rd.reg_nodes, tt_shared, rd.det != 0);
     const int tx = (int)(tile % rd.ntile[0]);
     const int ty = (int)(tile / rd.ntile[0]);
     const int x0 = tx * rd.tile[0], y0 = ty * rd.tile[1];
@@ -914,7 +1015,20 @@ __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &
                     id[ax] = jn[ax][ka]; id[bx] = jn[bx][kb]; id[cx] = jn[cx][kc];
                     const int64_t g = ((int64_t)id[2] * ny + id[1]) * nx + id[0];
                     const R v = kk * P[ax][ka] * perp;
-                    if (v != R(0)) atomicAdd(rd.F[6 + ax] + g, (double)v);
+                    if (v == R(0)) continue;
+                    if (rd.det) {
+                        if constexpr (sizeof(R) == 4) {
+                            atomicAdd((unsigned long long *)(rd.F[6 + ax] + g),
+                                      det_word32(v, rd.det_inv32));
+                        } else {
+                            unsigned long long hi, lo;
+                            det_words64(v, rd.det_inv64, hi, lo);
+                            atomicAdd((unsigned long long *)(rd.F[6 + ax] + g), hi);
+                            atomicAdd(rd.Jlo[ax] + g, lo);
+                        }
+                    } else {
+                        atomicAdd(rd.F[6 + ax] + g, (double)v);
+                    }
                 }
             }
         }

@@ -359,29 +359,72 @@ __global__ void __launch_bounds__(kBlock) k_rho(const __grid_constant__ RunDev r
     }
 }
 
-// max |D.E - rho| (App. B, Eq. gauss)
-__global__ void __launch_bounds__(kBlock) k_gauss(const __grid_constant__ RunDev rd,
-                                                  const double *rho, double *out)
+// Backward-difference divergence at integer node c of a field whose component a sits half a
+// cell up along a (E or J on the Yee grid): sum_a (F_a(c) - F_a(c - e_a)) / dx_a.
+__device__ __forceinline__ double div_node(const RunDev &rd, const double *const *F, int64_t c)
 {
-    double m = 0.0;
+    const int nx = rd.n[0], ny = rd.n[1], nz = rd.n[2];
+    const int i = (int)(c % nx);
+    const int j = (int)((c / nx) % ny);
+    const int k = (int)(c / ((int64_t)nx * ny));
+    const int im = (i == 0) ? nx - 1 : i - 1;
+    const int jm = (j == 0) ? ny - 1 : j - 1;
+    double dv = (F[0][c] - F[0][gidx(rd, im, j, k)]) * rd.idx[0]
+                + (F[1][c] - F[1][gidx(rd, i, jm, k)]) * rd.idx[1];
+    if (rd.dim == 3) {
+        const int km = (k == 0) ? nz - 1 : k - 1;
+        dv += (F[2][c] - F[2][gidx(rd, i, j, km)]) * rd.idx[2];
+    }
+    return dv;
+}
+
+// Charge-conservation residuals (App. B, Eq. gauss; Sec. 1 for the continuity equation of the
+// Esirkepov deposit), with G = D.E - rho at every node:
+//   out[0] = max |G|;
+//   gref_out: G written per node (the reference the drift is measured from);
+//   gref_in : out[1] = max |G - gref_in|;
+//   rho_prev: out[2] = max |(rho - rho_prev) inv_dt + D.J|, J = F[6..8].
+__global__ void __launch_bounds__(kBlock) k_gauss(const __grid_constant__ RunDev rd,
+                                                  const double *rho, double *out,
+                                                  const double *gref_in, double *gref_out,
+                                                  const double *rho_prev, double inv_dt)
+{
+    double m = 0.0, md = 0.0, mc = 0.0;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < rd.ncell;
          c += (int64_t)gridDim.x * blockDim.x) {
-        const int nx = rd.n[0], ny = rd.n[1], nz = rd.n[2];
-        const int i = (int)(c % nx);
-        const int j = (int)((c / nx) % ny);
-        const int k = (int)(c / ((int64_t)nx * ny));
-        const int im = (i == 0) ? nx - 1 : i - 1;
-        const int jm = (j == 0) ? ny - 1 : j - 1;
-        double dv = (rd.F[0][c] - rd.F[0][gidx(rd, im, j, k)]) * rd.idx[0]
-                    + (rd.F[1][c] - rd.F[1][gidx(rd, i, jm, k)]) * rd.idx[1];
-        if (rd.dim == 3) {
-            const int km = (k == 0) ? nz - 1 : k - 1;
-            dv += (rd.F[2][c] - rd.F[2][gidx(rd, i, j, km)]) * rd.idx[2];
-        }
-        m = fmax(m, fabs(dv - rho[c]));
+        const double g = div_node(rd, rd.F, c) - rho[c];
+        m = fmax(m, fabs(g));
+        if (gref_out) gref_out[c] = g;
+        if (gref_in) md = fmax(md, fabs(g - gref_in[c]));
+        if (rho_prev) mc = fmax(mc, fabs((rho[c] - rho_prev[c]) * inv_dt + div_node(rd, rd.F + 6, c)));
     }
     m = block_max(m);
     if (threadIdx.x == 0) atomic_max_nonneg(out, m);
+    if (gref_in) {
+        md = block_max(md);
+        if (threadIdx.x == 0) atomic_max_nonneg(out + 1, md);
+    }
+    if (rho_prev) {
+        mc = block_max(mc);
+        if (threadIdx.x == 0) atomic_max_nonneg(out + 2, mc);
+    }
+}
+
+// Fixed-point current of a deterministic run (RunDev::det) -> FP64, in place.
+__global__ void __launch_bounds__(kBlock) k_det_finish(const __grid_constant__ RunDev rd)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= rd.ncell) return;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        long long *w = (long long *)rd.F[6 + a];
+        if (rd.prec == 1) {
+            rd.F[6 + a][c] = (double)w[c] * (rd.det_scale * 0x1p-40);
+        } else {
+            const double v = (double)w[c] + (double)(long long)rd.Jlo[a][c] * 0x1p-32;
+            rd.F[6 + a][c] = v * (rd.det_scale * 0x1p-31);
+        }
+    }
 }
 
 inline unsigned grid_for(int64_t n)
@@ -425,16 +468,12 @@ cudaError_t launch_unpack(const RunDev &rd, int s, double *x, double *u, int64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t st)
+// rho of all species at their current positions (FP64, into rho, cleared first)
+static cudaError_t launch_rho(const RunDev &rd, double *rho, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(double), st);
+    cudaError_t e = cudaMemsetAsync(rho, 0, rd.ncell * sizeof(double), st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(rho, 0, rd.ncell * sizeof(double), st);
-    if (e != cudaSuccess) return e;
-    const unsigned gr = 1024;
-    k_field_energy<<<gr, kBlock, 0, st>>>(rd, out + 0);
     for (int s = 0; s < rd.nsp; ++s) {
-        k_kinetic<<<gr, kBlock, 0, st>>>(rd, s, out + 1);
         if (rd.sp[s].n == 0) continue;
         const unsigned g = grid_for(rd.sp[s].n);
         switch (rd.l) {
@@ -444,7 +483,37 @@ cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t
         default: k_rho<4><<<g, kBlock, 0, st>>>(rd, s, rho); break;
         }
     }
-    k_gauss<<<gr, kBlock, 0, st>>>(rd, rho, out + 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, const double *gref,
+                        const double *rho_prev, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, 6 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const unsigned gr = 1024;
+    k_field_energy<<<gr, kBlock, 0, st>>>(rd, out + 0);
+    for (int s = 0; s < rd.nsp; ++s) k_kinetic<<<gr, kBlock, 0, st>>>(rd, s, out + 1);
+    e = launch_rho(rd, rho, st);
+    if (e != cudaSuccess) return e;
+    k_gauss<<<gr, kBlock, 0, st>>>(rd, rho, out + 2, gref, nullptr, rho_prev, 1.0 / rd.dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_ref(const RunDev &rd, double *rho, double *gref, double *scratch,
+                             cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    e = launch_rho(rd, rho, st);
+    if (e != cudaSuccess) return e;
+    k_gauss<<<1024, kBlock, 0, st>>>(rd, rho, scratch, nullptr, gref, nullptr, 0.0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_det_finish(const RunDev &rd, cudaStream_t st)
+{
+    k_det_finish<<<grid_for(rd.ncell), kBlock, 0, st>>>(rd);
     return cudaGetLastError();
 }
 

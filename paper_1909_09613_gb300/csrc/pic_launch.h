@@ -36,8 +36,16 @@ cudaError_t launch_load_plasma(const RunDev &rd, int s, const LoadKeys &keys, in
 cudaError_t launch_unpack(const RunDev &rd, int s, double *x, double *u, int64_t *cell,
                           int64_t m, int64_t p0, cudaStream_t st);
 
-// diagnostics: out[0] field energy, out[1] kinetic, out[2] max gauss residual (device doubles)
-cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, cudaStream_t st);
+// diagnostics (device doubles): out[0] field energy sum, out[1] kinetic energy, out[2] max
+// |D.E - rho|, out[3] max |G - gref| (gref != null), out[4] max continuity residual against
+// rho_prev (rho_prev != null); rho receives the charge density of the current particles
+cudaError_t launch_diag(const RunDev &rd, double *out, double *rho, const double *gref,
+                        const double *rho_prev, cudaStream_t st);
+// G = D.E - rho of the current state into gref (rho and 3 doubles of scratch overwritten)
+cudaError_t launch_gauss_ref(const RunDev &rd, double *rho, double *gref, double *scratch,
+                             cudaStream_t st);
+// fixed-point current of a deterministic run -> FP64 (after the particle pass)
+cudaError_t launch_det_finish(const RunDev &rd, cudaStream_t st);
 
 // tile sort of one species
 cudaError_t launch_sort(const RunDev &rd, int s, int64_t *tile_start, void *const *dst_pos,

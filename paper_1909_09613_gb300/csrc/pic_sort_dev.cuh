@@ -1,5 +1,5 @@
 // Device bodies of the tile sort, shared by the single-run launches (pic_sort.cu) and the
-// batched launches (pic_batch.cu).  See pic_sort.cu for the two orders.
+// batched launches (pic_batch.cu).  See pic_sort.cu for the two orders and the stages.
 #pragma once
 #include "pic_common.cuh"
 
@@ -62,7 +62,9 @@ __device__ __forceinline__ int sort_block_excl_scan(int v, int *total)
     return r;
 }
 
-// 1. tile-major cell key of particle p and its slot in the cell
+// 1. tile-major cell key of particle p, the particle count of every key, and a provisional
+//    place among the particles of its key (taken from an atomic, so not reproducible; stage 5
+//    replaces it by the particle's rank in the previous order)
 __device__ __forceinline__ void sort_count_one(const RunDev &rd, int s, int64_t p)
 {
     const SpeciesDev &sp = rd.sp[s];
@@ -162,13 +164,33 @@ __device__ __forceinline__ void sort_layout_block(const RunDev &rd, const int64_
     }
 }
 
-// 5. copy particle p of species s to its sorted position in the destination buffers
-__device__ __forceinline__ void sort_scatter_one(const RunDev &rd, int s, int64_t p,
+// 5. the index of particle p at its provisional place in its cell's segment of the cell-major
+//    order (the segment of key k is cell_first[k] .. cell_first[k] + cnt[k] - 1)
+__device__ __forceinline__ void sort_place_one(const RunDev &rd, int64_t p)
+{
+    const int k = rd.sc.key[p];
+    rd.sc.idx[(int64_t)rd.sc.cell_first[k] + rd.sc.slot[p]] = (int32_t)p;
+}
+
+// 6. cell-major position r: the particle p placed there by stage 5 is moved to the position of
+//    its rank among the particles of its cell in the previous order (the number of indices
+//    below p in the segment), which makes the order stable and the same on every run: sorted
+//    by (tile, cell, previous index), or in the slot-major order by (tile, rank, cell).  The
+//    threads of a warp usually share a segment, so its loads are broadcasts; the cost grows
+//    with the square of a cell's occupancy.
+__device__ __forceinline__ void sort_scatter_one(const RunDev &rd, int s, int64_t r,
                                                  void *const *dp, void *const *dm, int32_t *dcell)
 {
     const SpeciesDev &sp = rd.sp[s];
-    const int64_t r = (int64_t)rd.sc.cell_first[rd.sc.key[p]] + rd.sc.slot[p];
-    const int64_t q = rd.slot_major ? (int64_t)rd.sc.pos[r] : r;
+    const int32_t p = rd.sc.idx[r];
+    const int k = rd.sc.key[p];
+    const int64_t first = rd.sc.cell_first[k];
+    const int m = rd.sc.cnt[k];
+    const int32_t *seg = rd.sc.idx + first;
+    int rank = 0;
+    for (int j = 0; j < m; ++j) rank += (__ldg(seg + j) < p) ? 1 : 0;
+    const int64_t rr = first + rank;
+    const int64_t q = rd.slot_major ? (int64_t)rd.sc.pos[rr] : rr;
     if (rd.prec == 1) {
         dcell[q] = sp.cell[p];
         for (int a = 0; a < rd.dim; ++a) ((float *)dp[a])[q] = ((const float *)sp.pos[a])[p];

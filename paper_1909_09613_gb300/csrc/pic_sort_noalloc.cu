@@ -21,12 +21,14 @@ constexpr int64_t kMaxKeys = (int64_t)1 << 20;       // tiles x cells per tile
 constexpr int64_t kMaxTiles = (int64_t)1 << 16;      // tiles
 
 // scratch layout: count[kMaxKeys] | cell_first[kMaxKeys] | slot[kMaxParticles] |
-//                 key[kMaxParticles] (all int32) | tile_count[kMaxTiles + 1] (int64)
+//                 key[kMaxParticles] | idx[kMaxParticles] (all int32) |
+//                 tile_count[kMaxTiles + 1] (int64)
 constexpr size_t kOffCount = 0;
 constexpr size_t kOffFirst = kOffCount + sizeof(int32_t) * kMaxKeys;
 constexpr size_t kOffSlot = kOffFirst + sizeof(int32_t) * kMaxKeys;
 constexpr size_t kOffKey = kOffSlot + sizeof(int32_t) * kMaxParticles;
-constexpr size_t kOffTiles = kOffKey + sizeof(int32_t) * kMaxParticles;
+constexpr size_t kOffIdx = kOffKey + sizeof(int32_t) * kMaxParticles;
+constexpr size_t kOffTiles = kOffIdx + sizeof(int32_t) * kMaxParticles;
 constexpr size_t kScratchBytes = kOffTiles + sizeof(int64_t) * (kMaxTiles + 1);
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
@@ -73,7 +75,8 @@ __device__ int block_scan(int v, int *total)
     return r;
 }
 
-// tile-major key of every particle's cell and its slot inside the cell
+// tile-major key of every particle's cell, the count of every key and a provisional place
+// inside the cell (from an atomic; k_nz_rank replaces it by the rank in the input order)
 __global__ void k_nz_count(Geo g, int64_t np, const int32_t *cell, unsigned char *scr)
 {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -152,18 +155,43 @@ __global__ void k_nz_scan(int64_t nt, unsigned char *scr, int64_t *tile_start)
     if (threadIdx.x == 0) tile_start[nt] = carry;
 }
 
-__global__ void k_nz_scatter(Geo g, int64_t np, const unsigned char *scr,
-                             const int64_t *tile_start, int64_t *perm)
+// every particle index at its provisional position of the cell-major order
+__global__ void k_nz_place(Geo g, int64_t np, unsigned char *scr, const int64_t *tile_start)
 {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= np) return;
     const int32_t *first = (const int32_t *)(scr + kOffFirst);
     const int32_t *slot = (const int32_t *)(scr + kOffSlot);
     const int32_t *key = (const int32_t *)(scr + kOffKey);
+    int32_t *idx = (int32_t *)(scr + kOffIdx);
     const int kk = key[p];
     if (kk < 0) return;
-    const int tile = kk / g.TC;
-    perm[tile_start[tile] + first[kk] + slot[p]] = p;
+    idx[tile_start[kk / g.TC] + first[kk] + slot[p]] = (int32_t)p;
+}
+
+// position r of the order: the particle placed there moves to the position of its rank among
+// the particles of its cell in the input order (stable and reproducible); positions past the
+// last tile (as many as particles outside the grid) get -1
+__global__ void k_nz_rank(Geo g, int64_t np, int64_t nt, const unsigned char *scr,
+                          const int64_t *tile_start, int64_t *perm)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= np) return;
+    if (r >= tile_start[nt]) {
+        perm[r] = -1;
+        return;
+    }
+    const int32_t *cnt = (const int32_t *)(scr + kOffCount);
+    const int32_t *first = (const int32_t *)(scr + kOffFirst);
+    const int32_t *key = (const int32_t *)(scr + kOffKey);
+    const int32_t *idx = (const int32_t *)(scr + kOffIdx);
+    const int32_t p = idx[r];
+    const int kk = key[p];
+    const int64_t start = tile_start[kk / g.TC] + first[kk];
+    const int m = cnt[kk];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) rank += (idx[start + j] < p) ? 1 : 0;
+    perm[start + rank] = p;
 }
 
 }  // namespace
@@ -210,6 +238,10 @@ extern "C" int pic_tile_sort_noalloc(const int32_t grid[3], const int32_t tile[3
     if (n > 0) k_nz_count<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, n, cell_dev, s);
     k_nz_tiles<<<(unsigned)ntiles, tb, 0, st>>>(g, s);
     k_nz_scan<<<1, 1024, 0, st>>>(ntiles, s, tile_start_dev);
-    if (n > 0) k_nz_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, n, s, tile_start_dev, perm_dev);
+    if (n > 0) {
+        k_nz_place<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, n, s, tile_start_dev);
+        k_nz_rank<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, n, ntiles, s, tile_start_dev,
+                                                               perm_dev);
+    }
     return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }

@@ -6,9 +6,11 @@ libpic's kernels (pic_step for a run on its own, pic_batch_step for a batch).
 * `Autotuner` picks the particle-tile extent and the sort interval of a run by timing short
   probe runs of the same spline order and particle density and keeping the fastest full step
   (sort cost included).
-* `make_run` builds a run from a request and loads its seeded particles on the device; for a
-  batchable run `fit_batch_tile` keeps the tuned tile only if its shared-memory stage still
-  lets the batched kernel hold two CTAs per SM (a batch runs at the largest stage of its runs).
+* `make_run` builds a run from a request and generates its seeded drifting pair plasma in HBM
+  with the library's device loader (pic_load_drifting_plasma: App. D's flip and boost of
+  Gaussian co-moving momenta); for a batchable run `fit_batch_tile` keeps the tuned tile only
+  if its shared-memory stage still lets the batched kernel hold two CTAs per SM (a batch runs
+  at the largest stage of its runs).
 * `Server` is a continuous-batching request loop: requests (NCI-scan runs: grid, c dt, drift
   gamma, particles per cell) arrive over time, are admitted when the device-memory budget has
   room, stay resident until their last step, and are advanced in chunks of steps -- every 2D
@@ -67,6 +69,27 @@ def _default_interval(dt: float, dim: int) -> int:
     return int(math.floor(2.0 / dt)) + 1 if dim == 2 else 8
 
 
+def species_constants(req: Request, s: int):
+    """(q, m, w, particles per cell, position species) of species s (0 = e-, 1 = e+) of a
+    request's pair plasma.  The weight gives the drifting plasma 16 cells per relativistic skin
+    depth (c / omega_p = 16 dx with dx = 1, as in Table 1): omega_p^2 = n q^2 / (gamma m) with
+    n = (ppc / 2) w / V_c, so w = omega_p^2 gamma V_c / (ppc / 2)."""
+    per = req.ppc // 2
+    omega_p = 1.0 / 16.0
+    w = omega_p * omega_p * req.gamma / per if per > 0 else 0.0
+    return (-1.0 if s == 0 else 1.0, 1.0, w, per, 0 if req.colocated else s)
+
+
+def load_request(run, req: Request, rng_run: Optional[int] = None):
+    """Generate the request's pair plasma in the run's particle stores on the device."""
+    rr = req.rid if req.rng_run < 0 else req.rng_run
+    if rng_run is not None:
+        rr = rng_run
+    for s in range(2):
+        q, m, w, per, pos = species_constants(req, s)
+        run.load_drifting_plasma(s, q, m, w, per, req.gamma, req.u_th, req.seed, rr, pos)
+
+
 class Autotuner:
     """Chooses (tile, sort interval) per (spline order, particles per cell) by timing probe runs.
 
@@ -94,22 +117,22 @@ class Autotuner:
 
     def _tune(self, l: int, ppc: int):
         import torch
-        import workloads
         best = None
-        wl = workloads.pair_plasma(self.probe_grid, (1.0, 1.0), self.probe_dt, l, 1, 20.0, 0.01,
-                                   ppc, device="cuda", seed=12345)
-        caps = [int(s.x.shape[1]) for s in wl.species]
+        probe = Request(rid=0, grid=(self.probe_grid[0], self.probe_grid[1], 1), dt=self.probe_dt,
+                        l=l, gamma=20.0, u_th=0.01, ppc=ppc, steps=0, seed=12345)
+        n = self.probe_grid[0] * self.probe_grid[1] * (ppc // 2)
+        caps = [n, n]
         base_si = _default_interval(self.probe_dt, 2)
         for tile in self.TILES:
             for frac in (1.0, 0.5):
                 si = max(1, int(round(base_si * frac)))
                 try:
-                    run = pic.Run(wl.grid, wl.dx, wl.dt, l, 1, precision=pic.PIC_FP32_MIXED,
-                                  capacity=caps, tile=(tile[0], tile[1], 1), sort_interval=si)
+                    run = pic.Run(probe.grid, (1.0, 1.0), probe.dt, l, 1,
+                                  precision=pic.PIC_FP32_MIXED, capacity=caps,
+                                  tile=(tile[0], tile[1], 1), sort_interval=si)
                 except pic.PicError:
                     continue
-                for i, s in enumerate(wl.species):
-                    run.load(i, s.q, s.m, s.w, s.x, s.u)
+                load_request(run, probe)
                 run.step(2)
                 torch.cuda.synchronize()
                 n = 2 * si
@@ -165,50 +188,54 @@ def fit_batch_tile(req: Request, tile, si):
     return tile, si
 
 
-def make_run(req: Request, precision=None, tuner: Optional[Autotuner] = None,
-             stream=None, device="cuda"):
-    """Create, bind and load one run for a request (seeded drifting pair plasma)."""
-    import workloads
+def request_tile(req: Request, tuner: Optional[Autotuner] = None, precision=None):
+    """(tile, sort interval) a run of this request uses ((None, 0): the library's defaults)."""
     if precision is None:
         precision = req.precision
-    dx = (1.0, 1.0, 1.0)
-    wl = workloads.pair_plasma(req.grid if req.dim == 3 else req.grid[:2], dx[:req.dim], req.dt,
-                               req.l, req.scheme, req.gamma, req.u_th, req.ppc, seed=req.seed,
-                               run=req.rid if req.rng_run < 0 else req.rng_run, device=device,
-                               colocated=req.colocated)
-    tile, si = (None, 0)
     if tuner is not None and req.batchable and precision == pic.PIC_FP32_MIXED:
         tile, si = tuner.choose(req.l, req.ppc, req.dt)
         tile = (min(tile[0], req.grid[0]), min(tile[1], req.grid[1]), 1)
-        tile, si = fit_batch_tile(req, tile, si)
-    caps = [int(s.x.shape[1]) for s in wl.species]
-    run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=precision, capacity=caps,
-                  tile=tile, sort_interval=si, stream=stream, solver=req.solver)
-    for i, s in enumerate(wl.species):
-        run.load(i, s.q, s.m, s.w, s.x, s.u)
-    del wl
+        return fit_batch_tile(req, tile, si)
+    return None, 0
+
+
+def make_run(req: Request, precision=None, tuner: Optional[Autotuner] = None,
+             stream=None, device="cuda"):
+    """Create, bind and load one run for a request: its seeded drifting pair plasma is
+    generated on the device (App. D; load_request)."""
+    if precision is None:
+        precision = req.precision
+    tile, si = request_tile(req, tuner, precision)
+    n = req.grid[0] * req.grid[1] * req.grid[2] * (req.ppc // 2)
+    run = pic.Run(req.grid, (1.0, 1.0, 1.0), req.dt, req.l, req.scheme, precision=precision,
+                  capacity=[n, n], tile=tile, sort_interval=si, stream=stream,
+                  device=device, solver=req.solver)
+    load_request(run, req)
     return run
 
 
-def footprint_estimate(req: Request, precision=None) -> int:
-    """Device bytes a request will hold (libpic's own footprint query, without device work)."""
-    dim = req.dim
+def footprint_estimate(req: Request, precision=None, tuner: Optional[Autotuner] = None) -> int:
+    """Device bytes a request will hold: libpic's own footprint query (no device work) with
+    the tile and sort interval the run will use (the sort scratch depends on the tile)."""
     grid = req.grid
     n = grid[0] * grid[1] * grid[2] * req.ppc // 2
     if precision is None:
         precision = req.precision
+    tile, si = request_tile(req, tuner, precision)
     opt = pic.pic_options()
     opt.precision = precision
     opt.n_species = 2
     opt.capacity[0] = n
     opt.capacity[1] = n
+    opt.solver = req.solver
+    if tile is not None:
+        opt.tile[0], opt.tile[1], opt.tile[2] = tile
+    opt.sort_interval = si
     ctx = pic.pic_create(grid, (1.0, 1.0, 1.0), req.dt, req.l, req.scheme, opt)
     try:
-        b = pic.pic_footprint(ctx)
+        return pic.pic_footprint(ctx)
     finally:
         pic.pic_destroy(ctx)
-    # the seeded FP64 input arrays are created on the device while loading
-    return b + n * 2 * (dim + 3) * 8
 
 
 @dataclass
@@ -297,9 +324,14 @@ class Server:
             torch.cuda.synchronize()
             for a in active.values():
                 a["done"] += k
-                ev = a["req"].record_every
-                if ev > 0 and a["done"] % ev == 0:
-                    self._record(a)
+            recording = [a for a in active.values()
+                         if a["req"].record_every > 0 and a["done"] % a["req"].record_every == 0]
+            # a batched sort swaps a run's particle buffers in the batch's device copy of its
+            # descriptor only: write the batch state back before reading a batched run's state
+            if batch is not None and any(a["req"].rid in batch_ids for a in recording):
+                batch.sync()
+            for a in recording:
+                self._record(a)
             finished = [r for r, a in active.items() if a["done"] >= a["req"].steps]
             if finished:
                 if batch is not None:

@@ -238,15 +238,21 @@ def test_table1_requests_follow_table_1():
 
 
 def test_neutral_start_colocates_species():
-    """colocated=True: positrons at the electrons' positions (rho = 0 at the start), momenta
-    independent; the default keeps independent positions."""
+    """colocated=True: the positrons take the electrons' positions (rho = 0 at the start),
+    momenta independent; the default keeps independent positions.  The engine's request
+    normalisation (the weight of a 16-cells-per-skin-depth plasma) equals the workload's."""
     import workloads
+    from paper_1909_09613_gb300 import engine
     a = workloads.pair_plasma((8, 4), (1.0, 1.0), 0.3, 2, 1, 50.0, 0.1, 4, colocated=True)
-    assert np.array_equal(a.species[0].x.numpy(), a.species[1].x.numpy())
-    assert not np.array_equal(a.species[0].u.numpy(), a.species[1].u.numpy())
     b = workloads.pair_plasma((8, 4), (1.0, 1.0), 0.3, 2, 1, 50.0, 0.1, 4)
-    assert not np.array_equal(b.species[0].x.numpy(), b.species[1].x.numpy())
-    assert np.array_equal(a.species[0].x.numpy(), b.species[0].x.numpy())
+    assert [s.pos_species for s in a.species] == [0, 0]
+    assert [s.pos_species for s in b.species] == [0, 1]
+    for wl, grid in ((b, (8, 4, 1)), (workloads.pair_plasma((6, 5, 4), (1.0,) * 3, 0.3, 2, 1, 20.0,
+                                                              0.01, 8), (6, 5, 4))):
+        req = engine.Request(rid=0, grid=grid, dt=0.3, l=2, gamma=wl.gamma, u_th=wl.u_th,
+                             ppc=wl.ppc, steps=1)
+        for i, s in enumerate(wl.species):
+            assert engine.species_constants(req, i) == (s.q, s.m, s.w, s.per_cell, s.pos_species)
 
 
 def test_fit_batch_tile_without_device_keeps_the_tuned_tile(lib):
@@ -275,3 +281,46 @@ def test_reference_arm_prints_the_contract_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["ms_per_step"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def _c_layout(struct, fields):
+    """offsetof of `fields` and sizeof of `struct` as the C compiler lays out include/pic.h."""
+    import subprocess
+    import tempfile
+    body = "".join('printf("%%zu ", offsetof(%s, %s));' % (struct, f) for f in fields)
+    src = ('#include <stdio.h>\n#include <stddef.h>\n#include "pic.h"\nint main(void){%s'
+           'printf("%%zu\\n", sizeof(%s));return 0;}\n' % (body, struct))
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        return [int(v) for v in subprocess.check_output([exe]).split()]
+
+
+@pytest.mark.parametrize("cls,struct", [(pic.pic_options, "pic_options"), (pic.pic_diag_t, "pic_diag_t")])
+def test_struct_layouts_match_the_header(cls, struct):
+    """The ctypes mirrors of the option and diagnostics structs have the C header's field
+    offsets and size (a field added on one side only would shift every later one)."""
+    names = [f[0] for f in cls._fields_]
+    want = _c_layout(struct, names)
+    got = [getattr(cls, n).offset for n in names] + [ctypes.sizeof(cls)]
+    assert got == want
+
+
+def test_create_validates_deterministic_flag(lib):
+    o = _opt((1000, 1000), pic.PIC_FP32_MIXED)
+    o.deterministic = 2
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_create((256, 128, 1), (1.0, 1.0, 1.0), 0.25, 3, pic.PIC_SCHEME_WT, o)
+    assert e.value.status == pic.PIC_EINVAL
+    # a deterministic FP32 run keeps 64-bit words in its shared current tile: 32 x 8 tiles
+    for det, tile in ((0, (64, 8, 1)), (1, (32, 8, 1))):
+        o.deterministic = det
+        ctx = pic.pic_create((256, 128, 1), (1.0, 1.0, 1.0), 0.25, 3, pic.PIC_SCHEME_WT, o)
+        try:
+            assert pic.pic_tile_info(ctx)[0] == tile
+            own, _, _ = pic.pic_smem_info(ctx)
+            assert own > 0
+        finally:
+            pic.pic_destroy(ctx)

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+import plasma
 import workloads
 
 torch = pytest.importorskip("torch")
@@ -26,12 +27,12 @@ def rel(a, b):
 
 def make(spec, solver=pic.PIC_SOLVER_YEE):
     grid, cdt, l, ppc, gamma, seed = spec
-    wl = workloads.pair_plasma(grid, (1.0, 1.0), cdt, l, 1, gamma, 0.01, ppc, seed=seed)
+    wl = plasma.pair_plasma(grid, (1.0, 1.0), cdt, l, 1, gamma, 0.01, ppc, seed=seed)
     caps = [int(s.x.shape[1]) for s in wl.species]
     run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=pic.PIC_FP32_MIXED, capacity=caps,
                   solver=solver)
     for i, s in enumerate(wl.species):
-        run.load(i, s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
+        run.load(i, s.q, s.m, s.w, s.x, s.u)
     rng = np.random.default_rng(seed)
     f = [0.02 * rng.standard_normal((1, grid[1], grid[0])) for _ in range(6)]
     for c in range(6):

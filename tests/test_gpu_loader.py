@@ -1,15 +1,17 @@
 """The drifting-plasma loaders on the device (pic_load_drifting_plasma and, for Juttner-Synge
-momenta by Sobol's method, pic_load_drifting_juttner; App. D) against the same distribution
-drawn by the seeded input generator and loaded from arrays: the two implement the one
-counter-based generator (SplitMix64) from its published definition, so cells, offsets, the
-accepted Sobol attempts and the flip decisions must agree exactly, and the momenta to the last
-bits of log/cos/sin."""
+momenta by Sobol's method, pic_load_drifting_juttner; App. D) against the FP64 oracle's loader
+(oracle.load_drifting).  Both implement the one counter-based generator (SplitMix64) from its
+published definition, so the cells, the positions, the stable tile order, the accepted Sobol
+attempts and the flip decisions must agree exactly, and the momenta to the last bits of
+log/cos/sin (the FP32 form: to one rounding of the stored FP32 value)."""
 import math
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads
+from test_gpu_parity import host_packed
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -17,67 +19,56 @@ pytestmark = pytest.mark.gpu
 import paper_1909_09613_gb300 as pic  # noqa: E402
 
 CASES = [((48, 20), 2, pic.PIC_FP64, 50.0, 0.01, 6),
-         ((48, 20), 3, pic.PIC_FP32_MIXED, 1000.0, 0.1, 8),
+         ((48, 20), 3, pic.PIC_FP32_MIXED, 1000.0, 0.1, 16),
          ((33, 17), 4, pic.PIC_FP32_MIXED, 20.0, 0.0, 4),
          ((12, 8, 6), 2, pic.PIC_FP64, 10.0, 0.05, 4)]
 
 
-def _pair(run_loader, grid, l, prec, gamma, u_th, ppc, colocated, theta=None):
-    dx = (1.0,) * len(grid)
-    wl = workloads.pair_plasma(grid, dx, 0.3, l, pic.PIC_SCHEME_WT, gamma, u_th, ppc,
-                               device="cuda", seed=77, run=3, colocated=colocated, theta=theta)
-    caps = [int(s.x.shape[1]) for s in wl.species]
-    r = pic.Run(wl.grid, wl.dx, wl.dt, l, pic.PIC_SCHEME_WT, precision=prec, capacity=caps)
+def _device_run(wl, prec):
+    caps = [wl.ncell * s.per_cell for s in wl.species]
+    r = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps)
     for i, s in enumerate(wl.species):
-        if run_loader and theta is not None:
-            r.load_drifting_juttner(i, s.q, s.m, s.w, ppc // 2, gamma, theta, seed=77, run=3,
-                                    pos_species=0 if colocated else i)
-        elif run_loader:
-            r.load_drifting_plasma(i, s.q, s.m, s.w, ppc // 2, gamma, u_th, seed=77, run=3,
-                                   pos_species=0 if colocated else i)
+        if wl.theta > 0.0:
+            r.load_drifting_juttner(i, s.q, s.m, s.w, s.per_cell, wl.gamma, wl.theta,
+                                    seed=wl.seed, run=wl.run, pos_species=s.pos_species)
         else:
-            r.load(i, s.q, s.m, s.w, s.x, s.u)
+            r.load_drifting_plasma(i, s.q, s.m, s.w, s.per_cell, wl.gamma, wl.u_th,
+                                   seed=wl.seed, run=wl.run, pos_species=s.pos_species)
     return r
 
 
-def _same_particles(a, b, prec):
-    for s in range(2):
-        xa, ua, ca = a.particles(s)
-        xb, ub, cb = b.particles(s)
-        assert np.array_equal(ca, cb)          # cells and the tile order: exact
-        # the order of the particles of one cell is not unique: compare per-cell sets
-        ka = np.lexsort(np.vstack([xa, ca[None, :]])[::-1])
-        kb = np.lexsort(np.vstack([xb, cb[None, :]])[::-1])
-        xa, ua, xb, ub = xa[:, ka], ua[:, ka], xb[:, kb], ub[:, kb]
-        assert np.array_equal(xa, xb)          # positions: exact
-        # one rounding of the stored form (an FP32 store may round a last-bit difference of
-        # log/cos either way)
+def _check_against_oracle(r, wl, prec):
+    """Every particle of the device load against the oracle's draw of the same counters, in
+    the oracle's stable tile order."""
+    for i, s in enumerate(wl.species):
+        x, u, failed = oracle.load_drifting(wl.grid, wl.dx, s.per_cell, wl.gamma, wl.u_th,
+                                            wl.theta, wl.seed, wl.run, i, s.pos_species)
+        assert failed == 0
+        cells, xp, up = host_packed(x, u, wl.grid, wl.dx, wl.dim, prec)
+        perm, ts = oracle.tile_sort(wl.grid, r.tile, cells,
+                                    oracle.SLOT_MAJOR if r.slot_major else oracle.CELL_MAJOR)
+        xg, ug, cg = r.particles(i)
+        assert np.array_equal(cg, cells[perm])               # cells and the stable order: exact
+        assert np.array_equal(r.tile_offsets(i), ts)
+        assert np.array_equal(xg, xp[:, perm])              # positions: exact
+        # momenta: log/cos/sin may differ in the last bit between the two math libraries; the
+        # FP32 store may round such a difference either way
         tol = 4e-16 if prec == pic.PIC_FP64 else 1.2e-7
-        assert np.max(np.abs(ua - ub)) <= tol * max(1.0, np.max(np.abs(ub)))
+        assert np.max(np.abs(ug - up[:, perm])) <= tol * max(1.0, np.max(np.abs(up)))
+    return r
 
 
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("colocated", [False, True])
-def test_device_loader_matches_generator(case, colocated):
+def test_device_loader_matches_oracle(case, colocated):
     grid, l, prec, gamma, u_th, ppc = case
-    a = _pair(True, grid, l, prec, gamma, u_th, ppc, colocated)
-    b = _pair(False, grid, l, prec, gamma, u_th, ppc, colocated)
-    _same_particles(a, b, prec)
-    a.step(3)
-    b.step(3)
-    # same particle sets; the summation order of the current (order within a cell) is not
-    # unique, so the fields agree to the rounding of the form's current accumulation.  (With
-    # the neutral start the net fields are the small difference of the species' currents, and
-    # comparing them measures that cancellation, not the loader.)
-    if not colocated:
-        ftol = 1e-12 if prec == pic.PIC_FP64 else 2e-6
-        for c in range(9):
-            fa, fb = a.field(c), b.field(c)
-            den = max(np.max(np.abs(fb)), 1e-300)
-            assert np.max(np.abs(fa - fb)) / den < ftol
-    assert a.diag()["error_flags"] == 0
-    a.close()
-    b.close()
+    wl = workloads.pair_plasma(grid, (1.0,) * len(grid), 0.3, l, pic.PIC_SCHEME_WT, gamma, u_th,
+                               ppc, seed=77, run=3, colocated=colocated)
+    r = _device_run(wl, prec)
+    _check_against_oracle(r, wl, prec)
+    r.step(2)
+    assert r.diag()["error_flags"] == 0
+    r.close()
 
 
 def test_device_loader_moments_and_cold_beam():
@@ -121,11 +112,12 @@ JCASES = [((48, 20), 2, pic.PIC_FP64, 50.0, 0.3, 6),
 
 
 @pytest.mark.parametrize("case", JCASES)
-def test_device_juttner_loader_matches_generator(case):
+def test_device_juttner_loader_matches_oracle(case):
     grid, l, prec, gamma, theta, ppc = case
-    a = _pair(True, grid, l, prec, gamma, 0.0, ppc, False, theta)
-    b = _pair(False, grid, l, prec, gamma, 0.0, ppc, False, theta)
-    _same_particles(a, b, prec)
+    wl = workloads.pair_plasma(grid, (1.0,) * len(grid), 0.3, l, pic.PIC_SCHEME_WT, gamma, 0.0,
+                               ppc, seed=77, run=3, theta=theta)
+    a = _device_run(wl, prec)
+    _check_against_oracle(a, wl, prec)
     # at gamma = 1 (no boost, no flip) the loaded |u| is the Sobol speed itself: mean gamma of
     # the Juttner-Synge distribution is 3 theta + K1(1/theta) / K2(1/theta)
     if gamma == 1.0:
@@ -134,15 +126,22 @@ def test_device_juttner_loader_matches_generator(case):
         g = np.sqrt(1.0 + np.sum(u * u, axis=0))
         expect = 3.0 * theta + kve(1, 1.0 / theta) / kve(2, 1.0 / theta)
         assert abs(g.mean() - expect) < 5.0 * g.std() / math.sqrt(g.size)
-    a.step(3)
-    b.step(3)
-    ftol = 1e-12 if prec == pic.PIC_FP64 else 2e-6
-    for c in range(9):
-        fa, fb = a.field(c), b.field(c)
-        den = max(np.max(np.abs(fb)), 1e-300)
-        assert np.max(np.abs(fa - fb)) / den < ftol
+    a.step(2)
     assert a.diag()["error_flags"] == 0
     with pytest.raises(pic.PicError):   # below the temperature the bounded sampler supports
         a.load_drifting_juttner(0, -1.0, 1.0, 1e-3, 1, gamma, 0.2, seed=5)
     a.close()
-    b.close()
+
+
+def test_engine_requests_load_on_the_device():
+    """The served and batched forms generate every request's plasma with the device loader:
+    a request's run holds the oracle's draw of the same streams."""
+    from paper_1909_09613_gb300 import engine
+    req = engine.Request(rid=5, grid=(40, 24, 1), dt=0.3, l=3, gamma=30.0, u_th=0.01, ppc=16,
+                         steps=1, seed=99)
+    r = engine.make_run(req)
+    wl = workloads.pair_plasma((40, 24), (1.0, 1.0), 0.3, 3, 1, 30.0, 0.01, 16, seed=99, run=5)
+    for i, s in enumerate(wl.species):
+        assert engine.species_constants(req, i) == (s.q, s.m, s.w, s.per_cell, s.pos_species)
+    _check_against_oracle(r, wl, req.precision)
+    r.close()

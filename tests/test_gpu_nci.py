@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-import workloads
+import plasma
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,7 +47,7 @@ def gpu_history(wl, prec, nsteps, every):
 def oracle_history(wl, nsteps, every):
     o = oracle.Sim(wl.grid[:2], wl.dx[:2], wl.dt, wl.l, wl.scheme)
     for s in wl.species:
-        o.add_species(s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
+        o.add_species(s.q, s.m, s.w, s.x, s.u)
     ts, us = [], []
     for k in range(0, nsteps, every):
         o.step(every)
@@ -61,7 +61,7 @@ def test_nci_growth_gpu_fp64_vs_oracle_small_config():
     """64x32, quadratic, cold pair plasma at gamma 20, c dt = 0.35, 200 steps, WT and MC."""
     rates = {}
     for scheme in (pic.PIC_SCHEME_MC, pic.PIC_SCHEME_WT):
-        wl = workloads.config_small(scheme=scheme)
+        wl = plasma.config_small(scheme=scheme)
         tg, ug = gpu_history(wl, pic.PIC_FP64, wl.steps, 5)
         to, uo = oracle_history(wl, wl.steps, 5)
         rates[scheme] = (growth_rate(tg, ug), growth_rate(to, uo))
@@ -79,7 +79,7 @@ def test_nci_growth_fp32_vs_fp64():
     500 steps."""
     res = {}
     for scheme in (pic.PIC_SCHEME_MC, pic.PIC_SCHEME_WT):
-        wl = workloads.config_large(scheme=scheme, device="cuda", scale=8)
+        wl = plasma.config_large(scheme=scheme, scale=8)
         t64, u64 = gpu_history(wl, pic.PIC_FP64, 500, 10)
         t32, u32 = gpu_history(wl, pic.PIC_FP32_MIXED, 500, 10)
         res[scheme] = (growth_rate(t32, u32), growth_rate(t64, u64))
@@ -96,7 +96,7 @@ def test_precision_form_error_growth_steps_1_10_100():
     fields after 1, 10 and 100 steps (max |FP32 - FP64| / max |FP64| per component, worst
     component).  Step 1 is the parity bar (2e-6); later steps show how the FP32 rounding of
     the particle state grows (measured on a GB300: 1.6e-6, 1.7e-6, 3.8e-6)."""
-    wl = workloads.config_large(scheme=pic.PIC_SCHEME_WT, device="cuda", scale=8)
+    wl = plasma.config_large(scheme=pic.PIC_SCHEME_WT, scale=8)
     caps = [int(s.x.shape[1]) for s in wl.species]
     runs = {}
     for prec in (pic.PIC_FP64, pic.PIC_FP32_MIXED):

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-import workloads
+import plasma
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -56,20 +56,55 @@ def smooth_fields(shape, amp, seed):
     return out
 
 
+def host_packed(x, u, grid, dx, dim, prec):
+    """The particle state a load stores, computed on the host from the input arrays: the cell
+    of every particle and, for the FP32 form, the positions and momenta rounded as stored (an
+    in-cell offset that rounds to 1.0 in FP32 carries into the next cell, decided in FP32 as
+    the packing kernel does).  Returns (cells, x, u) in physical FP64 units."""
+    x = np.array(x, dtype=np.float64)
+    u = np.array(u, dtype=np.float64)
+    cells = np.zeros(x.shape[1], dtype=np.int64)
+    stride = 1
+    for a in range(dim):
+        xi = x[a] / dx[a]
+        n = float(grid[a])
+        xi = np.where(xi >= n, xi - n, xi)
+        xi = np.where(xi < 0.0, xi + n, xi)
+        c = np.floor(xi)
+        if prec == pic.PIC_FP32_MIXED:
+            off = (xi - c).astype(np.float32)
+            carry = off >= np.float32(1.0)
+            off = np.where(carry, np.float32(0.0), off)
+            c = c + carry
+            c = np.where(c >= n, c - n, c)
+            x[a] = (c + off.astype(np.float64)) * dx[a]
+        cells += c.astype(np.int64) * stride
+        stride *= grid[a]
+    if prec == pic.PIC_FP32_MIXED:
+        u = u.astype(np.float32).astype(np.float64)
+    return cells, x, u
+
+
 def make_pair(wl, prec, fields=None, tile=None, sort_interval=0, solver=0):
-    """Same initial state on the GPU (libpic) and in the oracle.  The GPU's load packs and sorts
-    the particles; the oracle is then given the GPU's read-back (sorted, and in the FP32 form
-    already rounded) so both start from identical particle arrays in identical order."""
+    """Same initial state on the GPU (libpic) and in the oracle, both from the input arrays:
+    the GPU loads them (packing and tile-sorting), the oracle takes them in input order as the
+    load stores them (the FP32 rounding done on the host).  run.orc_perm[s] is the oracle's
+    stable tile order of species s (oracle.tile_sort of the packed cells): the GPU particle at
+    sorted position k is the oracle's particle orc_perm[s][k]."""
     caps = [int(s.x.shape[1]) for s in wl.species]
     run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps,
                   tile=tile, sort_interval=sort_interval, solver=solver)
     for i, s in enumerate(wl.species):
-        run.load(i, s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
+        run.load(i, s.q, s.m, s.w, s.x, s.u)
     dim = wl.dim
     orc = oracle.Sim(wl.grid[:dim], wl.dx[:dim], wl.dt, wl.l, wl.scheme, solver=solver)
+    run.orc_perm = []
     for i, s in enumerate(wl.species):
-        x, u, _ = run.particles(i)
+        cells, x, u = host_packed(s.x, s.u, wl.grid, wl.dx, dim, prec)
         orc.add_species(s.q, s.m, s.w, x, u)
+        perm, _ = oracle.tile_sort(wl.grid, run.tile, cells,
+                                   oracle.SLOT_MAJOR if run.slot_major else oracle.CELL_MAJOR)
+        run.orc_perm.append(perm)
     if fields is not None:
         for c, f in enumerate(fields):
             run.set_field(c, f)
@@ -78,12 +113,16 @@ def make_pair(wl, prec, fields=None, tile=None, sort_interval=0, solver=0):
 
 
 def compare_state(run, orc, nsp, tol, what=""):
+    """Fields element by element; particles position by position, the GPU's sorted position k
+    against the oracle's particle run.orc_perm[s][k] (one step after make_pair: no re-sort)."""
     errs = {}
     for c in range(9):
         errs["F%d" % c] = rel(run.field(c), orc.field(c))
     for s in range(nsp):
         xg, ug, _ = run.particles(s)
         xo, uo = orc.particles(s)
+        perm = run.orc_perm[s]
+        xo, uo = xo[:, perm], uo[:, perm]
         errs["u%d" % s] = rel(ug, uo)
         L = np.array([orc.grid[a] * orc.dx[a] for a in range(orc.dim)]).reshape(-1, 1)
         d = xg - xo
@@ -111,7 +150,7 @@ CASES_2D = [
 @pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
 def test_one_step_2d(case, prec):
     grid, dx, cdt, l, scheme, gamma, uth, ppc = case
-    wl = workloads.pair_plasma(grid, dx, cdt, l, scheme, gamma, uth, ppc, omega_p=0.2, seed=11)
+    wl = plasma.pair_plasma(grid, dx, cdt, l, scheme, gamma, uth, ppc, omega_p=0.2, seed=11)
     f = smooth_fields((1, grid[1], grid[0]), 0.05, seed=5)
     run, orc = make_pair(wl, prec, f)
     run.step(1)
@@ -126,13 +165,53 @@ def test_one_step_2d(case, prec):
                          ids=lambda c: "g%dx%dx%d_l%d_s%d" % (c[0] + (c[2], c[3])))
 def test_one_step_3d(case, prec):
     grid, cdt, l, scheme = case
-    wl = workloads.pair_plasma(grid, (1.0, 1.0, 1.0), cdt, l, scheme, 4.0, 0.1, 4, omega_p=0.2,
+    wl = plasma.pair_plasma(grid, (1.0, 1.0, 1.0), cdt, l, scheme, 4.0, 0.1, 4, omega_p=0.2,
                                seed=3)
     f = smooth_fields((grid[2], grid[1], grid[0]), 0.05, seed=9)
     run, orc = make_pair(wl, prec, f)
     run.step(1)
     orc.step(1)
     compare_state(run, orc, 2, FP64_TOL if prec == pic.PIC_FP64 else FP32_TOL, case)
+    run.close()
+
+
+def random_position_plasma(grid, l, per, gamma, u_th, seed, cdt=0.25):
+    """Pair plasma with positions uniform over the whole grid (Poisson cell counts, so the
+    warps of the cell-major order straddle cells and tile rows), momenta from the oracle's
+    App. D loader, plasma frequency of 16 cells per skin depth."""
+    wl = plasma.pair_plasma(grid, (1.0, 1.0), cdt, l, 1, gamma, u_th, 2 * per, seed=seed)
+    rng = np.random.default_rng(seed)
+    for s in wl.species:
+        n = s.x.shape[1]
+        s.x = rng.uniform(0, 1, (2, n)) * np.array(grid, dtype=float)[:, None]
+    return wl
+
+
+TIMED_CASES = {
+    # the large configuration on a 256x128 section: 32 per species in every cell, so every warp
+    # of the cell-major order holds the 32 particles of one cell
+    "config2_section_l3_ppc64": lambda: plasma.config_large(scale=8),
+    # Poisson cell counts on a ragged grid (200 = 3 x 64 + 8): warps straddle cells and rows
+    "l3_16_per_species_ragged": lambda: random_position_plasma((200, 72), 3, 16, 50.0, 0.01, 7),
+    "l3_8_per_species": lambda: random_position_plasma((128, 64), 3, 8, 50.0, 0.01, 8),
+    "l4_12_per_species": lambda: random_position_plasma((150, 40), 4, 12, 50.0, 0.01, 9),
+}
+
+
+@pytest.mark.parametrize("name", list(TIMED_CASES))
+def test_one_step_timed_configuration_fp32(name):
+    """The precision form in the configuration the benchmark times (FP32, cubic or quartic WT,
+    c dt = 0.25, gamma 50, u_th = 0.01, cell-major warp-summed deposit, default 64x8 tiles):
+    one step from the same state, J1..J3, E, B and every particle against the oracle at 2e-6."""
+    wl = TIMED_CASES[name]()
+    shape = (1, wl.grid[1], wl.grid[0])
+    f = smooth_fields(shape, 0.02, seed=12)
+    run, orc = make_pair(wl, pic.PIC_FP32_MIXED, f)
+    assert run.slot_major == 0 and tuple(run.tile) == (64, 8, 1)
+    run.step(1)
+    orc.step(1)
+    compare_state(run, orc, 2, FP32_TOL, name)
+    assert run.diag()["error_flags"] == 0
     run.close()
 
 
@@ -144,7 +223,7 @@ def test_one_step_m4_solver(case, prec):
     """The M4 Faraday stencil (App. C) on the GPU against the oracle, one step from the same
     state, and a few more steps (fields only) in FP64."""
     grid, dx, cdt = case
-    wl = workloads.pair_plasma(grid, dx, cdt, 3, 1, 4.0, 0.05, 4, omega_p=0.2, seed=13)
+    wl = plasma.pair_plasma(grid, dx, cdt, 3, 1, 4.0, 0.05, 4, omega_p=0.2, seed=13)
     shape = (grid[2] if len(grid) == 3 else 1, grid[1], grid[0])
     f = smooth_fields(shape, 0.05, seed=8)
     run, orc = make_pair(wl, prec, f, solver=pic.PIC_SOLVER_M4)
@@ -162,8 +241,8 @@ def test_one_step_m4_solver(case, prec):
 def test_multi_step_across_sorts_fp64():
     """20 steps at c dt = 0.35 (sort every 6 steps): fields and diagnostics stay at round-off
     from the oracle."""
-    wl = workloads.config_small(scheme=1)
-    wl2 = workloads.pair_plasma(wl.grid, wl.dx, wl.dt, wl.l, 1, 20.0, 0.01, 4,
+    wl = plasma.config_small(scheme=1)
+    wl2 = plasma.pair_plasma(wl.grid, wl.dx, wl.dt, wl.l, 1, 20.0, 0.01, 4,
                                 omega_p=wl.omega_p)
     run, orc = make_pair(wl2, pic.PIC_FP64)
     assert run.sort_interval < 20
@@ -191,7 +270,7 @@ def test_weight_cache_follows_sorts_and_reloads_fp64(l):
     step's Esirkepov deposit (l <= 3).  Every re-ordering must invalidate them: 16 steps with the
     automatic sort every 4 steps, an explicit sort after step 5 and a reload of one species
     (re-packed and re-sorted) after step 9, against the oracle."""
-    wl = workloads.pair_plasma((40, 24), (1.0, 1.0), 0.3, l, pic.PIC_SCHEME_WT, 5.0, 0.05, 6)
+    wl = plasma.pair_plasma((40, 24), (1.0, 1.0), 0.3, l, pic.PIC_SCHEME_WT, 5.0, 0.05, 6)
     run, orc = make_pair(wl, pic.PIC_FP64, sort_interval=4)
     run.step(5)
     orc.step(5)
@@ -216,54 +295,127 @@ def test_weight_cache_follows_sorts_and_reloads_fp64(l):
     run.close()
 
 
+TAG_SCALE = 2.0 ** -12  # (i + 1) * TAG_SCALE is exact in FP32 for i + 1 < 2^24
+
+
+def tagged_momenta(u):
+    """u with u_z replaced by a tag that identifies particle i exactly in both forms."""
+    u = np.array(u, dtype=np.float64)
+    u[2] = (np.arange(u.shape[1]) + 1) * TAG_SCALE
+    return u
+
+
+def read_tags(uz):
+    t = np.rint(np.asarray(uz) / TAG_SCALE).astype(np.int64) - 1
+    assert np.array_equal((t + 1) * TAG_SCALE, uz)
+    return t
+
+
+def packed_cells(x, grid, dx, dim, prec):
+    """Linear cell of every particle as the load computes it (FP32 form: an offset that rounds
+    to 1.0 in FP32 carries into the next cell, decided in FP32 as the packing kernel does)."""
+    cells = np.zeros(x.shape[1], dtype=np.int64)
+    stride = 1
+    for a in range(dim):
+        xi = x[a] / dx[a]
+        c = np.floor(xi)
+        if prec == pic.PIC_FP32_MIXED:
+            off = (xi - c).astype(np.float32)
+            c = c.astype(np.int64) + (off >= np.float32(1.0))
+            c = np.where(c >= grid[a], c - grid[a], c)
+        cells += c.astype(np.int64) * stride
+        stride *= grid[a]
+    return cells
+
+
 @pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("ppc", [6, 16], ids=["ppc6", "ppc16"])
 @pytest.mark.parametrize("grid,tile", [((64, 32, 1), None), ((37, 21, 1), (8, 4, 1)),
                                        ((12, 10, 8), None), ((5, 3, 1), None)])
-def test_tile_sort_bit_exact(prec, grid, tile):
-    """Cell at every sorted position and the tile offsets equal the oracle's order; the
-    particles of every cell are the same set."""
-    g = tuple(g for g in grid if True)
-    wl = workloads.pair_plasma(g if g[2] > 1 else g[:2], (1.0,) * (3 if g[2] > 1 else 2), 0.3, 2, 1,
-                               3.0, 0.1, 6, omega_p=0.2, seed=21)
+def test_tile_sort_bit_exact(prec, ppc, grid, tile):
+    """The sort is stable and reproducible: the permutation a load applies equals the oracle's
+    (tile, cell, input index) order -- or (tile, rank in cell, cell) for the slot-major order --
+    bit for bit, and so do the cell at every position and the tile offsets."""
+    g = tuple(grid)
+    dim = 3 if g[2] > 1 else 2
+    wl = plasma.pair_plasma(g if dim == 3 else g[:2], (1.0,) * dim, 0.3, 2, 1, 3.0, 0.1, ppc,
+                               omega_p=0.2, seed=21)
     caps = [int(s.x.shape[1]) for s in wl.species]
     run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps, tile=tile)
+    if prec == pic.PIC_FP32_MIXED:
+        assert run.slot_major == (0 if ppc // 2 >= 6 else 1)
+    us = [tagged_momenta(s.u) for s in wl.species]
     for i, s in enumerate(wl.species):
-        run.load(i, s.q, s.m, s.w, s.x.numpy(), s.u.numpy())
+        run.load(i, s.q, s.m, s.w, s.x, us[i])
     for i, s in enumerate(wl.species):
-        x0 = s.x.numpy()
-        cells_in = np.zeros(x0.shape[1], dtype=np.int64)
-        stride = 1
-        for a in range(wl.dim):
-            cells_in += np.floor(x0[a] / wl.dx[a]).astype(np.int64) * stride
-            stride *= wl.grid[a]
-        if prec == pic.PIC_FP32_MIXED:
-            # the FP32 form stores float(offset); an offset that rounds to 1.0 carries into
-            # the next cell (decided in FP32, as the packing kernel does)
-            cells_in = np.zeros(x0.shape[1], dtype=np.int64)
-            stride = 1
-            for a in range(wl.dim):
-                xi = x0[a] / wl.dx[a]
-                c = np.floor(xi)
-                off = (xi - c).astype(np.float32)
-                c = c.astype(np.int64) + (off >= np.float32(1.0))
-                c = np.where(c >= wl.grid[a], c - wl.grid[a], c)
-                cells_in += c * stride
-                stride *= wl.grid[a]
+        x0 = s.x
+        cells_in = packed_cells(x0, wl.grid, wl.dx, wl.dim, prec)
         perm, ts = oracle.tile_sort(wl.grid, run.tile, cells_in,
                                     oracle.SLOT_MAJOR if run.slot_major else oracle.CELL_MAJOR)
         xg, ug, cg = run.particles(i)
+        assert np.array_equal(read_tags(ug[2]), perm)
         assert np.array_equal(cg, cells_in[perm])
         assert np.array_equal(run.tile_offsets(i), ts)
-        # same particles in every cell (FP32 form: compare the packed values)
-        if prec == pic.PIC_FP64:
-            a = np.lexsort(np.vstack([x0, s.u.numpy()])[::-1])
-            b = np.lexsort(np.vstack([xg, ug])[::-1])
-            assert np.array_equal(np.vstack([x0, s.u.numpy()])[:, a], np.vstack([xg, ug])[:, b])
+        if prec == pic.PIC_FP64:  # the packed FP64 position is x / dx exactly
+            assert np.array_equal(xg, x0[:, perm])
+            assert np.array_equal(ug[:2], us[i][:2, perm])
     run.close()
 
 
+@pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("ppc", [4, 20], ids=["ppc4", "ppc20"])
+def test_tile_sort_stable_after_steps(prec, ppc):
+    """A re-sort after particles moved keeps the previous order inside every cell: neutral
+    particles (q = 0: no force, no current) drift for three steps, then pic_sort must apply the
+    oracle's stable order of the cells they reached, permutation included, on a ragged grid."""
+    grid, dt = (45, 27), 0.3
+    wl = plasma.pair_plasma(grid, (1.0, 1.0), dt, 3, 1, 3.0, 0.3, ppc, omega_p=0.2, seed=4)
+    caps = [int(s.x.shape[1]) for s in wl.species]
+    run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps,
+                  tile=(16, 8, 1), sort_interval=4)
+    for i, s in enumerate(wl.species):
+        run.load(i, 0.0, 1.0, s.w, s.x, tagged_momenta(s.u))
+    run.step(3)
+    before = [run.particles(i) for i in range(2)]
+    run.sort()
+    for i in range(2):
+        xb, ub, cb = before[i]
+        perm, ts = oracle.tile_sort(wl.grid, run.tile, cb,
+                                    oracle.SLOT_MAJOR if run.slot_major else oracle.CELL_MAJOR)
+        xa, ua, ca = run.particles(i)
+        assert np.array_equal(read_tags(ua[2]), read_tags(ub[2])[perm])
+        assert np.array_equal(ca, cb[perm])
+        assert np.array_equal(xa, xb[:, perm])
+        assert np.array_equal(run.tile_offsets(i), ts)
+    assert run.diag()["error_flags"] == 0
+    run.close()
+
+
+def test_tile_sort_one_crowded_cell():
+    """Degenerate occupancy: every particle of a species in one cell (the rank stage scans the
+    whole cell), the other species spread; the order is still the oracle's, bit for bit."""
+    grid = (24, 16)
+    n = 3000
+    rng = np.random.default_rng(8)
+    x0 = np.vstack([5.0 + rng.uniform(0, 1, n), 7.0 + rng.uniform(0, 1, n)])
+    x1 = rng.uniform(0, 1, (2, n)) * np.array(grid, dtype=float)[:, None]
+    u = tagged_momenta(rng.normal(0, 0.1, (3, n)))
+    for prec in (pic.PIC_FP64, pic.PIC_FP32_MIXED):
+        run = pic.Run(grid, (1.0, 1.0), 0.3, 2, 1, precision=prec, capacity=(n, n))
+        run.load(0, -1.0, 1.0, 0.1, x0, u)
+        run.load(1, 1.0, 1.0, 0.1, x1, u)
+        for i, x in enumerate((x0, x1)):
+            cells = packed_cells(x, (24, 16), (1.0, 1.0), 2, prec)
+            perm, ts = oracle.tile_sort((24, 16), run.tile, cells,
+                                        oracle.SLOT_MAJOR if run.slot_major else oracle.CELL_MAJOR)
+            _, ug, cg = run.particles(i)
+            assert np.array_equal(read_tags(ug[2]), perm)
+            assert np.array_equal(run.tile_offsets(i), ts)
+        run.close()
+
+
 def test_gauss_law_conserved_gpu_fp64():
-    wl = workloads.pair_plasma((48, 24), (1.0, 1.0), 0.3, 3, 1, 5.0, 0.05, 8, omega_p=0.3)
+    wl = plasma.pair_plasma((48, 24), (1.0, 1.0), 0.3, 3, 1, 5.0, 0.05, 8, omega_p=0.3)
     run, orc = make_pair(wl, pic.PIC_FP64)
     d0 = run.diag()
     run.step(60)
@@ -391,7 +543,7 @@ def test_wt_equals_mc_at_half_step_gpu():
     """c dt = dx/2: the WT tables reduce to W_l, so WT and MC steps agree (Sec. 2)."""
     outs = []
     for scheme in (0, 1):
-        wl = workloads.pair_plasma((32, 16), (1.0, 1.0), 0.5, 3, scheme, 4.0, 0.05, 4, omega_p=0.4)
+        wl = plasma.pair_plasma((32, 16), (1.0, 1.0), 0.5, 3, scheme, 4.0, 0.05, 4, omega_p=0.4)
         f = smooth_fields((1, 16, 32), 0.05, seed=1)
         run, orc = make_pair(wl, pic.PIC_FP64, f)
         run.step(3)

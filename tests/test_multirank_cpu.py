@@ -24,7 +24,9 @@ def _rank_main(rank, world, port, out):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
+    sys.path.insert(0, os.path.join(root, "tests"))
     import bench
+    import plasma
     import workloads
     dist.init_process_group("gloo", rank=rank, world_size=world)
     r, w, loc = bench._rank_env()
@@ -33,8 +35,9 @@ def _rank_main(rank, world, port, out):
     bench._barrier(True)
     ms_max = bench._max_over_ranks(ms, True)
     # the replica workloads differ (seed + rank) but have the same shape
-    wl = workloads.config_large(scheme=1, device="cpu", seed=workloads.BASE_SEED + rank, scale=64)
-    x0 = wl.species[0].x[:, :8].clone()
+    wl = plasma.fill(workloads.config_large(scheme=1, seed=workloads.BASE_SEED + rank, scale=64),
+                     count=8)
+    x0 = torch.from_numpy(wl.species[0].x[:, :8].copy())
     gathered = [torch.zeros_like(x0) for _ in range(world)]
     dist.all_gather(gathered, x0)
     n = wl.n_particles

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import MC, WT
+from oracle import MC, WT, Sim
 
 RNG = np.random.default_rng(1909096130)
 
@@ -486,11 +486,11 @@ def test_m4_phase_error_is_fourth_order():
 def test_gauss_law_conserved_over_run(solver):
     """The charge-conserving deposit keeps D.E - rho unchanged (App. B, Eq. gauss); the M4
     solver modifies only Faraday's stencil, so this still holds (Sec. 3)."""
-    import workloads
-    wl = workloads.pair_plasma((16, 8), (1.0, 1.0), 0.3, 3, WT, 5.0, 0.05, 4, omega_p=0.3)
+    import plasma
+    wl = plasma.pair_plasma((16, 8), (1.0, 1.0), 0.3, 3, WT, 5.0, 0.05, 4, omega_p=0.3)
     s = oracle.Sim(wl.grid[:2], wl.dx[:2], wl.dt, wl.l, WT, solver=solver)
     for sp in wl.species:
-        s.add_species(sp.q, sp.m, sp.w, sp.x.numpy(), sp.u.numpy())
+        s.add_species(sp.q, sp.m, sp.w, sp.x, sp.u)
     r0 = s.gauss_residual()
     s.step(200)
     r1 = s.gauss_residual()
@@ -501,13 +501,13 @@ def test_gauss_law_conserved_over_run(solver):
 
 def test_wt_equals_mc_at_half_step_full_run():
     """c dt = dx/2 with equal dx: the WT step is the MC step (Sec. 2)."""
-    import workloads
+    import plasma
     outs = []
     for scheme in (MC, WT):
-        wl = workloads.pair_plasma((16, 8), (1.0, 1.0), 0.5, 3, scheme, 4.0, 0.05, 4, omega_p=0.4)
+        wl = plasma.pair_plasma((16, 8), (1.0, 1.0), 0.5, 3, scheme, 4.0, 0.05, 4, omega_p=0.4)
         s = oracle.Sim(wl.grid[:2], wl.dx[:2], wl.dt, wl.l, scheme)
         for sp in wl.species:
-            s.add_species(sp.q, sp.m, sp.w, sp.x.numpy(), sp.u.numpy())
+            s.add_species(sp.q, sp.m, sp.w, sp.x, sp.u)
         s.step(8)
         outs.append((s.field(0), s.field(5), s.particles(0)[1]))
     for a, b in zip(*outs):
@@ -559,10 +559,10 @@ def test_tile_sort_order_brute_force(grid, tile, order):
 def test_loader_drift_moment():
     """<u_x> = gamma beta (<E'> + <u'_x^2 / E'>) for a drifting Maxwellian loaded with the
     App. D flip; without the volume-transform weight it would be gamma beta <E'>."""
-    import workloads
     gamma, uth = 2.0, 0.1
-    wl = workloads.pair_plasma((64, 64), (1.0, 1.0), 0.3, 2, WT, gamma, uth, 2 * 256)
-    ux = wl.species[0].u[0].numpy()
+    _, u, failed = oracle.load_drifting((64, 64), (1.0, 1.0), 256, gamma, uth, seed=3)
+    assert failed == 0
+    ux = u[0]
     beta = math.sqrt(1 - 1 / gamma ** 2)
     # co-moving moments by radial quadrature of the isotropic Gaussian
     r = np.linspace(0, 12 * uth, 200001)
@@ -575,6 +575,32 @@ def test_loader_drift_moment():
     err = ux.std() / math.sqrt(len(ux))
     assert abs(ux.mean() - expect) < 5 * err
     assert abs(no_flip - expect) > 20 * err
+    # the transverse components are the co-moving Gaussian itself (untouched by the boost)
+    assert abs(u[1].std() / uth - 1.0) < 0.01 and abs(u[2].mean()) < 5 * uth / math.sqrt(len(ux))
+
+
+def test_loader_positions_cold_beam_and_colocation():
+    """Particle p sits in cell p / per_cell (x fastest) at an offset in [0, 1); u_th = 0 gives the
+    cold beam u = (sqrt(gamma^2 - 1), 0, 0) exactly; a species loaded on another's positions
+    (pos_species) shares them exactly while its momenta are its own; a sub-range of particles
+    equals the same slice of a whole load (counter-based streams)."""
+    grid, per, gamma = (12, 5), 3, 7.0
+    x, u, _ = oracle.load_drifting(grid, (0.5, 2.0), per, gamma, 0.0, seed=9, species=1)
+    p = np.arange(grid[0] * grid[1] * per)
+    cell = p // per
+    ci = np.vstack([cell % grid[0], cell // grid[0]]).astype(np.float64)
+    off = x / np.array([[0.5], [2.0]]) - ci
+    assert np.all(off >= 0.0) and np.all(off < 1.0)
+    assert np.all(u[0] == math.sqrt(gamma * gamma - 1.0)) and np.all(u[1:] == 0.0)
+    xa, ua, _ = oracle.load_drifting(grid, (1.0, 1.0), per, gamma, 0.05, seed=9, species=0)
+    xb, ub, _ = oracle.load_drifting(grid, (1.0, 1.0), per, gamma, 0.05, seed=9, species=1,
+                                     pos_species=0)
+    xc, _, _ = oracle.load_drifting(grid, (1.0, 1.0), per, gamma, 0.05, seed=9, species=1)
+    assert np.array_equal(xa, xb) and not np.array_equal(xa, xc)
+    assert not np.array_equal(ua, ub)
+    xs, us, _ = oracle.load_drifting(grid, (1.0, 1.0), per, gamma, 0.05, seed=9, species=0,
+                                     first=17, count=40)
+    assert np.array_equal(xs, xa[:, 17:57]) and np.array_equal(us, ua[:, 17:57])
 
 
 # ------------------------------------------------------------------------------------------
@@ -722,17 +748,14 @@ def test_push_particle_in_uniform_fields(grid, dx, scheme):
 
 @pytest.mark.parametrize("theta", [0.3, 1.0, 4.0])
 def test_juttner_loader_matches_the_distribution(theta):
-    """App. D, Eq. Maxwell-dist-relativistic, sampled with Sobol's method by the seeded input
-    generator: the co-moving |u| follows f(u) ~ u^2 exp(-sqrt(1 + u^2)/theta) (CDF at five
-    sample quantiles against numerical integration), the mean Lorentz factor is the closed form
+    """App. D, Eq. Maxwell-dist-relativistic, sampled with Sobol's method by the oracle: the
+    co-moving |u| follows f(u) ~ u^2 exp(-sqrt(1 + u^2)/theta) (CDF at five sample quantiles
+    against numerical integration), the mean Lorentz factor is the closed form
     3 theta + K1(1/theta)/K2(1/theta), and the directions are isotropic."""
-    import torch
-    import workloads
     from scipy import integrate
     from scipy.special import kn
     n = 400000
-    keys = [workloads.stream_key(11, 0, 0, 40 + j) for j in range(4)]
-    u = workloads.juttner_speeds(theta, keys, torch.arange(n)).numpy()
+    u = oracle.juttner_speeds(theta, n, seed=11)
     assert not np.isnan(u).any()
     g = np.sqrt(1.0 + u * u)
     expect = 3.0 * theta + kn(1, 1.0 / theta) / kn(2, 1.0 / theta)
@@ -742,25 +765,24 @@ def test_juttner_loader_matches_the_distribution(theta):
     for q in (0.1, 0.25, 0.5, 0.75, 0.9):
         x = np.quantile(u, q)
         assert abs(integrate.quad(f, 0, x, limit=200)[0] / z - q) < 0.004
-    # a full load at rest (gamma0 = 1): isotropic momenta
-    wl = workloads.pair_plasma((32, 16), (1.0, 1.0), 0.3, 2, 1, 1.0, 0.0, 64, theta=theta)
-    up = wl.species[0].u.numpy()
+    # a full load at rest (gamma0 = 1: no boost, no flip): isotropic momenta whose magnitudes
+    # are the sampler's speeds
+    _, up, failed = oracle.load_drifting((32, 16), (1.0, 1.0), 32, 1.0, 0.0, theta=theta, seed=11)
+    assert failed == 0
     m2 = (up ** 2).mean(axis=1)
     assert np.max(np.abs(m2 / m2.mean() - 1.0)) < 0.03
+    sp = oracle.juttner_speeds(theta, up.shape[1], seed=11)
+    assert np.max(np.abs(np.sqrt((up ** 2).sum(axis=0)) - sp)) <= 1e-12 * np.max(sp)
 
 
-def test_juttner_attempt_bound(monkeypatch):
+def test_juttner_attempt_bound():
     """The bounded Sobol loop: with a single attempt per particle the accepted fraction is the
     acceptance probability of one attempt, P(eta^2 - u^2 > 1), evaluated by quadrature from the
     method's own construction (below), and every particle left without an accepted attempt is
-    marked NaN rather than given a biased speed."""
-    import torch
-    import workloads
+    marked rather than given a biased speed; the default bound leaves none at theta = 0.3."""
     from scipy import integrate
     theta, n = 0.3, 200000
-    keys = [workloads.stream_key(12, 0, 0, 40 + j) for j in range(4)]
-    monkeypatch.setattr(workloads, "JUTTNER_ATTEMPTS", 1)
-    u = workloads.juttner_speeds(theta, keys, torch.arange(n)).numpy()
+    u = oracle.juttner_speeds(theta, n, seed=12, attempts=1)
     acc = np.isfinite(u)
     # one attempt proposes u ~ Gamma(3, theta) (density u^2 e^{-u/theta} / (2 theta^3)) and
     # accepts it with probability e^{-(sqrt(1+u^2) - u)/theta}; the accepted fraction is the
@@ -770,7 +792,30 @@ def test_juttner_attempt_bound(monkeypatch):
     p = integrate.quad(f, 0, np.inf, limit=200)[0]
     assert abs(acc.mean() - p) < 5.0 * math.sqrt(p * (1 - p) / n)
     assert np.all(u[acc] > 0.0)
-    # with the default bound no particle is left unsampled at the lowest supported theta
-    monkeypatch.setattr(workloads, "JUTTNER_ATTEMPTS", 128)
-    u = workloads.juttner_speeds(theta, keys, torch.arange(n)).numpy()
+    u = oracle.juttner_speeds(theta, n, seed=12)
     assert np.isfinite(u).all()
+
+
+def test_threaded_particle_pass_equals_serial_pass():
+    """The timing build's particle pass over host threads (private currents added at the end)
+    gives the particles of the serial pass bit for bit and the same current up to the order of
+    the final additions."""
+    import plasma
+    import workloads
+    wl = plasma.fill(workloads.config_large(scale=16), count=20000)
+    res = []
+    for timing, threads in ((False, 1), (True, 4)):
+        s = Sim(wl.grid[:2], wl.dx[:2], wl.dt, wl.l, wl.scheme, timing=timing)
+        for sp in wl.species:
+            s.add_species(sp.q, sp.m, sp.w, sp.x, sp.u)
+        if timing:
+            assert s.particle_pass_threads(0, 20000, threads) == threads
+        else:
+            s.particle_pass(0, 20000)
+        res.append(([s.field(c) for c in (6, 7, 8)], [s.particles(i) for i in range(2)]))
+        s.close()
+    (ja, pa), (jb, pb) = res
+    for a, b in zip(ja, jb):
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a))
+    for (xa, ua), (xb, ub) in zip(pa, pb):
+        assert np.array_equal(xa, xb) and np.array_equal(ua, ub)
