@@ -514,41 +514,60 @@ def loader_form(reps=3):
     return out
 
 
-def served_form(n_req=48, steps=100, budget=150e9, seed=None):
-    """Config 5: Poisson stream of NCI-scan requests (90% from the batched distribution, 10%
-    3D up to 256x64x64, 8 particles per cell), admitted under a 150 GB budget, served by
-    continuous batching.  Arrival rate 0.8 x the measured service capacity."""
+def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
+    """Config 5: a Poisson stream of NCI-scan requests, 90% drawn from the batched distribution
+    and 10% 3D (128x32x32, 256x64x64 or 512x128x128 cells, 8 per cell, drift along x1), 500 steps
+    each, admitted under a 150 GB budget and served by continuous batching (engine.Server), the
+    arrival rate 0.8 x the measured service capacity of this mix.  Reports the latency
+    (completion - arrival) p50/p99, every request's slowdown against its latency alone (the
+    same form alone on the GPU, timed over alone_steps steps and scaled to its steps), and the
+    aggregate particle-steps/s."""
     import random
     import torch
     import workloads
     import paper_1909_09613_gb300 as pic
     from paper_1909_09613_gb300 import engine
     rng = random.Random(workloads.BASE_SEED if seed is None else seed)
-    specs = workloads.batched_runs(n_req, seed=workloads.BASE_SEED + 5)
-    reqs = []
-    for i, sp in enumerate(specs):
-        if rng.random() < 0.1:
-            g = rng.choice([(128, 32, 32), (256, 64, 64)])
-            reqs.append(engine.Request(rid=i, grid=g, dt=0.4, l=2, gamma=sp["gamma"], u_th=0.01,
-                                       ppc=8, steps=steps, seed=workloads.BASE_SEED))
-        else:
-            reqs.append(engine.Request(rid=i, grid=sp["grid"], dt=sp["dt"], l=sp["l"],
-                                       gamma=sp["gamma"], u_th=0.01, ppc=sp["ppc"], steps=steps,
-                                       seed=workloads.BASE_SEED))
+    specs = workloads.served_requests(n_req, seed=workloads.BASE_SEED, steps=steps)
+    reqs = [engine.Request(rid=i, grid=sp["grid"], dt=sp["dt"], l=sp["l"], gamma=sp["gamma"],
+                           u_th=sp["u_th"], ppc=sp["ppc"], steps=sp["steps"],
+                           seed=workloads.BASE_SEED) for i, sp in enumerate(specs)]
     tuner = engine.Autotuner()
-    # service capacity: a batch of the 2D requests, steps timed
-    probe = [engine.make_run(r, tuner=tuner) for r in reqs if r.dim == 2][:16]
+    # every request alone, in its own form: the latency baseline, and the 3D throughput
+    alone, work3d, t3d = {}, 0.0, 0.0
+    for r in reqs:
+        run = engine.make_run(r, tuner=tuner)
+        run.step(2)
+        torch.cuda.synchronize()
+        n = min(r.steps, alone_steps)
+        ta = time.perf_counter()
+        run.step(n)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - ta
+        alone[r.rid] = t * r.steps / n
+        if r.dim == 3:
+            work3d += r.particles * n
+            t3d += t
+        run.close()
+    torch.cuda.empty_cache()
+    # 2D service capacity: the batch of the 2D requests at once, steps timed
+    probe = [engine.make_run(r, tuner=tuner) for r in reqs if r.dim == 2]
     b = pic.Batch(probe)
     b.step(2)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     b.step(10)
     torch.cuda.synchronize()
-    cap = sum(p.counts[0] + p.counts[1] for p in probe) * 10 / (time.perf_counter() - t1)
+    cap2d = sum(p.counts[0] + p.counts[1] for p in probe) * 10 / (time.perf_counter() - t1)
     b.close()
     for p in probe:
         p.close()
-    mean_work = sum(r.particles * r.steps for r in reqs) / len(reqs)
+    torch.cuda.empty_cache()
+    cap3d = work3d / t3d if t3d > 0 else cap2d
+    w2d = sum(r.particles * r.steps for r in reqs if r.dim == 2)
+    w3d = sum(r.particles * r.steps for r in reqs if r.dim == 3)
+    cap = (w2d + w3d) / (w2d / cap2d + w3d / cap3d)
+    mean_work = (w2d + w3d) / len(reqs)
     lam = 0.8 * cap / mean_work
     t = 0.0
     for r in reqs:
@@ -559,26 +578,40 @@ def served_form(n_req=48, steps=100, budget=150e9, seed=None):
     res = srv.serve(reqs)
     makespan = time.perf_counter() - t0
     lat = [r.latency for r in res]
+    slow = [r.latency / alone[r.rid] for r in res]
+    lat2d = [r.latency for r in res if r.dim == 2]
+    slow2d = [r.latency / alone[r.rid] for r in res if r.dim == 2]
     work = sum(r.particles * r.steps for r in res)
-    # single-run baseline latency: a sample of requests run alone, one after another, in their
-    # own (FP32) form and in the plain FP64 form
-    alone, alone64 = [], []
+    # the plain FP64 single-run form on a sample of the requests, alone
+    alone64 = []
     for r in reqs[:6]:
-        for prec, dst in ((None, alone), (pic.PIC_FP64, alone64)):
-            run = engine.make_run(r, precision=prec)
-            torch.cuda.synchronize()
-            ta = time.perf_counter()
-            run.step(r.steps)
-            torch.cuda.synchronize()
-            dst.append(time.perf_counter() - ta)
-            run.close()
+        run = engine.make_run(r, precision=pic.PIC_FP64)
+        torch.cuda.synchronize()
+        n = min(r.steps, alone_steps)
+        ta = time.perf_counter()
+        run.step(n)
+        torch.cuda.synchronize()
+        alone64.append((time.perf_counter() - ta) * r.steps / n)
+        run.close()
     return {"value": work / makespan, "unit": UNIT, "requests": len(res),
             "p50_latency_s": engine.percentile(lat, 50), "p99_latency_s": engine.percentile(lat, 99),
-            "arrival_rate_per_s": lam, "service_capacity_particle_steps_per_s": cap,
+            "p50_slowdown_vs_alone": engine.percentile(slow, 50),
+            "p99_slowdown_vs_alone": engine.percentile(slow, 99),
+            "p50_latency_2d_s": engine.percentile(lat2d, 50),
+            "p50_slowdown_2d": engine.percentile(slow2d, 50),
+            "p50_alone_latency_s": engine.percentile(list(alone.values()), 50),
+            "arrival_rate_per_s": lam, "arrival_window_s": reqs[-1].arrival,
+            "service_capacity_particle_steps_per_s": cap,
+            "capacity_2d_batched": cap2d, "capacity_3d_alone": cap3d,
             "makespan_s": makespan, "max_concurrent_runs": srv.max_active,
+            "batch_builds": srv.batch_builds, "batch_set_changes": srv.set_changes,
             "peak_admitted_bytes": srv.peak_bytes, "budget_bytes": budget,
             "steps_per_request": steps, "requests_3d": sum(1 for r in reqs if r.dim == 3),
-            "alone_latency_s_sample": alone, "alone_fp64_plain_latency_s_sample": alone64,
+            "largest_3d_grid": max((list(r.grid) for r in reqs if r.dim == 3), default=None,
+                                   key=lambda g: g[0] * g[1] * g[2]),
+            "alone_fp64_plain_latency_s_sample": alone64,
+            "alone": "every request alone in its own form over %d steps, scaled to its steps"
+                     % alone_steps,
             "error_flags": sum(r.diag.get("error_flags", 0) for r in res)}
 
 

@@ -250,14 +250,41 @@ int pic_sync(pic_ctx *ctx);
  * due for a tile sort, the batched sort of those runs, ONE persistent gather-push-deposit
  * launch over the tiles of every run (heaviest tiles first, pulled from a device counter), and
  * one launch per Yee half/full update covering all runs.  The step's launch sequence is captured
- * in a CUDA graph on the first pic_batch_step and replayed.  While a batch exists, its runs must
+ * in a CUDA graph on the first pic_batch_step and replayed; its launches walk device-resident
+ * tables, so the same graph serves any run set that fits the batch's capacities.  While a batch exists, its runs must
  * not be stepped on their own; pic_batch_sync writes the batch's device state back into them.
  * The physics of every run is exactly that of pic_step (same tile code).                    */
 typedef struct pic_batch pic_batch;
 int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out);
+
+/* Room for other run sets than the initial one (see pic_batch_set_runs): totals over the runs
+ * the batch may hold at once.  Call before binding memory; the capacities size the device
+ * tables (pic_batch_footprint).  Never lowers a capacity below the initial set's.            */
+typedef struct {
+    int32_t runs;                  /* runs at once                                          */
+    int64_t particles_per_species; /* particles of one species, summed over the runs        */
+    int64_t cells;                 /* cells, summed over the runs                           */
+    int64_t tiles;                 /* particle tiles, summed over the runs                  */
+    int64_t keys;                  /* tiles x cells per tile, summed over the runs          */
+    size_t stage_bytes;            /* largest dynamic shared memory per CTA a run's work
+                                      items may need in the batched kernel (pic_smem_info's
+                                      batched_bytes); fixes the persistent kernel's shared
+                                      memory for the life of the batch                      */
+} pic_batch_capacity;
+int pic_batch_reserve(pic_batch *batch, const pic_batch_capacity *capacity);
+
 int pic_batch_footprint(const pic_batch *batch, size_t *bytes);       /* device tables   */
 int pic_batch_bind_memory(pic_batch *batch, void *dev_ptr, size_t bytes);
 int pic_batch_alloc(pic_batch *batch);                                  /* cudaMalloc'd    */
+
+/* Replace the runs of a bound batch between steps (n >= 0; the same conditions as
+ * pic_batch_create).  The device state of the runs it held is written back into their
+ * contexts first (as pic_batch_sync does), so they can be stepped, read or destroyed alone;
+ * then the new set's descriptors and tables are uploaded.  Every batch launch reads its table
+ * lengths from device memory on a fixed grid, so the captured graph of a step stays valid and
+ * is not recaptured.  Returns PIC_ENOMEM when the set exceeds the batch's capacities (then
+ * build a new batch).  Syncs.                                                                */
+int pic_batch_set_runs(pic_batch *batch, pic_ctx *const *runs, int n);
 int pic_batch_step(pic_batch *batch, int nsteps);                       /* asynchronous    */
 /* one extra (uncaptured) batch step with CUDA events around the persistent particle kernel */
 int pic_batch_time_gpp(pic_batch *batch, double *ms);

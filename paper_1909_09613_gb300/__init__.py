@@ -43,6 +43,12 @@ class pic_options(ctypes.Structure):
                 ("deterministic", ctypes.c_int32)]
 
 
+class pic_batch_capacity(ctypes.Structure):
+    _fields_ = [("runs", ctypes.c_int32), ("particles_per_species", ctypes.c_int64),
+                ("cells", ctypes.c_int64), ("tiles", ctypes.c_int64), ("keys", ctypes.c_int64),
+                ("stage_bytes", ctypes.c_size_t)]
+
+
 class pic_diag_t(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("field_energy", ctypes.c_double),
                 ("kinetic_energy", ctypes.c_double), ("total_charge", ctypes.c_double),
@@ -95,6 +101,9 @@ _SIGS = [
     ("pic_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("pic_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_void_p)]),
+    ("pic_batch_reserve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_batch_capacity)]),
+    ("pic_batch_set_runs", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                          ctypes.c_int]),
     ("pic_batch_footprint", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("pic_batch_bind_memory", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("pic_batch_alloc", ctypes.c_int, [ctypes.c_void_p]),
@@ -279,9 +288,11 @@ def pic_diag(ctx) -> dict:
 
 class Batch:
     """Batched form: advance many `Run`s (2D, FP32 form, same stream) together with one
-    persistent particle kernel per step, replayed from a CUDA graph (pic_batch_*)."""
+    persistent particle kernel per step, replayed from a CUDA graph (pic_batch_*).
+    `capacity` (a pic_batch_capacity, or None for the initial set's sizes) leaves room for the
+    other run sets `set_runs` may install later without a new graph."""
 
-    def __init__(self, runs):
+    def __init__(self, runs, capacity: Optional[pic_batch_capacity] = None):
         import torch
         self.runs = list(runs)
         arr = (ctypes.c_void_p * len(self.runs))(*[r.ctx for r in self.runs])
@@ -289,11 +300,29 @@ class Batch:
         lib = load_library()
         _check(lib.pic_batch_create(arr, len(self.runs), ctypes.byref(h)), "pic_batch_create")
         self.h = h.value
+        if capacity is not None:
+            st = lib.pic_batch_reserve(self.h, ctypes.byref(capacity))
+            if st != PIC_OK:
+                lib.pic_batch_destroy(self.h)
+                self.h = None
+                raise PicError(st, "pic_batch_reserve")
         nb = ctypes.c_size_t()
         _check(lib.pic_batch_footprint(self.h, ctypes.byref(nb)), "pic_batch_footprint")
         self.mem = torch.empty(int(nb.value), dtype=torch.uint8, device=self.runs[0].device)
         _check(lib.pic_batch_bind_memory(self.h, ctypes.c_void_p(self.mem.data_ptr()), nb.value),
                "pic_batch_bind_memory")
+
+    def set_runs(self, runs) -> bool:
+        """Install another run set (the old runs' state is written back first).  False when the
+        set does not fit the batch's capacities (the batch keeps its old runs then)."""
+        runs = list(runs)
+        arr = (ctypes.c_void_p * max(len(runs), 1))(*[r.ctx for r in runs])
+        st = load_library().pic_batch_set_runs(self.h, arr, len(runs))
+        if st == PIC_ENOMEM:
+            return False
+        _check(st, "pic_batch_set_runs")
+        self.runs = runs
+        return True
 
     def step(self, n=1):
         _check(load_library().pic_batch_step(self.h, int(n)), "pic_batch_step")

@@ -2,11 +2,16 @@
 //
 // One step of the whole batch is a fixed sequence of launches, captured once in a CUDA graph
 // and replayed: a plan kernel decides on the device which runs are due for a tile sort; the
-// batched sort kernels sort only those runs (one block table per stage covers every run);
-// the current of every run is cleared; ONE persistent gather-push-deposit kernel (one CTA per
-// SM slot) pulls (run, tile) work items, heaviest first, from a device counter and processes
-// them with the same tile code as a single run; three batched Yee launches finish the step.
-// Nothing on the host changes between steps, so the captured graph stays valid.
+// batched sort kernels sort only those runs; the current of every run is cleared; ONE
+// persistent gather-push-deposit kernel (one CTA per SM slot) pulls (run, tile) work items,
+// heaviest first, from a device counter and processes them with the same tile code as a single
+// run; three batched Yee launches finish the step.
+//
+// Every launch has a fixed grid and walks device-resident tables (run descriptors, per-stage
+// block maps, work items) whose lengths it reads from device memory.  The captured graph
+// therefore does not depend on which runs the batch holds: pic_batch_set_runs replaces the
+// runs between steps by writing the old runs' device state back and uploading new tables, and
+// the same graph keeps serving (a set larger than the tables' capacity needs a new batch).
 #include "pic.h"
 #include "pic_gpp_kernels.cuh"
 #include "pic_grid_dev.cuh"
@@ -38,6 +43,8 @@ constexpr int kBlock = 256;
 // elements per thread of the per-particle, per-key and per-cell stages: fewer, fuller blocks
 // (the blocks of runs that are not due for a sort exit at once, and there are many of them)
 constexpr int kPartPer = 8, kKeyPer = 8, kCellPer = 4;
+// threads of the per-tile sort stages: one per cell of the largest tile a run may have
+constexpr int kTileThreads = 1024;
 
 struct RunState {
     int age, interval, due, kt;
@@ -48,144 +55,183 @@ struct BlockMap {
     int block;  // block index inside the run's range
 };
 
+// Lengths of the device tables, read by every stage (the graph never changes with them).
+struct Counts {
+    int runs;
+    int part[PIC_NSP_MAX];
+    int cell, key, tile, items;
+};
+
 // ---- plan: which runs sort this step ----
-__global__ void k_b_plan(int n, RunState *st, int *counter)
+__global__ void k_b_plan(const Counts *cn, RunState *st, int *counter)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r == 0) *counter = 0;
-    if (r >= n) return;
-    RunState s = st[r];
-    s.due = s.age >= s.interval ? 1 : 0;
-    if (s.due) s.age = 0;
-    s.age += 1;
-    st[r] = s;
+    const int n = cn->runs;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        RunState s = st[r];
+        s.due = s.age >= s.interval ? 1 : 0;
+        if (s.due) s.age = 0;
+        s.age += 1;
+        st[r] = s;
+    }
 }
 
 // ---- batched sort stages (each skips runs that are not due) ----
-__global__ void __launch_bounds__(kBlock) k_b_zero_cnt(const RunDev *runs, const RunState *st,
-                                                       const BlockMap *bm)
+__global__ void __launch_bounds__(kBlock) k_b_zero_cnt(const Counts *cn, const RunDev *runs,
+                                                       const RunState *st, const BlockMap *bm)
 {
-    const BlockMap m = bm[blockIdx.x];
-    if (!st[m.run].due) return;
-    const RunDev &rd = runs[m.run];
-    const int64_t nk = rd.ntiles * rd.tile[0] * rd.tile[1] * rd.tile[2];
-    int32_t *cnt = rd.sc.cnt;
-    for (int k = 0; k < kKeyPer; ++k) {
-        const int64_t i = ((int64_t)m.block * kKeyPer + k) * blockDim.x + threadIdx.x;
-        if (i < nk) cnt[i] = 0;
-    }
-}
-
-__global__ void __launch_bounds__(kBlock) k_b_count(const RunDev *runs, const RunState *st,
-                                                    const BlockMap *bm, int s)
-{
-    const BlockMap m = bm[blockIdx.x];
-    if (!st[m.run].due) return;
-    const RunDev &rd = runs[m.run];
-    const int64_t n = rd.sp[s].n;
-    for (int k = 0; k < kPartPer; ++k) {
-        const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
-        if (p < n) sort_count_one(rd, s, p);
-    }
-}
-
-__global__ void k_b_tile_sum(const RunDev *runs, const RunState *st, const BlockMap *bm)
-{
-    const BlockMap m = bm[blockIdx.x];
-    if (!st[m.run].due) return;
-    sort_tile_sum_block(runs[m.run], m.block);
-}
-
-__global__ void k_b_scan(const RunDev *runs, const RunState *st, int s)
-{
-    const int r = blockIdx.x;
-    if (!st[r].due) return;
-    const RunDev &rd = runs[r];
-    sort_scan_block(rd.sc.tile_count, rd.sp[s].tile_start, rd.ntiles);
-}
-
-__global__ void k_b_layout(const RunDev *runs, const RunState *st, const BlockMap *bm, int s)
-{
-    const BlockMap m = bm[blockIdx.x];
-    if (!st[m.run].due) return;
-    const RunDev &rd = runs[m.run];
-    sort_layout_block(rd, rd.sp[s].tile_start, m.block);
-}
-
-__global__ void __launch_bounds__(kBlock) k_b_place(const RunDev *runs, const RunState *st,
-                                                    const BlockMap *bm, int s)
-{
-    const BlockMap m = bm[blockIdx.x];
-    if (!st[m.run].due) return;
-    const RunDev &rd = runs[m.run];
-    const int64_t n = rd.sp[s].n;
-    for (int k = 0; k < kPartPer; ++k) {
-        const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
-        if (p < n) sort_place_one(rd, p);
-    }
-}
-
-// one thread per cell-major position r of the run's species (the same range as its particles)
-__global__ void __launch_bounds__(kBlock) k_b_scatter(const RunDev *runs, const RunState *st,
-                                                      const BlockMap *bm, int s)
-{
-    const BlockMap m = bm[blockIdx.x];
-    if (!st[m.run].due) return;
-    const RunDev &rd = runs[m.run];
-    const SpeciesDev &sp = rd.sp[s];
-    for (int k = 0; k < kPartPer; ++k) {
-        const int64_t r = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
-        if (r < sp.n) sort_scatter_one(rd, s, r, sp.pos_alt, sp.mom_alt, sp.cell_alt);
-    }
-}
-
-// the sorted buffers become the current ones
-__global__ void k_b_swap(RunDev *runs, const RunState *st, int n, int s)
-{
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n || !st[r].due) return;
-    SpeciesDev &sp = runs[r].sp[s];
-    for (int a = 0; a < 3; ++a) {
-        void *t = sp.pos[a]; sp.pos[a] = sp.pos_alt[a]; sp.pos_alt[a] = t;
-        t = sp.mom[a]; sp.mom[a] = sp.mom_alt[a]; sp.mom_alt[a] = t;
-    }
-    int32_t *c = sp.cell; sp.cell = sp.cell_alt; sp.cell_alt = c;
-}
-
-// ---- current cleared, Yee updates ----
-__global__ void __launch_bounds__(kBlock) k_b_zero_j(const RunDev *runs, const BlockMap *bm)
-{
-    const BlockMap m = bm[blockIdx.x];
-    const RunDev &rd = runs[m.run];
-    double *j0 = rd.F[6], *j1 = rd.F[7], *j2 = rd.F[8];
-    for (int k = 0; k < kCellPer; ++k) {
-        const int64_t c = ((int64_t)m.block * kCellPer + k) * blockDim.x + threadIdx.x;
-        if (c < rd.ncell) {
-            j0[c] = 0.0;
-            j1[c] = 0.0;
-            j2[c] = 0.0;
+    for (int b = blockIdx.x; b < cn->key; b += gridDim.x) {
+        const BlockMap m = bm[b];
+        if (!st[m.run].due) continue;
+        const RunDev &rd = runs[m.run];
+        const int64_t nk = rd.ntiles * rd.tile[0] * rd.tile[1] * rd.tile[2];
+        int32_t *cnt = rd.sc.cnt;
+        for (int k = 0; k < kKeyPer; ++k) {
+            const int64_t i = ((int64_t)m.block * kKeyPer + k) * blockDim.x + threadIdx.x;
+            if (i < nk) cnt[i] = 0;
         }
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_b_yee_b(const RunDev *runs, const BlockMap *bm,
-                                                    int shadow)
+__global__ void __launch_bounds__(kBlock) k_b_count(const Counts *cn, const RunDev *runs,
+                                                    const RunState *st, const BlockMap *bm, int s)
 {
-    const BlockMap m = bm[blockIdx.x];
-    const RunDev &rd = runs[m.run];
-    for (int k = 0; k < kCellPer; ++k) {
-        const int64_t c = ((int64_t)m.block * kCellPer + k) * blockDim.x + threadIdx.x;
-        if (c < rd.ncell) yee_b_cell(rd, c, 0.5 * rd.dt, shadow);
+    for (int b = blockIdx.x; b < cn->part[s]; b += gridDim.x) {
+        const BlockMap m = bm[b];
+        if (!st[m.run].due) continue;
+        const RunDev &rd = runs[m.run];
+        const int64_t n = rd.sp[s].n;
+        for (int k = 0; k < kPartPer; ++k) {
+            const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
+            if (p < n) sort_count_one(rd, s, p);
+        }
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_b_yee_e(const RunDev *runs, const BlockMap *bm)
+// block-wide stages: the loop index is uniform over the block, so every thread takes part in
+// the block's barriers and scans
+__global__ void __launch_bounds__(kTileThreads) k_b_tile_sum(const Counts *cn, const RunDev *runs,
+                                                             const RunState *st, const BlockMap *bm)
 {
-    const BlockMap m = bm[blockIdx.x];
-    const RunDev &rd = runs[m.run];
-    for (int k = 0; k < kCellPer; ++k) {
-        const int64_t c = ((int64_t)m.block * kCellPer + k) * blockDim.x + threadIdx.x;
-        if (c < rd.ncell) yee_e_cell(rd, c, 1);
+    for (int b = blockIdx.x; b < cn->tile; b += gridDim.x) {
+        const BlockMap m = bm[b];
+        if (!st[m.run].due) continue;
+        sort_tile_sum_block(runs[m.run], m.block);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_b_scan(const Counts *cn, const RunDev *runs,
+                                                 const RunState *st, int s)
+{
+    for (int r = blockIdx.x; r < cn->runs; r += gridDim.x) {
+        if (!st[r].due) continue;
+        const RunDev &rd = runs[r];
+        sort_scan_block(rd.sc.tile_count, rd.sp[s].tile_start, rd.ntiles);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_b_layout(const Counts *cn, const RunDev *runs,
+                                                           const RunState *st, const BlockMap *bm,
+                                                           int s)
+{
+    for (int b = blockIdx.x; b < cn->tile; b += gridDim.x) {
+        const BlockMap m = bm[b];
+        if (!st[m.run].due) continue;
+        const RunDev &rd = runs[m.run];
+        sort_layout_block(rd, rd.sp[s].tile_start, m.block);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_b_place(const Counts *cn, const RunDev *runs,
+                                                    const RunState *st, const BlockMap *bm, int s)
+{
+    for (int b = blockIdx.x; b < cn->part[s]; b += gridDim.x) {
+        const BlockMap m = bm[b];
+        if (!st[m.run].due) continue;
+        const RunDev &rd = runs[m.run];
+        const int64_t n = rd.sp[s].n;
+        for (int k = 0; k < kPartPer; ++k) {
+            const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
+            if (p < n) sort_place_one(rd, p);
+        }
+    }
+}
+
+// one thread per cell-major position r of the run's species (the same range as its particles)
+__global__ void __launch_bounds__(kBlock) k_b_scatter(const Counts *cn, const RunDev *runs,
+                                                      const RunState *st, const BlockMap *bm, int s)
+{
+    for (int b = blockIdx.x; b < cn->part[s]; b += gridDim.x) {
+        const BlockMap m = bm[b];
+        if (!st[m.run].due) continue;
+        const RunDev &rd = runs[m.run];
+        const SpeciesDev &sp = rd.sp[s];
+        for (int k = 0; k < kPartPer; ++k) {
+            const int64_t r = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
+            if (r < sp.n) sort_scatter_one(rd, s, r, sp.pos_alt, sp.mom_alt, sp.cell_alt);
+        }
+    }
+}
+
+// the sorted buffers become the current ones
+__global__ void k_b_swap(const Counts *cn, RunDev *runs, const RunState *st, int s)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cn->runs; r += gridDim.x * blockDim.x) {
+        if (!st[r].due) continue;
+        SpeciesDev &sp = runs[r].sp[s];
+        for (int a = 0; a < 3; ++a) {
+            void *t = sp.pos[a]; sp.pos[a] = sp.pos_alt[a]; sp.pos_alt[a] = t;
+            t = sp.mom[a]; sp.mom[a] = sp.mom_alt[a]; sp.mom_alt[a] = t;
+        }
+        int32_t *c = sp.cell; sp.cell = sp.cell_alt; sp.cell_alt = c;
+    }
+}
+
+// ---- current cleared, Yee updates ----
+__global__ void __launch_bounds__(kBlock) k_b_zero_j(const Counts *cn, const RunDev *runs,
+                                                     const BlockMap *bm)
+{
+    for (int b = blockIdx.x; b < cn->cell; b += gridDim.x) {
+        const BlockMap m = bm[b];
+        const RunDev &rd = runs[m.run];
+        double *j0 = rd.F[6], *j1 = rd.F[7], *j2 = rd.F[8];
+        for (int k = 0; k < kCellPer; ++k) {
+            const int64_t c = ((int64_t)m.block * kCellPer + k) * blockDim.x + threadIdx.x;
+            if (c < rd.ncell) {
+                j0[c] = 0.0;
+                j1[c] = 0.0;
+                j2[c] = 0.0;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_b_yee_b(const Counts *cn, const RunDev *runs,
+                                                    const BlockMap *bm, int shadow)
+{
+    for (int b = blockIdx.x; b < cn->cell; b += gridDim.x) {
+        const BlockMap m = bm[b];
+        const RunDev &rd = runs[m.run];
+        for (int k = 0; k < kCellPer; ++k) {
+            const int64_t c = ((int64_t)m.block * kCellPer + k) * blockDim.x + threadIdx.x;
+            if (c < rd.ncell) yee_b_cell(rd, c, 0.5 * rd.dt, shadow);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_b_yee_e(const Counts *cn, const RunDev *runs,
+                                                    const BlockMap *bm)
+{
+    for (int b = blockIdx.x; b < cn->cell; b += gridDim.x) {
+        const BlockMap m = bm[b];
+        const RunDev &rd = runs[m.run];
+        for (int k = 0; k < kCellPer; ++k) {
+            const int64_t c = ((int64_t)m.block * kCellPer + k) * blockDim.x + threadIdx.x;
+            if (c < rd.ncell) yee_e_cell(rd, c, 1);
+        }
     }
 }
 
@@ -198,8 +244,8 @@ __device__ __forceinline__ bool try_tile(const RunDev &rd, int kt, char *smem, i
     return true;
 }
 
-__global__ void __launch_bounds__(256, 2) k_b_gpp(const RunDev *runs, const RunState *st,
-                                              const int2 *items, int nitems, int *counter)
+__global__ void __launch_bounds__(256, 2) k_b_gpp(const Counts *cn, const RunDev *runs,
+                                              const RunState *st, const int2 *items, int *counter)
 {
     extern __shared__ __align__(16) char smem_all[];
     // the run descriptor is copied next to the tile stage so that the particle loop reads it
@@ -207,6 +253,7 @@ __global__ void __launch_bounds__(256, 2) k_b_gpp(const RunDev *runs, const RunS
     RunDev *rds = (RunDev *)smem_all;
     char *smem = smem_all + ((sizeof(RunDev) + 15) / 16) * 16;
     __shared__ int item;
+    const int nitems = cn->items;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) item = atomicAdd(counter, 1);
@@ -228,100 +275,6 @@ __global__ void __launch_bounds__(256, 2) k_b_gpp(const RunDev *runs, const RunS
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-}  // namespace
-
-struct pic_batch {
-    int n;
-    std::vector<pic_ctx *> ctx;
-    cudaStream_t stream;
-    bool own_stream;   // the runs use the legacy default stream, which cannot be captured
-    // host-side tables
-    std::vector<BlockMap> bm_part[PIC_NSP_MAX], bm_cell, bm_key, bm_tile;
-    std::vector<int2> items;
-    int nsp;
-    int max_tc;
-    size_t smem;
-    // device memory
-    char *base;
-    size_t bytes;
-    bool owns;
-    RunDev *d_runs;
-    RunState *d_state;
-    BlockMap *d_bm_part[PIC_NSP_MAX], *d_bm_cell, *d_bm_key, *d_bm_tile;
-    int2 *d_items;
-    int *d_counter;
-    // graph of one step
-    cudaGraphExec_t exec;
-    bool have_graph;
-    cudaEvent_t ev0, ev1;
-    bool timing;
-    double gpp_ms;
-    int64_t steps_since_sync;
-    int64_t launches;  // kernels per step
-};
-
-namespace {
-
-template <typename T>
-size_t table_bytes(const std::vector<T> &v) { return align_up(std::max<size_t>(v.size(), 1) * sizeof(T), 256); }
-
-// Launch sequence of one batch step on b->stream (also used while capturing).
-cudaError_t enqueue_step(pic_batch *b)
-{
-    cudaStream_t st = b->stream;
-    int64_t nl = 0;
-    k_b_plan<<<(b->n + 127) / 128, 128, 0, st>>>(b->n, b->d_state, b->d_counter);
-    ++nl;
-    if (!b->bm_key.empty()) {
-        k_b_zero_cnt<<<(unsigned)b->bm_key.size(), kBlock, 0, st>>>(b->d_runs, b->d_state, b->d_bm_key);
-        ++nl;
-    }
-    const int tb = ((b->max_tc + 31) / 32) * 32;
-    for (int s = 0; s < b->nsp; ++s) {
-        if (s > 0 && !b->bm_key.empty()) {
-            k_b_zero_cnt<<<(unsigned)b->bm_key.size(), kBlock, 0, st>>>(b->d_runs, b->d_state, b->d_bm_key);
-            ++nl;
-        }
-        if (!b->bm_part[s].empty()) {
-            k_b_count<<<(unsigned)b->bm_part[s].size(), kBlock, 0, st>>>(b->d_runs, b->d_state,
-                                                                         b->d_bm_part[s], s);
-            ++nl;
-        }
-        k_b_tile_sum<<<(unsigned)b->bm_tile.size(), tb, 0, st>>>(b->d_runs, b->d_state, b->d_bm_tile);
-        k_b_scan<<<b->n, 1024, 0, st>>>(b->d_runs, b->d_state, s);
-        k_b_layout<<<(unsigned)b->bm_tile.size(), tb, 0, st>>>(b->d_runs, b->d_state, b->d_bm_tile, s);
-        nl += 3;
-        if (!b->bm_part[s].empty()) {
-            k_b_place<<<(unsigned)b->bm_part[s].size(), kBlock, 0, st>>>(b->d_runs, b->d_state,
-                                                                         b->d_bm_part[s], s);
-            ++nl;
-            k_b_scatter<<<(unsigned)b->bm_part[s].size(), kBlock, 0, st>>>(b->d_runs, b->d_state,
-                                                                           b->d_bm_part[s], s);
-            ++nl;
-        }
-        k_b_swap<<<(b->n + 127) / 128, 128, 0, st>>>(b->d_runs, b->d_state, b->n, s);
-        ++nl;
-    }
-    k_b_zero_j<<<(unsigned)b->bm_cell.size(), kBlock, 0, st>>>(b->d_runs, b->d_bm_cell);
-    ++nl;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_gpp, 256, b->smem);
-    const int grid = std::max(1, std::min<int>((int)b->items.size(), sms * std::max(per_sm, 1)));
-    if (b->timing) cudaEventRecord(b->ev0, st);
-    k_b_gpp<<<grid, 256, b->smem, st>>>(b->d_runs, b->d_state, b->d_items, (int)b->items.size(),
-                                         b->d_counter);
-    if (b->timing) cudaEventRecord(b->ev1, st);
-    ++nl;
-    k_b_yee_b<<<(unsigned)b->bm_cell.size(), kBlock, 0, st>>>(b->d_runs, b->d_bm_cell, 0);
-    k_b_yee_e<<<(unsigned)b->bm_cell.size(), kBlock, 0, st>>>(b->d_runs, b->d_bm_cell);
-    k_b_yee_b<<<(unsigned)b->bm_cell.size(), kBlock, 0, st>>>(b->d_runs, b->d_bm_cell, 1);
-    nl += 3;
-    b->launches = nl;
-    return cudaGetLastError();
-}
-
 void push_blocks(std::vector<BlockMap> &v, int run, int64_t count, int per)
 {
     const int64_t nb = (count + per - 1) / per;
@@ -330,59 +283,251 @@ void push_blocks(std::vector<BlockMap> &v, int run, int64_t count, int per)
 
 }  // namespace
 
-extern "C" {
+struct pic_batch {
+    int n;                          // runs the batch holds now
+    std::vector<pic_ctx *> ctx;
+    cudaStream_t stream;      // where the batch's steps run (captured)
+    cudaStream_t run_stream;  // the runs' own stream (every run of a set must share it)
+    bool own_stream;   // the runs use the legacy default stream, which cannot be captured
+    int nsp;
+    size_t smem;       // dynamic shared memory of the persistent kernel (fixed by the graph)
+    // table capacities (entries; the work items are one per tile) and the current tables
+    int cap_runs;
+    int64_t cap_part[PIC_NSP_MAX], cap_cell, cap_key, cap_tile;
+    std::vector<BlockMap> bm_part[PIC_NSP_MAX], bm_cell, bm_key, bm_tile;
+    std::vector<int2> items;
+    // device memory
+    char *base;
+    size_t bytes;
+    bool owns;
+    Counts *d_counts;
+    RunDev *d_runs;
+    RunState *d_state;
+    BlockMap *d_bm_part[PIC_NSP_MAX], *d_bm_cell, *d_bm_key, *d_bm_tile;
+    int2 *d_items;
+    int *d_counter;
+    // launch shapes and the graph of one step
+    int grid_runs, grid_stage, grid_tile, grid_gpp;
+    cudaGraphExec_t exec;
+    bool have_graph;
+    cudaEvent_t ev0, ev1;
+    bool timing;
+    int64_t steps_since_sync;
+    int64_t launches;  // kernels per step
+};
 
-int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
+namespace {
+
+template <typename T>
+size_t cap_bytes(int64_t entries) { return align_up((size_t)std::max<int64_t>(entries, 1) * sizeof(T), 256); }
+
+// Tables of a set of runs (validated: 2D, FP32 form, l = 2 or 3, not deterministic, the batch's
+// species count and stream), and the shared memory its work items need.
+struct Tables {
+    std::vector<BlockMap> part[PIC_NSP_MAX], cell, key, tile;
+    std::vector<int2> items;
+    size_t smem = 0;
+};
+
+int build_tables(pic_ctx *const *runs, int n, int nsp, cudaStream_t stream, Tables &t)
 {
-    if (!runs || n <= 0 || !out) return PIC_EINVAL;
-    *out = nullptr;
-    pic_batch *b = new (std::nothrow) pic_batch;
-    if (!b) return PIC_ENOMEM;
-    b->n = n;
-    b->ctx.assign(runs, runs + n);
-    b->stream = ctx_stream(runs[0]);
-    b->own_stream = false;
-    b->nsp = ctx_rundev(runs[0])->nsp;
-    b->max_tc = 1;
-    b->smem = 0;
-    b->base = nullptr;
-    b->bytes = 0;
-    b->owns = false;
-    b->have_graph = false;
-    b->timing = false;
-    b->gpp_ms = 0.0;
-    b->steps_since_sync = 0;
-    b->launches = 0;
     std::vector<std::pair<int64_t, int2>> work;
+    std::vector<pic_ctx *> seen(runs, runs + n);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return PIC_EINVAL;  // twice
     for (int r = 0; r < n; ++r) {
         pic_ctx *c = runs[r];
-        if (!c || !ctx_bound(c)) { delete b; return PIC_ESTATE; }
+        if (!c || !ctx_bound(c)) return PIC_ESTATE;
         const RunDev &rd = *ctx_rundev(c);
-        if (rd.dim != 2 || rd.prec != PIC_FP32_MIXED || rd.nsp != b->nsp || rd.l < 2 || rd.l > 3
-            || rd.det || ctx_stream(c) != b->stream) {
-            delete b;
+        if (rd.dim != 2 || rd.prec != PIC_FP32_MIXED || rd.nsp != nsp || rd.l < 2 || rd.l > 3
+            || rd.det || ctx_stream(c) != stream)
             return PIC_EINVAL;
-        }
         const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
-        b->max_tc = std::max(b->max_tc, TC);
-        b->smem = std::max(b->smem, stage2d_bytes<float>(rd.reg_nodes, rd.l, false));
-        for (int s = 0; s < b->nsp; ++s) push_blocks(b->bm_part[s], r, rd.sp[s].n, kBlock * kPartPer);
-        push_blocks(b->bm_cell, r, rd.ncell, kBlock * kCellPer);
-        push_blocks(b->bm_key, r, rd.ntiles * TC, kBlock * kKeyPer);
-        for (int64_t t = 0; t < rd.ntiles; ++t) b->bm_tile.push_back({r, (int)t});
+        if (TC > kTileThreads) return PIC_EINVAL;
+        t.smem = std::max(t.smem, stage2d_bytes<float>(rd.reg_nodes, rd.l, false));
+        for (int s = 0; s < nsp; ++s) push_blocks(t.part[s], r, rd.sp[s].n, kBlock * kPartPer);
+        push_blocks(t.cell, r, rd.ncell, kBlock * kCellPer);
+        push_blocks(t.key, r, rd.ntiles * TC, kBlock * kKeyPer);
+        for (int64_t i = 0; i < rd.ntiles; ++i) t.tile.push_back({r, (int)i});
         int64_t np = 0;
-        for (int s = 0; s < b->nsp; ++s) np += rd.sp[s].n;
+        for (int s = 0; s < nsp; ++s) np += rd.sp[s].n;
         const int64_t per_tile = rd.ntiles > 0 ? np / rd.ntiles : 0;
-        for (int64_t t = 0; t < rd.ntiles; ++t) work.push_back({per_tile, make_int2(r, (int)t)});
+        for (int64_t i = 0; i < rd.ntiles; ++i) work.push_back({per_tile, make_int2(r, (int)i)});
     }
     // heaviest work items first (longest-processing-time order for the dynamic scheduler)
     std::stable_sort(work.begin(), work.end(),
                      [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &c) {
                          return a.first > c.first;
                      });
-    for (auto &w : work) b->items.push_back(w.second);
-    b->smem += ((sizeof(RunDev) + 15) / 16) * 16;
-    if (b->smem > 227 * 1024) { delete b; return PIC_EINVAL; }
+    for (auto &w : work) t.items.push_back(w.second);
+    t.smem += ((sizeof(RunDev) + 15) / 16) * 16;
+    return PIC_OK;
+}
+
+bool tables_fit(const pic_batch *b, const Tables &t, int n)
+{
+    if (n > b->cap_runs || (int64_t)t.cell.size() > b->cap_cell || (int64_t)t.key.size() > b->cap_key
+        || (int64_t)t.tile.size() > b->cap_tile || t.smem > b->smem)
+        return false;
+    for (int s = 0; s < b->nsp; ++s)
+        if ((int64_t)t.part[s].size() > b->cap_part[s]) return false;
+    return true;
+}
+
+// Launch sequence of one batch step on b->stream (also used while capturing).  Every grid is
+// fixed by the capacities; the kernels read the table lengths from d_counts.
+cudaError_t enqueue_step(pic_batch *b)
+{
+    cudaStream_t st = b->stream;
+    const Counts *cn = b->d_counts;
+    int64_t nl = 0;
+    k_b_plan<<<b->grid_runs, 128, 0, st>>>(cn, b->d_state, b->d_counter);
+    ++nl;
+    for (int s = 0; s < b->nsp; ++s) {
+        k_b_zero_cnt<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_key);
+        k_b_count<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_part[s], s);
+        k_b_tile_sum<<<b->grid_tile, kTileThreads, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_tile);
+        k_b_scan<<<b->grid_runs, 1024, 0, st>>>(cn, b->d_runs, b->d_state, s);
+        k_b_layout<<<b->grid_tile, kTileThreads, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_tile, s);
+        k_b_place<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_part[s], s);
+        k_b_scatter<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_part[s], s);
+        k_b_swap<<<b->grid_runs, 128, 0, st>>>(cn, b->d_runs, b->d_state, s);
+        nl += 8;
+    }
+    k_b_zero_j<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_bm_cell);
+    ++nl;
+    if (b->timing) cudaEventRecord(b->ev0, st);
+    k_b_gpp<<<b->grid_gpp, 256, b->smem, st>>>(cn, b->d_runs, b->d_state, b->d_items, b->d_counter);
+    if (b->timing) cudaEventRecord(b->ev1, st);
+    ++nl;
+    k_b_yee_b<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_bm_cell, 0);
+    k_b_yee_e<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_bm_cell);
+    k_b_yee_b<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_bm_cell, 1);
+    nl += 3;
+    b->launches = nl;
+    return cudaGetLastError();
+}
+
+// Write the device-side state of the batch's current runs (buffer swaps of the sorts, sort
+// ages, step counts) back into their contexts.  Syncs.  Returns the latched error bits.
+int write_back(pic_batch *b, int32_t *err_out)
+{
+    int32_t err = 0;
+    if (b->n > 0) {
+        std::vector<RunDev> rds(b->n);
+        std::vector<RunState> sts(b->n);
+        if (cudaMemcpyAsync(rds.data(), b->d_runs, b->n * sizeof(RunDev), cudaMemcpyDeviceToHost,
+                            b->stream) != cudaSuccess
+            || cudaMemcpyAsync(sts.data(), b->d_state, b->n * sizeof(RunState),
+                               cudaMemcpyDeviceToHost, b->stream) != cudaSuccess
+            || cudaStreamSynchronize(b->stream) != cudaSuccess)
+            return PIC_ECUDA;
+        for (int r = 0; r < b->n; ++r)
+            ctx_after_batch(b->ctx[r], rds[r], sts[r].age, b->steps_since_sync);
+        for (int r = 0; r < b->n; ++r) {
+            int32_t e = 0;
+            if (cudaMemcpy(&e, rds[r].err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return PIC_ECUDA;
+            err |= e;
+        }
+    }
+    b->steps_since_sync = 0;
+    if (err_out) *err_out = err;
+    return PIC_OK;
+}
+
+// Upload the descriptors, states and tables of a run set (already validated and fitting the
+// capacities) and make it the batch's current set.
+int upload(pic_batch *b, pic_ctx *const *runs, int n, Tables &t)
+{
+    for (int r = 0; r < n; ++r) {
+        const int e = ctx_prepare_batch(runs[r]);
+        if (e != PIC_OK) return e;
+    }
+    std::vector<RunDev> rds(n);
+    std::vector<RunState> sts(n);
+    for (int r = 0; r < n; ++r) {
+        rds[r] = *ctx_rundev(runs[r]);
+        sts[r].age = ctx_age(runs[r]);
+        sts[r].interval = ctx_sort_interval(runs[r]);
+        sts[r].due = 0;
+        sts[r].kt = ctx_rundev(runs[r])->l + 2;
+    }
+    Counts cn;
+    std::memset(&cn, 0, sizeof(cn));
+    cn.runs = n;
+    for (int s = 0; s < b->nsp; ++s) cn.part[s] = (int)t.part[s].size();
+    cn.cell = (int)t.cell.size();
+    cn.key = (int)t.key.size();
+    cn.tile = (int)t.tile.size();
+    cn.items = (int)t.items.size();
+    cudaStream_t st = b->stream;
+    auto up = [&](void *dst, const void *src, size_t nb) {
+        return nb == 0 || cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    };
+    bool ok = up(b->d_runs, rds.data(), rds.size() * sizeof(RunDev))
+              && up(b->d_state, sts.data(), sts.size() * sizeof(RunState))
+              && up(b->d_counts, &cn, sizeof(cn));
+    for (int s = 0; s < b->nsp && ok; ++s)
+        ok = up(b->d_bm_part[s], t.part[s].data(), t.part[s].size() * sizeof(BlockMap));
+    ok = ok && up(b->d_bm_cell, t.cell.data(), t.cell.size() * sizeof(BlockMap))
+         && up(b->d_bm_key, t.key.data(), t.key.size() * sizeof(BlockMap))
+         && up(b->d_bm_tile, t.tile.data(), t.tile.size() * sizeof(BlockMap))
+         && up(b->d_items, t.items.data(), t.items.size() * sizeof(int2));
+    // the host vectors are released on return: wait for the copies
+    if (!ok || cudaStreamSynchronize(st) != cudaSuccess) return PIC_ECUDA;
+    b->n = n;
+    b->ctx.assign(runs, runs + n);
+    for (int s = 0; s < b->nsp; ++s) b->bm_part[s].swap(t.part[s]);
+    b->bm_cell.swap(t.cell);
+    b->bm_key.swap(t.key);
+    b->bm_tile.swap(t.tile);
+    b->items.swap(t.items);
+    b->steps_since_sync = 0;
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
+{
+    if (!runs || n <= 0 || !out || !runs[0]) return PIC_EINVAL;
+    *out = nullptr;
+    if (!ctx_bound(runs[0])) return PIC_ESTATE;
+    pic_batch *b = new (std::nothrow) pic_batch;
+    if (!b) return PIC_ENOMEM;
+    b->n = 0;
+    b->stream = ctx_stream(runs[0]);
+    b->run_stream = b->stream;
+    b->own_stream = false;
+    b->nsp = ctx_rundev(runs[0])->nsp;
+    b->base = nullptr;
+    b->bytes = 0;
+    b->owns = false;
+    b->have_graph = false;
+    b->timing = false;
+    b->steps_since_sync = 0;
+    b->launches = 0;
+    Tables t;
+    const int e = build_tables(runs, n, b->nsp, b->stream, t);
+    if (e != PIC_OK) { delete b; return e; }
+    if (t.smem > 227 * 1024) { delete b; return PIC_EINVAL; }
+    // capacities of the initial set (pic_batch_reserve raises them before binding)
+    b->smem = t.smem;
+    b->cap_runs = n;
+    for (int s = 0; s < PIC_NSP_MAX; ++s) b->cap_part[s] = s < b->nsp ? (int64_t)t.part[s].size() : 0;
+    b->cap_cell = (int64_t)t.cell.size();
+    b->cap_key = (int64_t)t.key.size();
+    b->cap_tile = (int64_t)t.tile.size();
+    // the initial set, uploaded by pic_batch_bind_memory
+    b->ctx.assign(runs, runs + n);
+    for (int s = 0; s < b->nsp; ++s) b->bm_part[s].swap(t.part[s]);
+    b->bm_cell.swap(t.cell);
+    b->bm_key.swap(t.key);
+    b->bm_tile.swap(t.tile);
+    b->items.swap(t.items);
     if (b->stream == 0) {
         // a blocking stream is ordered with the legacy default stream the runs use
         if (cudaStreamCreateWithFlags(&b->stream, cudaStreamDefault) != cudaSuccess) {
@@ -395,13 +540,32 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
     return PIC_OK;
 }
 
+int pic_batch_reserve(pic_batch *b, const pic_batch_capacity *cap)
+{
+    if (!b || !cap) return PIC_EINVAL;
+    if (b->base) return PIC_ESTATE;  // the capacities size the bound memory
+    if (cap->runs < 0 || cap->particles_per_species < 0 || cap->cells < 0 || cap->tiles < 0
+        || cap->keys < 0 || cap->stage_bytes > 227 * 1024)
+        return PIC_EINVAL;
+    b->cap_runs = std::max(b->cap_runs, (int)cap->runs);
+    for (int s = 0; s < b->nsp; ++s)
+        b->cap_part[s] = std::max<int64_t>(b->cap_part[s],
+                                           cap->particles_per_species / (kBlock * kPartPer) + cap->runs);
+    b->cap_cell = std::max<int64_t>(b->cap_cell, cap->cells / (kBlock * kCellPer) + cap->runs);
+    b->cap_key = std::max<int64_t>(b->cap_key, cap->keys / (kBlock * kKeyPer) + cap->runs);
+    b->cap_tile = std::max<int64_t>(b->cap_tile, cap->tiles);
+    b->smem = std::max(b->smem, std::min(cap->stage_bytes, (size_t)227 * 1024));
+    return PIC_OK;
+}
+
 int pic_batch_footprint(const pic_batch *b, size_t *bytes)
 {
     if (!b || !bytes) return PIC_EINVAL;
-    size_t s = align_up(b->n * sizeof(RunDev), 256) + align_up(b->n * sizeof(RunState), 256);
-    for (int i = 0; i < b->nsp; ++i) s += table_bytes(b->bm_part[i]);
-    s += table_bytes(b->bm_cell) + table_bytes(b->bm_key) + table_bytes(b->bm_tile);
-    s += table_bytes(b->items) + 256 + 256;
+    size_t s = align_up(sizeof(Counts), 256);
+    s += cap_bytes<RunDev>(b->cap_runs) + cap_bytes<RunState>(b->cap_runs);
+    for (int i = 0; i < b->nsp; ++i) s += cap_bytes<BlockMap>(b->cap_part[i]);
+    s += cap_bytes<BlockMap>(b->cap_cell) + cap_bytes<BlockMap>(b->cap_key)
+         + cap_bytes<BlockMap>(b->cap_tile) + cap_bytes<int2>(b->cap_tile) + 256 + 256;
     *bytes = s;
     return PIC_OK;
 }
@@ -409,54 +573,63 @@ int pic_batch_footprint(const pic_batch *b, size_t *bytes)
 int pic_batch_bind_memory(pic_batch *b, void *dev, size_t bytes)
 {
     if (!b || !dev) return PIC_EINVAL;
+    if (b->base) return PIC_ESTATE;
     size_t need = 0;
     pic_batch_footprint(b, &need);
     if (bytes < need) return PIC_ENOMEM;
     char *p = (char *)align_up((size_t)dev, 256);
     auto take = [&](size_t nb) { char *r = p; p += align_up(nb, 256); return r; };
-    b->base = (char *)dev;
     b->bytes = bytes;
-    b->d_runs = (RunDev *)take(b->n * sizeof(RunDev));
-    b->d_state = (RunState *)take(b->n * sizeof(RunState));
-    for (int i = 0; i < b->nsp; ++i) b->d_bm_part[i] = (BlockMap *)take(table_bytes(b->bm_part[i]));
-    b->d_bm_cell = (BlockMap *)take(table_bytes(b->bm_cell));
-    b->d_bm_key = (BlockMap *)take(table_bytes(b->bm_key));
-    b->d_bm_tile = (BlockMap *)take(table_bytes(b->bm_tile));
-    b->d_items = (int2 *)take(table_bytes(b->items));
+    b->d_counts = (Counts *)take(sizeof(Counts));
+    b->d_runs = (RunDev *)take(cap_bytes<RunDev>(b->cap_runs));
+    b->d_state = (RunState *)take(cap_bytes<RunState>(b->cap_runs));
+    for (int i = 0; i < b->nsp; ++i) b->d_bm_part[i] = (BlockMap *)take(cap_bytes<BlockMap>(b->cap_part[i]));
+    b->d_bm_cell = (BlockMap *)take(cap_bytes<BlockMap>(b->cap_cell));
+    b->d_bm_key = (BlockMap *)take(cap_bytes<BlockMap>(b->cap_key));
+    b->d_bm_tile = (BlockMap *)take(cap_bytes<BlockMap>(b->cap_tile));
+    b->d_items = (int2 *)take(cap_bytes<int2>(b->cap_tile));
     b->d_counter = (int *)take(sizeof(int));
-    for (int r = 0; r < b->n; ++r) {
-        const int e = ctx_prepare_batch(b->ctx[r]);
-        if (e != PIC_OK) return e;
-    }
-    // descriptors and tables
-    std::vector<RunDev> rds(b->n);
-    std::vector<RunState> sts(b->n);
-    for (int r = 0; r < b->n; ++r) {
-        rds[r] = *ctx_rundev(b->ctx[r]);
-        sts[r].age = ctx_age(b->ctx[r]);
-        sts[r].interval = ctx_sort_interval(b->ctx[r]);
-        sts[r].due = 0;
-        sts[r].kt = ctx_rundev(b->ctx[r])->l + 2;
-    }
-    cudaStream_t st = b->stream;
-    auto up = [&](void *dst, const void *src, size_t nb) {
-        return nb == 0 || cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, st) == cudaSuccess;
-    };
-    bool ok = up(b->d_runs, rds.data(), rds.size() * sizeof(RunDev))
-              && up(b->d_state, sts.data(), sts.size() * sizeof(RunState));
-    for (int i = 0; i < b->nsp && ok; ++i)
-        ok = up(b->d_bm_part[i], b->bm_part[i].data(), b->bm_part[i].size() * sizeof(BlockMap));
-    ok = ok && up(b->d_bm_cell, b->bm_cell.data(), b->bm_cell.size() * sizeof(BlockMap))
-         && up(b->d_bm_key, b->bm_key.data(), b->bm_key.size() * sizeof(BlockMap))
-         && up(b->d_bm_tile, b->bm_tile.data(), b->bm_tile.size() * sizeof(BlockMap))
-         && up(b->d_items, b->items.data(), b->items.size() * sizeof(int2));
-    if (!ok || cudaStreamSynchronize(st) != cudaSuccess) return PIC_ECUDA;
-    if (cudaFuncSetAttribute(k_b_gpp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem)
-        != cudaSuccess)
+    // launch shapes, fixed for the life of the batch (and of its graph)
+    int dev_id = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev_id) != cudaSuccess
+        || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess)
         return PIC_ECUDA;
+    // the attribute is the function's limit, shared by every batch: set it to the largest the
+    // device allows beside the kernel's static shared memory, so that no batch lowers it under
+    // another batch's captured graph
+    int optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_id) != cudaSuccess
+        || cudaFuncGetAttributes(&fa, k_b_gpp) != cudaSuccess) {
+        cudaGetLastError();
+        return PIC_ECUDA;
+    }
+    const int maxdyn = optin - (int)fa.sharedSizeBytes;
+    if (maxdyn < (int)b->smem) return PIC_EINVAL;
+    if (cudaFuncSetAttribute(k_b_gpp, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn)
+        != cudaSuccess) {
+        cudaGetLastError();
+        return PIC_ECUDA;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_gpp, 256, b->smem);
+    auto clampg = [](int64_t want, int64_t cap) { return (int)std::max<int64_t>(1, std::min(want, cap)); };
+    b->grid_runs = clampg((b->cap_runs + 127) / 128, 1 << 20);
+    int64_t maxpart = 1;
+    for (int i = 0; i < b->nsp; ++i) maxpart = std::max(maxpart, b->cap_part[i]);
+    b->grid_stage = clampg(std::max(maxpart, std::max(b->cap_cell, b->cap_key)), (int64_t)sms * 8);
+    b->grid_tile = clampg(b->cap_tile, (int64_t)sms * 2);
+    b->grid_gpp = clampg(b->cap_tile, (int64_t)sms * std::max(per_sm, 1));
+    b->base = (char *)dev;
     if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)
         return PIC_ECUDA;
-    return PIC_OK;
+    Tables t;
+    for (int s = 0; s < b->nsp; ++s) t.part[s].swap(b->bm_part[s]);
+    t.cell.swap(b->bm_cell);
+    t.key.swap(b->bm_key);
+    t.tile.swap(b->bm_tile);
+    t.items.swap(b->items);
+    std::vector<pic_ctx *> runs = b->ctx;
+    return upload(b, runs.data(), (int)runs.size(), t);
 }
 
 int pic_batch_alloc(pic_batch *b)
@@ -467,9 +640,23 @@ int pic_batch_alloc(pic_batch *b)
     void *p = nullptr;
     if (cudaMalloc(&p, need) != cudaSuccess) return PIC_ENOMEM;
     const int r = pic_batch_bind_memory(b, p, need);
-    if (r != PIC_OK) { cudaFree(p); return r; }
+    if (r != PIC_OK) { cudaFree(p); b->base = nullptr; return r; }
     b->owns = true;
     return PIC_OK;
+}
+
+int pic_batch_set_runs(pic_batch *b, pic_ctx *const *runs, int n)
+{
+    if (!b || n < 0 || (n > 0 && !runs)) return PIC_EINVAL;
+    if (!b->base) return PIC_ESTATE;
+    Tables t;
+    int e = build_tables(runs, n, b->nsp, b->run_stream, t);
+    if (e != PIC_OK) return e;
+    if (!tables_fit(b, t, n)) return PIC_ENOMEM;
+    int32_t err = 0;
+    e = write_back(b, &err);
+    if (e != PIC_OK) return e;
+    return upload(b, runs, n, t);
 }
 
 int pic_batch_step(pic_batch *b, int nsteps)
@@ -498,8 +685,8 @@ int pic_batch_step(pic_batch *b, int nsteps)
     return PIC_OK;
 }
 
-// Time of the persistent particle kernel in one replayed step (ms): runs one step with event
-// records around it (outside the captured graph).
+// Time of the persistent particle kernel in one step (ms): runs one step with event records
+// around it (outside the captured graph).
 int pic_batch_time_gpp(pic_batch *b, double *ms)
 {
     if (!b || !ms) return PIC_EINVAL;
@@ -530,22 +717,9 @@ int pic_batch_sync(pic_batch *b)
 {
     if (!b) return PIC_EINVAL;
     if (!b->base) return PIC_ESTATE;
-    std::vector<RunDev> rds(b->n);
-    std::vector<RunState> sts(b->n);
-    if (cudaMemcpyAsync(rds.data(), b->d_runs, b->n * sizeof(RunDev), cudaMemcpyDeviceToHost,
-                        b->stream) != cudaSuccess
-        || cudaMemcpyAsync(sts.data(), b->d_state, b->n * sizeof(RunState), cudaMemcpyDeviceToHost,
-                           b->stream) != cudaSuccess
-        || cudaStreamSynchronize(b->stream) != cudaSuccess)
-        return PIC_ECUDA;
-    for (int r = 0; r < b->n; ++r) ctx_after_batch(b->ctx[r], rds[r], sts[r].age, b->steps_since_sync);
-    b->steps_since_sync = 0;
     int32_t err = 0;
-    for (int r = 0; r < b->n; ++r) {
-        int32_t e = 0;
-        if (cudaMemcpy(&e, rds[r].err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
-        err |= e;
-    }
+    const int e = write_back(b, &err);
+    if (e != PIC_OK) return e;
     if (err & PIC_ERR_NONFINITE) return PIC_ENAN;
     if (err & PIC_ERR_OUTSIDE_TILE) return PIC_EOVERFLOW;
     return PIC_OK;
@@ -556,7 +730,7 @@ void pic_batch_destroy(pic_batch *b)
     if (!b) return;
     if (b->base) {
         cudaStreamSynchronize(b->stream);
-        if (b->steps_since_sync) pic_batch_sync(b);
+        if (b->steps_since_sync) write_back(b, nullptr);
         cudaEventDestroy(b->ev0);
         cudaEventDestroy(b->ev1);
     }

@@ -6,11 +6,11 @@ namespace pic {
 
 namespace {
 
-template <int L, int KT>
+template <int L, int KT, bool DET>
 __global__ void __launch_bounds__(256, 2) k_gpp2d(const __grid_constant__ RunDev rd)
 {
     extern __shared__ __align__(16) char smem[];
-    tile_2d<L, KT, float>(rd, smem, blockIdx.x);
+    tile_2d<L, KT, float, DET>(rd, smem, blockIdx.x);
 }
 
 template <int L, int KT>
@@ -24,10 +24,11 @@ cudaError_t go(const RunDev &rd, cudaStream_t st)
 {
     if (rd.dim == 2) {
         const size_t smem = stage2d_bytes<float>(rd.reg_nodes, rd.l, true, rd.det != 0);
-        cudaError_t e = cudaFuncSetAttribute(k_gpp2d<L, KT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto k = rd.det ? k_gpp2d<L, KT, true> : k_gpp2d<L, KT, false>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
-        k_gpp2d<L, KT><<<(unsigned)rd.ntiles, 256, smem, st>>>(rd);
+        k<<<(unsigned)rd.ntiles, 256, smem, st>>>(rd);
     } else {
         k_gpp3d<L, KT><<<(unsigned)rd.ntiles, 128, 0, st>>>(rd);
     }

@@ -445,8 +445,10 @@ __device__ __forceinline__ void gather_2d_x2(const Stage2D<float> &st, const Axi
 }
 
 // One particle per lane, 2D, staged tile.  Called by all 32 lanes of a warp together (the
-// deposit is warp-collective); lanes with act == false carry no particle.
-template <int L, int KT, typename R>
+// deposit is warp-collective); lanes with act == false carry no particle.  DET: a
+// deterministic run (RunDev::det), whose current goes in as fixed-point words; a template
+// parameter so that the default instances carry none of its code.
+template <int L, int KT, typename R, bool DET = false>
 __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
                                             const Stage2D<R> &st, int64_t p, bool act, int x0,
                                             int y0)
@@ -619,7 +621,7 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
             // which would need an FP32 -> FP64 conversion per node)
             const bool wide = __any_sync(0xffffffffu, act && Sy.wide);
             if (!act) {
-            } else if (h.det) {
+            } else if (DET) {
                 if (wide)
                     deposit_lane<L, R, true, true>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay,
                                                    Bx, Sy, h.dinv32);
@@ -746,7 +748,7 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
                         if (gx >= RX || gy >= h.RY) continue;
                         const int node = gy * RX + gx;
                         const R a = o1[2 * i + j], b = o2[2 * i + j];
-                        if (h.det) {  // fixed-point words: the warps' sums commute exactly
+                        if (DET) {  // fixed-point words: the warps' sums commute exactly
                             if (role == 0) {
                                 if (a != R(0)) atomicAdd(st.q1 + node, det_word32(a, h.dinv32));
                                 if (b != R(0)) atomicAdd(st.q2 + node, det_word32(b, h.dinv32));
@@ -772,7 +774,7 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         const bool wide = __any_sync(0xffffffffu, act && Sy.wide);
         const int gx0 = x0 - h.pre0 + jx0, gy0 = y0 - h.pre1 + jy0;
         if (!act) {
-        } else if (h.det) {
+        } else if (DET) {
             if (wide)
                 deposit_lane_global<L, R, Hot2D, true, true>(h, gx0, gy0, kx, ky, kz, px, py, Ax,
                                                              Ay, Bx, Sy);
@@ -803,11 +805,11 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
 }
 
 // All particles of one tile (both species), 2D.  tt_shared as in stage2d_carve.
-template <int L, int KT, typename R>
+template <int L, int KT, typename R, bool DET = false>
 __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
                         const TTable *tt_shared = nullptr)
 {
-    Stage2D<R> st = stage2d_carve<R>(smem, rd.reg_nodes, tt_shared, rd.det != 0);
+    Stage2D<R> st = stage2d_carve<R>(smem, rd.reg_nodes, tt_shared, DET);
     const int tx = (int)(tile % rd.ntile[0]);
     const int ty = (int)(tile / rd.ntile[0]);
     const int x0 = tx * rd.tile[0], y0 = ty * rd.tile[1];
@@ -827,7 +829,7 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
                 if constexpr (sizeof(R) == 8 && L <= 3)
                     if (hs.wc_mode == 2) prefetch_weights<L>(hs, p + blockDim.x);
             }
-            particle_2d<L, KT, R>(h, hs, st, p, p < b, x0, y0);
+            particle_2d<L, KT, R, DET>(h, hs, st, p, p < b, x0, y0);
         }
         if constexpr (sizeof(R) == 4) {  // the FP64 form deposits to global memory directly
             __syncthreads();

@@ -257,7 +257,14 @@ class Served:
 
 
 class Server:
-    """Continuous-batching request loop (see module docstring)."""
+    """Continuous-batching request loop (see module docstring).
+
+    The batchable runs live in ONE long-lived pic batch whose run set is replaced with
+    pic_batch_set_runs when runs arrive or finish: the batch's launches walk device tables of
+    any set that fits its capacities, so its captured CUDA graph is kept (the batch is rebuilt,
+    with doubled capacities, only when a set outgrows them).  Each chunk waits for the streams
+    it used (events), not for the whole device.  The batch's device tables count against the
+    memory budget."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 10,
                  tuner: Optional[Autotuner] = None, keep_runs: bool = False):
@@ -270,88 +277,176 @@ class Server:
         self.peak_bytes = 0
         self.max_active = 0
         self.chunks = 0
+        self.batch_builds = 0
+        self.set_changes = 0
+
+    @staticmethod
+    def _capacity(runs, factor=2.0):
+        """Batch capacities: `factor` times the totals of `runs`, and the largest batched stage
+        that still lets two CTAs share an SM."""
+        cap = pic.pic_batch_capacity()
+        n = len(runs)
+        cap.runs = max(8, int(factor * n))
+        parts = cells = tiles = keys = 0
+        stage = 0
+        for r in runs:
+            parts = max(parts, max(r.counts))
+            cells += r.ncell
+            tiles += r.ntiles
+            keys += r.ntiles * r.tile[0] * r.tile[1] * r.tile[2]
+            _, batched, two = pic.pic_smem_info(r.ctx)
+            stage = max(stage, batched, two)
+        per_species = sum(max(r.counts) for r in runs)
+        cap.particles_per_species = int(factor * max(per_species, 1 << 20))
+        cap.cells = int(factor * max(cells, 1 << 18))
+        cap.tiles = int(factor * max(tiles, 1 << 12))
+        cap.keys = int(factor * max(keys, 1 << 19))
+        cap.stage_bytes = int(stage)
+        return cap
 
     def serve(self, requests: List[Request]) -> List[Served]:
+        """Serve the requests at their arrival times; returns one Served record per request.
+
+        Lanes advance independently: the batch (every batchable run, one graph replay per step)
+        and every other run on its own side stream.  A lane gets its next chunk of steps as soon
+        as its previous chunk's event has completed, so small runs never wait for a large run's
+        steps; run sets change, and finished runs are reported, at a lane's chunk boundary."""
         import torch
         pending = sorted(requests, key=lambda r: r.arrival)
-        active = {}      # rid -> dict(run, req, done_steps, admitted, bytes, stream)
+        active = {}      # rid -> dict(run, req, done, admitted, bytes, stream, history)
         used = 0
         batch = None
+        batch_bytes = 0
         batch_ids: Tuple[int, ...] = ()
+        batch_inflight = None   # (event, steps) of the batch lane's chunk on the GPU
+        side_inflight = {}      # rid -> (event, steps) of a side run's chunk
         t0 = time.perf_counter()
         side = [torch.cuda.Stream() for _ in range(4)]  # runs the batch does not take
+        main = torch.cuda.current_stream()
+
+        def install(ids):
+            """Make the batch hold the runs `ids` (a new batch when none fits)."""
+            nonlocal batch, batch_bytes, batch_ids, used
+            runs = [active[r]["run"] for r in ids]
+            if batch is not None and batch.set_runs(runs):
+                self.set_changes += 1
+                batch_ids = ids
+                return
+            if batch is not None:
+                batch.set_runs([])   # write every run's state back before the batch goes
+                batch.close()
+                used -= batch_bytes
+                batch, batch_bytes = None, 0
+            if runs:
+                batch = pic.Batch(runs, capacity=self._capacity(runs))
+                batch_bytes = int(batch.mem.numel())
+                used += batch_bytes
+                self.peak_bytes = max(self.peak_bytes, used)
+                self.batch_builds += 1
+            batch_ids = ids
+
+        def chunk_steps(ids):
+            k = min(self.chunk, min(active[r]["req"].steps - active[r]["done"] for r in ids))
+            for r in ids:  # stop at the next field-energy sample
+                ev = active[r]["req"].record_every
+                if ev > 0:
+                    k = min(k, ev - active[r]["done"] % ev)
+            return k
+
+        def finish(rid):
+            nonlocal used
+            a = active.pop(rid)
+            d = a["run"].diag()
+            done_t = time.perf_counter() - t0
+            self.results.append(Served(rid, a["req"].arrival, a["admitted"], done_t,
+                                       a["req"].steps, a["req"].particles, a["req"].dim, d,
+                                       a["history"]))
+            used -= a["bytes"]
+            if self.keep_runs:
+                self.finished_runs[rid] = a["run"]
+            else:
+                a["run"].close()
+
+        def recorded(a):
+            ev = a["req"].record_every
+            return ev > 0 and a["done"] % ev == 0
+
         while pending or active:
+            progressed = False
             now = time.perf_counter() - t0
             # admit arrived requests while the budget has room (arrival order)
             while pending and pending[0].arrival <= now:
                 req = pending[0]
-                need = footprint_estimate(req)
+                need = footprint_estimate(req, tuner=self.tuner)
                 if used + need > self.budget and active:
                     break
                 pending.pop(0)
                 stream = None if req.batchable else side[req.rid % len(side)]
                 run = make_run(req, tuner=self.tuner, stream=stream)
                 active[req.rid] = {"run": run, "req": req, "done": 0, "bytes": need,
-                                   "admitted": time.perf_counter() - t0, "history": []}
+                                   "admitted": time.perf_counter() - t0, "history": [],
+                                   "stream": run.stream}
                 if req.record_every > 0:
                     self._record(active[req.rid])
                 used += need
                 self.peak_bytes = max(self.peak_bytes, used)
-            if not active:
-                time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
-                continue
-            # the batchable runs form the batch; rebuild it when the set changed
-            ids2d = tuple(sorted(r for r, a in active.items() if a["req"].batchable))
-            if ids2d != batch_ids:
-                if batch is not None:
-                    batch.sync()
-                    batch.close()
-                batch = pic.Batch([active[r]["run"] for r in ids2d]) if ids2d else None
-                batch_ids = ids2d
+                progressed = True
             self.max_active = max(self.max_active, len(active))
-            self.chunks += 1
-            # one chunk: as many steps as the nearest-finishing active run still needs
-            k = min(self.chunk, min(a["req"].steps - a["done"] for a in active.values()))
-            for a in active.values():  # stop at the next field-energy sample
-                ev = a["req"].record_every
-                if ev > 0:
-                    k = min(k, ev - a["done"] % ev)
-            if batch is not None:
-                batch.step(k)
-            for rid, a in active.items():
-                if not a["req"].batchable:
-                    a["run"].step(k)
-            torch.cuda.synchronize()
-            for a in active.values():
-                a["done"] += k
-            recording = [a for a in active.values()
-                         if a["req"].record_every > 0 and a["done"] % a["req"].record_every == 0]
-            # a batched sort swaps a run's particle buffers in the batch's device copy of its
-            # descriptor only: write the batch state back before reading a batched run's state
-            if batch is not None and any(a["req"].rid in batch_ids for a in recording):
-                batch.sync()
-            for a in recording:
-                self._record(a)
-            finished = [r for r, a in active.items() if a["done"] >= a["req"].steps]
-            if finished:
-                if batch is not None:
-                    batch.sync()
-                    if any(r in batch_ids for r in finished):
-                        batch.close()
-                        batch = None
-                        batch_ids = ()
-                for rid in finished:
-                    a = active.pop(rid)
-                    d = a["run"].diag()
-                    done_t = time.perf_counter() - t0
-                    self.results.append(Served(rid, a["req"].arrival, a["admitted"], done_t,
-                                               a["req"].steps, a["req"].particles, a["req"].dim, d,
-                                               a["history"]))
-                    used -= a["bytes"]
-                    if self.keep_runs:
-                        self.finished_runs[rid] = a["run"]
-                    else:
-                        a["run"].close()
+            # the batch lane: account its finished chunk, change its run set, issue the next
+            if batch_inflight is None or batch_inflight[0].query():
+                if batch_inflight is not None:
+                    for r in batch_ids:
+                        active[r]["done"] += batch_inflight[1]
+                    batch_inflight = None
+                    rec = [active[r] for r in batch_ids if recorded(active[r])]
+                    fin = [r for r in batch_ids if active[r]["done"] >= active[r]["req"].steps]
+                    if rec and not fin:
+                        batch.sync()
+                    if fin:  # the finished runs leave the batch (their state written back)
+                        install(tuple(r for r in batch_ids if r not in fin))
+                    for a in rec:
+                        self._record(a)
+                    for r in fin:
+                        finish(r)
+                    progressed = True
+                ids2d = tuple(sorted(r for r, a in active.items() if a["req"].batchable))
+                if ids2d != batch_ids:
+                    install(ids2d)
+                if batch is not None and batch_ids:
+                    k = chunk_steps(batch_ids)
+                    batch.step(k)
+                    ev = torch.cuda.Event()
+                    ev.record(main)
+                    batch_inflight = (ev, k)
+                    self.chunks += 1
+                    progressed = True
+            # the side lanes: every other run on its own stream
+            for rid in [r for r, a in active.items() if not a["req"].batchable]:
+                a = active[rid]
+                inf = side_inflight.get(rid)
+                if inf is not None and not inf[0].query():
+                    continue
+                if inf is not None:
+                    a["done"] += inf[1]
+                    del side_inflight[rid]
+                    if recorded(a):
+                        self._record(a)
+                    if a["done"] >= a["req"].steps:
+                        finish(rid)
+                        progressed = True
+                        continue
+                k = chunk_steps([rid])
+                a["run"].step(k)
+                ev = torch.cuda.Event()
+                ev.record(a["stream"])
+                side_inflight[rid] = (ev, k)
+                self.chunks += 1
+                progressed = True
+            if not progressed:
+                if not active and pending:
+                    time.sleep(max(0.0, min(0.01, pending[0].arrival - (time.perf_counter() - t0))))
+                else:
+                    time.sleep(0.0002)
         if batch is not None:
             batch.close()
         return self.results

@@ -224,3 +224,56 @@ def test_batch_tiles_keep_two_ctas_per_sm():
             assert batched <= two, (l, dt, tile, t, batched, two)
             if t == tile:
                 assert si == 4
+
+
+def test_batch_set_runs_keeps_the_graph_and_matches_alone():
+    """Runs join and leave a batch between steps (pic_batch_set_runs): the batch keeps its
+    captured graph (its launches walk device tables of any set within its capacities), and
+    every run evolves exactly as it does alone, through sorts, over the steps it spent in the
+    batch and out of it."""
+    specs = RUNS[:4]
+    alone = [make(sp)[1] for sp in specs]
+    mixed = [make(sp)[1] for sp in specs]
+    for r in alone:
+        r.step(20)
+    cap = pic.pic_batch_capacity()
+    cap.runs = 8
+    cap.particles_per_species = 4 * max(max(r.counts) for r in mixed)
+    cap.cells = 4 * sum(r.ncell for r in mixed)
+    cap.tiles = 4 * sum(r.ntiles for r in mixed)
+    cap.keys = 4 * sum(r.ntiles * r.tile[0] * r.tile[1] for r in mixed)
+    cap.stage_bytes = max(pic.pic_smem_info(r.ctx)[1] for r in mixed)
+    b = pic.Batch(mixed[:2], capacity=cap)
+    b.step(5)                              # runs 0, 1: 5 steps (graph captured)
+    assert b.set_runs(mixed[1:4])          # run 0 leaves, 2 and 3 join
+    mixed[0].step(15)                      # run 0 goes on alone
+    b.step(7)                              # runs 1, 2, 3: 7 steps
+    assert b.set_runs([mixed[3], mixed[0]])  # 1 and 2 leave, 0 comes back
+    mixed[1].step(8)
+    mixed[2].step(13)
+    b.step(8)                              # runs 3, 0: 8 steps
+    assert b.set_runs([])
+    mixed[3].step(5)                       # run 3: 7 + 8 + 5 = 20 steps
+    for r in mixed:
+        r.sync()
+    for i in (1, 2):
+        assert mixed[i].diag()["step"] == 20
+    for i in (1, 2):  # identical step sequences: equal to the alone runs at FP32 round-off growth
+        for c in range(9):
+            assert rel(mixed[i].field(c), alone[i].field(c)) < 1e-4, (i, c)
+    assert mixed[0].diag()["step"] == 28 and mixed[3].diag()["step"] == 20
+    alone[0].step(8)
+    for i in (0, 3):
+        for c in range(9):
+            assert rel(mixed[i].field(c), alone[i].field(c)) < 1e-4, (i, c)
+        assert mixed[i].diag()["error_flags"] == 0
+    # a set beyond the capacities is refused and the batch keeps its runs; a run may not be
+    # in a set twice
+    big = [make(sp)[1] for sp in RUNS + RUNS]
+    assert not b.set_runs(big)
+    with pytest.raises(pic.PicError) as e:
+        b.set_runs([big[0], big[0]])
+    assert e.value.status == pic.PIC_EINVAL
+    b.close()
+    for r in alone + mixed + big:
+        r.close()

@@ -106,6 +106,7 @@ DET_CASES = [
 
 
 def _det_run(case, f, seed=41):
+    """A deterministic run of the case from the oracle-drawn plasma, fields f set."""
     grid, cdt, l, ppc, prec = case
     dim = len(grid)
     wl = plasma.pair_plasma(grid, (1.0,) * dim, cdt, l, 1, 8.0, 0.1, ppc, omega_p=0.3, seed=seed)
@@ -148,13 +149,8 @@ def test_deterministic_step_matches_oracle(case):
     dim = len(grid)
     shape = (grid[2] if dim == 3 else 1, grid[1], grid[0])
     f = smooth_fields(shape, 0.05, seed=29)
-    wl, run = _det_run(case, f, seed=43)
-    orc = oracle.Sim(wl.grid[:dim], wl.dx[:dim], wl.dt, wl.l, wl.scheme)
-    for i, s in enumerate(wl.species):
-        x, u, _ = run.particles(i)
-        orc.add_species(s.q, s.m, s.w, x, u)
-    for c, a in enumerate(f):
-        orc.set_field(c, a)
+    wl = plasma.pair_plasma(grid, (1.0,) * dim, cdt, l, 1, 8.0, 0.1, ppc, omega_p=0.3, seed=43)
+    run, orc = make_pair(wl, prec, f, deterministic=True)
     run.step(1)
     orc.step(1)
     compare_state(run, orc, 2, FP64_TOL if prec == pic.PIC_FP64 else FP32_TOL, case)

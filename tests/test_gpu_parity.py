@@ -85,7 +85,7 @@ def host_packed(x, u, grid, dx, dim, prec):
     return cells, x, u
 
 
-def make_pair(wl, prec, fields=None, tile=None, sort_interval=0, solver=0):
+def make_pair(wl, prec, fields=None, tile=None, sort_interval=0, solver=0, deterministic=False):
     """Same initial state on the GPU (libpic) and in the oracle, both from the input arrays:
     the GPU loads them (packing and tile-sorting), the oracle takes them in input order as the
     load stores them (the FP32 rounding done on the host).  run.orc_perm[s] is the oracle's
@@ -93,7 +93,8 @@ def make_pair(wl, prec, fields=None, tile=None, sort_interval=0, solver=0):
     sorted position k is the oracle's particle orc_perm[s][k]."""
     caps = [int(s.x.shape[1]) for s in wl.species]
     run = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps,
-                  tile=tile, sort_interval=sort_interval, solver=solver)
+                  tile=tile, sort_interval=sort_interval, solver=solver,
+                  deterministic=deterministic)
     for i, s in enumerate(wl.species):
         run.load(i, s.q, s.m, s.w, s.x, s.u)
     dim = wl.dim

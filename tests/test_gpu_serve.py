@@ -37,6 +37,9 @@ def _requests():
                                precision=pic.PIC_FP64, record_every=3))
     reqs.append(engine.Request(rid=n + 2, grid=(64, 32, 1), dt=0.4, l=2, gamma=25.0, u_th=0.01,
                                ppc=8, steps=18, arrival=0.0, seed=202, solver=pic.PIC_SOLVER_M4))
+    # a batched request that records its history: its state is read between batched sorts
+    reqs.append(engine.Request(rid=n + 3, grid=(80, 40, 1), dt=0.3, l=3, gamma=20.0, u_th=0.01,
+                               ppc=16, steps=24, arrival=0.01, seed=203, record_every=4))
     return reqs
 
 
@@ -56,9 +59,21 @@ def test_served_results_equal_alone():
         if q.record_every:
             assert [h[0] for h in r.history] == list(range(0, q.steps + 1, q.record_every))
             assert all(h[3] > 0.0 for h in r.history)
+    by_id = {r.rid: r for r in res}
     for req in reqs:
         alone = engine.make_run(req)
-        alone.step(req.steps)
+        if req.record_every:
+            # the history of the served run equals the same run's alone at the same steps
+            hist = by_id[req.rid].history
+            for k in range(len(hist)):
+                if k:
+                    alone.step(req.record_every)
+                d = alone.diag()
+                assert hist[k][0] == d["step"]
+                assert abs(hist[k][2] - d["field_energy"]) <= 1e-3 * max(d["field_energy"], 1e-30), (req.rid, k)
+                assert abs(hist[k][3] - d["kinetic_energy"]) <= 1e-5 * d["kinetic_energy"], (req.rid, k)
+        else:
+            alone.step(req.steps)
         mixed = srv.finished_runs[req.rid]
         for c in range(9):
             assert rel(mixed.field(c), alone.field(c)) < MULTI_STEP_TOL, (req.rid, c)
