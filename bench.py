@@ -582,9 +582,9 @@ def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
     lat2d = [r.latency for r in res if r.dim == 2]
     slow2d = [r.latency / alone[r.rid] for r in res if r.dim == 2]
     work = sum(r.particles * r.steps for r in res)
-    # the plain FP64 single-run form on a sample of the requests, alone
+    # the plain FP64 single-run form on a sample of the 2D requests, alone
     alone64 = []
-    for r in reqs[:6]:
+    for r in [q for q in reqs if q.dim == 2][:6]:
         run = engine.make_run(r, precision=pic.PIC_FP64)
         torch.cuda.synchronize()
         n = min(r.steps, alone_steps)

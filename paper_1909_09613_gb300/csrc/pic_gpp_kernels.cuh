@@ -32,14 +32,14 @@ constexpr int kTileWarps = 8;
 // start at most SXM nodes apart along x and SYM along y is a sum over lanes of outer products
 // (J1 = sum px (x) Ay, J2 = sum Ax (x) py, J3 = sum Ax (x) S0y + Bx (x) DSy, in the notation of
 // particle_2d) on a common NX x NY block of nodes.  Every lane writes its factor vectors,
-// shifted into the block, as a record of float4 pairs; lane t then sums a 2 x 2 node block of
-// J1 and J2 (the first PX*PY lanes) or of J3 (the next PX*PY) over the 32 records.
-//   x part of a record, per x pair p (nodes 2p, 2p+1):
-//     (px, px, Ax, Ax) then (Ax, Ax, Bx, Bx)
-//   y part, per y pair q (nodes 2q, 2q+1):
-//     (Ay, Ay, py, py) then (S0y, S0y, DSy, DSy)
-// RS (floats per record) is a multiple of 4 with RS / 4 odd, so that the float4 stores of 8
-// consecutive lanes fall in distinct banks.
+// shifted into the block, as a record (x part: px, Ax, Bx over NX nodes; y part: Ay, py, S0y,
+// DSy over NY nodes); then each lane sums, over the 32 records, one term (J1, J2, or one of the
+// two products of J3) on a 2 x BY sub-block of nodes (BY = NY / 2): per record one 64-bit load
+// of its two x factors and BY 32-bit loads of its y factors, all of them shared-memory
+// broadcasts within the record.  That is 2 + BY wavefronts per record for the warp, against 8
+// for two 128-bit loads per lane (a 128-bit load takes a wavefront per quarter warp): the sums
+// are bound by shared-memory wavefronts, not by issue.  RS (floats per record) is a multiple of
+// 4 with RS / 4 odd, so that the float4 stores of 8 consecutive lanes fall in distinct banks.
 template <int L>
 struct DepFrame {
     // Along y the windows of a group start at most SYM rows apart: for odd l a particle's
@@ -50,9 +50,13 @@ struct DepFrame {
     static constexpr int PX = (L + 2 + 2 + 1) / 2, PY = (L + 2 + SYM + 1) / 2;
     static constexpr int NX = 2 * PX, NY = 2 * PY;
     static constexpr int SXM = NX - (L + 2);
-    static constexpr int RS0 = 8 * (PX + PY);
-    static constexpr int RS = ((RS0 / 4) % 2 == 0) ? RS0 + 4 : RS0;
-    static_assert(2 * PX * PY <= 32, "one lane per 2 x 2 node block and component group");
+    static constexpr int BY = NY / 2;            // y nodes of a lane's sub-block
+    static constexpr int NBT = (NX / 2) * 2;     // sub-blocks of one term
+    static constexpr int XS = 3 * NX, YS = 4 * NY;
+    static constexpr int RS0 = XS + YS;
+    static constexpr int RS1 = (RS0 + 3) / 4 * 4;
+    static constexpr int RS = ((RS1 / 4) % 2 == 0) ? RS1 + 4 : RS1;
+    static_assert(4 * NBT <= 32, "one lane per sub-block and term");
 };
 
 // Floats of one warp's deposit records for spline order l (host-side sizing).
@@ -636,13 +640,13 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
         } else {
         float *rec = st.rec + (threadIdx.x >> 5) * (32 * FR::RS);
         float4 *mine = (float4 *)(rec + lane * FR::RS);
-        // this lane's output block: role 0 sums J1 and J2, role 1 sums J3, role 2 idles
-        constexpr int NB = FR::PX * FR::PY;
-        const int role = lane < NB ? 0 : (lane < 2 * NB ? 1 : 2);
-        const int rl = lane - (role == 1 ? NB : 0);
-        const int bp = role == 2 ? 0 : rl % FR::PX, bq = role == 2 ? 0 : rl / FR::PX;
-        const int xo = 8 * bp + (role == 1 ? 4 : 0);
-        const int yo = 8 * FR::PX + 8 * bq + (role == 1 ? 4 : 0);
+        // this lane's sum: term t (0: J1 = px Ay, 1: J2 = Ax py, 2: J3 from Ax S0y, 3: J3 from
+        // Bx DSy; lanes past the four terms idle) on the sub-block (bx, by) of the frame
+        const int term = lane / FR::NBT, sb = lane % FR::NBT;
+        const int bx = sb % (FR::NX / 2), by = sb / (FR::NX / 2);
+        const bool sums = term < 4;
+        const int xo = sums ? (term == 0 ? 0 : (term == 3 ? 2 * FR::NX : FR::NX)) + 2 * bx : 0;
+        const int yo = sums ? FR::XS + term * FR::NY + FR::BY * by : FR::XS;
         // passes over groups of lanes that fit one common block (usually one pass; a warp that
         // straddles the end of a tile row takes two)
         bool todo = act;
@@ -656,15 +660,17 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
             const int ox = in ? jx0 - mnx : 0, oy = in ? jy0 - mny : 0;
             const R gin = in ? R(1) : R(0);
             __syncwarp();  // the previous pass has read every record
-            // x part: block node A holds this lane's window node A - ox (zero outside it); the
-            // factors are scaled first, then shifted by ox = 0..SXM in two steps (ox & 1, ox & 2)
-            R sp[L + 2], sa[L + 2], sb[L + 2];
+            // the record: block node A holds this lane's window node A - ox (zero outside it);
+            // the x factors are scaled first, then shifted by ox = 0..SXM in two steps (ox & 1,
+            // ox & 2); the y factors are shifted by oy (0 when SYM = 0)
+            float r[FR::RS1];
+            R sp[L + 2], sa[L + 2], sb2[L + 2];
             const R gkx = gin * kx;
 #pragma unroll
             for (int k = 0; k < L + 2; ++k) {
                 sp[k] = (k <= L) ? gkx * px[k] : R(0);
                 sa[k] = gin * Ax[k];
-                sb[k] = gin * Bx[k];
+                sb2[k] = gin * Bx[k];
             }
             const bool sh1 = (ox & 1) != 0, sh2 = (ox & 2) != 0;
             R tp[L + 3], ta[L + 3], tb[L + 3];
@@ -672,28 +678,20 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
             for (int k = 0; k < L + 3; ++k) {
                 const R p0 = (k < L + 2) ? sp[k] : R(0), p1 = (k >= 1) ? sp[k - 1] : R(0);
                 const R a0 = (k < L + 2) ? sa[k] : R(0), a1 = (k >= 1) ? sa[k - 1] : R(0);
-                const R b0 = (k < L + 2) ? sb[k] : R(0), b1 = (k >= 1) ? sb[k - 1] : R(0);
+                const R b0 = (k < L + 2) ? sb2[k] : R(0), b1 = (k >= 1) ? sb2[k - 1] : R(0);
                 tp[k] = sh1 ? p1 : p0;
                 ta[k] = sh1 ? a1 : a0;
                 tb[k] = sh1 ? b1 : b0;
             }
 #pragma unroll
-            for (int pp = 0; pp < FR::PX; ++pp) {
-                R pv[2], av[2], bv[2];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int A = 2 * pp + i;
-                    const R p0 = (A < L + 3) ? tp[A] : R(0), p2 = (A >= 2 && A - 2 < L + 3) ? tp[A - 2] : R(0);
-                    const R a0 = (A < L + 3) ? ta[A] : R(0), a2 = (A >= 2 && A - 2 < L + 3) ? ta[A - 2] : R(0);
-                    const R b0 = (A < L + 3) ? tb[A] : R(0), b2 = (A >= 2 && A - 2 < L + 3) ? tb[A - 2] : R(0);
-                    pv[i] = sh2 ? p2 : p0;
-                    av[i] = sh2 ? a2 : a0;
-                    bv[i] = sh2 ? b2 : b0;
-                }
-                mine[2 * pp] = make_float4(pv[0], pv[1], av[0], av[1]);
-                mine[2 * pp + 1] = make_float4(av[0], av[1], bv[0], bv[1]);
+            for (int A = 0; A < FR::NX; ++A) {
+                const R p0 = (A < L + 3) ? tp[A] : R(0), p2 = (A >= 2 && A - 2 < L + 3) ? tp[A - 2] : R(0);
+                const R a0 = (A < L + 3) ? ta[A] : R(0), a2 = (A >= 2 && A - 2 < L + 3) ? ta[A - 2] : R(0);
+                const R b0 = (A < L + 3) ? tb[A] : R(0), b2 = (A >= 2 && A - 2 < L + 3) ? tb[A - 2] : R(0);
+                r[A] = sh2 ? p2 : p0;
+                r[FR::NX + A] = sh2 ? a2 : a0;
+                r[2 * FR::NX + A] = sh2 ? b2 : b0;
             }
-            // y part: block node B holds window node B - oy (oy = 0 when SYM = 0)
             R ty[4][L + 2];  // Ay, ky py, kz S0y, kz DSy
 #pragma unroll
             for (int k = 0; k < L + 2; ++k) {
@@ -703,65 +701,56 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
                 ty[3][k] = kz * Sy.ds[k];
             }
 #pragma unroll
-            for (int qq = 0; qq < FR::PY; ++qq) {
-                R yv[4][2];
+            for (int Bn = 0; Bn < FR::NY; ++Bn) {
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int Bn = 2 * qq + i;
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) {
-                        const R v0 = (Bn <= L + 1) ? ty[f][Bn] : R(0);
-                        if constexpr (FR::SYM == 0) {
-                            yv[f][i] = v0;
-                        } else {
-                            const R v1 = (Bn >= 1 && Bn - 1 <= L + 1) ? ty[f][Bn - 1] : R(0);
-                            yv[f][i] = (oy == 1) ? v1 : v0;
-                        }
+                for (int f = 0; f < 4; ++f) {
+                    const R v0 = (Bn <= L + 1) ? ty[f][Bn] : R(0);
+                    if constexpr (FR::SYM == 0) {
+                        r[FR::XS + f * FR::NY + Bn] = v0;
+                    } else {
+                        const R v1 = (Bn >= 1 && Bn - 1 <= L + 1) ? ty[f][Bn - 1] : R(0);
+                        r[FR::XS + f * FR::NY + Bn] = (oy == 1) ? v1 : v0;
                     }
                 }
-                R *ay = yv[0], *pyv = yv[1], *s0 = yv[2], *d0 = yv[3];
-                mine[2 * FR::PX + 2 * qq] = make_float4(ay[0], ay[1], pyv[0], pyv[1]);
-                mine[2 * FR::PX + 2 * qq + 1] = make_float4(s0[0], s0[1], d0[0], d0[1]);
             }
-            __syncwarp();
-            // sum this lane's 2 x 2 node block over the 32 records
-            R o1[4] = {R(0), R(0), R(0), R(0)}, o2[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
+            for (int k = FR::RS0; k < FR::RS1; ++k) r[k] = 0.0f;
+#pragma unroll
+            for (int v = 0; v < FR::RS1 / 4; ++v)
+                mine[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+            __syncwarp();
+            // this lane's term on its 2 x BY sub-block, summed over the 32 records
+            R o[2][FR::BY];
+#pragma unroll
+            for (int k = 0; k < FR::BY; ++k) o[0][k] = o[1][k] = R(0);
+#pragma unroll 8
             for (int q = 0; q < 32; ++q) {
-                const float4 xv = *(const float4 *)(rec + q * FR::RS + xo);
-                const float4 yv = *(const float4 *)(rec + q * FR::RS + yo);
-                o1[0] += xv.x * yv.x;
-                o1[1] += xv.x * yv.y;
-                o1[2] += xv.y * yv.x;
-                o1[3] += xv.y * yv.y;
-                o2[0] += xv.z * yv.z;
-                o2[1] += xv.z * yv.w;
-                o2[2] += xv.w * yv.z;
-                o2[3] += xv.w * yv.w;
+                const float *rq = rec + q * FR::RS;
+                const float2 xv = *(const float2 *)(rq + xo);
+                R yv[FR::BY];
+#pragma unroll
+                for (int k = 0; k < FR::BY; ++k) yv[k] = rq[yo + k];
+#pragma unroll
+                for (int k = 0; k < FR::BY; ++k) {
+                    o[0][k] += xv.x * yv[k];
+                    o[1][k] += xv.y * yv[k];
+                }
             }
-            if (role != 2) {
+            if (sums) {
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int gx = mnx + 2 * bp + i, gy = mny + 2 * bq + j;
-                        if (gx >= RX || gy >= h.RY) continue;
+                    for (int k = 0; k < FR::BY; ++k) {
+                        const int gx = mnx + 2 * bx + i, gy = mny + FR::BY * by + k;
+                        const R v = o[i][k];
+                        if (gx >= RX || gy >= h.RY || v == R(0)) continue;
                         const int node = gy * RX + gx;
-                        const R a = o1[2 * i + j], b = o2[2 * i + j];
                         if (DET) {  // fixed-point words: the warps' sums commute exactly
-                            if (role == 0) {
-                                if (a != R(0)) atomicAdd(st.q1 + node, det_word32(a, h.dinv32));
-                                if (b != R(0)) atomicAdd(st.q2 + node, det_word32(b, h.dinv32));
-                            } else {
-                                const R c = a + b;
-                                if (c != R(0)) atomicAdd(st.q3 + node, det_word32(c, h.dinv32));
-                            }
-                        } else if (role == 0) {
-                            if (a != R(0)) atomicAdd(st.j1 + node, a);
-                            if (b != R(0)) atomicAdd(st.j2 + node, b);
+                            unsigned long long *t = term == 0 ? st.q1 : (term == 1 ? st.q2 : st.q3);
+                            atomicAdd(t + node, det_word32(v, h.dinv32));
                         } else {
-                            const R c = a + b;
-                            if (c != R(0)) atomicAdd(st.j3 + node, c);
+                            R *t = term == 0 ? st.j1 : (term == 1 ? st.j2 : st.j3);
+                            atomicAdd(t + node, v);
                         }
                     }
                 }

@@ -262,13 +262,21 @@ class Server:
     The batchable runs live in ONE long-lived pic batch whose run set is replaced with
     pic_batch_set_runs when runs arrive or finish: the batch's launches walk device tables of
     any set that fits its capacities, so its captured CUDA graph is kept (the batch is rebuilt,
-    with doubled capacities, only when a set outgrows them).  Each chunk waits for the streams
-    it used (events), not for the whole device.  The batch's device tables count against the
-    memory budget."""
+    with doubled capacities, only when a set outgrows them).  Each lane waits for its own
+    streams (events), not for the whole device.  The batch's device tables count against the
+    memory budget.
+
+    Streams carry priorities, so that short requests are not queued behind the thread blocks of
+    a large one: the batch (small 2D runs) runs on the highest-priority stream, other runs of
+    fewer than `large_particles` particles on medium-priority side streams, larger runs on
+    low-priority ones.  The GPU's block scheduler then starts a waiting block of a
+    higher-priority stream before more blocks of a lower one."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 10,
-                 tuner: Optional[Autotuner] = None, keep_runs: bool = False):
+                 tuner: Optional[Autotuner] = None, keep_runs: bool = False,
+                 large_particles: int = 1 << 24):
         self.budget = float(budget_bytes)
+        self.large_particles = int(large_particles)
         self.chunk = int(chunk)
         self.tuner = tuner
         self.keep_runs = keep_runs
@@ -321,8 +329,10 @@ class Server:
         batch_inflight = None   # (event, steps) of the batch lane's chunk on the GPU
         side_inflight = {}      # rid -> (event, steps) of a side run's chunk
         t0 = time.perf_counter()
-        side = [torch.cuda.Stream() for _ in range(4)]  # runs the batch does not take
-        main = torch.cuda.current_stream()
+        # priorities: lower numbers are served first (torch clamps them to the device's range)
+        main = torch.cuda.Stream(priority=-3)                       # the batch
+        side = [torch.cuda.Stream(priority=-1) for _ in range(4)]   # smaller side runs
+        side_lo = [torch.cuda.Stream(priority=0) for _ in range(2)]  # large side runs
 
         def install(ids):
             """Make the batch hold the runs `ids` (a new batch when none fits)."""
@@ -381,7 +391,12 @@ class Server:
                 if used + need > self.budget and active:
                     break
                 pending.pop(0)
-                stream = None if req.batchable else side[req.rid % len(side)]
+                if req.batchable:
+                    stream = main
+                elif req.particles < self.large_particles:
+                    stream = side[req.rid % len(side)]
+                else:
+                    stream = side_lo[req.rid % len(side_lo)]
                 run = make_run(req, tuner=self.tuner, stream=stream)
                 active[req.rid] = {"run": run, "req": req, "done": 0, "bytes": need,
                                    "admitted": time.perf_counter() - t0, "history": [],
