@@ -262,10 +262,8 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out);
  * tables (pic_batch_footprint).  Never lowers a capacity below the initial set's.            */
 typedef struct {
     int32_t runs;                  /* runs at once                                          */
-    int64_t particles_per_species; /* particles of one species, summed over the runs        */
     int64_t cells;                 /* cells, summed over the runs                           */
     int64_t tiles;                 /* particle tiles, summed over the runs                  */
-    int64_t keys;                  /* tiles x cells per tile, summed over the runs          */
     size_t stage_bytes;            /* largest dynamic shared memory per CTA a run's work
                                       items may need in the batched kernel (pic_smem_info's
                                       batched_bytes); fixes the persistent kernel's shared

@@ -44,8 +44,7 @@ class pic_options(ctypes.Structure):
 
 
 class pic_batch_capacity(ctypes.Structure):
-    _fields_ = [("runs", ctypes.c_int32), ("particles_per_species", ctypes.c_int64),
-                ("cells", ctypes.c_int64), ("tiles", ctypes.c_int64), ("keys", ctypes.c_int64),
+    _fields_ = [("runs", ctypes.c_int32), ("cells", ctypes.c_int64), ("tiles", ctypes.c_int64),
                 ("stage_bytes", ctypes.c_size_t)]
 
 

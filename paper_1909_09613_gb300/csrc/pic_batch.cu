@@ -55,133 +55,163 @@ struct BlockMap {
     int block;  // block index inside the run's range
 };
 
-// Lengths of the device tables, read by every stage (the graph never changes with them).
+// Lengths of the device tables, read by every stage (the graph never changes with them), and
+// the number of runs due for a tile sort this step (written by k_b_plan).
 struct Counts {
     int runs;
-    int part[PIC_NSP_MAX];
-    int cell, key, tile, items;
+    int cell, items;
+    int due;
 };
 
 // ---- plan: which runs sort this step ----
-__global__ void k_b_plan(const Counts *cn, RunState *st, int *counter)
+// One block: every run's sort age advances, and the runs due for a sort are listed in run
+// order (a block scan of the due flags), for the sort stages to walk.
+__global__ void __launch_bounds__(1024) k_b_plan(Counts *cn, RunState *st, int *due, int *counter)
 {
+    __shared__ int tot;
+    if (threadIdx.x == 0) *counter = 0;
     const int n = cn->runs;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        RunState s = st[r];
-        s.due = s.age >= s.interval ? 1 : 0;
-        if (s.due) s.age = 0;
-        s.age += 1;
-        st[r] = s;
+    int base = 0;
+    for (int r0 = 0; r0 < n; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x;
+        int flag = 0;
+        if (r < n) {
+            RunState s = st[r];
+            s.due = s.age >= s.interval ? 1 : 0;
+            if (s.due) s.age = 0;
+            s.age += 1;
+            st[r] = s;
+            flag = s.due;
+        }
+        const int pos = sort_block_excl_scan(flag, &tot);
+        if (flag) due[base + pos] = r;
+        base += tot;
+        __syncthreads();
     }
+    if (threadIdx.x == 0) cn->due = base;
 }
 
-// ---- batched sort stages (each skips runs that are not due) ----
-__global__ void __launch_bounds__(kBlock) k_b_zero_cnt(const Counts *cn, const RunDev *runs,
-                                                       const RunState *st, const BlockMap *bm)
+// ---- batched sort stages: each walks the due runs only.  Work block e of the d-th due run
+// goes to CUDA block (e + 97 d) mod gridDim, so that the few work blocks of small runs spread
+// over the grid instead of queueing on its first blocks. ----
+__device__ __forceinline__ int64_t part_blocks(int64_t n)
 {
-    for (int b = blockIdx.x; b < cn->key; b += gridDim.x) {
-        const BlockMap m = bm[b];
-        if (!st[m.run].due) continue;
-        const RunDev &rd = runs[m.run];
+    return (n + kBlock * kPartPer - 1) / (kBlock * kPartPer);
+}
+
+// first work block of due run d that this CUDA block takes
+__device__ __forceinline__ int64_t first_block(int d)
+{
+    const int shift = (int)((97ll * d) % gridDim.x);
+    return (blockIdx.x + gridDim.x - shift) % gridDim.x;
+}
+
+__global__ void __launch_bounds__(kBlock) k_b_zero_cnt(const Counts *cn, const RunDev *runs,
+                                                       const int *due)
+{
+    const int nd = cn->due;
+    for (int d = 0; d < nd; ++d) {
+        const RunDev &rd = runs[due[d]];
         const int64_t nk = rd.ntiles * rd.tile[0] * rd.tile[1] * rd.tile[2];
         int32_t *cnt = rd.sc.cnt;
-        for (int k = 0; k < kKeyPer; ++k) {
-            const int64_t i = ((int64_t)m.block * kKeyPer + k) * blockDim.x + threadIdx.x;
-            if (i < nk) cnt[i] = 0;
-        }
+        const int64_t nb = (nk + kBlock * kKeyPer - 1) / (kBlock * kKeyPer);
+        for (int64_t e = first_block(d); e < nb; e += gridDim.x)
+            for (int k = 0; k < kKeyPer; ++k) {
+                const int64_t i = (e * kKeyPer + k) * blockDim.x + threadIdx.x;
+                if (i < nk) cnt[i] = 0;
+            }
     }
 }
 
 __global__ void __launch_bounds__(kBlock) k_b_count(const Counts *cn, const RunDev *runs,
-                                                    const RunState *st, const BlockMap *bm, int s)
+                                                    const int *due, int s)
 {
-    for (int b = blockIdx.x; b < cn->part[s]; b += gridDim.x) {
-        const BlockMap m = bm[b];
-        if (!st[m.run].due) continue;
-        const RunDev &rd = runs[m.run];
+    const int nd = cn->due;
+    for (int d = 0; d < nd; ++d) {
+        const RunDev &rd = runs[due[d]];
         const int64_t n = rd.sp[s].n;
-        for (int k = 0; k < kPartPer; ++k) {
-            const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
-            if (p < n) sort_count_one(rd, s, p);
+        for (int64_t e = first_block(d); e < part_blocks(n); e += gridDim.x)
+            for (int k = 0; k < kPartPer; ++k) {
+                const int64_t p = (e * kPartPer + k) * blockDim.x + threadIdx.x;
+                if (p < n) sort_count_one(rd, s, p);
+            }
+    }
+}
+
+// block-wide stages: the loop indices are uniform over the block, so every thread takes part
+// in the block's barriers and scans
+__global__ void __launch_bounds__(kTileThreads) k_b_tile_sum(const Counts *cn, const RunDev *runs,
+                                                             const int *due)
+{
+    const int nd = cn->due;
+    for (int d = 0; d < nd; ++d) {
+        const RunDev &rd = runs[due[d]];
+        for (int64_t t = first_block(d); t < rd.ntiles; t += gridDim.x) {
+            sort_tile_sum_block(rd, t);
+            __syncthreads();
         }
     }
 }
 
-// block-wide stages: the loop index is uniform over the block, so every thread takes part in
-// the block's barriers and scans
-__global__ void __launch_bounds__(kTileThreads) k_b_tile_sum(const Counts *cn, const RunDev *runs,
-                                                             const RunState *st, const BlockMap *bm)
-{
-    for (int b = blockIdx.x; b < cn->tile; b += gridDim.x) {
-        const BlockMap m = bm[b];
-        if (!st[m.run].due) continue;
-        sort_tile_sum_block(runs[m.run], m.block);
-        __syncthreads();
-    }
-}
-
 __global__ void __launch_bounds__(1024) k_b_scan(const Counts *cn, const RunDev *runs,
-                                                 const RunState *st, int s)
+                                                 const int *due, int s)
 {
-    for (int r = blockIdx.x; r < cn->runs; r += gridDim.x) {
-        if (!st[r].due) continue;
-        const RunDev &rd = runs[r];
+    for (int d = blockIdx.x; d < cn->due; d += gridDim.x) {
+        const RunDev &rd = runs[due[d]];
         sort_scan_block(rd.sc.tile_count, rd.sp[s].tile_start, rd.ntiles);
         __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(kTileThreads) k_b_layout(const Counts *cn, const RunDev *runs,
-                                                           const RunState *st, const BlockMap *bm,
-                                                           int s)
+                                                           const int *due, int s)
 {
-    for (int b = blockIdx.x; b < cn->tile; b += gridDim.x) {
-        const BlockMap m = bm[b];
-        if (!st[m.run].due) continue;
-        const RunDev &rd = runs[m.run];
-        sort_layout_block(rd, rd.sp[s].tile_start, m.block);
-        __syncthreads();
+    const int nd = cn->due;
+    for (int d = 0; d < nd; ++d) {
+        const RunDev &rd = runs[due[d]];
+        for (int64_t t = first_block(d); t < rd.ntiles; t += gridDim.x) {
+            sort_layout_block(rd, rd.sp[s].tile_start, t);
+            __syncthreads();
+        }
     }
 }
 
 __global__ void __launch_bounds__(kBlock) k_b_place(const Counts *cn, const RunDev *runs,
-                                                    const RunState *st, const BlockMap *bm, int s)
+                                                    const int *due, int s)
 {
-    for (int b = blockIdx.x; b < cn->part[s]; b += gridDim.x) {
-        const BlockMap m = bm[b];
-        if (!st[m.run].due) continue;
-        const RunDev &rd = runs[m.run];
+    const int nd = cn->due;
+    for (int d = 0; d < nd; ++d) {
+        const RunDev &rd = runs[due[d]];
         const int64_t n = rd.sp[s].n;
-        for (int k = 0; k < kPartPer; ++k) {
-            const int64_t p = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
-            if (p < n) sort_place_one(rd, p);
-        }
+        for (int64_t e = first_block(d); e < part_blocks(n); e += gridDim.x)
+            for (int k = 0; k < kPartPer; ++k) {
+                const int64_t p = (e * kPartPer + k) * blockDim.x + threadIdx.x;
+                if (p < n) sort_place_one(rd, p);
+            }
     }
 }
 
 // one thread per cell-major position r of the run's species (the same range as its particles)
 __global__ void __launch_bounds__(kBlock) k_b_scatter(const Counts *cn, const RunDev *runs,
-                                                      const RunState *st, const BlockMap *bm, int s)
+                                                      const int *due, int s)
 {
-    for (int b = blockIdx.x; b < cn->part[s]; b += gridDim.x) {
-        const BlockMap m = bm[b];
-        if (!st[m.run].due) continue;
-        const RunDev &rd = runs[m.run];
+    const int nd = cn->due;
+    for (int d = 0; d < nd; ++d) {
+        const RunDev &rd = runs[due[d]];
         const SpeciesDev &sp = rd.sp[s];
-        for (int k = 0; k < kPartPer; ++k) {
-            const int64_t r = ((int64_t)m.block * kPartPer + k) * blockDim.x + threadIdx.x;
-            if (r < sp.n) sort_scatter_one(rd, s, r, sp.pos_alt, sp.mom_alt, sp.cell_alt);
-        }
+        for (int64_t e = first_block(d); e < part_blocks(sp.n); e += gridDim.x)
+            for (int k = 0; k < kPartPer; ++k) {
+                const int64_t r = (e * kPartPer + k) * blockDim.x + threadIdx.x;
+                if (r < sp.n) sort_scatter_one(rd, s, r, sp.pos_alt, sp.mom_alt, sp.cell_alt);
+            }
     }
 }
 
 // the sorted buffers become the current ones
-__global__ void k_b_swap(const Counts *cn, RunDev *runs, const RunState *st, int s)
+__global__ void k_b_swap(const Counts *cn, RunDev *runs, const int *due, int s)
 {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cn->runs; r += gridDim.x * blockDim.x) {
-        if (!st[r].due) continue;
-        SpeciesDev &sp = runs[r].sp[s];
+    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < cn->due; d += gridDim.x * blockDim.x) {
+        SpeciesDev &sp = runs[due[d]].sp[s];
         for (int a = 0; a < 3; ++a) {
             void *t = sp.pos[a]; sp.pos[a] = sp.pos_alt[a]; sp.pos_alt[a] = t;
             t = sp.mom[a]; sp.mom[a] = sp.mom_alt[a]; sp.mom_alt[a] = t;
@@ -293,8 +323,8 @@ struct pic_batch {
     size_t smem;       // dynamic shared memory of the persistent kernel (fixed by the graph)
     // table capacities (entries; the work items are one per tile) and the current tables
     int cap_runs;
-    int64_t cap_part[PIC_NSP_MAX], cap_cell, cap_key, cap_tile;
-    std::vector<BlockMap> bm_part[PIC_NSP_MAX], bm_cell, bm_key, bm_tile;
+    int64_t cap_cell, cap_tile;
+    std::vector<BlockMap> bm_cell;
     std::vector<int2> items;
     // device memory
     char *base;
@@ -303,11 +333,12 @@ struct pic_batch {
     Counts *d_counts;
     RunDev *d_runs;
     RunState *d_state;
-    BlockMap *d_bm_part[PIC_NSP_MAX], *d_bm_cell, *d_bm_key, *d_bm_tile;
+    int *d_due;        // runs due for a sort this step (k_b_plan)
+    BlockMap *d_bm_cell;
     int2 *d_items;
     int *d_counter;
     // launch shapes and the graph of one step
-    int grid_runs, grid_stage, grid_tile, grid_gpp;
+    int grid_runs, grid_scan, grid_stage, grid_tile, grid_gpp;
     cudaGraphExec_t exec;
     bool have_graph;
     cudaEvent_t ev0, ev1;
@@ -324,7 +355,7 @@ size_t cap_bytes(int64_t entries) { return align_up((size_t)std::max<int64_t>(en
 // Tables of a set of runs (validated: 2D, FP32 form, l = 2 or 3, not deterministic, the batch's
 // species count and stream), and the shared memory its work items need.
 struct Tables {
-    std::vector<BlockMap> part[PIC_NSP_MAX], cell, key, tile;
+    std::vector<BlockMap> cell;
     std::vector<int2> items;
     size_t smem = 0;
 };
@@ -345,10 +376,7 @@ int build_tables(pic_ctx *const *runs, int n, int nsp, cudaStream_t stream, Tabl
         const int TC = rd.tile[0] * rd.tile[1] * rd.tile[2];
         if (TC > kTileThreads) return PIC_EINVAL;
         t.smem = std::max(t.smem, stage2d_bytes<float>(rd.reg_nodes, rd.l, false));
-        for (int s = 0; s < nsp; ++s) push_blocks(t.part[s], r, rd.sp[s].n, kBlock * kPartPer);
         push_blocks(t.cell, r, rd.ncell, kBlock * kCellPer);
-        push_blocks(t.key, r, rd.ntiles * TC, kBlock * kKeyPer);
-        for (int64_t i = 0; i < rd.ntiles; ++i) t.tile.push_back({r, (int)i});
         int64_t np = 0;
         for (int s = 0; s < nsp; ++s) np += rd.sp[s].n;
         const int64_t per_tile = rd.ntiles > 0 ? np / rd.ntiles : 0;
@@ -366,12 +394,8 @@ int build_tables(pic_ctx *const *runs, int n, int nsp, cudaStream_t stream, Tabl
 
 bool tables_fit(const pic_batch *b, const Tables &t, int n)
 {
-    if (n > b->cap_runs || (int64_t)t.cell.size() > b->cap_cell || (int64_t)t.key.size() > b->cap_key
-        || (int64_t)t.tile.size() > b->cap_tile || t.smem > b->smem)
-        return false;
-    for (int s = 0; s < b->nsp; ++s)
-        if ((int64_t)t.part[s].size() > b->cap_part[s]) return false;
-    return true;
+    return !(n > b->cap_runs || (int64_t)t.cell.size() > b->cap_cell
+             || (int64_t)t.items.size() > b->cap_tile || t.smem > b->smem);
 }
 
 // Launch sequence of one batch step on b->stream (also used while capturing).  Every grid is
@@ -381,17 +405,17 @@ cudaError_t enqueue_step(pic_batch *b)
     cudaStream_t st = b->stream;
     const Counts *cn = b->d_counts;
     int64_t nl = 0;
-    k_b_plan<<<b->grid_runs, 128, 0, st>>>(cn, b->d_state, b->d_counter);
+    k_b_plan<<<1, 1024, 0, st>>>(b->d_counts, b->d_state, b->d_due, b->d_counter);
     ++nl;
     for (int s = 0; s < b->nsp; ++s) {
-        k_b_zero_cnt<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_key);
-        k_b_count<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_part[s], s);
-        k_b_tile_sum<<<b->grid_tile, kTileThreads, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_tile);
-        k_b_scan<<<b->grid_runs, 1024, 0, st>>>(cn, b->d_runs, b->d_state, s);
-        k_b_layout<<<b->grid_tile, kTileThreads, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_tile, s);
-        k_b_place<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_part[s], s);
-        k_b_scatter<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_state, b->d_bm_part[s], s);
-        k_b_swap<<<b->grid_runs, 128, 0, st>>>(cn, b->d_runs, b->d_state, s);
+        k_b_zero_cnt<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_due);
+        k_b_count<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_due, s);
+        k_b_tile_sum<<<b->grid_tile, kTileThreads, 0, st>>>(cn, b->d_runs, b->d_due);
+        k_b_scan<<<b->grid_scan, 1024, 0, st>>>(cn, b->d_runs, b->d_due, s);
+        k_b_layout<<<b->grid_tile, kTileThreads, 0, st>>>(cn, b->d_runs, b->d_due, s);
+        k_b_place<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_due, s);
+        k_b_scatter<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_due, s);
+        k_b_swap<<<b->grid_runs, 128, 0, st>>>(cn, b->d_runs, b->d_due, s);
         nl += 8;
     }
     k_b_zero_j<<<b->grid_stage, kBlock, 0, st>>>(cn, b->d_runs, b->d_bm_cell);
@@ -456,10 +480,7 @@ int upload(pic_batch *b, pic_ctx *const *runs, int n, Tables &t)
     Counts cn;
     std::memset(&cn, 0, sizeof(cn));
     cn.runs = n;
-    for (int s = 0; s < b->nsp; ++s) cn.part[s] = (int)t.part[s].size();
     cn.cell = (int)t.cell.size();
-    cn.key = (int)t.key.size();
-    cn.tile = (int)t.tile.size();
     cn.items = (int)t.items.size();
     cudaStream_t st = b->stream;
     auto up = [&](void *dst, const void *src, size_t nb) {
@@ -468,20 +489,13 @@ int upload(pic_batch *b, pic_ctx *const *runs, int n, Tables &t)
     bool ok = up(b->d_runs, rds.data(), rds.size() * sizeof(RunDev))
               && up(b->d_state, sts.data(), sts.size() * sizeof(RunState))
               && up(b->d_counts, &cn, sizeof(cn));
-    for (int s = 0; s < b->nsp && ok; ++s)
-        ok = up(b->d_bm_part[s], t.part[s].data(), t.part[s].size() * sizeof(BlockMap));
     ok = ok && up(b->d_bm_cell, t.cell.data(), t.cell.size() * sizeof(BlockMap))
-         && up(b->d_bm_key, t.key.data(), t.key.size() * sizeof(BlockMap))
-         && up(b->d_bm_tile, t.tile.data(), t.tile.size() * sizeof(BlockMap))
          && up(b->d_items, t.items.data(), t.items.size() * sizeof(int2));
     // the host vectors are released on return: wait for the copies
     if (!ok || cudaStreamSynchronize(st) != cudaSuccess) return PIC_ECUDA;
     b->n = n;
     b->ctx.assign(runs, runs + n);
-    for (int s = 0; s < b->nsp; ++s) b->bm_part[s].swap(t.part[s]);
     b->bm_cell.swap(t.cell);
-    b->bm_key.swap(t.key);
-    b->bm_tile.swap(t.tile);
     b->items.swap(t.items);
     b->steps_since_sync = 0;
     return PIC_OK;
@@ -517,16 +531,11 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
     // capacities of the initial set (pic_batch_reserve raises them before binding)
     b->smem = t.smem;
     b->cap_runs = n;
-    for (int s = 0; s < PIC_NSP_MAX; ++s) b->cap_part[s] = s < b->nsp ? (int64_t)t.part[s].size() : 0;
     b->cap_cell = (int64_t)t.cell.size();
-    b->cap_key = (int64_t)t.key.size();
-    b->cap_tile = (int64_t)t.tile.size();
+    b->cap_tile = (int64_t)t.items.size();
     // the initial set, uploaded by pic_batch_bind_memory
     b->ctx.assign(runs, runs + n);
-    for (int s = 0; s < b->nsp; ++s) b->bm_part[s].swap(t.part[s]);
     b->bm_cell.swap(t.cell);
-    b->bm_key.swap(t.key);
-    b->bm_tile.swap(t.tile);
     b->items.swap(t.items);
     if (b->stream == 0) {
         // a blocking stream is ordered with the legacy default stream the runs use
@@ -544,15 +553,10 @@ int pic_batch_reserve(pic_batch *b, const pic_batch_capacity *cap)
 {
     if (!b || !cap) return PIC_EINVAL;
     if (b->base) return PIC_ESTATE;  // the capacities size the bound memory
-    if (cap->runs < 0 || cap->particles_per_species < 0 || cap->cells < 0 || cap->tiles < 0
-        || cap->keys < 0 || cap->stage_bytes > 227 * 1024)
+    if (cap->runs < 0 || cap->cells < 0 || cap->tiles < 0 || cap->stage_bytes > 227 * 1024)
         return PIC_EINVAL;
     b->cap_runs = std::max(b->cap_runs, (int)cap->runs);
-    for (int s = 0; s < b->nsp; ++s)
-        b->cap_part[s] = std::max<int64_t>(b->cap_part[s],
-                                           cap->particles_per_species / (kBlock * kPartPer) + cap->runs);
     b->cap_cell = std::max<int64_t>(b->cap_cell, cap->cells / (kBlock * kCellPer) + cap->runs);
-    b->cap_key = std::max<int64_t>(b->cap_key, cap->keys / (kBlock * kKeyPer) + cap->runs);
     b->cap_tile = std::max<int64_t>(b->cap_tile, cap->tiles);
     b->smem = std::max(b->smem, std::min(cap->stage_bytes, (size_t)227 * 1024));
     return PIC_OK;
@@ -562,10 +566,9 @@ int pic_batch_footprint(const pic_batch *b, size_t *bytes)
 {
     if (!b || !bytes) return PIC_EINVAL;
     size_t s = align_up(sizeof(Counts), 256);
-    s += cap_bytes<RunDev>(b->cap_runs) + cap_bytes<RunState>(b->cap_runs);
-    for (int i = 0; i < b->nsp; ++i) s += cap_bytes<BlockMap>(b->cap_part[i]);
-    s += cap_bytes<BlockMap>(b->cap_cell) + cap_bytes<BlockMap>(b->cap_key)
-         + cap_bytes<BlockMap>(b->cap_tile) + cap_bytes<int2>(b->cap_tile) + 256 + 256;
+    s += cap_bytes<RunDev>(b->cap_runs) + cap_bytes<RunState>(b->cap_runs)
+         + cap_bytes<int>(b->cap_runs);
+    s += cap_bytes<BlockMap>(b->cap_cell) + cap_bytes<int2>(b->cap_tile) + 256 + 256;
     *bytes = s;
     return PIC_OK;
 }
@@ -583,10 +586,8 @@ int pic_batch_bind_memory(pic_batch *b, void *dev, size_t bytes)
     b->d_counts = (Counts *)take(sizeof(Counts));
     b->d_runs = (RunDev *)take(cap_bytes<RunDev>(b->cap_runs));
     b->d_state = (RunState *)take(cap_bytes<RunState>(b->cap_runs));
-    for (int i = 0; i < b->nsp; ++i) b->d_bm_part[i] = (BlockMap *)take(cap_bytes<BlockMap>(b->cap_part[i]));
+    b->d_due = (int *)take(cap_bytes<int>(b->cap_runs));
     b->d_bm_cell = (BlockMap *)take(cap_bytes<BlockMap>(b->cap_cell));
-    b->d_bm_key = (BlockMap *)take(cap_bytes<BlockMap>(b->cap_key));
-    b->d_bm_tile = (BlockMap *)take(cap_bytes<BlockMap>(b->cap_tile));
     b->d_items = (int2 *)take(cap_bytes<int2>(b->cap_tile));
     b->d_counter = (int *)take(sizeof(int));
     // launch shapes, fixed for the life of the batch (and of its graph)
@@ -614,19 +615,15 @@ int pic_batch_bind_memory(pic_batch *b, void *dev, size_t bytes)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_gpp, 256, b->smem);
     auto clampg = [](int64_t want, int64_t cap) { return (int)std::max<int64_t>(1, std::min(want, cap)); };
     b->grid_runs = clampg((b->cap_runs + 127) / 128, 1 << 20);
-    int64_t maxpart = 1;
-    for (int i = 0; i < b->nsp; ++i) maxpart = std::max(maxpart, b->cap_part[i]);
-    b->grid_stage = clampg(std::max(maxpart, std::max(b->cap_cell, b->cap_key)), (int64_t)sms * 8);
-    b->grid_tile = clampg(b->cap_tile, (int64_t)sms * 2);
+    b->grid_scan = clampg(b->cap_runs, sms);
+    b->grid_stage = (int)sms * 8;
+    b->grid_tile = (int)sms * 2;
     b->grid_gpp = clampg(b->cap_tile, (int64_t)sms * std::max(per_sm, 1));
     b->base = (char *)dev;
     if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)
         return PIC_ECUDA;
     Tables t;
-    for (int s = 0; s < b->nsp; ++s) t.part[s].swap(b->bm_part[s]);
     t.cell.swap(b->bm_cell);
-    t.key.swap(b->bm_key);
-    t.tile.swap(b->bm_tile);
     t.items.swap(b->items);
     std::vector<pic_ctx *> runs = b->ctx;
     return upload(b, runs.data(), (int)runs.size(), t);

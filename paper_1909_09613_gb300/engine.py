@@ -295,20 +295,15 @@ class Server:
         cap = pic.pic_batch_capacity()
         n = len(runs)
         cap.runs = max(8, int(factor * n))
-        parts = cells = tiles = keys = 0
+        cells = tiles = 0
         stage = 0
         for r in runs:
-            parts = max(parts, max(r.counts))
             cells += r.ncell
             tiles += r.ntiles
-            keys += r.ntiles * r.tile[0] * r.tile[1] * r.tile[2]
             _, batched, two = pic.pic_smem_info(r.ctx)
             stage = max(stage, batched, two)
-        per_species = sum(max(r.counts) for r in runs)
-        cap.particles_per_species = int(factor * max(per_species, 1 << 20))
         cap.cells = int(factor * max(cells, 1 << 18))
         cap.tiles = int(factor * max(tiles, 1 << 12))
-        cap.keys = int(factor * max(keys, 1 << 19))
         cap.stage_bytes = int(stage)
         return cap
 

@@ -298,7 +298,8 @@ def _c_layout(struct, fields):
         return [int(v) for v in subprocess.check_output([exe]).split()]
 
 
-@pytest.mark.parametrize("cls,struct", [(pic.pic_options, "pic_options"), (pic.pic_diag_t, "pic_diag_t")])
+@pytest.mark.parametrize("cls,struct", [(pic.pic_options, "pic_options"), (pic.pic_diag_t, "pic_diag_t"),
+                                        (pic.pic_batch_capacity, "pic_batch_capacity")])
 def test_struct_layouts_match_the_header(cls, struct):
     """The ctypes mirrors of the option and diagnostics structs have the C header's field
     offsets and size (a field added on one side only would shift every later one)."""

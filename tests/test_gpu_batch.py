@@ -238,10 +238,8 @@ def test_batch_set_runs_keeps_the_graph_and_matches_alone():
         r.step(20)
     cap = pic.pic_batch_capacity()
     cap.runs = 8
-    cap.particles_per_species = 4 * max(max(r.counts) for r in mixed)
     cap.cells = 4 * sum(r.ncell for r in mixed)
     cap.tiles = 4 * sum(r.ntiles for r in mixed)
-    cap.keys = 4 * sum(r.ntiles * r.tile[0] * r.tile[1] for r in mixed)
     cap.stage_bytes = max(pic.pic_smem_info(r.ctx)[1] for r in mixed)
     b = pic.Batch(mixed[:2], capacity=cap)
     b.step(5)                              # runs 0, 1: 5 steps (graph captured)
