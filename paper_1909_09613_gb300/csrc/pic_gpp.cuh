@@ -165,43 +165,25 @@ __device__ __forceinline__ void bspline_dd(float a, float b, float *D)
 // a slowly moving particle is not lost to the cancellation of S1 - S0 in single precision.
 // The particle moves from psi0 to psi0 + delta on the spline's local lattice; if that leaves
 // [0,1) the stencil base moves by one node and the difference is split at the lattice point,
-// where the basis polynomials of neighbouring nodes agree (P_{k-1}(0) = P_k(1)).
-template <int L>
+// where the basis polynomials of neighbouring nodes agree (P_{k-1}(0) = P_k(1)).  In every case
+// DS[k] = al Da[k] + be Db[k - 1] with Da, Db divided differences over the two parts of the move:
+//   same base: al = delta over [psi0, psi1], be = 0
+//   up:        al = 1 - psi0 over [psi0, 1], be = delta - al over [0, be] (new psi)
+//   down:      al = -e over [1 - e, 1], be = -psi0 over [0, psi0], with e = -delta - psi0 the
+//              overshoot below the lattice point (new psi = 1 - e); the window starts one node
+//              lower
+// COLLECTIVE (all 32 lanes of the warp call together): a warp none of whose lanes changes base
+// evaluates the one divided difference of the same-base case, any other warp evaluates the
+// general form once, on every lane, instead of the cases one after the other.
+template <int L, bool COLLECTIVE = false>
 __device__ __forceinline__ void axis_shapes_dd(float d_old, float delta, AxisS<L, float> &s)
 {
     float p0, w0[L + 1];
     const int b0 = spline_base<L, float>(d_old, false, p0);
     bspline<L, float>(p0, w0);
     const float p1 = p0 + delta;
-    s.wide = true;
-    if (p1 >= 1.0f) {            // base moves up: window starts at b0
-        s.wb = b0;
-        const float a = 1.0f - p0;     // part of the move before the lattice point
-        const float b = delta - a;     // part after it (new psi)
-        float Da[L + 1], Db[L + 1];
-        bspline_dd<L>(p0, 1.0f, Da);
-        bspline_dd<L>(0.0f, b, Db);
-#pragma unroll
-        for (int k = 0; k < L + 2; ++k) {
-            s.s0[k] = (k <= L) ? w0[k] : 0.0f;
-            const float up = (k >= 1) ? b * Db[k - 1] : 0.0f;
-            const float lo = (k <= L) ? a * Da[k] : 0.0f;
-            s.ds[k] = up + lo;
-        }
-    } else if (p1 < 0.0f) {      // base moves down: window starts at b0 - 1
-        s.wb = b0 - 1;
-        const float e = -delta - p0;   // overshoot below the lattice point (new psi = 1 - e)
-        float Da[L + 1], Db[L + 1];
-        bspline_dd<L>(1.0f - e, 1.0f, Da);
-        bspline_dd<L>(0.0f, p0, Db);
-#pragma unroll
-        for (int k = 0; k < L + 2; ++k) {
-            s.s0[k] = (k >= 1) ? w0[k - 1] : 0.0f;
-            const float a1 = (k <= L) ? -e * Da[k] : 0.0f;
-            const float a2 = (k >= 1) ? -p0 * Db[k - 1] : 0.0f;
-            s.ds[k] = a1 + a2;
-        }
-    } else {                     // same base
+    const bool up = p1 >= 1.0f, dn = p1 < 0.0f;
+    if (COLLECTIVE ? !__any_sync(0xffffffffu, up || dn) : !(up || dn)) {
         s.wb = b0;
         s.wide = false;
         float D[L + 1];
@@ -211,6 +193,26 @@ __device__ __forceinline__ void axis_shapes_dd(float d_old, float delta, AxisS<L
             s.s0[k] = (k <= L) ? w0[k] : 0.0f;
             s.ds[k] = (k <= L) ? delta * D[k] : 0.0f;
         }
+        return;
+    }
+    const float e = -delta - p0;
+    const float al = up ? 1.0f - p0 : (dn ? -e : delta);
+    const float alo = dn ? 1.0f - e : p0;
+    const float ahi = (up || dn) ? 1.0f : p1;
+    const float be = up ? delta - al : (dn ? -p0 : 0.0f);
+    const float bhi = up ? be : (dn ? p0 : 0.0f);
+    float Da[L + 1], Db[L + 1];
+    bspline_dd<L>(alo, ahi, Da);
+    bspline_dd<L>(0.0f, bhi, Db);
+    s.wb = dn ? b0 - 1 : b0;
+    s.wide = up || dn;
+#pragma unroll
+    for (int k = 0; k < L + 2; ++k) {
+        const float w_lo = (k <= L) ? w0[k] : 0.0f, w_hi = (k >= 1) ? w0[k - 1] : 0.0f;
+        s.s0[k] = dn ? w_hi : w_lo;
+        const float lo = (k <= L) ? al * Da[k] : 0.0f;
+        const float hi = (k >= 1) ? be * Db[k - 1] : 0.0f;
+        s.ds[k] = lo + hi;
     }
 }
 

@@ -36,18 +36,22 @@ constexpr int kTileWarps = 8;
 // DSy over NY nodes); then each lane sums, over the 32 records, one term (J1, J2, or one of the
 // two products of J3) on a 2 x BY sub-block of nodes (BY = NY / 2): per record one 64-bit load
 // of its two x factors and BY 32-bit loads of its y factors, all of them shared-memory
-// broadcasts within the record.  That is 2 + BY wavefronts per record for the warp, against 8
-// for two 128-bit loads per lane (a 128-bit load takes a wavefront per quarter warp): the sums
-// are bound by shared-memory wavefronts, not by issue.  RS (floats per record) is a multiple of
-// 4 with RS / 4 odd, so that the float4 stores of 8 consecutive lanes fall in distinct banks.
-template <int L>
+// broadcasts within the record, and BY packed FMAs.  That is 2 + BY wavefronts per record for
+// the warp, against 8 for two 128-bit loads per lane (a 128-bit load takes a wavefront per
+// quarter warp): the sums are bound by shared-memory wavefronts and issue, not by arithmetic.
+// RS (floats per record) is a multiple of 4 with RS / 4 odd, so that the float4 stores of 8
+// consecutive lanes fall in distinct banks.  NARROW: no lane of the group moved its y window
+// base, so every window's last row (node l + 1) is zero and the frame has l + 1 + SYM rows
+// (rounded up to even) instead of l + 2 + SYM.
+template <int L, bool NARROW = false>
 struct DepFrame {
     // Along y the windows of a group start at most SYM rows apart: for odd l a particle's
     // integer-node window starts at a fixed offset from its cell, so the lanes of one cell row
     // share it (SYM = 0; a warp straddling the end of a tile row takes a second pass); for even
     // l the start moves by one with the in-cell offset (SYM = 1).  Along x, up to SXM nodes.
     static constexpr int SYM = (L % 2 == 0) ? 1 : 0;
-    static constexpr int PX = (L + 2 + 2 + 1) / 2, PY = (L + 2 + SYM + 1) / 2;
+    static constexpr int WYN = NARROW ? L + 1 : L + 2;  // y nodes of one lane's window
+    static constexpr int PX = (L + 2 + 2 + 1) / 2, PY = (WYN + SYM + 1) / 2;
     static constexpr int NX = 2 * PX, NY = 2 * PY;
     static constexpr int SXM = NX - (L + 2);
     static constexpr int BY = NY / 2;            // y nodes of a lane's sub-block
@@ -448,6 +452,136 @@ __device__ __forceinline__ void gather_2d_x2(const Stage2D<float> &st, const Axi
     }
 }
 
+// One pass of the FP32 warp deposit on frame FR (DepFrame): every lane writes its factor
+// record, shifted by (ox, oy) into the frame and scaled by gin (1 for the lanes of this pass's
+// group, 0 for the others), then each lane sums its term on its sub-block over the 32 records and
+// adds it to the shared current.  The two products of J3 (terms 2 and 3, lanes NBT apart) are
+// added together first, so that no two lanes of one atomic instruction address the same node.
+// mnx, mny: frame origin (tile-local node); kx, ky, kz: the species' current scales.
+template <class FR, int L, bool DET>
+__device__ __forceinline__ void warp_frame_pass(const Hot2D &h, const Stage2D<float> &st,
+                                                float gin, int ox, int oy, int mnx, int mny,
+                                                float kx, float ky, float kz, const float *px,
+                                                const float *py, const float *Ax, const float *Ay,
+                                                const float *Bx, const AxisS<L, float> &Sy)
+{
+    const int lane = threadIdx.x & 31;
+    // the warp's record area is sized for the widest frame of order l
+    float *rec = st.rec + (threadIdx.x >> 5) * (32 * DepFrame<L>::RS);
+    float4 *mine = (float4 *)(rec + lane * FR::RS);
+    // the record: block node A holds this lane's window node A - ox (zero outside it); the x
+    // factors are scaled first, then shifted by ox = 0..SXM in two steps (ox & 1, ox & 2); the
+    // y factors are shifted by oy (0 when SYM = 0)
+    float r[FR::RS1];
+    float sp[L + 2], sa[L + 2], sb2[L + 2];
+    const float gkx = gin * kx;
+#pragma unroll
+    for (int k = 0; k < L + 2; ++k) {
+        sp[k] = (k <= L) ? gkx * px[k] : 0.0f;
+        sa[k] = gin * Ax[k];
+        sb2[k] = gin * Bx[k];
+    }
+    const bool sh1 = (ox & 1) != 0, sh2 = (ox & 2) != 0;
+    float tp[L + 3], ta[L + 3], tb[L + 3];
+#pragma unroll
+    for (int k = 0; k < L + 3; ++k) {
+        const float p0 = (k < L + 2) ? sp[k] : 0.0f, p1 = (k >= 1) ? sp[k - 1] : 0.0f;
+        const float a0 = (k < L + 2) ? sa[k] : 0.0f, a1 = (k >= 1) ? sa[k - 1] : 0.0f;
+        const float b0 = (k < L + 2) ? sb2[k] : 0.0f, b1 = (k >= 1) ? sb2[k - 1] : 0.0f;
+        tp[k] = sh1 ? p1 : p0;
+        ta[k] = sh1 ? a1 : a0;
+        tb[k] = sh1 ? b1 : b0;
+    }
+#pragma unroll
+    for (int A = 0; A < FR::NX; ++A) {
+        const float p0 = (A < L + 3) ? tp[A] : 0.0f;
+        const float p2 = (A >= 2 && A - 2 < L + 3) ? tp[A - 2] : 0.0f;
+        const float a0 = (A < L + 3) ? ta[A] : 0.0f;
+        const float a2 = (A >= 2 && A - 2 < L + 3) ? ta[A - 2] : 0.0f;
+        const float b0 = (A < L + 3) ? tb[A] : 0.0f;
+        const float b2 = (A >= 2 && A - 2 < L + 3) ? tb[A - 2] : 0.0f;
+        r[A] = sh2 ? p2 : p0;
+        r[FR::NX + A] = sh2 ? a2 : a0;
+        r[2 * FR::NX + A] = sh2 ? b2 : b0;
+    }
+    float ty[4][L + 2];  // Ay, ky py, kz S0y, kz DSy
+#pragma unroll
+    for (int k = 0; k < L + 2; ++k) {
+        ty[0][k] = Ay[k];
+        ty[1][k] = (k <= L) ? ky * py[k] : 0.0f;
+        ty[2][k] = kz * Sy.s0[k];
+        ty[3][k] = kz * Sy.ds[k];
+    }
+#pragma unroll
+    for (int Bn = 0; Bn < FR::NY; ++Bn) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const float v0 = (Bn <= L + 1) ? ty[f][Bn] : 0.0f;
+            if constexpr (FR::SYM == 0) {
+                r[FR::XS + f * FR::NY + Bn] = v0;
+            } else {
+                const float v1 = (Bn >= 1 && Bn - 1 <= L + 1) ? ty[f][Bn - 1] : 0.0f;
+                r[FR::XS + f * FR::NY + Bn] = (oy == 1) ? v1 : v0;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = FR::RS0; k < FR::RS1; ++k) r[k] = 0.0f;
+#pragma unroll
+    for (int v = 0; v < FR::RS1 / 4; ++v)
+        mine[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+    __syncwarp();
+    // this lane's sum: term t (0: J1 = px Ay, 1: J2 = Ax py, 2: J3 from Ax S0y, 3: J3 from
+    // Bx DSy; lanes past the four terms idle) on the sub-block (bx, by) of the frame, as packed
+    // pairs (the sub-block's two x nodes; each lane rounded as the scalar FMA)
+    const int term = lane / FR::NBT, sb = lane % FR::NBT;
+    const int bx = sb % (FR::NX / 2), by = sb / (FR::NX / 2);
+    const bool sums = term < 4;
+    const int xo = sums ? (term == 0 ? 0 : (term == 3 ? 2 * FR::NX : FR::NX)) + 2 * bx : 0;
+    const int yo = sums ? FR::XS + term * FR::NY + FR::BY * by : FR::XS;
+    float2 o[FR::BY];
+#pragma unroll
+    for (int k = 0; k < FR::BY; ++k) o[k] = make_float2(0.0f, 0.0f);
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+        const float *rq = rec + q * FR::RS;
+        const float2 xv = *(const float2 *)(rq + xo);
+#pragma unroll
+        for (int k = 0; k < FR::BY; ++k) {
+            const float yv = rq[yo + k];
+            o[k] = __ffma2_rn(xv, make_float2(yv, yv), o[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < FR::BY; ++k) {
+        const float ox3 = __shfl_down_sync(0xffffffffu, o[k].x, FR::NBT);
+        const float oy3 = __shfl_down_sync(0xffffffffu, o[k].y, FR::NBT);
+        if (term == 2) {
+            o[k].x += ox3;
+            o[k].y += oy3;
+        }
+    }
+    if (term < 3) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+#pragma unroll
+            for (int k = 0; k < FR::BY; ++k) {
+                const int gx = mnx + 2 * bx + i, gy = mny + FR::BY * by + k;
+                const float v = i == 0 ? o[k].x : o[k].y;
+                if (gx >= h.RX || gy >= h.RY || v == 0.0f) continue;
+                const int node = gy * h.RX + gx;
+                if (DET) {  // fixed-point words: the warps' sums commute exactly
+                    unsigned long long *t = term == 0 ? st.q1 : (term == 1 ? st.q2 : st.q3);
+                    atomicAdd(t + node, det_word32(v, h.dinv32));
+                } else {
+                    float *t = term == 0 ? st.j1 : (term == 1 ? st.j2 : st.j3);
+                    atomicAdd(t + node, v);
+                }
+            }
+        }
+    }
+}
+
 // One particle per lane, 2D, staged tile.  Called by all 32 lanes of a warp together (the
 // deposit is warp-collective); lanes with act == false carry no particle.  DET: a
 // deterministic run (RunDev::det), whose current goes in as fixed-point words; a template
@@ -576,8 +710,8 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
     // ---- Esirkepov deposit ----
     AxisS<L, R> Sx, Sy;
     if constexpr (sizeof(R) == 4) {
-        axis_shapes_dd<L>(s.d[0], dl[0], Sx);
-        axis_shapes_dd<L>(s.d[1], dl[1], Sy);
+        axis_shapes_dd<L, true>(s.d[0], dl[0], Sx);  // all 32 lanes take part
+        axis_shapes_dd<L, true>(s.d[1], dl[1], Sy);
     } else {
         // old-position weights: from the cache the previous step wrote at this particle's
         // stored position (bit-identical to evaluating them), else evaluated.  (l = 4 keeps
@@ -638,124 +772,26 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
                 deposit_lane<L, R, false>(st, RX, jx0, jy0, kx, ky, kz, px, py, Ax, Ay, Bx, Sy);
             }
         } else {
-        float *rec = st.rec + (threadIdx.x >> 5) * (32 * FR::RS);
-        float4 *mine = (float4 *)(rec + lane * FR::RS);
-        // this lane's sum: term t (0: J1 = px Ay, 1: J2 = Ax py, 2: J3 from Ax S0y, 3: J3 from
-        // Bx DSy; lanes past the four terms idle) on the sub-block (bx, by) of the frame
-        const int term = lane / FR::NBT, sb = lane % FR::NBT;
-        const int bx = sb % (FR::NX / 2), by = sb / (FR::NX / 2);
-        const bool sums = term < 4;
-        const int xo = sums ? (term == 0 ? 0 : (term == 3 ? 2 * FR::NX : FR::NX)) + 2 * bx : 0;
-        const int yo = sums ? FR::XS + term * FR::NY + FR::BY * by : FR::XS;
         // passes over groups of lanes that fit one common block (usually one pass; a warp that
         // straddles the end of a tile row takes two)
         bool todo = act;
         while (__any_sync(0xffffffffu, todo)) {
-        const int mny = __reduce_min_sync(0xffffffffu, todo ? jy0 : 0x7fffffff);
-        const bool rowok = todo && jy0 <= mny + FR::SYM;
-        const int mnx = __reduce_min_sync(0xffffffffu, rowok ? jx0 : 0x7fffffff);
-        const bool in = rowok && jx0 <= mnx + FR::SXM;
-        todo = todo && !in;
-        {
+            const int mny = __reduce_min_sync(0xffffffffu, todo ? jy0 : 0x7fffffff);
+            const bool rowok = todo && jy0 <= mny + FR::SYM;
+            const int mnx = __reduce_min_sync(0xffffffffu, rowok ? jx0 : 0x7fffffff);
+            const bool in = rowok && jx0 <= mnx + FR::SXM;
+            todo = todo && !in;
             const int ox = in ? jx0 - mnx : 0, oy = in ? jy0 - mny : 0;
             const R gin = in ? R(1) : R(0);
             __syncwarp();  // the previous pass has read every record
-            // the record: block node A holds this lane's window node A - ox (zero outside it);
-            // the x factors are scaled first, then shifted by ox = 0..SXM in two steps (ox & 1,
-            // ox & 2); the y factors are shifted by oy (0 when SYM = 0)
-            float r[FR::RS1];
-            R sp[L + 2], sa[L + 2], sb2[L + 2];
-            const R gkx = gin * kx;
-#pragma unroll
-            for (int k = 0; k < L + 2; ++k) {
-                sp[k] = (k <= L) ? gkx * px[k] : R(0);
-                sa[k] = gin * Ax[k];
-                sb2[k] = gin * Bx[k];
-            }
-            const bool sh1 = (ox & 1) != 0, sh2 = (ox & 2) != 0;
-            R tp[L + 3], ta[L + 3], tb[L + 3];
-#pragma unroll
-            for (int k = 0; k < L + 3; ++k) {
-                const R p0 = (k < L + 2) ? sp[k] : R(0), p1 = (k >= 1) ? sp[k - 1] : R(0);
-                const R a0 = (k < L + 2) ? sa[k] : R(0), a1 = (k >= 1) ? sa[k - 1] : R(0);
-                const R b0 = (k < L + 2) ? sb2[k] : R(0), b1 = (k >= 1) ? sb2[k - 1] : R(0);
-                tp[k] = sh1 ? p1 : p0;
-                ta[k] = sh1 ? a1 : a0;
-                tb[k] = sh1 ? b1 : b0;
-            }
-#pragma unroll
-            for (int A = 0; A < FR::NX; ++A) {
-                const R p0 = (A < L + 3) ? tp[A] : R(0), p2 = (A >= 2 && A - 2 < L + 3) ? tp[A - 2] : R(0);
-                const R a0 = (A < L + 3) ? ta[A] : R(0), a2 = (A >= 2 && A - 2 < L + 3) ? ta[A - 2] : R(0);
-                const R b0 = (A < L + 3) ? tb[A] : R(0), b2 = (A >= 2 && A - 2 < L + 3) ? tb[A - 2] : R(0);
-                r[A] = sh2 ? p2 : p0;
-                r[FR::NX + A] = sh2 ? a2 : a0;
-                r[2 * FR::NX + A] = sh2 ? b2 : b0;
-            }
-            R ty[4][L + 2];  // Ay, ky py, kz S0y, kz DSy
-#pragma unroll
-            for (int k = 0; k < L + 2; ++k) {
-                ty[0][k] = Ay[k];
-                ty[1][k] = (k <= L) ? ky * py[k] : R(0);
-                ty[2][k] = kz * Sy.s0[k];
-                ty[3][k] = kz * Sy.ds[k];
-            }
-#pragma unroll
-            for (int Bn = 0; Bn < FR::NY; ++Bn) {
-#pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    const R v0 = (Bn <= L + 1) ? ty[f][Bn] : R(0);
-                    if constexpr (FR::SYM == 0) {
-                        r[FR::XS + f * FR::NY + Bn] = v0;
-                    } else {
-                        const R v1 = (Bn >= 1 && Bn - 1 <= L + 1) ? ty[f][Bn - 1] : R(0);
-                        r[FR::XS + f * FR::NY + Bn] = (oy == 1) ? v1 : v0;
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = FR::RS0; k < FR::RS1; ++k) r[k] = 0.0f;
-#pragma unroll
-            for (int v = 0; v < FR::RS1 / 4; ++v)
-                mine[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
-            __syncwarp();
-            // this lane's term on its 2 x BY sub-block, summed over the 32 records
-            R o[2][FR::BY];
-#pragma unroll
-            for (int k = 0; k < FR::BY; ++k) o[0][k] = o[1][k] = R(0);
-#pragma unroll 8
-            for (int q = 0; q < 32; ++q) {
-                const float *rq = rec + q * FR::RS;
-                const float2 xv = *(const float2 *)(rq + xo);
-                R yv[FR::BY];
-#pragma unroll
-                for (int k = 0; k < FR::BY; ++k) yv[k] = rq[yo + k];
-#pragma unroll
-                for (int k = 0; k < FR::BY; ++k) {
-                    o[0][k] += xv.x * yv[k];
-                    o[1][k] += xv.y * yv[k];
-                }
-            }
-            if (sums) {
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-#pragma unroll
-                    for (int k = 0; k < FR::BY; ++k) {
-                        const int gx = mnx + 2 * bx + i, gy = mny + FR::BY * by + k;
-                        const R v = o[i][k];
-                        if (gx >= RX || gy >= h.RY || v == R(0)) continue;
-                        const int node = gy * RX + gx;
-                        if (DET) {  // fixed-point words: the warps' sums commute exactly
-                            unsigned long long *t = term == 0 ? st.q1 : (term == 1 ? st.q2 : st.q3);
-                            atomicAdd(t + node, det_word32(v, h.dinv32));
-                        } else {
-                            R *t = term == 0 ? st.j1 : (term == 1 ? st.j2 : st.j3);
-                            atomicAdd(t + node, v);
-                        }
-                    }
-                }
-            }
-        }
+            // a group none of whose lanes moved its y window base leaves row l + 1 of every
+            // window at exact zeros (S0y = DSy = 0): its frame is two rows lower
+            if (__any_sync(0xffffffffu, in && Sy.wide))
+                warp_frame_pass<DepFrame<L, false>, L, DET>(h, st, gin, ox, oy, mnx, mny, kx, ky,
+                                                            kz, px, py, Ax, Ay, Bx, Sy);
+            else
+                warp_frame_pass<DepFrame<L, true>, L, DET>(h, st, gin, ox, oy, mnx, mny, kx, ky,
+                                                           kz, px, py, Ax, Ay, Bx, Sy);
         }
         }
     } else {
