@@ -56,7 +56,12 @@ struct DepFrame {
     static constexpr int SXM = NX - (L + 2);
     static constexpr int BY = NY / 2;            // y nodes of a lane's sub-block
     static constexpr int NBT = (NX / 2) * 2;     // sub-blocks of one term
-    static constexpr int XS = 3 * NX, YS = 4 * NY;
+    // x part padded to a multiple of 4 floats, so that every term's y factors start 16-byte
+    // aligned within the record
+    static constexpr int XS = (3 * NX + 3) / 4 * 4, YS = 4 * NY;
+    // HALF: the two half warps sum the even and the odd records, each lane one term on a
+    // 2 x NY block (one 64-bit and one 64- or 128-bit load and NY packed FMAs per record)
+    static constexpr bool HALF = (NY == 2 || NY == 4) && 4 * (NX / 2) <= 16;
     static constexpr int RS0 = XS + YS;
     static constexpr int RS1 = (RS0 + 3) / 4 * 4;
     static constexpr int RS = ((RS1 / 4) % 2 == 0) ? RS1 + 4 : RS1;
@@ -526,56 +531,128 @@ __device__ __forceinline__ void warp_frame_pass(const Hot2D &h, const Stage2D<fl
         }
     }
 #pragma unroll
+    for (int k = 3 * FR::NX; k < FR::XS; ++k) r[k] = 0.0f;
+#pragma unroll
     for (int k = FR::RS0; k < FR::RS1; ++k) r[k] = 0.0f;
 #pragma unroll
     for (int v = 0; v < FR::RS1 / 4; ++v)
         mine[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
     __syncwarp();
-    // this lane's sum: term t (0: J1 = px Ay, 1: J2 = Ax py, 2: J3 from Ax S0y, 3: J3 from
-    // Bx DSy; lanes past the four terms idle) on the sub-block (bx, by) of the frame, as packed
-    // pairs (the sub-block's two x nodes; each lane rounded as the scalar FMA)
-    const int term = lane / FR::NBT, sb = lane % FR::NBT;
-    const int bx = sb % (FR::NX / 2), by = sb / (FR::NX / 2);
-    const bool sums = term < 4;
-    const int xo = sums ? (term == 0 ? 0 : (term == 3 ? 2 * FR::NX : FR::NX)) + 2 * bx : 0;
-    const int yo = sums ? FR::XS + term * FR::NY + FR::BY * by : FR::XS;
-    float2 o[FR::BY];
+    if constexpr (FR::HALF) {
+        // lane (half, term, bx): term t (0: J1 = px Ay, 1: J2 = Ax py, 2: J3 from Ax S0y, 3: J3
+        // from Bx DSy; lanes past the four terms idle) on the frame columns 2 bx, 2 bx + 1 and
+        // all NY rows, summed over the records of parity `half`, as packed pairs (each lane
+        // rounded as the scalar FMA)
+        constexpr int NBX = FR::NX / 2;
+        const int half = lane >> 4, hl = lane & 15;
+        const int term = hl / NBX, bx = hl % NBX;
+        const bool sums = term < 4;
+        const int xo = sums ? (term == 0 ? 0 : (term == 3 ? 2 * FR::NX : FR::NX)) + 2 * bx : 0;
+        const int yo = sums ? FR::XS + term * FR::NY : FR::XS;
+        float2 o[FR::NY];
 #pragma unroll
-    for (int k = 0; k < FR::BY; ++k) o[k] = make_float2(0.0f, 0.0f);
+        for (int j = 0; j < FR::NY; ++j) o[j] = make_float2(0.0f, 0.0f);
 #pragma unroll 8
-    for (int q = 0; q < 32; ++q) {
-        const float *rq = rec + q * FR::RS;
-        const float2 xv = *(const float2 *)(rq + xo);
+        for (int q = 0; q < 16; ++q) {
+            const float *rq = rec + (2 * q + half) * FR::RS;
+            const float2 xv = *(const float2 *)(rq + xo);
+            float yv[FR::NY];
+            if constexpr (FR::NY == 4) {
+                const float4 t = *(const float4 *)(rq + yo);
+                yv[0] = t.x; yv[1] = t.y; yv[2] = t.z; yv[3] = t.w;
+            } else {
+                const float2 t = *(const float2 *)(rq + yo);
+                yv[0] = t.x; yv[1] = t.y;
+            }
 #pragma unroll
-        for (int k = 0; k < FR::BY; ++k) {
-            const float yv = rq[yo + k];
-            o[k] = __ffma2_rn(xv, make_float2(yv, yv), o[k]);
+            for (int j = 0; j < FR::NY; ++j) o[j] = __ffma2_rn(xv, make_float2(yv[j], yv[j]), o[j]);
         }
-    }
+        // both halves' sums (a + b = b + a: the halves hold the same value), then J3's two
+        // products (terms 2 and 3, NBX lanes apart within the half)
 #pragma unroll
-    for (int k = 0; k < FR::BY; ++k) {
-        const float ox3 = __shfl_down_sync(0xffffffffu, o[k].x, FR::NBT);
-        const float oy3 = __shfl_down_sync(0xffffffffu, o[k].y, FR::NBT);
-        if (term == 2) {
-            o[k].x += ox3;
-            o[k].y += oy3;
+        for (int j = 0; j < FR::NY; ++j) {
+            o[j].x += __shfl_xor_sync(0xffffffffu, o[j].x, 16);
+            o[j].y += __shfl_xor_sync(0xffffffffu, o[j].y, 16);
         }
-    }
-    if (term < 3) {
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
+        for (int j = 0; j < FR::NY; ++j) {
+            const float ox3 = __shfl_down_sync(0xffffffffu, o[j].x, NBX);
+            const float oy3 = __shfl_down_sync(0xffffffffu, o[j].y, NBX);
+            if (term == 2) {
+                o[j].x += ox3;
+                o[j].y += oy3;
+            }
+        }
+        // the halves add the lower and the upper NY / 2 rows
+        if (term < 3) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+#pragma unroll
+                for (int jj = 0; jj < FR::NY / 2; ++jj) {
+                    const int j = half ? FR::NY / 2 + jj : jj;
+                    const float vlo = i == 0 ? o[jj].x : o[jj].y;
+                    const float vhi = i == 0 ? o[FR::NY / 2 + jj].x : o[FR::NY / 2 + jj].y;
+                    const float v = half ? vhi : vlo;
+                    const int gx = mnx + 2 * bx + i, gy = mny + j;
+                    if (gx >= h.RX || gy >= h.RY || v == 0.0f) continue;
+                    const int node = gy * h.RX + gx;
+                    if (DET) {  // fixed-point words: the warps' sums commute exactly
+                        unsigned long long *t = term == 0 ? st.q1 : (term == 1 ? st.q2 : st.q3);
+                        atomicAdd(t + node, det_word32(v, h.dinv32));
+                    } else {
+                        float *t = term == 0 ? st.j1 : (term == 1 ? st.j2 : st.j3);
+                        atomicAdd(t + node, v);
+                    }
+                }
+            }
+        }
+    } else {
+        // this lane's sum: term t (0: J1 = px Ay, 1: J2 = Ax py, 2: J3 from Ax S0y, 3: J3 from
+        // Bx DSy; lanes past the four terms idle) on the sub-block (bx, by) of the frame, as packed
+        // pairs (the sub-block's two x nodes; each lane rounded as the scalar FMA)
+        const int term = lane / FR::NBT, sb = lane % FR::NBT;
+        const int bx = sb % (FR::NX / 2), by = sb / (FR::NX / 2);
+        const bool sums = term < 4;
+        const int xo = sums ? (term == 0 ? 0 : (term == 3 ? 2 * FR::NX : FR::NX)) + 2 * bx : 0;
+        const int yo = sums ? FR::XS + term * FR::NY + FR::BY * by : FR::XS;
+        float2 o[FR::BY];
+#pragma unroll
+        for (int k = 0; k < FR::BY; ++k) o[k] = make_float2(0.0f, 0.0f);
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+            const float *rq = rec + q * FR::RS;
+            const float2 xv = *(const float2 *)(rq + xo);
 #pragma unroll
             for (int k = 0; k < FR::BY; ++k) {
-                const int gx = mnx + 2 * bx + i, gy = mny + FR::BY * by + k;
-                const float v = i == 0 ? o[k].x : o[k].y;
-                if (gx >= h.RX || gy >= h.RY || v == 0.0f) continue;
-                const int node = gy * h.RX + gx;
-                if (DET) {  // fixed-point words: the warps' sums commute exactly
-                    unsigned long long *t = term == 0 ? st.q1 : (term == 1 ? st.q2 : st.q3);
-                    atomicAdd(t + node, det_word32(v, h.dinv32));
-                } else {
-                    float *t = term == 0 ? st.j1 : (term == 1 ? st.j2 : st.j3);
-                    atomicAdd(t + node, v);
+                const float yv = rq[yo + k];
+                o[k] = __ffma2_rn(xv, make_float2(yv, yv), o[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < FR::BY; ++k) {
+            const float ox3 = __shfl_down_sync(0xffffffffu, o[k].x, FR::NBT);
+            const float oy3 = __shfl_down_sync(0xffffffffu, o[k].y, FR::NBT);
+            if (term == 2) {
+                o[k].x += ox3;
+                o[k].y += oy3;
+            }
+        }
+        if (term < 3) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+#pragma unroll
+                for (int k = 0; k < FR::BY; ++k) {
+                    const int gx = mnx + 2 * bx + i, gy = mny + FR::BY * by + k;
+                    const float v = i == 0 ? o[k].x : o[k].y;
+                    if (gx >= h.RX || gy >= h.RY || v == 0.0f) continue;
+                    const int node = gy * h.RX + gx;
+                    if (DET) {  // fixed-point words: the warps' sums commute exactly
+                        unsigned long long *t = term == 0 ? st.q1 : (term == 1 ? st.q2 : st.q3);
+                        atomicAdd(t + node, det_word32(v, h.dinv32));
+                    } else {
+                        float *t = term == 0 ? st.j1 : (term == 1 ? st.j2 : st.j3);
+                        atomicAdd(t + node, v);
+                    }
                 }
             }
         }
