@@ -81,8 +81,9 @@ typedef struct {
                                App. C (beta_ij = (c dt/dx_j)^2/12, delta_i = ((c dt/dx_i)^2-1)/12,
                                Eq. Maxwell-A); Ampere's stencil is the Yee one in both        */
     int32_t tile_order;     /* order of the particles of a tile in the FP32 form:
-                               PIC_ORDER_AUTO (0): cell-major when a species holds >= 6
-                               particles per cell, else slot-major; PIC_ORDER_CELL (1):
+                               PIC_ORDER_AUTO (0): cell-major when a species holds >= 4
+                               (odd spline order) or >= 6 (even) particles per cell, else
+                               slot-major; PIC_ORDER_CELL (1):
                                (tile, cell, slot), the warp deposits of neighbouring lanes are
                                summed through shared memory; PIC_ORDER_SLOT (2): (tile, slot,
                                cell), every lane adds its own window with shared atomics.

@@ -453,19 +453,26 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
         rd.pre[a] = rd.drift[a] + lo;
         rd.post[a] = rd.drift[a] + hi;
         rd.reg[a] = rd.tile[a] + rd.pre[a] + rd.post[a];
+        // an even row stride keeps every even node of a staged row 8-byte aligned (the FP32
+        // deposit adds neighbouring x nodes in pairs)
+        if (a == 0 && (rd.reg[0] & 1)) { rd.post[0] += 1; rd.reg[0] += 1; }
         nodes *= rd.reg[a];
     }
     rd.reg_nodes = nodes;
     // Tile order.  The FP32 form sums the currents of a warp's lanes through shared memory when
     // their windows lie in a few neighbouring cells of a row: cell-major order gives that, and
-    // measured on a GB300 it is the faster one from about 6 particles of a species per cell up
-    // (1024x512, cubic: 16 per cell 9.0 vs 7.7, 64 per cell 14.9 vs 8.9 G particle-steps/s);
-    // below that (and in the FP64 form, which deposits per lane) the slot-major order puts the
-    // lanes of a warp in different cells for per-lane shared atomics.
+    // measured on a GB300 (512x256 pair plasma, FP32 particle kernel, ns per particle, cell-major
+    // vs slot-major) it is the faster one from 4 particles of a species per cell up for odd l,
+    // whose lanes of one row share their y window (cubic: 4 per species 0.102 vs 0.135, 8 per
+    // species 0.075 vs 0.123), and from 6 up for even l (quadratic: 4 per species 0.132 vs
+    // 0.096, 6 per species 0.092 vs 0.090, 8 per species 0.083 vs 0.086); below that (and in
+    // the FP64 form, which deposits per lane) the slot-major order puts the lanes of a warp in
+    // different cells for per-lane shared atomics.
     {
         int64_t capmax = 0;
         for (int s = 0; s < o.n_species; ++s) capmax = std::max(capmax, (int64_t)o.capacity[s]);
-        const bool dense = rd.ncell > 0 && capmax >= 6 * rd.ncell;
+        const int64_t per_cell_min = (spline_order & 1) ? 4 : 6;
+        const bool dense = rd.ncell > 0 && capmax >= per_cell_min * rd.ncell;
         if (o.tile_order < PIC_ORDER_AUTO || o.tile_order > PIC_ORDER_SLOT) { delete c; return PIC_EINVAL; }
         const bool cell = o.tile_order == PIC_ORDER_AUTO ? dense : o.tile_order == PIC_ORDER_CELL;
         rd.slot_major = (rd.prec == PIC_FP32_MIXED && cell) ? 0 : 1;

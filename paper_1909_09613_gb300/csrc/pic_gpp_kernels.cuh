@@ -228,6 +228,26 @@ __device__ __forceinline__ bool local_coord(int c, int origin, int tile, int dri
     return l >= -drift && l < tile + drift;
 }
 
+// Add (a, b) to the two FP32 values at p (8-byte aligned: two neighbouring x nodes of a staged
+// row that starts at an even node) with one 64-bit compare-and-swap loop and a packed add, each
+// half rounded as the scalar add.  Shared-memory FP32 additions are compare-and-swap loops
+// either way; this one serves two nodes.
+__device__ __forceinline__ void atomic_add_pair(float *p, float a, float b)
+{
+    unsigned long long *q = (unsigned long long *)p;
+    unsigned long long old = *q, got;
+    do {
+        float2 f = make_float2(__uint_as_float((unsigned)old),
+                               __uint_as_float((unsigned)(old >> 32)));
+        f = __fadd2_rn(f, make_float2(a, b));
+        const unsigned long long nw = (unsigned long long)__float_as_uint(f.x)
+                                      | ((unsigned long long)__float_as_uint(f.y) << 32);
+        got = atomicCAS(q, old, nw);
+        if (got == old) break;
+        old = got;
+    } while (true);
+}
+
 // One lane's Esirkepov window (Sec. 1: W_x = DSx (S0y + DSy/2) summed along x, W_y likewise,
 // W_z = S0x S0y + DSx S0y/2 + S0x DSy/2 + DSx DSy/3) added to the shared current tile with
 // atomics (WY as in deposit_lane_global below); DET: as fixed-point words (RunDev::det).
@@ -583,8 +603,20 @@ __device__ __forceinline__ void warp_frame_pass(const Hot2D &h, const Stage2D<fl
                 o[j].y += oy3;
             }
         }
-        // the halves add the lower and the upper NY / 2 rows
-        if (term < 3) {
+        // the halves add the lower and the upper NY / 2 rows; with an even frame origin each
+        // lane's two x nodes are one aligned pair (the row stride is even)
+        if (!DET && (mnx & 1) == 0) {
+            if (term < 3) {
+                float *t = term == 0 ? st.j1 : (term == 1 ? st.j2 : st.j3);
+#pragma unroll
+                for (int jj = 0; jj < FR::NY / 2; ++jj) {
+                    const float2 v = half ? o[FR::NY / 2 + jj] : o[jj];
+                    const int gx = mnx + 2 * bx, gy = mny + (half ? FR::NY / 2 + jj : jj);
+                    if (gx >= h.RX || gy >= h.RY || (v.x == 0.0f && v.y == 0.0f)) continue;
+                    atomic_add_pair(t + gy * h.RX + gx, v.x, v.y);
+                }
+            }
+        } else if (term < 3) {
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
 #pragma unroll
@@ -637,7 +669,17 @@ __device__ __forceinline__ void warp_frame_pass(const Hot2D &h, const Stage2D<fl
                 o[k].y += oy3;
             }
         }
-        if (term < 3) {
+        if (!DET && (mnx & 1) == 0) {
+            if (term < 3) {
+                float *t = term == 0 ? st.j1 : (term == 1 ? st.j2 : st.j3);
+#pragma unroll
+                for (int k = 0; k < FR::BY; ++k) {
+                    const int gx = mnx + 2 * bx, gy = mny + FR::BY * by + k;
+                    if (gx >= h.RX || gy >= h.RY || (o[k].x == 0.0f && o[k].y == 0.0f)) continue;
+                    atomic_add_pair(t + gy * h.RX + gx, o[k].x, o[k].y);
+                }
+            }
+        } else if (term < 3) {
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
 #pragma unroll
