@@ -492,6 +492,12 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     return PIC_OK;
 }
 
+// The 3D FP32 form (not deterministic) sums its current in an FP32 buffer (RunDev::J32).
+static bool uses_j32(const RunDev &rd)
+{
+    return rd.dim == 3 && rd.prec == PIC_FP32_MIXED && !rd.det;
+}
+
 int pic_footprint(const pic_ctx *c, size_t *bytes)
 {
     if (!c || !bytes) return PIC_EINVAL;
@@ -518,6 +524,7 @@ int pic_footprint(const pic_ctx *c, size_t *bytes)
     b += staging_size(rd, capmax);                // host<->device staging (chunked)
     b += 3 * align_up(rd.ncell * sizeof(double), A);  // rho, rho_prev, gref
     if (rd.det && rd.prec == PIC_FP64) b += 3 * align_up(rd.ncell * sizeof(double), A);  // jlo
+    if (uses_j32(rd)) b += align_up(3 * rd.ncell * sizeof(float), A);                   // J32
     b += 2 * A;                                   // diag out, err
     b += A;                                       // base alignment slack
     (void)captot;
@@ -583,6 +590,11 @@ int pic_bind_memory(pic_ctx *c, void *dev, size_t bytes)
     if (rd.det && rd.prec == PIC_FP64) {
         c->jlo = (unsigned long long *)take(3 * rd.ncell * sizeof(double));
         for (int a = 0; a < 3; ++a) rd.Jlo[a] = c->jlo + a * rd.ncell;
+    }
+    for (int a = 0; a < 3; ++a) rd.J32[a] = nullptr;
+    if (uses_j32(rd)) {
+        float *j = (float *)take(3 * rd.ncell * sizeof(float));
+        for (int a = 0; a < 3; ++a) rd.J32[a] = j + a * rd.ncell;
     }
     c->rho_prev_valid = false;
     c->gref_valid = false;
@@ -721,9 +733,14 @@ int pic_step(pic_ctx *c, int nsteps)
             if (r != PIC_OK) return r;
         }
         refresh_species_ptrs(c);
-        if (cudaMemsetAsync(rd.F[6], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess) return PIC_ECUDA;
-        if (cudaMemsetAsync(rd.F[7], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess) return PIC_ECUDA;
-        if (cudaMemsetAsync(rd.F[8], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess) return PIC_ECUDA;
+        if (rd.J32[0]) {  // F[6..8] are written whole from J32 after the particle pass
+            if (cudaMemsetAsync(rd.J32[0], 0, 3 * rd.ncell * sizeof(float), c->stream) != cudaSuccess)
+                return PIC_ECUDA;
+        } else {
+            for (int a = 6; a < 9; ++a)
+                if (cudaMemsetAsync(rd.F[a], 0, rd.ncell * sizeof(double), c->stream) != cudaSuccess)
+                    return PIC_ECUDA;
+        }
         if (c->jlo && cudaMemsetAsync(c->jlo, 0, 3 * rd.ncell * sizeof(double), c->stream) != cudaSuccess)
             return PIC_ECUDA;
         if (c->have_events) {
@@ -737,6 +754,9 @@ int pic_step(pic_ctx *c, int nsteps)
         c->gpp_launches += 1;
         if (rd.det) {  // the fixed-point sums become the FP64 current
             if (launch_det_finish(rd, c->stream) != cudaSuccess) return PIC_ECUDA;
+            c->kernel_launches += 1;
+        } else if (rd.J32[0]) {  // the FP32 sums become the FP64 current
+            if (launch_j32_finish(rd, c->stream) != cudaSuccess) return PIC_ECUDA;
             c->kernel_launches += 1;
         }
         for (int s = 0; s < rd.nsp; ++s) c->wc_valid[s] = c->wc[s] != nullptr;

@@ -115,6 +115,9 @@ struct RunDev {
     // fields (FP64, index (k*ny + j)*nx + i) and FP32 shadows of E, B (precision form)
     double *F[9];
     float *Fs[6];
+    // 3D FP32 form (not deterministic): the current summed by FP32 L2 reductions (index as F),
+    // converted into F[6..8] after the particle pass; null otherwise
+    float *J32[3];
     TTable tt[3];
     int nsp;
     SpeciesDev sp[PIC_NSP_MAX];

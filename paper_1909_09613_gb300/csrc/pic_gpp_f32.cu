@@ -13,8 +13,10 @@ __global__ void __launch_bounds__(256, 2) k_gpp2d(const __grid_constant__ RunDev
     tile_2d<L, KT, float, DET>(rd, smem, blockIdx.x);
 }
 
+// l <= 2: four blocks per SM (at most 128 registers; the gather through L1 is latency-bound, so
+// the extra warps help); higher orders keep their registers
 template <int L, int KT>
-__global__ void __launch_bounds__(128) k_gpp3d(const __grid_constant__ RunDev rd)
+__global__ void __launch_bounds__(128, (L <= 2 ? 4 : 1)) k_gpp3d(const __grid_constant__ RunDev rd)
 {
     tile_3d<L, KT, float>(rd, blockIdx.x);
 }

@@ -983,7 +983,8 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
     }
 }
 
-// One particle, 3D: fields through L1 (read-only path), current by global FP64 atomics.
+// One particle, 3D: fields through L1 (read-only path), current by global reductions (FP32
+// form: into the FP32 current RunDev::J32; FP64 form: into F[6..8]).
 template <int L, int KT, typename R>
 __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &sp, int64_t p)
 {
@@ -1172,6 +1173,10 @@ __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &
                             atomicAdd((unsigned long long *)(rd.F[6 + ax] + g), hi);
                             atomicAdd(rd.Jlo[ax] + g, lo);
                         }
+                    } else if constexpr (sizeof(R) == 4) {
+                        // FP32 L2 reductions: 2.4x the FP64 rate, and no FP32 -> FP64
+                        // conversion on the FP64 pipe per contribution
+                        atomicAdd(rd.J32[ax] + g, v);
                     } else {
                         atomicAdd(rd.F[6 + ax] + g, (double)v);
                     }

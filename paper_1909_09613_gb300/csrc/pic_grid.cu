@@ -427,6 +427,14 @@ __global__ void __launch_bounds__(kBlock) k_det_finish(const __grid_constant__ R
     }
 }
 
+__global__ void __launch_bounds__(kBlock) k_j32_finish(const __grid_constant__ RunDev rd)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= rd.ncell) return;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rd.F[6 + a][c] = (double)rd.J32[a][c];
+}
+
 inline unsigned grid_for(int64_t n)
 {
     return (unsigned)((n + kBlock - 1) / kBlock);
@@ -514,6 +522,12 @@ cudaError_t launch_gauss_ref(const RunDev &rd, double *rho, double *gref, double
 cudaError_t launch_det_finish(const RunDev &rd, cudaStream_t st)
 {
     k_det_finish<<<grid_for(rd.ncell), kBlock, 0, st>>>(rd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_j32_finish(const RunDev &rd, cudaStream_t st)
+{
+    k_j32_finish<<<grid_for(rd.ncell), kBlock, 0, st>>>(rd);
     return cudaGetLastError();
 }
 

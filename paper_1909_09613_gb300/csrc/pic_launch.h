@@ -46,6 +46,8 @@ cudaError_t launch_gauss_ref(const RunDev &rd, double *rho, double *gref, double
                              cudaStream_t st);
 // fixed-point current of a deterministic run -> FP64 (after the particle pass)
 cudaError_t launch_det_finish(const RunDev &rd, cudaStream_t st);
+// FP32 current of a 3D FP32 run (RunDev::J32) -> F[6..8] (after the particle pass)
+cudaError_t launch_j32_finish(const RunDev &rd, cudaStream_t st);
 
 // tile sort of one species
 cudaError_t launch_sort(const RunDev &rd, int s, int64_t *tile_start, void *const *dst_pos,
