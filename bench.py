@@ -632,8 +632,8 @@ def main():
     ap.add_argument("--t1-independent", action="store_true",
                     help="table1 form: species at independent positions (non-neutral start)")
     ap.add_argument("--form", default="both", choices=["both", "fp64", "fp32", "batched", "served",
-                                                       "table1"],
-                    help="fp32/batched/served: time only that form (profiling runs)")
+                                                       "table1", "3d"],
+                    help="fp32/batched/served/3d: time only that form (profiling runs)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--runs", type=int, default=256, help="batched form: number of runs")
     ap.add_argument("--max-nx", type=int, default=512, help="batched form: largest grid x")
@@ -700,6 +700,11 @@ def main():
                if args.form == "batched" else served_form())
         if rank == 0:
             print(json.dumps({"form": args.form, **out}))
+        return
+    if args.form == "3d":
+        out = form_3d(args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"form": "3d", **out}))
         return
     if args.form == "fp32":
         r32 = time_form(wl, pic.PIC_FP32_MIXED, args.steps, args.warmup, dist_on, clocks=False)
