@@ -964,16 +964,34 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
         const SpeciesDev &sp = rd.sp[s];
         const HotSp<R> hs = make_hotsp<R>(sp);
         const int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
-        // warp-uniform trip count: a warp's lanes take 32 consecutive particles
-        const int64_t wbase = a + (threadIdx.x & ~31);
-        for (int64_t q = wbase; q < b; q += blockDim.x) {
-            const int64_t p = q + (threadIdx.x & 31);
-            if (p + blockDim.x < b) {
-                prefetch_particle<R>(hs, p + blockDim.x);
-                if constexpr (sizeof(R) == 8 && L <= 3)
-                    if (hs.wc_mode == 2) prefetch_weights<L>(hs, p + blockDim.x);
+        if constexpr (sizeof(R) == 4) {
+            // every warp takes a contiguous chunk of the tile's particles of this species (for a
+            // uniform plasma in the cell-major order, one row of cells), so that the warps'
+            // frames, a row apart, rarely race for the same nodes of the tile: 5.53 -> 5.38 ms
+            // on the 134M-particle FP32 step (slot-major runs, whose lanes deposit one by one,
+            // lose about 5%; a runtime choice between the two loops cost the dense kernel more)
+            const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            const int64_t groups = (b - a + 31) / 32;
+            const int64_t gw = (groups + kTileWarps - 1) / kTileWarps;
+            const int64_t ca = a + 32 * min(groups, (int64_t)w * gw);
+            const int64_t cb = min(b, a + 32 * min(groups, (int64_t)(w + 1) * gw));
+            for (int64_t q = ca; q < cb; q += 32) {  // warp-uniform trip count
+                const int64_t p = q + lane;
+                if (p + 32 < cb) prefetch_particle<R>(hs, p + 32);
+                particle_2d<L, KT, R, DET>(h, hs, st, p, p < cb, x0, y0);
             }
-            particle_2d<L, KT, R, DET>(h, hs, st, p, p < b, x0, y0);
+        } else {
+            // warp-uniform trip count: a warp's lanes take 32 consecutive particles
+            const int64_t wbase = a + (threadIdx.x & ~31);
+            for (int64_t q = wbase; q < b; q += blockDim.x) {
+                const int64_t p = q + (threadIdx.x & 31);
+                if (p + blockDim.x < b) {
+                    prefetch_particle<R>(hs, p + blockDim.x);
+                    if constexpr (sizeof(R) == 8 && L <= 3)
+                        if (hs.wc_mode == 2) prefetch_weights<L>(hs, p + blockDim.x);
+                }
+                particle_2d<L, KT, R, DET>(h, hs, st, p, p < b, x0, y0);
+            }
         }
         if constexpr (sizeof(R) == 4) {  // the FP64 form deposits to global memory directly
             __syncthreads();
