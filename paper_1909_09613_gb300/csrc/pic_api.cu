@@ -439,7 +439,15 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     // sort interval and staged region
     double dmax = 0.0;
     for (int a = 0; a < dim; ++a) dmax = std::max(dmax, rd.dtt[a]);
-    int K = o.sort_interval > 0 ? o.sort_interval : (dim == 2 ? (int)std::floor(2.0 / dmax) + 1 : 8);
+    // default sort interval: particles stay within the staged halo until the next sort --
+    // 2 cells in 2D, 1 cell in the FP32 3D form (whose tile stage would not fit in shared memory
+    // with more), and 8 steps for the FP64 3D form, which reads its fields through L1
+    int K = o.sort_interval;
+    if (K <= 0) {
+        if (dim == 2) K = (int)std::floor(2.0 / dmax) + 1;
+        else if (o.precision == PIC_FP32_MIXED) K = (int)std::floor(1.0 / dmax) + 1;
+        else K = 8;
+    }
     c->sort_interval = std::max(1, K);
     int64_t nodes = 1;
     for (int a = 0; a < 3; ++a) {
@@ -484,7 +492,7 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     }
     c->stream = (cudaStream_t)(uintptr_t)o.stream;
     c->smem = 0;
-    if (dim == 2) {
+    if (dim == 2 || rd.prec == PIC_FP32_MIXED) {
         c->smem = rd.prec == PIC_FP32_MIXED ? gpp_smem_bytes_f32(rd) : gpp_smem_bytes_f64(rd);
         if (c->smem > 227 * 1024) { delete c; return PIC_EINVAL; }
     }

@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(256, 2) k_gpp2d(const __grid_constant__ RunDev
 template <int L, int KT>
 __global__ void __launch_bounds__(128, (L <= 2 ? 4 : 1)) k_gpp3d(const __grid_constant__ RunDev rd)
 {
-    tile_3d<L, KT, float>(rd, blockIdx.x);
+    extern __shared__ __align__(16) float sf3[];
+    tile_3d<L, KT, float>(rd, blockIdx.x, sf3);
 }
 
 template <int L, int KT>
@@ -32,7 +33,11 @@ cudaError_t go(const RunDev &rd, cudaStream_t st)
         if (e != cudaSuccess) return e;
         k<<<(unsigned)rd.ntiles, 256, smem, st>>>(rd);
     } else {
-        k_gpp3d<L, KT><<<(unsigned)rd.ntiles, 128, 0, st>>>(rd);
+        const size_t smem = stage3d_bytes(rd);
+        cudaError_t e = cudaFuncSetAttribute(k_gpp3d<L, KT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_gpp3d<L, KT><<<(unsigned)rd.ntiles, 128, smem, st>>>(rd);
     }
     return cudaGetLastError();
 }
@@ -53,7 +58,8 @@ cudaError_t launch_gpp_f32(const RunDev &rd, int kt, cudaStream_t st)
 
 size_t gpp_smem_bytes_f32(const RunDev &rd)
 {
-    return rd.dim == 2 ? stage2d_bytes<float>(rd.reg_nodes, rd.l, true, rd.det != 0) : 0;
+    return rd.dim == 2 ? stage2d_bytes<float>(rd.reg_nodes, rd.l, true, rd.det != 0)
+                       : stage3d_bytes(rd);
 }
 
 // Dynamic shared memory a work item of this run needs in the batched kernel: the copy of the
