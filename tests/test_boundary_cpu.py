@@ -325,3 +325,48 @@ def test_create_validates_deterministic_flag(lib):
             assert own > 0
         finally:
             pic.pic_destroy(ctx)
+
+
+@pytest.mark.parametrize("dtt", [0.1, 0.25, 0.4, 0.5, 0.6])
+def test_default_sort_interval_keeps_particles_in_the_halo(lib, dtt):
+    """The default sort interval K bounds the drift since the last sort, (K - 1) c dt/dx, by
+    the staged halo: 2 cells in 2D, 1 cell in the 3D FP32 form (whose tile stage holds one
+    cell of drift), and K = 8 for the 3D FP64 form (fields through L1).  The FP32 3D stage
+    must fit in shared memory."""
+    cases = [((128, 64, 1), pic.PIC_FP64, 2), ((128, 64, 1), pic.PIC_FP32_MIXED, 2),
+             ((64, 16, 16), pic.PIC_FP32_MIXED, 1), ((64, 16, 16), pic.PIC_FP64, None)]
+    for grid, prec, drift in cases:
+        if grid[2] > 1 and dtt * np.sqrt(3.0) >= 1.0:
+            continue  # beyond the 3D Courant limit
+        n = grid[0] * grid[1] * grid[2] * 4
+        ctx = pic.pic_create(grid, (1.0, 1.0, 1.0), dtt, 2, pic.PIC_SCHEME_WT, _opt((n, n), prec))
+        try:
+            _, _, si, _ = pic.pic_tile_info(ctx)
+            if drift is None:
+                assert si == 8
+            else:
+                assert si == int(np.floor(drift / dtt)) + 1
+                assert (si - 1) * dtt <= drift + 1e-12
+            if grid[2] > 1 and prec == pic.PIC_FP32_MIXED:
+                own = pic.pic_smem_info(ctx)[0]
+                assert 0 < own <= 48 * 1024  # four 128-thread blocks per SM
+        finally:
+            pic.pic_destroy(ctx)
+
+
+@pytest.mark.parametrize("l,per_species,cell_major", [(3, 4, True), (3, 3, False), (2, 4, False),
+                                                       (2, 6, True), (4, 5, False), (1, 4, True)])
+def test_tile_order_threshold_depends_on_spline_order(lib, l, per_species, cell_major):
+    """FP32 runs use the cell-major tile order from 4 particles of a species per cell for odd l
+    (the lanes of one cell row share their y window) and from 6 for even l; the FP64 form always
+    uses the slot-major order."""
+    grid = (128, 64, 1)
+    n = grid[0] * grid[1] * per_species
+    for prec in (pic.PIC_FP32_MIXED, pic.PIC_FP64):
+        ctx = pic.pic_create(grid, (1.0, 1.0, 1.0), 0.3, l, pic.PIC_SCHEME_WT, _opt((n, n), prec))
+        try:
+            slot_major = pic.pic_tile_info(ctx)[3]
+            want = 0 if (cell_major and prec == pic.PIC_FP32_MIXED) else 1
+            assert slot_major == want, (l, per_species, prec)
+        finally:
+            pic.pic_destroy(ctx)
