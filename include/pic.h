@@ -134,7 +134,10 @@ int pic_alloc(pic_ctx *ctx);
  * (rho = q w W_l / V_c, Sec. 2 Eq. shape-real), n <= capacity particles.
  *   x: host, dim x n FP64 SoA, physical positions (wrapped into [0, n_i dx_i));
  *   u: host, 3 x n FP64 SoA, u = gamma v (units of c), the momentum at t^{n-1/2}.
- * Copies host -> device, packs into the context's precision form and tile-sorts. Syncs.   */
+ * Copies host -> device, packs into the context's precision form and tile-sorts. Syncs.
+ * Page-locked host arrays that the device can address (cudaHostAlloc, cudaHostRegister) are
+ * read in place by the packing kernel; pageable ones go through a staging buffer in chunks.
+ * The arrays are not modified.                                                             */
 int pic_load_particles(pic_ctx *ctx, int species, double q, double m, double w, int64_t n,
                        const double *x, const double *u);
 

@@ -271,8 +271,23 @@ int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n
     if (!(m > 0.0) || !(w >= 0.0) || (n > 0 && (!x || !u))) return PIC_EINVAL;
     set_species(c, species, q, m, w, n);
     const int d = c->rd.dim;
-    if (on_device) {
-        if (launch_pack(c->rd, species, x, n, u, n, n, 0, c->stream) != cudaSuccess) return PIC_ECUDA;
+    // page-locked host arrays the device can address (cudaHostAlloc / cudaHostRegister) are read
+    // by the packing kernel in place, over the host link, without the staging copies
+    const double *xd = nullptr, *ud = nullptr;
+    if (!on_device && n > 0) {
+        cudaPointerAttributes ax, au;
+        if (cudaPointerGetAttributes(&ax, x) == cudaSuccess && ax.type == cudaMemoryTypeHost
+            && ax.devicePointer && cudaPointerGetAttributes(&au, u) == cudaSuccess
+            && au.type == cudaMemoryTypeHost && au.devicePointer) {
+            xd = (const double *)ax.devicePointer;
+            ud = (const double *)au.devicePointer;
+        }
+        cudaGetLastError();  // a pageable pointer is not an error here
+    }
+    if (on_device || xd) {
+        if (launch_pack(c->rd, species, on_device ? x : xd, n, on_device ? u : ud, n, n, 0,
+                        c->stream) != cudaSuccess)
+            return PIC_ECUDA;
         if (n > 0) c->kernel_launches += 1;
     } else if (n > 0) {
         // host arrays go through the two halves of the staging buffer in turn: the copies of

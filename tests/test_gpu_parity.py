@@ -552,3 +552,31 @@ def test_wt_equals_mc_at_half_step_gpu():
         run.close()
     for a, b in zip(*outs):
         assert rel(a, b) < 1e-13
+
+
+@pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("grid", [(48, 24), (12, 10, 8)], ids=["2d", "3d"])
+def test_load_from_pinned_host_arrays_matches_pageable(prec, grid):
+    """pic_load_particles reads page-locked host arrays in place (no staging copies) and
+    pageable ones through the staging buffer: both must store the same particles, bit for bit,
+    in the same tile order."""
+    dim = len(grid)
+    wl = plasma.pair_plasma(grid, (1.0,) * dim, 0.3, 2, 1, 5.0, 0.1, 12, omega_p=0.2, seed=33)
+    caps = [int(s.x.shape[1]) for s in wl.species]
+    runs = []
+    for pinned in (False, True):
+        r = pic.Run(wl.grid, wl.dx, wl.dt, wl.l, wl.scheme, precision=prec, capacity=caps)
+        for i, s in enumerate(wl.species):
+            x = np.ascontiguousarray(s.x, dtype=np.float64)
+            u = np.ascontiguousarray(s.u, dtype=np.float64)
+            if pinned:
+                x, u = torch.from_numpy(x).pin_memory(), torch.from_numpy(u).pin_memory()
+                assert x.is_pinned()
+            r.load(i, s.q, s.m, s.w, x, u)
+        runs.append(r)
+    for i in range(len(wl.species)):
+        a, b = runs[0].particles(i), runs[1].particles(i)
+        for va, vb in zip(a, b):
+            assert np.array_equal(va, vb)
+    for r in runs:
+        r.close()
