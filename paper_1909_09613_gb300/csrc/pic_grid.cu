@@ -308,13 +308,35 @@ __global__ void __launch_bounds__(kBlock) k_kinetic(const __grid_constant__ RunD
 
 // rho = sum q w W_l / V_c at integer nodes (FP64 atomics): the l + 1 non-zero B-spline
 // weights per axis from the basis polynomials, the same S0 the Esirkepov deposit starts from.
+// A block covers kRhoPer * kBlock consecutive particles of the store, and the lanes of a warp
+// take particles 32 apart: in the cell-major order 32 neighbours in the store usually share a
+// cell, and their FP64 reductions to the same nodes would be serialised by L2, while particles
+// 32 apart sit in different cells.
+constexpr int kRhoPer = 4;
+static_assert(kBlock / 32 * kRhoPer == 32, "a warp's lanes cover 32 particles 32 apart");
+
+template <int L>
+__device__ __forceinline__ void rho_particle(const RunDev &rd, const SpeciesDev &sp, int64_t p,
+                                             double *rho);
+
 template <int L>
 __global__ void __launch_bounds__(kBlock) k_rho(const __grid_constant__ RunDev rd, int s,
                                                 double *rho)
 {
     const SpeciesDev &sp = rd.sp[s];
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= sp.n) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = blockIdx.x * (int64_t)kBlock * kRhoPer;
+#pragma unroll 1
+    for (int r = 0; r < kRhoPer; ++r) {
+        const int64_t p = base + lane * 32 + warp + (kBlock / 32) * r;
+        if (p < sp.n) rho_particle<L>(rd, sp, p, rho);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void rho_particle(const RunDev &rd, const SpeciesDev &sp, int64_t p,
+                                             double *rho)
+{
     int c[3] = {0, 0, 0};
     double d[3] = {0, 0, 0};
     if (rd.prec == 1) {
@@ -344,15 +366,15 @@ __global__ void __launch_bounds__(kBlock) k_rho(const __grid_constant__ RunDev r
     const double qw = sp.q * sp.w / vc;
     const int nk = rd.dim == 3 ? L + 1 : 1;
     for (int kk = 0; kk < nk; ++kk) {
-        const int gk = rd.dim == 3 ? wrap_idx(c[2] + b[2] + kk, rd.n[2]) : 0;
+        const int gk = rd.dim == 3 ? wrap_near(c[2] + b[2] + kk, rd.n[2]) : 0;
         const double wk = rd.dim == 3 ? qw * w[2][kk] : qw;
 #pragma unroll
         for (int jj = 0; jj <= L; ++jj) {
-            const int gj = wrap_idx(c[1] + b[1] + jj, rd.n[1]);
+            const int gj = wrap_near(c[1] + b[1] + jj, rd.n[1]);
             const double wjk = wk * w[1][jj];
 #pragma unroll
             for (int ii = 0; ii <= L; ++ii) {
-                const int gi = wrap_idx(c[0] + b[0] + ii, rd.n[0]);
+                const int gi = wrap_near(c[0] + b[0] + ii, rd.n[0]);
                 atomicAdd(rho + gidx(rd, gi, gj, gk), wjk * w[0][ii]);
             }
         }
@@ -483,7 +505,7 @@ static cudaError_t launch_rho(const RunDev &rd, double *rho, cudaStream_t st)
     if (e != cudaSuccess) return e;
     for (int s = 0; s < rd.nsp; ++s) {
         if (rd.sp[s].n == 0) continue;
-        const unsigned g = grid_for(rd.sp[s].n);
+        const unsigned g = grid_for((rd.sp[s].n + kRhoPer - 1) / kRhoPer);
         switch (rd.l) {
         case 1: k_rho<1><<<g, kBlock, 0, st>>>(rd, s, rho); break;
         case 2: k_rho<2><<<g, kBlock, 0, st>>>(rd, s, rho); break;
