@@ -366,12 +366,23 @@ def batched_form(steps, warmup, n_runs=256, max_nx=512, baselines=True):
     items, launches = b.info()
     b.close()
     flags = sum(r.diag()["error_flags"] for r in runs)
+    # the persistent particle kernel against the measured HBM copy rate, with the precision
+    # form's algorithmic bytes (particle state read and written, fields read and current written)
+    ncell = sum(int(math.prod(r.grid)) for r in reqs)
+    pb, gb = BYTES["fp32"]
+    alg = n_part * pb + ncell * gb
+    peaks, peak_kind = _peaks()
+    ach = alg / (gpp_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "k_b_gpp (persistent, every run's tiles)", "kernel_ms": gpp_ms,
+                "algorithmic_bytes": alg, "peak_source": "%s hbm_gbs" % peak_kind}
     if not baselines:
         for r in runs:
             r.close()
         return {"value": n_part * steps / (ms * 1e-3), "unit": UNIT, "runs": n_runs,
                 "particles": n_part, "ms_per_step": ms / steps, "gpp_ms_per_step": gpp_ms,
-                "error_flags": flags}
+                "roofline": roofline, "error_flags": flags}
     # the same runs one after another, each through pic_step (FP32 form)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -399,6 +410,7 @@ def batched_form(steps, warmup, n_runs=256, max_nx=512, baselines=True):
     return {"value": n_part * steps / (ms * 1e-3), "unit": UNIT, "runs": n_runs,
             "particles": n_part, "steps": steps, "ms_per_step": ms / steps,
             "gpp_ms_per_step": gpp_ms, "work_items": items, "launches_per_step": launches,
+            "roofline": roofline,
             "graph": "one CUDA graph per batch step, replayed",
             "sequential_fp32_particle_steps_per_s": n_part / (seq32_ms * 1e-3),
             "sequential_fp64_plain_particle_steps_per_s": n_part / t64,
