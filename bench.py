@@ -68,12 +68,18 @@ def _peaks():
 
 
 def kernel_digest():
-    """sha256 (16 hex digits) of the particle kernel's source files."""
+    """sha256 (16 hex digits) of the particle kernel's source files with comments and blank
+    space left out: an edit of a comment does not change the kernel the counts describe."""
     import hashlib
+    import re
     from paper_1909_09613_gb300 import _build
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(_build.CSRC, f), "rb").read())
+        txt = open(os.path.join(_build.CSRC, f)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        txt = "\n".join(line.strip() for line in txt.splitlines() if line.strip())
+        h.update(txt.encode())
     return h.hexdigest()[:16]
 
 

@@ -9,7 +9,9 @@
 // its lanes' currents through shared memory into a J tile that is added to the global FP64
 // current with one atomic per tile node and component, once per species; the FP64 form, bound
 // by its FP64 pipe, adds every contribution to the global current as an L2 reduction.  In 3D
-// fields are read through the L1 cache and the current goes straight to global reductions.
+// the FP32 form stages its tile's fields in shared memory too (the FP64 form reads them through
+// L1), and every current contribution goes straight to a global reduction (FP32 form: into an
+// FP32 current converted to FP64 once per step).
 #pragma once
 #include "pic_common.cuh"
 

@@ -33,12 +33,13 @@ constexpr int kTileWarps = 8;
 // (J1 = sum px (x) Ay, J2 = sum Ax (x) py, J3 = sum Ax (x) S0y + Bx (x) DSy, in the notation of
 // particle_2d) on a common NX x NY block of nodes.  Every lane writes its factor vectors,
 // shifted into the block, as a record (x part: px, Ax, Bx over NX nodes; y part: Ay, py, S0y,
-// DSy over NY nodes); then each lane sums, over the 32 records, one term (J1, J2, or one of the
-// two products of J3) on a 2 x BY sub-block of nodes (BY = NY / 2): per record one 64-bit load
-// of its two x factors and BY 32-bit loads of its y factors, all of them shared-memory
-// broadcasts within the record, and BY packed FMAs.  That is 2 + BY wavefronts per record for
-// the warp, against 8 for two 128-bit loads per lane (a 128-bit load takes a wavefront per
-// quarter warp): the sums are bound by shared-memory wavefronts and issue, not by arithmetic.
+// DSy over NY nodes); then the lanes sum the 32 records, each lane one term (J1, J2, or one of
+// the two products of J3) on a block of nodes with packed FMAs, every load a shared-memory
+// broadcast within its record: on a HALF frame (NY = 2 or 4) the two half warps take the even
+// and the odd records, each lane a 2 x NY block from one 64-bit and one 64- or 128-bit load per
+// record; otherwise each lane takes a 2 x BY block (BY = NY / 2) over all 32 records, from one
+// 64-bit and BY 32-bit loads.  The sums are bound by shared-memory wavefronts and issue, not by
+// arithmetic (a 128-bit load takes a wavefront per quarter warp, a 64-bit one per half warp).
 // RS (floats per record) is a multiple of 4 with RS / 4 odd, so that the float4 stores of 8
 // consecutive lanes fall in distinct banks.  NARROW: no lane of the group moved its y window
 // base, so every window's last row (node l + 1) is zero and the frame has l + 1 + SYM rows
