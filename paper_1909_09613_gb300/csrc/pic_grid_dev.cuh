@@ -68,9 +68,15 @@ __device__ __forceinline__ void yee_b_cell(const RunDev &rd, int64_t c, double h
         const double *E1 = rd.F[0], *E2 = rd.F[1], *E3 = rd.F[2];
         const double e1 = E1[c], e2 = E2[c], e3 = E3[c];
         const double idx = rd.idx[0], idy = rd.idx[1], idz = rd.idx[2];
-        c1 = (E3[gidx(rd, i, jp, k)] - e3) * idy - (E2[gidx(rd, i, j, kp)] - e2) * idz;
-        c2 = (E1[gidx(rd, i, j, kp)] - e1) * idz - (E3[gidx(rd, ip, j, k)] - e3) * idx;
-        c3 = (E2[gidx(rd, ip, j, k)] - e2) * idx - (E1[gidx(rd, i, jp, k)] - e1) * idy;
+        if (rd.dim == 2) {  // the z differences are exact zeros: the same values, fewer FP64 ops
+            c1 = (E3[gidx(rd, i, jp, k)] - e3) * idy;
+            c2 = -((E3[gidx(rd, ip, j, k)] - e3) * idx);
+            c3 = (E2[gidx(rd, ip, j, k)] - e2) * idx - (E1[gidx(rd, i, jp, k)] - e1) * idy;
+        } else {
+            c1 = (E3[gidx(rd, i, jp, k)] - e3) * idy - (E2[gidx(rd, i, j, kp)] - e2) * idz;
+            c2 = (E1[gidx(rd, i, j, kp)] - e1) * idz - (E3[gidx(rd, ip, j, k)] - e3) * idx;
+            c3 = (E2[gidx(rd, ip, j, k)] - e2) * idx - (E1[gidx(rd, i, jp, k)] - e1) * idy;
+        }
     }
     const double b1 = rd.F[3][c] - h * c1;
     const double b2 = rd.F[4][c] - h * c2;
@@ -99,13 +105,19 @@ __device__ __forceinline__ void yee_e_cell(const RunDev &rd, int64_t c, int shad
     const double idx = rd.idx[0], idy = rd.idx[1], idz = rd.idx[2];
     const double dt = rd.dt;
     const double dB3dy = (b3 - B3[gidx(rd, i, jm, k)]) * idy;
-    const double dB2dz = (b2 - B2[gidx(rd, i, j, km)]) * idz;
-    const double dB1dz = (b1 - B1[gidx(rd, i, j, km)]) * idz;
     const double dB3dx = (b3 - B3[gidx(rd, im, j, k)]) * idx;
     const double dB2dx = (b2 - B2[gidx(rd, im, j, k)]) * idx;
     const double dB1dy = (b1 - B1[gidx(rd, i, jm, k)]) * idy;
-    const double e1 = rd.F[0][c] + dt * (dB3dy - dB2dz) - dt * rd.F[6][c];
-    const double e2 = rd.F[1][c] + dt * (dB1dz - dB3dx) - dt * rd.F[7][c];
+    double e1, e2;
+    if (rd.dim == 2) {  // the z differences are exact zeros: the same values, fewer FP64 ops
+        e1 = rd.F[0][c] + dt * dB3dy - dt * rd.F[6][c];
+        e2 = rd.F[1][c] + dt * (-dB3dx) - dt * rd.F[7][c];
+    } else {
+        const double dB2dz = (b2 - B2[gidx(rd, i, j, km)]) * idz;
+        const double dB1dz = (b1 - B1[gidx(rd, i, j, km)]) * idz;
+        e1 = rd.F[0][c] + dt * (dB3dy - dB2dz) - dt * rd.F[6][c];
+        e2 = rd.F[1][c] + dt * (dB1dz - dB3dx) - dt * rd.F[7][c];
+    }
     const double e3 = rd.F[2][c] + dt * (dB2dx - dB1dy) - dt * rd.F[8][c];
     rd.F[0][c] = e1;
     rd.F[1][c] = e2;
