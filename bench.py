@@ -45,7 +45,13 @@ WORKLOAD = "pair_2048x1024_l3_WT_g50_uth0.01_ppc64_cdt0.25"
 #              pipe), reported beside the roofline as extra traffic.
 #   FP32 form: 2 x (4 cell + 2 x 4 offset + 3 x 4 momentum) = 48 B;
 #              grid: FP32 shadow of E, B (6 x 4 B) + FP64 J (3 x 8 B) = 48 B per cell.
-BYTES = {"fp64": (80.0, 72.0), "fp32": (48.0, 48.0)}
+# Algorithmic bytes per particle-step and per cell-step of each form (the method's per-unit
+# figures): the particle state read and written once, and the grid traffic of a whole step per
+# cell (FP64: gather 48 + J 72 + Yee 120; FP32: FP64 Yee 192 + FP32 shadows 24 + gather 24 +
+# J 72), amortised over the particles.  KERNEL_GRID_BYTES: the particle kernel's own grid bytes
+# (fields read, current written), for the kernel-only view reported beside the roofline.
+BYTES = {"fp64": (80.0, 240.0), "fp32": (48.0, 310.0)}
+KERNEL_GRID_BYTES = {"fp64": 72.0, "fp32": 48.0}
 WEIGHT_CACHE_BYTES_FP64_L3 = 128.0
 SCHEDULERS_PER_SM = 4
 # The particle kernel's sources: the counts of profiles/counts.txt (from one ncu capture) are
@@ -382,7 +388,8 @@ def batched_form(steps, warmup, n_runs=256, max_nx=512, baselines=True):
     roofline = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None,
                 "kernel": "k_b_gpp (persistent, every run's tiles)", "kernel_ms": gpp_ms,
-                "algorithmic_bytes": alg, "peak_source": "%s hbm_gbs" % peak_kind}
+                "algorithmic_bytes": alg, "bytes_per_unit": {"particle": pb, "cell": gb},
+                "peak_source": "%s hbm_gbs" % peak_kind}
     if not baselines:
         for r in runs:
             r.close()
@@ -835,6 +842,9 @@ def main():
                          "traffic": c32.get("dram_bytes_per_launch"),
                          "kernel": "k_gpp2d<3,4> (float)", "kernel_ms": g32 * 1e3,
                          "algorithmic_bytes": ab, "peak_source": "%s hbm_gbs" % peak_kind,
+                         "bytes_per_unit": {"particle": pb, "cell": gb},
+                         "kernel_grid_only_frac": (r32["n"] * pb + r32["ncell"] * KERNEL_GRID_BYTES["fp32"])
+                                                  / g32 / 1e9 / peaks["hbm_gbs"],
                          "counts_digest": digest, "counts_from_profile": bool(c32)},
             "charge_conservation": r32["charge_conservation"],
             "gpu_launches": r32["launches"], "clocks": r32["clocks"]}
