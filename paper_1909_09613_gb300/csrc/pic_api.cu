@@ -276,9 +276,14 @@ int load_common(pic_ctx *c, int species, double q, double m, double w, int64_t n
     const double *xd = nullptr, *ud = nullptr;
     if (!on_device && n > 0) {
         cudaPointerAttributes ax, au;
-        if (cudaPointerGetAttributes(&ax, x) == cudaSuccess && ax.type == cudaMemoryTypeHost
-            && ax.devicePointer && cudaPointerGetAttributes(&au, u) == cudaSuccess
-            && au.type == cudaMemoryTypeHost && au.devicePointer) {
+        int dev = -1;
+        // the device pointers are this device's (memory pinned through another device's
+        // context takes the staging path)
+        if (cudaGetDevice(&dev) == cudaSuccess
+            && cudaPointerGetAttributes(&ax, x) == cudaSuccess && ax.type == cudaMemoryTypeHost
+            && ax.devicePointer && ax.device == dev
+            && cudaPointerGetAttributes(&au, u) == cudaSuccess
+            && au.type == cudaMemoryTypeHost && au.devicePointer && au.device == dev) {
             xd = (const double *)ax.devicePointer;
             ud = (const double *)au.devicePointer;
         }
