@@ -639,6 +639,7 @@ def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
             "capacity_2d_batched": cap2d, "capacity_3d_alone": cap3d,
             "makespan_s": makespan, "max_concurrent_runs": srv.max_active,
             "batch_builds": srv.batch_builds, "batch_set_changes": srv.set_changes,
+            "batch_lane_runs": srv.lane_runs, "longest_host_block_s": srv.host_block_s,
             "peak_admitted_bytes": srv.peak_bytes, "budget_bytes": budget,
             "steps_per_request": steps, "requests_3d": sum(1 for r in reqs if r.dim == 3),
             "largest_3d_grid": max((list(r.grid) for r in reqs if r.dim == 3), default=None,

@@ -252,7 +252,9 @@ int pic_sync(pic_ctx *ctx);
  * species count, same stream; each created,
  * bound and loaded as usual) advanced together.  One batch step = device-side choice of the runs
  * due for a tile sort, the batched sort of those runs, ONE persistent gather-push-deposit
- * launch over the tiles of every run (heaviest tiles first, pulled from a device counter), and
+ * launch over the tiles of every run (heaviest tiles first, pulled from a device counter; when
+ * the set holds few particles, tiles heavier than the average load of a CTA slot are split into
+ * up to 8 work items that share their particles, so that small runs are not paced by one CTA), and
  * one launch per Yee half/full update covering all runs.  The step's launch sequence is captured
  * in a CUDA graph on the first pic_batch_step and replayed; its launches walk device-resident
  * tables, so the same graph serves any run set that fits the batch's capacities.  While a batch exists, its runs must
@@ -267,7 +269,9 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out);
 typedef struct {
     int32_t runs;                  /* runs at once                                          */
     int64_t cells;                 /* cells, summed over the runs                           */
-    int64_t tiles;                 /* particle tiles, summed over the runs                  */
+    int64_t tiles;                 /* work items of the particle kernel: the runs' tiles,
+                                      summed; a set of few particles splits its heavier tiles
+                                      into up to 8 items each, which count here too          */
     size_t stage_bytes;            /* largest dynamic shared memory per CTA a run's work
                                       items may need in the batched kernel (pic_smem_info's
                                       batched_bytes); fixes the persistent kernel's shared

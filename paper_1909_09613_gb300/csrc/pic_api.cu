@@ -438,8 +438,12 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
     // tiles
     // default tiles (measured on the 2048x1024 cubic workload: the FP32 form is 2% faster with
     // 64x8 than with 32x8, the FP64 form the same with both); a deterministic FP32 run keeps
-    // 64-bit words in its shared current tile and takes 32x8 so that two CTAs share an SM
-    const int deft[2][3] = {{rd.prec == PIC_FP32_MIXED && !rd.det ? 64 : 32, 8, 1}, {8, 4, 4}};
+    // 64-bit words in its shared current tile and takes 32x8 so that two CTAs share an SM.  3D
+    // (256x64x64 quadratic pair plasma, 8 per cell, ms per step): the FP32 form 1.95 with 16x4x2
+    // against 2.15 with 8x4x4 (a warp's 32 cells span 16 nodes of two rows, fewer L2 sectors per
+    // reduction of its deposit), the FP64 form 13.1 with either
+    const bool f32 = rd.prec == PIC_FP32_MIXED && !rd.det;
+    const int deft[2][3] = {{f32 ? 64 : 32, 8, 1}, {f32 ? 16 : 8, 4, f32 ? 2 : 4}};
     for (int a = 0; a < 3; ++a) {
         int t = o.tile[a] > 0 ? o.tile[a] : deft[dim - 2][a];
         if (a >= dim) t = 1;
@@ -487,6 +491,17 @@ int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_
         nodes *= rd.reg[a];
     }
     rd.reg_nodes = nodes;
+    // padded FP32 current of the 3D FP32 form: the Esirkepov window of a particle in cell c
+    // spans nodes c - jp_lo .. c + l + 1 - (l - 1) / 2 along every axis
+    rd.jp_lo = 0;
+    for (int a = 0; a < 3; ++a) rd.jp[a] = rd.n[a];
+    if (dim == 3 && rd.prec == PIC_FP32_MIXED && !rd.det) {
+        const int lo = (spline_order - 1) / 2 + 1 + (spline_order % 2 == 0 ? 1 : 0);
+        const int hi = spline_order + 1 - (spline_order - 1) / 2;
+        rd.jp_lo = lo;
+        for (int a = 0; a < 3; ++a) rd.jp[a] = rd.n[a] + lo + hi;
+    }
+    rd.jp_nodes = (int64_t)rd.jp[0] * rd.jp[1] * rd.jp[2];
     // Tile order.  The FP32 form sums the currents of a warp's lanes through shared memory when
     // their windows lie in a few neighbouring cells of a row: cell-major order gives that, and
     // measured on a GB300 (512x256 pair plasma, FP32 particle kernel, ns per particle, cell-major
@@ -552,7 +567,7 @@ int pic_footprint(const pic_ctx *c, size_t *bytes)
     b += staging_size(rd, capmax);                // host<->device staging (chunked)
     b += 3 * align_up(rd.ncell * sizeof(double), A);  // rho, rho_prev, gref
     if (rd.det && rd.prec == PIC_FP64) b += 3 * align_up(rd.ncell * sizeof(double), A);  // jlo
-    if (uses_j32(rd)) b += align_up(3 * rd.ncell * sizeof(float), A);                   // J32
+    if (uses_j32(rd)) b += align_up(3 * rd.jp_nodes * sizeof(float), A);                // J32
     b += 2 * A;                                   // diag out, err
     b += A;                                       // base alignment slack
     (void)captot;
@@ -621,8 +636,8 @@ int pic_bind_memory(pic_ctx *c, void *dev, size_t bytes)
     }
     for (int a = 0; a < 3; ++a) rd.J32[a] = nullptr;
     if (uses_j32(rd)) {
-        float *j = (float *)take(3 * rd.ncell * sizeof(float));
-        for (int a = 0; a < 3; ++a) rd.J32[a] = j + a * rd.ncell;
+        float *j = (float *)take(3 * rd.jp_nodes * sizeof(float));
+        for (int a = 0; a < 3; ++a) rd.J32[a] = j + a * rd.jp_nodes;
     }
     c->rho_prev_valid = false;
     c->gref_valid = false;
@@ -762,7 +777,7 @@ int pic_step(pic_ctx *c, int nsteps)
         }
         refresh_species_ptrs(c);
         if (rd.J32[0]) {  // F[6..8] are written whole from J32 after the particle pass
-            if (cudaMemsetAsync(rd.J32[0], 0, 3 * rd.ncell * sizeof(float), c->stream) != cudaSuccess)
+            if (cudaMemsetAsync(rd.J32[0], 0, 3 * rd.jp_nodes * sizeof(float), c->stream) != cudaSuccess)
                 return PIC_ECUDA;
         } else {
             for (int a = 6; a < 9; ++a)

@@ -45,6 +45,9 @@ constexpr int kBlock = 256;
 constexpr int kPartPer = 8, kKeyPer = 8, kCellPer = 4;
 // threads of the per-tile sort stages: one per cell of the largest tile a run may have
 constexpr int kTileThreads = 1024;
+// work items of a split tile: at most kPartMax, each of at least kPartMin particles
+constexpr int kPartMax = 8;
+constexpr int64_t kPartMin = 2048;
 
 struct RunState {
     int age, interval, due, kt;
@@ -267,15 +270,15 @@ __global__ void __launch_bounds__(kBlock) k_b_yee_e(const Counts *cn, const RunD
 
 // ---- the persistent gather-push-deposit kernel over all runs' tiles ----
 template <int L, int KT>
-__device__ __forceinline__ bool try_tile(const RunDev &rd, int kt, char *smem, int64_t tile)
+__device__ __forceinline__ bool try_tile(const RunDev &rd, int kt, char *smem, const int4 &w)
 {
     if (rd.l != L || kt != KT) return false;
-    tile_2d<L, KT, float>(rd, smem, tile, rd.tt);  // the descriptor copy holds the tables
+    tile_2d<L, KT, float>(rd, smem, w.y, rd.tt, w.z, w.w);  // the descriptor copy holds the tables
     return true;
 }
 
 __global__ void __launch_bounds__(256, 2) k_b_gpp(const Counts *cn, const RunDev *runs,
-                                              const RunState *st, const int2 *items, int *counter)
+                                              const RunState *st, const int4 *items, int *counter)
 {
     extern __shared__ __align__(16) char smem_all[];
     // the run descriptor is copied next to the tile stage so that the particle loop reads it
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(256, 2) k_b_gpp(const Counts *cn, const RunDev
         __syncthreads();
         const int it = item;
         if (it >= nitems) return;
-        const int2 w = items[it];
+        const int4 w = items[it];  // run, tile, part, parts
         const int kt = st[w.x].kt;
         for (int i = threadIdx.x; i < (int)(sizeof(RunDev) / sizeof(int)); i += blockDim.x)
             ((int *)rds)[i] = ((const int *)(runs + w.x))[i];
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(256, 2) k_b_gpp(const Counts *cn, const RunDev
         const RunDev &rd = *rds;
         // every run in a batch uses the wide integer-node stencil (l + 2 nodes; the extra
         // weight is zero when c dt <= dx/2), so two instances cover the batch
-        if (!(try_tile<2, 4>(rd, kt, smem, w.y) || try_tile<3, 5>(rd, kt, smem, w.y)))
+        if (!(try_tile<2, 4>(rd, kt, smem, w) || try_tile<3, 5>(rd, kt, smem, w)))
             set_err(rd.err, 1);
     }
 }
@@ -325,7 +328,7 @@ struct pic_batch {
     int cap_runs;
     int64_t cap_cell, cap_tile;
     std::vector<BlockMap> bm_cell;
-    std::vector<int2> items;
+    std::vector<int4> items;
     // device memory
     char *base;
     size_t bytes;
@@ -335,7 +338,7 @@ struct pic_batch {
     RunState *d_state;
     int *d_due;        // runs due for a sort this step (k_b_plan)
     BlockMap *d_bm_cell;
-    int2 *d_items;
+    int4 *d_items;
     int *d_counter;
     // launch shapes and the graph of one step
     int grid_runs, grid_scan, grid_stage, grid_tile, grid_gpp;
@@ -356,13 +359,13 @@ size_t cap_bytes(int64_t entries) { return align_up((size_t)std::max<int64_t>(en
 // species count and stream), and the shared memory its work items need.
 struct Tables {
     std::vector<BlockMap> cell;
-    std::vector<int2> items;
+    std::vector<int4> items;
     size_t smem = 0;
 };
 
 int build_tables(pic_ctx *const *runs, int n, int nsp, cudaStream_t stream, Tables &t)
 {
-    std::vector<std::pair<int64_t, int2>> work;
+    std::vector<std::pair<int64_t, int4>> work;
     std::vector<pic_ctx *> seen(runs, runs + n);
     std::sort(seen.begin(), seen.end());
     if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return PIC_EINVAL;  // twice
@@ -380,11 +383,31 @@ int build_tables(pic_ctx *const *runs, int n, int nsp, cudaStream_t stream, Tabl
         int64_t np = 0;
         for (int s = 0; s < nsp; ++s) np += rd.sp[s].n;
         const int64_t per_tile = rd.ntiles > 0 ? np / rd.ntiles : 0;
-        for (int64_t i = 0; i < rd.ntiles; ++i) work.push_back({per_tile, make_int2(r, (int)i)});
+        for (int64_t i = 0; i < rd.ntiles; ++i) work.push_back({per_tile, make_int4(r, (int)i, 0, 1)});
+    }
+    // A set of few particles leaves most CTA slots of the persistent kernel idle while the
+    // heaviest tiles take the whole step: split every tile that holds more than the average
+    // load of a slot (and more than kPartMin particles) into up to kPartMax items that share
+    // its particles.
+    {
+        int dev_id = 0, sms = 0;
+        if (cudaGetDevice(&dev_id) != cudaSuccess
+            || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess)
+            return PIC_ECUDA;
+        int64_t total = 0;
+        for (const auto &w : work) total += w.first;
+        const int64_t share = std::max<int64_t>(total / (2 * (int64_t)std::max(sms, 1)), kPartMin);
+        std::vector<std::pair<int64_t, int4>> split;
+        for (const auto &w : work) {
+            const int parts = (int)std::min<int64_t>(kPartMax, std::max<int64_t>(1, (w.first + share - 1) / share));
+            for (int k = 0; k < parts; ++k)
+                split.push_back({w.first / parts, make_int4(w.second.x, w.second.y, k, parts)});
+        }
+        work.swap(split);
     }
     // heaviest work items first (longest-processing-time order for the dynamic scheduler)
     std::stable_sort(work.begin(), work.end(),
-                     [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &c) {
+                     [](const std::pair<int64_t, int4> &a, const std::pair<int64_t, int4> &c) {
                          return a.first > c.first;
                      });
     for (auto &w : work) t.items.push_back(w.second);
@@ -490,7 +513,7 @@ int upload(pic_batch *b, pic_ctx *const *runs, int n, Tables &t)
               && up(b->d_state, sts.data(), sts.size() * sizeof(RunState))
               && up(b->d_counts, &cn, sizeof(cn));
     ok = ok && up(b->d_bm_cell, t.cell.data(), t.cell.size() * sizeof(BlockMap))
-         && up(b->d_items, t.items.data(), t.items.size() * sizeof(int2));
+         && up(b->d_items, t.items.data(), t.items.size() * sizeof(int4));
     // the host vectors are released on return: wait for the copies
     if (!ok || cudaStreamSynchronize(st) != cudaSuccess) return PIC_ECUDA;
     b->n = n;
@@ -568,7 +591,7 @@ int pic_batch_footprint(const pic_batch *b, size_t *bytes)
     size_t s = align_up(sizeof(Counts), 256);
     s += cap_bytes<RunDev>(b->cap_runs) + cap_bytes<RunState>(b->cap_runs)
          + cap_bytes<int>(b->cap_runs);
-    s += cap_bytes<BlockMap>(b->cap_cell) + cap_bytes<int2>(b->cap_tile) + 256 + 256;
+    s += cap_bytes<BlockMap>(b->cap_cell) + cap_bytes<int4>(b->cap_tile) + 256 + 256;
     *bytes = s;
     return PIC_OK;
 }
@@ -588,7 +611,7 @@ int pic_batch_bind_memory(pic_batch *b, void *dev, size_t bytes)
     b->d_state = (RunState *)take(cap_bytes<RunState>(b->cap_runs));
     b->d_due = (int *)take(cap_bytes<int>(b->cap_runs));
     b->d_bm_cell = (BlockMap *)take(cap_bytes<BlockMap>(b->cap_cell));
-    b->d_items = (int2 *)take(cap_bytes<int2>(b->cap_tile));
+    b->d_items = (int4 *)take(cap_bytes<int4>(b->cap_tile));
     b->d_counter = (int *)take(sizeof(int));
     // launch shapes, fixed for the life of the batch (and of its graph)
     int dev_id = 0, sms = 0, per_sm = 0;

@@ -115,9 +115,15 @@ struct RunDev {
     // fields (FP64, index (k*ny + j)*nx + i) and FP32 shadows of E, B (precision form)
     double *F[9];
     float *Fs[6];
-    // 3D FP32 form (not deterministic): the current summed by FP32 L2 reductions (index as F),
-    // converted into F[6..8] after the particle pass; null otherwise
+    // 3D FP32 form (not deterministic): the current summed by FP32 L2 reductions, converted
+    // into F[6..8] after the particle pass; null otherwise.  It is padded: jp_lo ghost nodes
+    // below and jp[a] - n[a] - jp_lo above the grid along every axis, so that every deposit
+    // window lies inside it unwrapped (node (i, j, k) of the grid at ((k + jp_lo) jp[1] + j +
+    // jp_lo) jp[0] + i + jp_lo); the conversion adds every node's periodic images.
     float *J32[3];
+    int jp_lo;
+    int jp[3];
+    int64_t jp_nodes;
     TTable tt[3];
     int nsp;
     SpeciesDev sp[PIC_NSP_MAX];

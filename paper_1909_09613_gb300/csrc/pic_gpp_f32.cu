@@ -13,32 +13,14 @@ __global__ void __launch_bounds__(256, 2) k_gpp2d(const __grid_constant__ RunDev
     tile_2d<L, KT, float, DET>(rd, smem, blockIdx.x);
 }
 
-// l <= 2: four blocks per SM (at most 128 registers; the gather through L1 is latency-bound, so
-// the extra warps help); higher orders keep their registers
-template <int L, int KT>
-__global__ void __launch_bounds__(128, (L <= 2 ? 4 : 1)) k_gpp3d(const __grid_constant__ RunDev rd)
-{
-    extern __shared__ __align__(16) float sf3[];
-    tile_3d<L, KT, float>(rd, blockIdx.x, sf3);
-}
-
 template <int L, int KT>
 cudaError_t go(const RunDev &rd, cudaStream_t st)
 {
-    if (rd.dim == 2) {
-        const size_t smem = stage2d_bytes<float>(rd.reg_nodes, rd.l, true, rd.det != 0);
-        auto k = rd.det ? k_gpp2d<L, KT, true> : k_gpp2d<L, KT, false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<(unsigned)rd.ntiles, 256, smem, st>>>(rd);
-    } else {
-        const size_t smem = stage3d_bytes(rd);
-        cudaError_t e = cudaFuncSetAttribute(k_gpp3d<L, KT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_gpp3d<L, KT><<<(unsigned)rd.ntiles, 128, smem, st>>>(rd);
-    }
+    const size_t smem = stage2d_bytes<float>(rd.reg_nodes, rd.l, true, rd.det != 0);
+    auto k = rd.det ? k_gpp2d<L, KT, true> : k_gpp2d<L, KT, false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)rd.ntiles, 256, smem, st>>>(rd);
     return cudaGetLastError();
 }
 
@@ -46,6 +28,7 @@ cudaError_t go(const RunDev &rd, cudaStream_t st)
 
 cudaError_t launch_gpp_f32(const RunDev &rd, int kt, cudaStream_t st)
 {
+    if (rd.dim != 2) return launch_gpp3d(rd, kt, st);
     const bool wide = kt > rd.l + 1;
     switch (rd.l) {
     case 1: return wide ? go<1, 3>(rd, st) : go<1, 2>(rd, st);
@@ -59,7 +42,7 @@ cudaError_t launch_gpp_f32(const RunDev &rd, int kt, cudaStream_t st)
 size_t gpp_smem_bytes_f32(const RunDev &rd)
 {
     return rd.dim == 2 ? stage2d_bytes<float>(rd.reg_nodes, rd.l, true, rd.det != 0)
-                       : stage3d_bytes(rd);
+                       : gpp3d_smem_bytes(rd);
 }
 
 // Dynamic shared memory a work item of this run needs in the batched kernel: the copy of the

@@ -14,24 +14,13 @@ __global__ void __launch_bounds__(256, 2) k_gpp2d(const __grid_constant__ RunDev
 }
 
 template <int L, int KT>
-__global__ void __launch_bounds__(128) k_gpp3d(const __grid_constant__ RunDev rd)
-{
-    tile_3d<L, KT, double>(rd, blockIdx.x);
-}
-
-template <int L, int KT>
 cudaError_t go(const RunDev &rd, cudaStream_t st)
 {
-    if (rd.dim == 2) {
-        const size_t smem = stage2d_bytes<double>(rd.reg_nodes, rd.l);
-        auto k = rd.det ? k_gpp2d<L, KT, true> : k_gpp2d<L, KT, false>;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        k<<<(unsigned)rd.ntiles, 256, smem, st>>>(rd);
-    } else {
-        k_gpp3d<L, KT><<<(unsigned)rd.ntiles, 128, 0, st>>>(rd);
-    }
+    const size_t smem = stage2d_bytes<double>(rd.reg_nodes, rd.l);
+    auto k = rd.det ? k_gpp2d<L, KT, true> : k_gpp2d<L, KT, false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)rd.ntiles, 256, smem, st>>>(rd);
     return cudaGetLastError();
 }
 
@@ -39,6 +28,7 @@ cudaError_t go(const RunDev &rd, cudaStream_t st)
 
 cudaError_t launch_gpp_f64(const RunDev &rd, int kt, cudaStream_t st)
 {
+    if (rd.dim != 2) return launch_gpp3d(rd, kt, st);
     const bool wide = kt > rd.l + 1;
     switch (rd.l) {
     case 1: return wide ? go<1, 3>(rd, st) : go<1, 2>(rd, st);

@@ -1,5 +1,5 @@
-// Tile kernels of the fused particle pass (2D shared-memory staged, 3D L1/global) and the
-// per-tile driver shared by the single-run and the batched launches.
+// Tile kernels of the fused particle pass in 2D (shared-memory staged) and the per-tile
+// driver shared by the single-run and the batched launches (3D: pic_gpp3d.cuh).
 #pragma once
 #include "pic_gpp.cuh"
 
@@ -949,10 +949,13 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
     }
 }
 
-// All particles of one tile (both species), 2D.  tt_shared as in stage2d_carve.
+// All particles of one tile (both species), 2D.  tt_shared as in stage2d_carve.  With
+// nparts > 1 only part `part` of every species' particles of the tile (a contiguous share of
+// its range): the batched kernel splits the heavy tiles of a small run set over several CTAs,
+// each staging the tile and adding its own share of the current.
 template <int L, int KT, typename R, bool DET = false>
 __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
-                        const TTable *tt_shared = nullptr)
+                        const TTable *tt_shared = nullptr, int part = 0, int nparts = 1)
 {
     Stage2D<R> st = stage2d_carve<R>(smem, rd.reg_nodes, tt_shared, DET);
     const int tx = (int)(tile % rd.ntile[0]);
@@ -964,7 +967,12 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
     for (int s = 0; s < rd.nsp; ++s) {
         const SpeciesDev &sp = rd.sp[s];
         const HotSp<R> hs = make_hotsp<R>(sp);
-        const int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
+        int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
+        if (nparts > 1) {
+            const int64_t len = b - a;
+            b = a + len * (part + 1) / nparts;
+            a += len * part / nparts;
+        }
         if constexpr (sizeof(R) == 4) {
             // every warp takes a contiguous chunk of the tile's particles of this species (for a
             // uniform plasma in the cell-major order, one row of cells), so that the warps'
@@ -1000,303 +1008,6 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
             __syncthreads();
         }
     }
-}
-
-// Stage the FP32 fields of 3D tile (x0, y0, z0) and its halo in shared memory: six arrays of
-// reg_nodes floats (E1, E2, E3, B1, B2, B3), x fastest.
-__device__ inline void stage3d_load(const RunDev &rd, float *sf, int x0, int y0, int z0)
-{
-    const int RX = rd.reg[0], RY = rd.reg[1];
-    const int64_t nodes = rd.reg_nodes;
-    for (int64_t n = threadIdx.x; n < nodes; n += blockDim.x) {
-        const int rx = (int)(n % RX), r2 = (int)(n / RX);
-        const int ry = r2 % RY, rz = r2 / RY;
-        const int gx = wrap_idx(x0 - rd.pre[0] + rx, rd.n[0]);
-        const int gy = wrap_idx(y0 - rd.pre[1] + ry, rd.n[1]);
-        const int gz = wrap_idx(z0 - rd.pre[2] + rz, rd.n[2]);
-        const int64_t g = ((int64_t)gz * rd.n[1] + gy) * rd.n[0] + gx;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) sf[c * nodes + n] = __ldg(rd.Fs[c] + g);
-    }
-}
-
-// One particle, 3D: fields from the tile's shared-memory stage (STAGED, FP32 form: sf, tile
-// origin x0, y0, z0) or through L1 (FP64 form), current by global reductions (FP32 form: into
-// the FP32 current RunDev::J32; FP64 form: into F[6..8]).
-template <int L, int KT, typename R, bool STAGED = false>
-__device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &sp, int64_t p,
-                                            const float *sf = nullptr, int x0 = 0, int y0 = 0,
-                                            int z0 = 0)
-{
-    PState<R> s;
-    load_particle<3, R>(rd, sp, p, s);
-    const int nx = rd.n[0], ny = rd.n[1], nz = rd.n[2];
-    AxisW<L, KT, R> w[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) axis_weights<L, KT, R>(rd.tt[a], s.d[a], w[a]);
-    // node indices: staged (local to the tile's region) or wrapped global
-    int ih[3][L + 1], it[3][KT];
-    int64_t RXs = nx, RYs = ny;
-    if constexpr (STAGED) {
-        const int org[3] = {x0, y0, z0};
-        RXs = rd.reg[0];
-        RYs = rd.reg[1];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            int lc;
-            if (!local_coord(s.c[a], org[a], rd.tile[a], rd.drift[a], rd.n[a], lc)) {
-                set_err(rd.err, 1);  // outside the staged halo: the sort interval was exceeded
-                return;
-            }
-            const int sa = lc + rd.pre[a];
-#pragma unroll
-            for (int k = 0; k <= L; ++k) ih[a][k] = sa + w[a].bh + k;
-#pragma unroll
-            for (int k = 0; k < KT; ++k) it[a][k] = sa + w[a].bt + k;
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-#pragma unroll
-            for (int k = 0; k <= L; ++k) ih[a][k] = wrap_idx(s.c[a] + w[a].bh + k, rd.n[a]);
-#pragma unroll
-            for (int k = 0; k < KT; ++k) it[a][k] = wrap_idx(s.c[a] + w[a].bt + k, rd.n[a]);
-        }
-    }
-    const int64_t snodes = rd.reg_nodes;
-    auto fld = [&](int comp, int64_t g) -> R {
-        if constexpr (STAGED) return sf[comp * snodes + g];
-        else if constexpr (sizeof(R) == 4) return __ldg(rd.Fs[comp] + g);
-        else return __ldg(rd.F[comp] + g);
-    };
-    R E[3], B[3];
-    // E1: W T T ; E2: T W T ; E3: T T W ; B1: T W W ; B2: W T W ; B3: W W T
-    {
-        R acc = R(0);
-#pragma unroll
-        for (int c = 0; c < KT; ++c) {
-            R r2 = R(0);
-#pragma unroll
-            for (int b = 0; b < KT; ++b) {
-                const int64_t row = ((int64_t)it[2][c] * RYs + it[1][b]) * RXs;
-                R r1 = R(0);
-#pragma unroll
-                for (int a = 0; a <= L; ++a) r1 += w[0].wh[a] * fld(0, row + ih[0][a]);
-                r2 += w[1].wt[b] * r1;
-            }
-            acc += w[2].wt[c] * r2;
-        }
-        E[0] = acc;
-    }
-    {
-        R acc = R(0);
-#pragma unroll
-        for (int c = 0; c < KT; ++c) {
-            R r2 = R(0);
-#pragma unroll
-            for (int b = 0; b <= L; ++b) {
-                const int64_t row = ((int64_t)it[2][c] * RYs + ih[1][b]) * RXs;
-                R r1 = R(0);
-#pragma unroll
-                for (int a = 0; a < KT; ++a) r1 += w[0].wt[a] * fld(1, row + it[0][a]);
-                r2 += w[1].wh[b] * r1;
-            }
-            acc += w[2].wt[c] * r2;
-        }
-        E[1] = acc;
-    }
-    {
-        R acc = R(0);
-#pragma unroll
-        for (int c = 0; c <= L; ++c) {
-            R r2 = R(0);
-#pragma unroll
-            for (int b = 0; b < KT; ++b) {
-                const int64_t row = ((int64_t)ih[2][c] * RYs + it[1][b]) * RXs;
-                R r1 = R(0);
-#pragma unroll
-                for (int a = 0; a < KT; ++a) r1 += w[0].wt[a] * fld(2, row + it[0][a]);
-                r2 += w[1].wt[b] * r1;
-            }
-            acc += w[2].wh[c] * r2;
-        }
-        E[2] = acc;
-    }
-    {
-        R acc = R(0);
-#pragma unroll
-        for (int c = 0; c <= L; ++c) {
-            R r2 = R(0);
-#pragma unroll
-            for (int b = 0; b <= L; ++b) {
-                const int64_t row = ((int64_t)ih[2][c] * RYs + ih[1][b]) * RXs;
-                R r1 = R(0);
-#pragma unroll
-                for (int a = 0; a < KT; ++a) r1 += w[0].wt[a] * fld(3, row + it[0][a]);
-                r2 += w[1].wh[b] * r1;
-            }
-            acc += w[2].wh[c] * r2;
-        }
-        B[0] = acc;
-    }
-    {
-        R acc = R(0);
-#pragma unroll
-        for (int c = 0; c <= L; ++c) {
-            R r2 = R(0);
-#pragma unroll
-            for (int b = 0; b < KT; ++b) {
-                const int64_t row = ((int64_t)ih[2][c] * RYs + it[1][b]) * RXs;
-                R r1 = R(0);
-#pragma unroll
-                for (int a = 0; a <= L; ++a) r1 += w[0].wh[a] * fld(4, row + ih[0][a]);
-                r2 += w[1].wt[b] * r1;
-            }
-            acc += w[2].wh[c] * r2;
-        }
-        B[1] = acc;
-    }
-    {
-        R acc = R(0);
-#pragma unroll
-        for (int c = 0; c < KT; ++c) {
-            R r2 = R(0);
-#pragma unroll
-            for (int b = 0; b <= L; ++b) {
-                const int64_t row = ((int64_t)it[2][c] * RYs + ih[1][b]) * RXs;
-                R r1 = R(0);
-#pragma unroll
-                for (int a = 0; a <= L; ++a) r1 += w[0].wh[a] * fld(5, row + ih[0][a]);
-                r2 += w[1].wh[b] * r1;
-            }
-            acc += w[2].wt[c] * r2;
-        }
-        B[2] = acc;
-    }
-
-    const R ig = boris<R>(R(sp.qmdt_half), E, B, s.u);
-    R o[3], dl[3], xs[3];
-    int cn[3], shv[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        dl[a] = R(rd.dtt[a]) * s.u[a] * ig;
-        shv[a] = move_axis<R>(s.d[a], dl[a], s.c[a], rd.n[a], o[a], cn[a], xs[a]);
-    }
-
-    AxisS<L, R> S[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if constexpr (sizeof(R) == 4) axis_shapes_dd<L>(s.d[a], dl[a], S[a]);
-        else axis_shapes<L, R>(s.d[a], shv[a], o[a], S[a]);
-    }
-    R DS[3][L + 2], P[3][L + 2];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        R acc = R(0);
-#pragma unroll
-        for (int k = 0; k < L + 2; ++k) {
-            DS[a][k] = S[a].ds[k];
-            acc += DS[a][k];
-            P[a][k] = acc;
-        }
-    }
-    // node offsets of the window along each axis (the grid has at most 2^30 cells: 32-bit)
-    int off[3][L + 2];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int stride = a == 0 ? 1 : (a == 1 ? nx : nx * ny);
-#pragma unroll
-        for (int k = 0; k < L + 2; ++k) off[a][k] = wrap_near(s.c[a] + S[a].wb + k, rd.n[a]) * stride;
-    }
-    const R third = R(1) / R(3);
-    // W_a = DS_a (S0_b S0_c + DS_b S0_c / 2 + S0_b DS_c / 2 + DS_b DS_c / 3), prefix along a
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        const int bx = (ax + 1) % 3, cx = (ax + 2) % 3;
-        const R kk = R(sp.kx[ax]);
-        R kP[L + 1];
-#pragma unroll
-        for (int ka = 0; ka <= L; ++ka) kP[ka] = kk * P[ax][ka];
-#pragma unroll
-        for (int kb = 0; kb < L + 2; ++kb) {
-#pragma unroll
-            for (int kc = 0; kc < L + 2; ++kc) {
-                const R perp = S[bx].s0[kb] * (S[cx].s0[kc] + R(0.5) * DS[cx][kc])
-                               + DS[bx][kb] * (R(0.5) * S[cx].s0[kc] + third * DS[cx][kc]);
-                if (perp == R(0)) continue;
-                const int base = off[bx][kb] + off[cx][kc];
-#pragma unroll
-                for (int ka = 0; ka <= L; ++ka) {
-                    const int g = base + off[ax][ka];
-                    const R v = kP[ka] * perp;
-                    if (v == R(0)) continue;
-                    if (rd.det) {
-                        if constexpr (sizeof(R) == 4) {
-                            atomicAdd((unsigned long long *)(rd.F[6 + ax] + g),
-                                      det_word32(v, rd.det_inv32));
-                        } else {
-                            unsigned long long hi, lo;
-                            det_words64(v, rd.det_inv64, hi, lo);
-                            atomicAdd((unsigned long long *)(rd.F[6 + ax] + g), hi);
-                            atomicAdd(rd.Jlo[ax] + g, lo);
-                        }
-                    } else if constexpr (sizeof(R) == 4) {
-                        // FP32 L2 reductions: 2.4x the FP64 rate, and no FP32 -> FP64
-                        // conversion on the FP64 pipe per contribution
-                        atomicAdd(rd.J32[ax] + g, v);
-                    } else {
-                        atomicAdd(rd.F[6 + ax] + g, (double)v);
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ((R *)sp.mom[a])[p] = s.u[a];
-    if constexpr (sizeof(R) == 4) {
-        sp.cell[p] = (cn[2] * ny + cn[1]) * nx + cn[0];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ((float *)sp.pos[a])[p] = o[a];
-    } else {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ((double *)sp.pos[a])[p] = xs[a];  // = cn + o
-    }
-    (void)nz;
-}
-
-// All particles of one 3D tile.  FP32 form: the tile's fields and halo are staged in shared
-// memory first (sf, 6 x reg_nodes floats; the FP32 3D sort interval keeps every particle
-// within one cell of its sorted tile); FP64 form: fields through L1.
-template <int L, int KT, typename R>
-__device__ void tile_3d(const RunDev &rd, int64_t tile, float *sf = nullptr)
-{
-    if constexpr (sizeof(R) == 4) {
-        const int tx = (int)(tile % rd.ntile[0]);
-        const int ty = (int)((tile / rd.ntile[0]) % rd.ntile[1]);
-        const int tz = (int)(tile / ((int64_t)rd.ntile[0] * rd.ntile[1]));
-        const int x0 = tx * rd.tile[0], y0 = ty * rd.tile[1], z0 = tz * rd.tile[2];
-        stage3d_load(rd, sf, x0, y0, z0);
-        __syncthreads();
-        for (int s = 0; s < rd.nsp; ++s) {
-            const SpeciesDev &sp = rd.sp[s];
-            const int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
-            for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x)
-                particle_3d<L, KT, R, true>(rd, sp, p, sf, x0, y0, z0);
-        }
-    } else {
-        for (int s = 0; s < rd.nsp; ++s) {
-            const SpeciesDev &sp = rd.sp[s];
-            const int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
-            for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x)
-                particle_3d<L, KT, R>(rd, sp, p);
-        }
-    }
-}
-
-// Dynamic shared memory of a 3D tile block (FP32 form: the staged fields).
-__host__ __device__ inline size_t stage3d_bytes(const RunDev &rd)
-{
-    return (size_t)6 * rd.reg_nodes * sizeof(float);
 }
 
 }  // namespace pic

@@ -449,12 +449,25 @@ __global__ void __launch_bounds__(kBlock) k_det_finish(const __grid_constant__ R
     }
 }
 
+// The padded FP32 current (RunDev::J32) -> F[6..8]: every grid node gets the sum, in FP64, of
+// its periodic images in the padded buffer (padded index i + jp_lo + m n along each axis).
 __global__ void __launch_bounds__(kBlock) k_j32_finish(const __grid_constant__ RunDev rd)
 {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= rd.ncell) return;
+    const int i = (int)(c % rd.n[0]);
+    const int64_t r = c / rd.n[0];
+    const int j = (int)(r % rd.n[1]), k = (int)(r / rd.n[1]);
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int kp = (k + rd.jp_lo) % rd.n[2]; kp < rd.jp[2]; kp += rd.n[2])
+        for (int jq = (j + rd.jp_lo) % rd.n[1]; jq < rd.jp[1]; jq += rd.n[1])
+            for (int ip = (i + rd.jp_lo) % rd.n[0]; ip < rd.jp[0]; ip += rd.n[0]) {
+                const int64_t q = ((int64_t)kp * rd.jp[1] + jq) * rd.jp[0] + ip;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) rd.F[6 + a][c] = (double)rd.J32[a][c];
+                for (int a = 0; a < 3; ++a) s[a] += (double)rd.J32[a][q];
+            }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rd.F[6 + a][c] = s[a];
 }
 
 inline unsigned grid_for(int64_t n)

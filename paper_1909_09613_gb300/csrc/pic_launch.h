@@ -10,6 +10,9 @@ int ttable_eval_host(const TTable *t, int l, double delta, double *w);
 // fused gather-push-deposit over all tiles of one run
 cudaError_t launch_gpp(const RunDev &rd, int kt, cudaStream_t st);
 size_t gpp_smem_bytes(const RunDev &rd);
+// the 3D particle pass of either form (pic_gpp3d.cu); dynamic shared memory of its blocks
+cudaError_t launch_gpp3d(const RunDev &rd, int kt, cudaStream_t st);
+size_t gpp3d_smem_bytes(const RunDev &rd);
 
 // Yee and grid kernels
 cudaError_t launch_yee_b(const RunDev &rd, double h, bool shadow, cudaStream_t st);

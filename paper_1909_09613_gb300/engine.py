@@ -14,15 +14,17 @@ libpic's kernels (pic_step for a run on its own, pic_batch_step for a batch).
 * `Server` is a continuous-batching request loop: requests (NCI-scan runs: grid, c dt, drift
   gamma, particles per cell) arrive over time, are admitted when the device-memory budget has
   room, stay resident until their last step, and are advanced in chunks of steps -- every 2D
-  quadratic or cubic run of the FP32 form in one batch (one persistent particle kernel per
-  step), every other run (3D, quartic, plain FP64) on a side stream, all concurrently.  When
-  runs finish or arrive, the batch is rebuilt at the next chunk boundary.  It reports the
+  quadratic or cubic run of the FP32 form in one of two batches, small runs and larger ones
+  (one persistent particle kernel per step each), every other run (3D, quartic, plain FP64)
+  on a side stream, all concurrently.  When runs finish or arrive, a batch's run set changes
+  at its next chunk boundary.  It reports the
   latency (completion - arrival) of every request and, for requests that ask for it, the
   field-energy history (E/E0 of the Table 1 scan).
 * `table1_requests` builds the requests of the paper's Table 1 NCI scan.
 """
 from __future__ import annotations
 
+import collections
 import math
 import time
 from dataclasses import dataclass, field
@@ -256,27 +258,45 @@ class Served:
         return self.done - self.arrival
 
 
+class _BatchLane:
+    """One batch of the server: its stream, the pic batch, the runs it holds and the chunk of
+    steps it has on the GPU."""
+
+    def __init__(self, stream):
+        self.stream = stream
+        self.batch = None
+        self.bytes = 0
+        self.ids: Tuple[int, ...] = ()
+        self.inflight = collections.deque()   # (event, steps) of the chunks on the GPU
+
+
 class Server:
     """Continuous-batching request loop (see module docstring).
 
-    The batchable runs live in ONE long-lived pic batch whose run set is replaced with
+    The batchable runs live in long-lived pic batches whose run sets are replaced with
     pic_batch_set_runs when runs arrive or finish: the batch's launches walk device tables of
-    any set that fits its capacities, so its captured CUDA graph is kept (the batch is rebuilt,
-    with doubled capacities, only when a set outgrows them).  Each lane waits for its own
-    streams (events), not for the whole device.  The batch's device tables count against the
-    memory budget.
+    any set that fits its capacities, so its captured CUDA graph is kept (a batch is rebuilt,
+    with doubled capacities, only when a set outgrows them).  Two batches, by size: runs of
+    fewer than `small_particles` particles share one, larger runs the other, so that a short
+    request is not paced by the step of a large run (a batch advances all its runs one step at
+    a time, so its step lasts as long as its total work).  Each lane waits for its own streams
+    (events), not for the whole device.  The batches' device tables count against the memory
+    budget.
 
     Streams carry priorities, so that short requests are not queued behind the thread blocks of
-    a large one: the batch (small 2D runs) runs on the highest-priority stream, other runs of
-    fewer than `large_particles` particles on medium-priority side streams, larger runs on
-    low-priority ones.  The GPU's block scheduler then starts a waiting block of a
-    higher-priority stream before more blocks of a lower one."""
+    a large one: the batch of small runs runs on the highest-priority stream, the batch of the
+    larger 2D runs next, other runs of fewer than `large_particles` particles on
+    medium-priority side streams, larger runs on low-priority ones.  The GPU's block scheduler
+    then starts a waiting block of a higher-priority stream before more blocks of a lower one."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 10,
                  tuner: Optional[Autotuner] = None, keep_runs: bool = False,
-                 large_particles: int = 1 << 24):
+                 large_particles: int = 1 << 24, small_particles: int = 1 << 20,
+                 depth: int = 2):
         self.budget = float(budget_bytes)
+        self.depth = max(1, int(depth))   # chunks a batch lane keeps queued on its stream
         self.large_particles = int(large_particles)
+        self.small_particles = int(small_particles)
         self.chunk = int(chunk)
         self.tuner = tuner
         self.keep_runs = keep_runs
@@ -287,6 +307,8 @@ class Server:
         self.chunks = 0
         self.batch_builds = 0
         self.set_changes = 0
+        self.lane_runs = [0, 0]   # runs served by the batch of small runs, of larger runs
+        self.host_block_s = 0.0   # longest admission (run set-up and load) or end-of-run read
 
     @staticmethod
     def _capacity(runs, factor=2.0):
@@ -303,65 +325,79 @@ class Server:
             _, batched, two = pic.pic_smem_info(r.ctx)
             stage = max(stage, batched, two)
         cap.cells = int(factor * max(cells, 1 << 18))
-        cap.tiles = int(factor * max(tiles, 1 << 12))
+        # work items: a small set splits its heavier tiles into up to 8 items
+        cap.tiles = int(8 * factor * max(tiles, 1 << 12))
         cap.stage_bytes = int(stage)
         return cap
+
+    def lane_of(self, req: Request) -> int:
+        """Batch lane of a batchable request: 0 (small runs) or 1 (larger runs)."""
+        return 0 if req.particles < self.small_particles else 1
 
     def serve(self, requests: List[Request]) -> List[Served]:
         """Serve the requests at their arrival times; returns one Served record per request.
 
-        Lanes advance independently: the batch (every batchable run, one graph replay per step)
-        and every other run on its own side stream.  A lane gets its next chunk of steps as soon
-        as its previous chunk's event has completed, so small runs never wait for a large run's
+        Lanes advance independently: each batch (its runs, one graph replay per step) and every
+        other run on its own side stream.  A lane gets its next chunk of steps as soon as its
+        previous chunk's event has completed, so small runs never wait for a large run's
         steps; run sets change, and finished runs are reported, at a lane's chunk boundary."""
         import torch
         pending = sorted(requests, key=lambda r: r.arrival)
-        active = {}      # rid -> dict(run, req, done, admitted, bytes, stream, history)
+        active = {}      # rid -> dict(run, req, done, admitted, bytes, stream, history, lane)
         used = 0
-        batch = None
-        batch_bytes = 0
-        batch_ids: Tuple[int, ...] = ()
-        batch_inflight = None   # (event, steps) of the batch lane's chunk on the GPU
         side_inflight = {}      # rid -> (event, steps) of a side run's chunk
         t0 = time.perf_counter()
         # priorities: lower numbers are served first (torch clamps them to the device's range)
-        main = torch.cuda.Stream(priority=-3)                       # the batch
-        side = [torch.cuda.Stream(priority=-1) for _ in range(4)]   # smaller side runs
-        side_lo = [torch.cuda.Stream(priority=0) for _ in range(2)]  # large side runs
+        lanes = [_BatchLane(torch.cuda.Stream(priority=-3)),   # batch of small 2D runs
+                 _BatchLane(torch.cuda.Stream(priority=-2))]   # batch of larger 2D runs
 
-        def install(ids):
-            """Make the batch hold the runs `ids` (a new batch when none fits)."""
-            nonlocal batch, batch_bytes, batch_ids, used
+        def install(lane, ids):
+            """Make the lane's batch hold the runs `ids` (a new batch when none fits)."""
+            nonlocal used
             runs = [active[r]["run"] for r in ids]
-            if batch is not None and batch.set_runs(runs):
+            if lane.batch is not None and lane.batch.set_runs(runs):
                 self.set_changes += 1
-                batch_ids = ids
+                lane.ids = ids
                 return
-            if batch is not None:
-                batch.set_runs([])   # write every run's state back before the batch goes
-                batch.close()
-                used -= batch_bytes
-                batch, batch_bytes = None, 0
+            if lane.batch is not None:
+                lane.batch.set_runs([])   # write every run's state back before the batch goes
+                lane.batch.close()
+                used -= lane.bytes
+                lane.batch, lane.bytes = None, 0
             if runs:
-                batch = pic.Batch(runs, capacity=self._capacity(runs))
-                batch_bytes = int(batch.mem.numel())
-                used += batch_bytes
+                lane.batch = pic.Batch(runs, capacity=self._capacity(runs))
+                lane.bytes = int(lane.batch.mem.numel())
+                used += lane.bytes
                 self.peak_bytes = max(self.peak_bytes, used)
                 self.batch_builds += 1
-            batch_ids = ids
+            lane.ids = ids
 
-        def chunk_steps(ids):
-            k = min(self.chunk, min(active[r]["req"].steps - active[r]["done"] for r in ids))
+        def chunk_steps(ids, ahead=0):
+            """Steps of the next chunk of runs `ids`, `ahead` steps past their completed ones."""
+            k = min(self.chunk, min(active[r]["req"].steps - active[r]["done"] - ahead for r in ids))
             for r in ids:  # stop at the next field-energy sample
                 ev = active[r]["req"].record_every
                 if ev > 0:
-                    k = min(k, ev - active[r]["done"] % ev)
+                    k = min(k, ev - (active[r]["done"] + ahead) % ev)
             return k
+
+        def stops(ids, ahead):
+            """A run of `ids` samples its field energy or ends `ahead` steps past its completed
+            steps (the host must act there before more steps are queued)."""
+            for r in ids:
+                a = active[r]
+                n = a["done"] + ahead
+                ev = a["req"].record_every
+                if n >= a["req"].steps or (ev > 0 and n % ev == 0):
+                    return True
+            return False
 
         def finish(rid):
             nonlocal used
             a = active.pop(rid)
+            tb = time.perf_counter()
             d = a["run"].diag()
+            self.host_block_s = max(self.host_block_s, time.perf_counter() - tb)
             done_t = time.perf_counter() - t0
             self.results.append(Served(rid, a["req"].arrival, a["admitted"], done_t,
                                        a["req"].steps, a["req"].particles, a["req"].dim, d,
@@ -386,52 +422,74 @@ class Server:
                 if used + need > self.budget and active:
                     break
                 pending.pop(0)
-                if req.batchable:
-                    stream = main
-                elif req.particles < self.large_particles:
-                    stream = side[req.rid % len(side)]
+                lane = self.lane_of(req) if req.batchable else -1
+                if lane >= 0:
+                    stream = lanes[lane].stream
+                    self.lane_runs[lane] += 1
                 else:
-                    stream = side_lo[req.rid % len(side_lo)]
+                    # a side run has a stream of its own: loading it (and reading its
+                    # diagnostics when it ends) waits for that stream only, not for the chunk
+                    # another run has in flight
+                    stream = torch.cuda.Stream(priority=-1 if req.particles < self.large_particles
+                                               else 0)
+                tb = time.perf_counter()
                 run = make_run(req, tuner=self.tuner, stream=stream)
+                self.host_block_s = max(self.host_block_s, time.perf_counter() - tb)
                 active[req.rid] = {"run": run, "req": req, "done": 0, "bytes": need,
                                    "admitted": time.perf_counter() - t0, "history": [],
-                                   "stream": run.stream}
+                                   "stream": run.stream, "lane": lane}
                 if req.record_every > 0:
                     self._record(active[req.rid])
                 used += need
                 self.peak_bytes = max(self.peak_bytes, used)
                 progressed = True
             self.max_active = max(self.max_active, len(active))
-            # the batch lane: account its finished chunk, change its run set, issue the next
-            if batch_inflight is None or batch_inflight[0].query():
-                if batch_inflight is not None:
-                    for r in batch_ids:
-                        active[r]["done"] += batch_inflight[1]
-                    batch_inflight = None
-                    rec = [active[r] for r in batch_ids if recorded(active[r])]
-                    fin = [r for r in batch_ids if active[r]["done"] >= active[r]["req"].steps]
-                    if rec and not fin:
-                        batch.sync()
-                    if fin:  # the finished runs leave the batch (their state written back)
-                        install(tuple(r for r in batch_ids if r not in fin))
-                    for a in rec:
-                        self._record(a)
-                    for r in fin:
-                        finish(r)
-                    progressed = True
-                ids2d = tuple(sorted(r for r, a in active.items() if a["req"].batchable))
-                if ids2d != batch_ids:
-                    install(ids2d)
-                if batch is not None and batch_ids:
-                    k = chunk_steps(batch_ids)
-                    batch.step(k)
+            # the batch lanes: account finished chunks, change the run set, keep up to
+            # `depth` chunks queued on the lane's stream (the GPU does not wait for the host
+            # between chunks) as long as no run of the set reaches a field-energy sample or its
+            # last step and no admitted run waits to join
+            for li, lane in enumerate(lanes):
+                done_chunk = False
+                while lane.inflight and lane.inflight[0][0].query():
+                    _, k = lane.inflight.popleft()
+                    for r in lane.ids:
+                        active[r]["done"] += k
+                    done_chunk = True
+                if lane.inflight:
+                    if done_chunk:
+                        progressed = True
+                else:
+                    if done_chunk:
+                        rec = [active[r] for r in lane.ids if recorded(active[r])]
+                        fin = [r for r in lane.ids if active[r]["done"] >= active[r]["req"].steps]
+                        if rec and not fin:
+                            lane.batch.sync()
+                        if fin:  # the finished runs leave the batch (their state written back)
+                            install(lane, tuple(r for r in lane.ids if r not in fin))
+                        for a in rec:
+                            self._record(a)
+                        for r in fin:
+                            finish(r)
+                        progressed = True
+                    ids = tuple(sorted(r for r, a in active.items() if a["lane"] == li))
+                    if ids != lane.ids:
+                        install(lane, ids)
+                if lane.batch is None or not lane.ids:
+                    continue
+                joining = any(a["lane"] == li and r not in lane.ids for r, a in active.items())
+                while len(lane.inflight) < self.depth:
+                    ahead = sum(k for _, k in lane.inflight)
+                    if lane.inflight and (joining or stops(lane.ids, ahead)):
+                        break
+                    k = chunk_steps(lane.ids, ahead)
+                    lane.batch.step(k)
                     ev = torch.cuda.Event()
-                    ev.record(main)
-                    batch_inflight = (ev, k)
+                    ev.record(lane.stream)
+                    lane.inflight.append((ev, k))
                     self.chunks += 1
                     progressed = True
             # the side lanes: every other run on its own stream
-            for rid in [r for r, a in active.items() if not a["req"].batchable]:
+            for rid in [r for r, a in active.items() if a["lane"] < 0]:
                 a = active[rid]
                 inf = side_inflight.get(rid)
                 if inf is not None and not inf[0].query():
@@ -457,8 +515,9 @@ class Server:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - (time.perf_counter() - t0))))
                 else:
                     time.sleep(0.0002)
-        if batch is not None:
-            batch.close()
+        for lane in lanes:
+            if lane.batch is not None:
+                lane.batch.close()
         return self.results
 
     @staticmethod

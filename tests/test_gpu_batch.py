@@ -125,7 +125,9 @@ def test_batch_graph_replay_and_timing():
     runs = [make(spec)[1] for spec in RUNS]
     b = pic.Batch(runs)
     items, launches = b.info()
-    assert items == sum(r.ntiles for r in runs)
+    # one work item per tile, the heavier tiles of this small set split into up to 8 items
+    tiles = sum(r.ntiles for r in runs)
+    assert tiles < items <= 8 * tiles
     b.step(3)
     ms = b.time_gpp()
     assert ms > 0.0

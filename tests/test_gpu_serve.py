@@ -1,8 +1,8 @@
 """Served form (engine.Server): requests arrive over time, are admitted under a device-memory
-budget, share one batch (2D) or run on their own streams (3D) concurrently, and each result
-must equal the same request run alone, within the FP32 multi-step tolerance (the order of the
-floating-point atomics differs between the two, so results agree to round-off growth, not bit
-for bit)."""
+budget, share one of two batches (2D, by size) or run on their own streams (3D) concurrently,
+and each result must equal the same request run alone, within the FP32 multi-step tolerance
+(the order of the floating-point atomics differs between the two, so results agree to
+round-off growth, not bit for bit)."""
 import numpy as np
 import pytest
 
@@ -48,10 +48,12 @@ def test_served_results_equal_alone():
     # budget for roughly three resident runs: admission has to wait for memory
     sizes = sorted(engine.footprint_estimate(r) for r in reqs)
     budget = sum(sizes[-3:])
-    srv = engine.Server(budget_bytes=budget, chunk=5, keep_runs=True)
+    # the size split puts batchable requests in both batch lanes (small and larger runs)
+    srv = engine.Server(budget_bytes=budget, chunk=5, keep_runs=True, small_particles=20000)
     res = srv.serve(reqs)
     assert sorted(r.rid for r in res) == list(range(len(reqs)))
     assert srv.max_active >= 2          # work of several requests overlapped
+    assert min(srv.lane_runs) >= 2      # both batches served runs
     assert srv.peak_bytes <= budget
     for r in res:
         assert r.latency >= 0.0 and r.diag["error_flags"] == 0
