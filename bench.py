@@ -554,8 +554,9 @@ def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
     each, admitted under a 150 GB budget and served by continuous batching (engine.Server), the
     arrival rate 0.8 x the measured service capacity of this mix.  Reports the latency
     (completion - arrival) p50/p99, every request's slowdown against its latency alone (the
-    same form alone on the GPU, timed over alone_steps steps and scaled to its steps), and the
-    aggregate particle-steps/s."""
+    same form alone on the GPU: its set-up and load, its steps timed over alone_steps steps and
+    scaled to its steps, and the final diagnostics read, the span the served latency covers; the
+    slowdown against the steps alone is reported beside it), and the aggregate particle-steps/s."""
     import random
     import torch
     import workloads
@@ -567,10 +568,16 @@ def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
                            u_th=sp["u_th"], ppc=sp["ppc"], steps=sp["steps"],
                            seed=workloads.BASE_SEED) for i, sp in enumerate(specs)]
     tuner = engine.Autotuner()
-    # every request alone, in its own form: the latency baseline, and the 3D throughput
-    alone, work3d, t3d = {}, 0.0, 0.0
+    # every request alone, in its own form: the latency baseline (what a server with nothing
+    # else to do takes: the run's set-up and load, its steps and the final diagnostics read;
+    # the steps timed over alone_steps and scaled), and the 3D throughput
+    alone, alone_steps_only, work3d, t3d = {}, {}, 0.0, 0.0
     for r in reqs:
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
         run = engine.make_run(r, tuner=tuner)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - ts
         run.step(2)
         torch.cuda.synchronize()
         n = min(r.steps, alone_steps)
@@ -578,7 +585,11 @@ def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
         run.step(n)
         torch.cuda.synchronize()
         t = time.perf_counter() - ta
-        alone[r.rid] = t * r.steps / n
+        td = time.perf_counter()
+        run.diag()
+        t_diag = time.perf_counter() - td
+        alone_steps_only[r.rid] = t * r.steps / n
+        alone[r.rid] = t_setup + alone_steps_only[r.rid] + t_diag
         if r.dim == 3:
             work3d += r.particles * n
             t3d += t
@@ -613,8 +624,10 @@ def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
     makespan = time.perf_counter() - t0
     lat = [r.latency for r in res]
     slow = [r.latency / alone[r.rid] for r in res]
+    slow_steps = [r.latency / alone_steps_only[r.rid] for r in res]
     lat2d = [r.latency for r in res if r.dim == 2]
     slow2d = [r.latency / alone[r.rid] for r in res if r.dim == 2]
+    wait2d = [r.admitted - r.arrival for r in res if r.dim == 2]
     work = sum(r.particles * r.steps for r in res)
     # the plain FP64 single-run form on a sample of the 2D requests, alone
     alone64 = []
@@ -631,22 +644,31 @@ def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
             "p50_latency_s": engine.percentile(lat, 50), "p99_latency_s": engine.percentile(lat, 99),
             "p50_slowdown_vs_alone": engine.percentile(slow, 50),
             "p99_slowdown_vs_alone": engine.percentile(slow, 99),
+            "p50_slowdown_vs_alone_steps_only": engine.percentile(slow_steps, 50),
+            "p99_slowdown_vs_alone_steps_only": engine.percentile(slow_steps, 99),
             "p50_latency_2d_s": engine.percentile(lat2d, 50),
             "p50_slowdown_2d": engine.percentile(slow2d, 50),
+            "p50_admission_wait_2d_s": engine.percentile(wait2d, 50),
             "p50_alone_latency_s": engine.percentile(list(alone.values()), 50),
+            "p50_alone_steps_only_s": engine.percentile(list(alone_steps_only.values()), 50),
             "arrival_rate_per_s": lam, "arrival_window_s": reqs[-1].arrival,
             "service_capacity_particle_steps_per_s": cap,
             "capacity_2d_batched": cap2d, "capacity_3d_alone": cap3d,
             "makespan_s": makespan, "max_concurrent_runs": srv.max_active,
             "batch_builds": srv.batch_builds, "batch_set_changes": srv.set_changes,
             "batch_lane_runs": srv.lane_runs, "longest_host_block_s": srv.host_block_s,
+            "batch_lanes": [{"chunks": st["chunks"], "steps": st["steps"],
+                             "mean_runs_per_step": st["run_steps"] / max(st["steps"], 1),
+                             "ms_per_step": st["gpu_ms"] / max(st["steps"], 1)}
+                            for st in srv.lane_stats],
             "peak_admitted_bytes": srv.peak_bytes, "budget_bytes": budget,
             "steps_per_request": steps, "requests_3d": sum(1 for r in reqs if r.dim == 3),
             "largest_3d_grid": max((list(r.grid) for r in reqs if r.dim == 3), default=None,
                                    key=lambda g: g[0] * g[1] * g[2]),
             "alone_fp64_plain_latency_s_sample": alone64,
-            "alone": "every request alone in its own form over %d steps, scaled to its steps"
-                     % alone_steps,
+            "alone": "every request alone in its own form: set-up and load, its steps (timed "
+                     "over %d and scaled) and the final diagnostics read; steps_only: the steps "
+                     "alone" % alone_steps,
             "error_flags": sum(r.diag.get("error_flags", 0) for r in res)}
 
 

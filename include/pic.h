@@ -276,6 +276,12 @@ typedef struct {
                                       items may need in the batched kernel (pic_smem_info's
                                       batched_bytes); fixes the persistent kernel's shared
                                       memory for the life of the batch                      */
+    int32_t ctas_per_sm;           /* CTAs of the persistent particle kernel per SM (0: as
+                                      many as fit, two).  The persistent CTAs hold their SM
+                                      slots for the whole particle pass, so a batch that
+                                      shares the GPU with a more urgent one (a server's batch
+                                      of short requests on a higher-priority stream) can take
+                                      one per SM and leave the other slot to it             */
 } pic_batch_capacity;
 int pic_batch_reserve(pic_batch *batch, const pic_batch_capacity *capacity);
 

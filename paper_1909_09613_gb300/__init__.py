@@ -45,7 +45,7 @@ class pic_options(ctypes.Structure):
 
 class pic_batch_capacity(ctypes.Structure):
     _fields_ = [("runs", ctypes.c_int32), ("cells", ctypes.c_int64), ("tiles", ctypes.c_int64),
-                ("stage_bytes", ctypes.c_size_t)]
+                ("stage_bytes", ctypes.c_size_t), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class pic_diag_t(ctypes.Structure):

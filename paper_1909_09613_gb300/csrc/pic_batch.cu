@@ -348,6 +348,7 @@ struct pic_batch {
     bool timing;
     int64_t steps_since_sync;
     int64_t launches;  // kernels per step
+    int ctas_per_sm;   // cap on the persistent kernel's CTAs per SM (0: none)
 };
 
 namespace {
@@ -547,6 +548,7 @@ int pic_batch_create(pic_ctx *const *runs, int n, pic_batch **out)
     b->timing = false;
     b->steps_since_sync = 0;
     b->launches = 0;
+    b->ctas_per_sm = 0;
     Tables t;
     const int e = build_tables(runs, n, b->nsp, b->stream, t);
     if (e != PIC_OK) { delete b; return e; }
@@ -576,8 +578,10 @@ int pic_batch_reserve(pic_batch *b, const pic_batch_capacity *cap)
 {
     if (!b || !cap) return PIC_EINVAL;
     if (b->base) return PIC_ESTATE;  // the capacities size the bound memory
-    if (cap->runs < 0 || cap->cells < 0 || cap->tiles < 0 || cap->stage_bytes > 227 * 1024)
+    if (cap->runs < 0 || cap->cells < 0 || cap->tiles < 0 || cap->stage_bytes > 227 * 1024
+        || cap->ctas_per_sm < 0)
         return PIC_EINVAL;
+    b->ctas_per_sm = cap->ctas_per_sm;
     b->cap_runs = std::max(b->cap_runs, (int)cap->runs);
     b->cap_cell = std::max<int64_t>(b->cap_cell, cap->cells / (kBlock * kCellPer) + cap->runs);
     b->cap_tile = std::max<int64_t>(b->cap_tile, cap->tiles);
@@ -641,6 +645,7 @@ int pic_batch_bind_memory(pic_batch *b, void *dev, size_t bytes)
     b->grid_scan = clampg(b->cap_runs, sms);
     b->grid_stage = (int)sms * 8;
     b->grid_tile = (int)sms * 2;
+    if (b->ctas_per_sm > 0) per_sm = std::min(per_sm, b->ctas_per_sm);
     b->grid_gpp = clampg(b->cap_tile, (int64_t)sms * std::max(per_sm, 1));
     b->base = (char *)dev;
     if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)

@@ -267,7 +267,8 @@ class _BatchLane:
         self.batch = None
         self.bytes = 0
         self.ids: Tuple[int, ...] = ()
-        self.inflight = collections.deque()   # (event, steps) of the chunks on the GPU
+        self.inflight = collections.deque()   # (end event, steps, start event) of the chunks on the GPU
+        self.captured = False  # the batch's first step (its graph capture) has been issued
 
 
 class Server:
@@ -287,14 +288,39 @@ class Server:
     a large one: the batch of small runs runs on the highest-priority stream, the batch of the
     larger 2D runs next, other runs of fewer than `large_particles` particles on
     medium-priority side streams, larger runs on low-priority ones.  The GPU's block scheduler
-    then starts a waiting block of a higher-priority stream before more blocks of a lower one."""
+    then starts a waiting block of a higher-priority stream before more blocks of a lower one.
+
+    Priorities order only the start of thread blocks; the particle kernels of a 2D batch need a
+    large share of an SM each (256 threads of 128 registers, about 100 KB of shared memory), and
+    beside 3D runs and a batch of larger runs, whose blocks fill the SMs, they wait for room
+    (measured: the batch of small runs took 0.49 ms per step with 1.07 runs on average, against
+    0.1-0.2 ms for one such run alone).  So short requests go first (`preempt`): while the batch
+    of small runs holds runs, the other lanes get no new chunks, and their chunks are sized to
+    about `chunk_ms` of GPU time, which bounds how long a short request shares the GPU with
+    them; the persistent particle kernel of the batch of larger runs takes one CTA per SM
+    (`large_lane_ctas_per_sm`), leaving the other slot to the batch of small runs."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 10,
                  tuner: Optional[Autotuner] = None, keep_runs: bool = False,
                  large_particles: int = 1 << 24, small_particles: int = 1 << 20,
-                 depth: int = 2):
+                 depth: int = 2, batch_reserve_bytes: int = 1 << 21,
+                 large_lane_ctas_per_sm: int = 1, preempt: bool = True,
+                 chunk_ms: float = 4.0):
         self.budget = float(budget_bytes)
         self.depth = max(1, int(depth))   # chunks a batch lane keeps queued on its stream
+        # budget held for the device tables of a batch lane that has none yet (its first
+        # request is admitted before the batch exists); the batch's own bytes replace it
+        self.batch_reserve = int(batch_reserve_bytes)
+        # the persistent particle kernel of the batch of larger runs holds its SM slots for the
+        # whole pass (stream priorities only order the start of CTAs): one CTA per SM leaves
+        # the other slot to the batch of small runs
+        self.large_lane_ctas_per_sm = int(large_lane_ctas_per_sm)
+        # short requests first: while the batch of small runs has runs, the other lanes finish
+        # the chunks they have queued but get no new ones, and their chunks are sized to about
+        # chunk_ms of GPU time (from their measured step time), so that a short request waits
+        # at most about that long for the GPU
+        self.preempt = bool(preempt)
+        self.chunk_ms = float(chunk_ms)
         self.large_particles = int(large_particles)
         self.small_particles = int(small_particles)
         self.chunk = int(chunk)
@@ -308,12 +334,15 @@ class Server:
         self.batch_builds = 0
         self.set_changes = 0
         self.lane_runs = [0, 0]   # runs served by the batch of small runs, of larger runs
-        self.host_block_s = 0.0   # longest admission (run set-up and load) or end-of-run read
+        self.host_block_s = 0.0   # longest end-of-run read on the loop thread
+        # per batch lane: chunks, steps, run-steps and the GPU time of its chunks (events on the
+        # lane's stream around each chunk)
+        self.lane_stats = [dict(chunks=0, steps=0, run_steps=0, gpu_ms=0.0) for _ in range(2)]
 
     @staticmethod
-    def _capacity(runs, factor=2.0):
-        """Batch capacities: `factor` times the totals of `runs`, and the largest batched stage
-        that still lets two CTAs share an SM."""
+    def _capacity(runs, factor=2.0, ctas_per_sm=0):
+        """Batch capacities: `factor` times the totals of `runs`, the largest batched stage
+        that still lets two CTAs share an SM, and the persistent kernel's CTAs per SM."""
         cap = pic.pic_batch_capacity()
         n = len(runs)
         cap.runs = max(8, int(factor * n))
@@ -326,8 +355,9 @@ class Server:
             stage = max(stage, batched, two)
         cap.cells = int(factor * max(cells, 1 << 18))
         # work items: a small set splits its heavier tiles into up to 8 items
-        cap.tiles = int(8 * factor * max(tiles, 1 << 12))
+        cap.tiles = int(factor * max(8 * tiles, 1 << 12))
         cap.stage_bytes = int(stage)
+        cap.ctas_per_sm = int(ctas_per_sm)
         return cap
 
     def lane_of(self, req: Request) -> int:
@@ -341,19 +371,30 @@ class Server:
         other run on its own side stream.  A lane gets its next chunk of steps as soon as its
         previous chunk's event has completed, so small runs never wait for a large run's
         steps; run sets change, and finished runs are reported, at a lane's chunk boundary."""
+        import concurrent.futures as cf
         import torch
         pending = sorted(requests, key=lambda r: r.arrival)
+        # preempting (and time-sized chunks) only matters when short requests are to come
+        preempt = self.preempt and any(r.batchable and self.lane_of(r) == 0 for r in requests)
         active = {}      # rid -> dict(run, req, done, admitted, bytes, stream, history, lane)
+        # admitted requests whose run is being created and loaded by the loader thread (the
+        # library's calls release the interpreter, so the loop keeps the lanes fed meanwhile):
+        # rid -> (future, request, bytes, lane)
+        loading = {}
+        loader = cf.ThreadPoolExecutor(max_workers=1)
         used = 0
-        side_inflight = {}      # rid -> (event, steps) of a side run's chunk
+        side_inflight = {}      # rid -> (end event, steps, start event) of a side run's chunk
         t0 = time.perf_counter()
         # priorities: lower numbers are served first (torch clamps them to the device's range)
         lanes = [_BatchLane(torch.cuda.Stream(priority=-3)),   # batch of small 2D runs
                  _BatchLane(torch.cuda.Stream(priority=-2))]   # batch of larger 2D runs
 
-        def install(lane, ids):
-            """Make the lane's batch hold the runs `ids` (a new batch when none fits)."""
+        reserved = set()   # lanes whose batch tables are held in the budget by batch_reserve
+
+        def install(li, ids):
+            """Make lane li's batch hold the runs `ids` (a new batch when none fits)."""
             nonlocal used
+            lane = lanes[li]
             runs = [active[r]["run"] for r in ids]
             if lane.batch is not None and lane.batch.set_runs(runs):
                 self.set_changes += 1
@@ -365,16 +406,25 @@ class Server:
                 used -= lane.bytes
                 lane.batch, lane.bytes = None, 0
             if runs:
-                lane.batch = pic.Batch(runs, capacity=self._capacity(runs))
+                lane.batch = pic.Batch(runs, capacity=self._capacity(
+                    runs, ctas_per_sm=self.large_lane_ctas_per_sm if li == 1 else 0))
+                lane.captured = False
                 lane.bytes = int(lane.batch.mem.numel())
                 used += lane.bytes
+                if li in reserved:
+                    reserved.discard(li)
+                    used -= self.batch_reserve
                 self.peak_bytes = max(self.peak_bytes, used)
                 self.batch_builds += 1
             lane.ids = ids
 
-        def chunk_steps(ids, ahead=0):
-            """Steps of the next chunk of runs `ids`, `ahead` steps past their completed ones."""
-            k = min(self.chunk, min(active[r]["req"].steps - active[r]["done"] - ahead for r in ids))
+        def chunk_steps(ids, ahead=0, ms_per_step=0.0):
+            """Steps of the next chunk of runs `ids`, `ahead` steps past their completed ones
+            (at most about chunk_ms of GPU time when preempting and the step time is known)."""
+            k = self.chunk
+            if preempt and ms_per_step > 0.0:
+                k = max(1, min(k, int(self.chunk_ms / ms_per_step)))
+            k = min(k, min(active[r]["req"].steps - active[r]["done"] - ahead for r in ids))
             for r in ids:  # stop at the next field-energy sample
                 ev = active[r]["req"].record_every
                 if ev > 0:
@@ -412,17 +462,22 @@ class Server:
             ev = a["req"].record_every
             return ev > 0 and a["done"] % ev == 0
 
-        while pending or active:
+        while pending or active or loading:
             progressed = False
             now = time.perf_counter() - t0
             # admit arrived requests while the budget has room (arrival order)
             while pending and pending[0].arrival <= now:
                 req = pending[0]
                 need = footprint_estimate(req, tuner=self.tuner)
-                if used + need > self.budget and active:
+                lane = self.lane_of(req) if req.batchable else -1
+                extra = (self.batch_reserve if lane >= 0 and lanes[lane].batch is None
+                         and lane not in reserved else 0)
+                if used + need + extra > self.budget and (active or loading):
                     break
                 pending.pop(0)
-                lane = self.lane_of(req) if req.batchable else -1
+                if extra:
+                    reserved.add(lane)
+                    used += extra
                 if lane >= 0:
                     stream = lanes[lane].stream
                     self.lane_runs[lane] += 1
@@ -432,28 +487,39 @@ class Server:
                     # another run has in flight
                     stream = torch.cuda.Stream(priority=-1 if req.particles < self.large_particles
                                                else 0)
-                tb = time.perf_counter()
-                run = make_run(req, tuner=self.tuner, stream=stream)
-                self.host_block_s = max(self.host_block_s, time.perf_counter() - tb)
-                active[req.rid] = {"run": run, "req": req, "done": 0, "bytes": need,
-                                   "admitted": time.perf_counter() - t0, "history": [],
-                                   "stream": run.stream, "lane": lane}
-                if req.record_every > 0:
-                    self._record(active[req.rid])
+                loading[req.rid] = (loader.submit(make_run, req, tuner=self.tuner, stream=stream),
+                                    req, need, lane)
                 used += need
                 self.peak_bytes = max(self.peak_bytes, used)
+                progressed = True
+            # runs the loader thread has finished join the lanes
+            for rid in [r for r, v in loading.items() if v[0].done()]:
+                fut, req, need, lane = loading.pop(rid)
+                run = fut.result()
+                active[rid] = {"run": run, "req": req, "done": 0, "bytes": need,
+                               "admitted": time.perf_counter() - t0, "history": [],
+                               "stream": run.stream, "lane": lane}
+                if req.record_every > 0:
+                    self._record(active[rid])
                 progressed = True
             self.max_active = max(self.max_active, len(active))
             # the batch lanes: account finished chunks, change the run set, keep up to
             # `depth` chunks queued on the lane's stream (the GPU does not wait for the host
             # between chunks) as long as no run of the set reaches a field-energy sample or its
             # last step and no admitted run waits to join
+            urgent = preempt and (any(a["lane"] == 0 for a in active.values())
+                                        or any(v[3] == 0 for v in loading.values()))
             for li, lane in enumerate(lanes):
                 done_chunk = False
                 while lane.inflight and lane.inflight[0][0].query():
-                    _, k = lane.inflight.popleft()
+                    ev, k, ev0 = lane.inflight.popleft()
                     for r in lane.ids:
                         active[r]["done"] += k
+                    st = self.lane_stats[li]
+                    st["chunks"] += 1
+                    st["steps"] += k
+                    st["run_steps"] += k * len(lane.ids)
+                    st["gpu_ms"] += ev0.elapsed_time(ev)
                     done_chunk = True
                 if lane.inflight:
                     if done_chunk:
@@ -465,7 +531,7 @@ class Server:
                         if rec and not fin:
                             lane.batch.sync()
                         if fin:  # the finished runs leave the batch (their state written back)
-                            install(lane, tuple(r for r in lane.ids if r not in fin))
+                            install(li, tuple(r for r in lane.ids if r not in fin))
                         for a in rec:
                             self._record(a)
                         for r in fin:
@@ -473,19 +539,30 @@ class Server:
                         progressed = True
                     ids = tuple(sorted(r for r, a in active.items() if a["lane"] == li))
                     if ids != lane.ids:
-                        install(lane, ids)
+                        install(li, ids)
                 if lane.batch is None or not lane.ids:
                     continue
+                if li > 0 and urgent:
+                    continue
                 joining = any(a["lane"] == li and r not in lane.ids for r, a in active.items())
+                st = self.lane_stats[li]
+                msps = st["gpu_ms"] / st["steps"] if li > 0 and st["steps"] else 0.0
                 while len(lane.inflight) < self.depth:
-                    ahead = sum(k for _, k in lane.inflight)
+                    ahead = sum(c[1] for c in lane.inflight)
                     if lane.inflight and (joining or stops(lane.ids, ahead)):
                         break
-                    k = chunk_steps(lane.ids, ahead)
+                    k = chunk_steps(lane.ids, ahead, msps)
+                    if not lane.captured:
+                        # the first step captures the batch's graph on the lane's stream, on
+                        # which the loader thread also loads the lane's new runs: let it finish
+                        cf.wait([v[0] for v in loading.values()])
+                        lane.captured = True
+                    ev0 = torch.cuda.Event(enable_timing=True)
+                    ev0.record(lane.stream)
                     lane.batch.step(k)
-                    ev = torch.cuda.Event()
+                    ev = torch.cuda.Event(enable_timing=True)
                     ev.record(lane.stream)
-                    lane.inflight.append((ev, k))
+                    lane.inflight.append((ev, k, ev0))
                     self.chunks += 1
                     progressed = True
             # the side lanes: every other run on its own stream
@@ -496,6 +573,7 @@ class Server:
                     continue
                 if inf is not None:
                     a["done"] += inf[1]
+                    a["ms_per_step"] = inf[2].elapsed_time(inf[0]) / inf[1]
                     del side_inflight[rid]
                     if recorded(a):
                         self._record(a)
@@ -503,18 +581,24 @@ class Server:
                         finish(rid)
                         progressed = True
                         continue
-                k = chunk_steps([rid])
+                if urgent:
+                    continue
+                # the first chunk of a side run is one step, which measures its step time
+                k = chunk_steps([rid], 0, a.get("ms_per_step", 1e9 if preempt else 0.0))
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev0.record(a["stream"])
                 a["run"].step(k)
-                ev = torch.cuda.Event()
+                ev = torch.cuda.Event(enable_timing=True)
                 ev.record(a["stream"])
-                side_inflight[rid] = (ev, k)
+                side_inflight[rid] = (ev, k, ev0)
                 self.chunks += 1
                 progressed = True
             if not progressed:
-                if not active and pending:
+                if not active and not loading and pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - (time.perf_counter() - t0))))
                 else:
                     time.sleep(0.0002)
+        loader.shutdown()
         for lane in lanes:
             if lane.batch is not None:
                 lane.batch.close()
