@@ -572,6 +572,8 @@ def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
     # else to do takes: the run's set-up and load, its steps and the final diagnostics read;
     # the steps timed over alone_steps and scaled), and the 3D throughput
     alone, alone_steps_only, work3d, t3d = {}, {}, 0.0, 0.0
+    for r in reqs:  # tune first: a request's set-up time must not include the autotuner's probes
+        engine.request_tile(r, tuner)
     for r in reqs:
         torch.cuda.synchronize()
         ts = time.perf_counter()
