@@ -270,10 +270,11 @@ __global__ void __launch_bounds__(kBlock) k_b_yee_e(const Counts *cn, const RunD
 
 // ---- the persistent gather-push-deposit kernel over all runs' tiles ----
 template <int L, int KT>
-__device__ __forceinline__ bool try_tile(const RunDev &rd, int kt, char *smem, const int4 &w)
+__device__ __forceinline__ bool try_tile(const RunDev &rd, int kt, char *smem, int tile,
+                                         const int *split)
 {
     if (rd.l != L || kt != KT) return false;
-    tile_2d<L, KT, float>(rd, smem, w.y, rd.tt, w.z, w.w);  // the descriptor copy holds the tables
+    tile_2d<L, KT, float>(rd, smem, tile, rd.tt, split);  // the descriptor copy holds the tables
     return true;
 }
 
@@ -286,14 +287,18 @@ __global__ void __launch_bounds__(256, 2) k_b_gpp(const Counts *cn, const RunDev
     RunDev *rds = (RunDev *)smem_all;
     char *smem = smem_all + ((sizeof(RunDev) + 15) / 16) * 16;
     __shared__ int item;
+    __shared__ int4 work;  // run, tile, part, parts
     const int nitems = cn->items;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) {
+            item = atomicAdd(counter, 1);
+            if (item < nitems) work = items[item];
+        }
         __syncthreads();
         const int it = item;
         if (it >= nitems) return;
-        const int4 w = items[it];  // run, tile, part, parts
+        const int2 w = make_int2(work.x, work.y);
         const int kt = st[w.x].kt;
         for (int i = threadIdx.x; i < (int)(sizeof(RunDev) / sizeof(int)); i += blockDim.x)
             ((int *)rds)[i] = ((const int *)(runs + w.x))[i];
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(256, 2) k_b_gpp(const Counts *cn, const RunDev
         const RunDev &rd = *rds;
         // every run in a batch uses the wide integer-node stencil (l + 2 nodes; the extra
         // weight is zero when c dt <= dx/2), so two instances cover the batch
-        if (!(try_tile<2, 4>(rd, kt, smem, w) || try_tile<3, 5>(rd, kt, smem, w)))
+        if (!(try_tile<2, 4>(rd, kt, smem, w.y, &work.z) || try_tile<3, 5>(rd, kt, smem, w.y, &work.z)))
             set_err(rd.err, 1);
     }
 }

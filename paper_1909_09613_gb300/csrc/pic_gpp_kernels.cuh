@@ -949,13 +949,14 @@ __device__ __forceinline__ void particle_2d(const Hot2D h, const HotSp<R> hs,
     }
 }
 
-// All particles of one tile (both species), 2D.  tt_shared as in stage2d_carve.  With
-// nparts > 1 only part `part` of every species' particles of the tile (a contiguous share of
-// its range): the batched kernel splits the heavy tiles of a small run set over several CTAs,
-// each staging the tile and adding its own share of the current.
+// All particles of one tile (both species), 2D.  tt_shared as in stage2d_carve.  split (in
+// shared memory: part, parts), when given with parts > 1: only that part of every species'
+// particles of the tile (a contiguous share of its range) -- the batched kernel splits the
+// heavy tiles of a small run set over several CTAs, each staging the tile and adding its own
+// share of the current.  (Read where used, so that it holds no registers across the tile.)
 template <int L, int KT, typename R, bool DET = false>
 __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
-                        const TTable *tt_shared = nullptr, int part = 0, int nparts = 1)
+                        const TTable *tt_shared = nullptr, const int *split = nullptr)
 {
     Stage2D<R> st = stage2d_carve<R>(smem, rd.reg_nodes, tt_shared, DET);
     const int tx = (int)(tile % rd.ntile[0]);
@@ -968,10 +969,10 @@ __device__ void tile_2d(const RunDev &rd, char *smem, int64_t tile,
         const SpeciesDev &sp = rd.sp[s];
         const HotSp<R> hs = make_hotsp<R>(sp);
         int64_t a = sp.tile_start[tile], b = sp.tile_start[tile + 1];
-        if (nparts > 1) {
-            const int64_t len = b - a;
-            b = a + len * (part + 1) / nparts;
-            a += len * part / nparts;
+        if (split != nullptr && split[1] > 1) {  // (fewer than 2^27 particles per tile)
+            const int len = (int)(b - a), part = split[0], parts = split[1];
+            b = a + (len * (part + 1)) / parts;
+            a += (len * part) / parts;
         }
         if constexpr (sizeof(R) == 4) {
             // every warp takes a contiguous chunk of the tile's particles of this species (for a
