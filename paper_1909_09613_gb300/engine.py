@@ -17,9 +17,10 @@ libpic's kernels (pic_step for a run on its own, pic_batch_step for a batch).
   quadratic or cubic run of the FP32 form in one of two batches, small runs and larger ones
   (one persistent particle kernel per step each), every other run (3D, quartic, plain FP64)
   on a side stream, all concurrently.  When runs finish or arrive, a batch's run set changes
-  at its next chunk boundary.  It reports the
-  latency (completion - arrival) of every request and, for requests that ask for it, the
-  field-energy history (E/E0 of the Table 1 scan).
+  at its next chunk boundary.  Short requests go first (the other lanes wait at chunk
+  boundaries while the batch of small runs holds runs), and runs that each fill the GPU take
+  turns in arrival order.  It reports the latency (completion - arrival) of every request and,
+  for requests that ask for it, the field-energy history (E/E0 of the Table 1 scan).
 * `table1_requests` builds the requests of the paper's Table 1 NCI scan.
 """
 from __future__ import annotations
@@ -298,14 +299,15 @@ class Server:
     of small runs holds runs, the other lanes get no new chunks, and their chunks are sized to
     about `chunk_ms` of GPU time, which bounds how long a short request shares the GPU with
     them; the persistent particle kernel of the batch of larger runs takes one CTA per SM
-    (`large_lane_ctas_per_sm`), leaving the other slot to the batch of small runs."""
+    (`large_lane_ctas_per_sm`), leaving the other slot to the batch of small runs.  Side runs of
+    `large_particles` and more take turns (`max_large` at a time, in arrival order)."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 10,
                  tuner: Optional[Autotuner] = None, keep_runs: bool = False,
                  large_particles: int = 1 << 24, small_particles: int = 1 << 20,
                  depth: int = 2, batch_reserve_bytes: int = 1 << 21,
                  large_lane_ctas_per_sm: int = 1, preempt: bool = True,
-                 chunk_ms: float = 4.0):
+                 chunk_ms: float = 4.0, max_large: int = 1):
         self.budget = float(budget_bytes)
         self.depth = max(1, int(depth))   # chunks a batch lane keeps queued on its stream
         # budget held for the device tables of a batch lane that has none yet (its first
@@ -321,6 +323,10 @@ class Server:
         # at most about that long for the GPU
         self.preempt = bool(preempt)
         self.chunk_ms = float(chunk_ms)
+        # side runs of large_particles and more step max_large at a time, in arrival order: one
+        # such run already fills the GPU, so several at once only share it (each finishing as
+        # late as the last) where turns let the earlier ones finish first
+        self.max_large = max(1, int(max_large))
         self.large_particles = int(large_particles)
         self.small_particles = int(small_particles)
         self.chunk = int(chunk)
@@ -565,7 +571,11 @@ class Server:
                     lane.inflight.append((ev, k, ev0))
                     self.chunks += 1
                     progressed = True
-            # the side lanes: every other run on its own stream
+            # the side lanes: every other run on its own stream; the runs of large_particles
+            # and more (each one fills the GPU) take turns in arrival order, max_large at once
+            large = sorted((a["req"].arrival, r) for r, a in active.items()
+                           if a["lane"] < 0 and a["req"].particles >= self.large_particles)
+            large_turn = {r for _, r in large[:self.max_large]}
             for rid in [r for r, a in active.items() if a["lane"] < 0]:
                 a = active[rid]
                 inf = side_inflight.get(rid)
@@ -582,6 +592,8 @@ class Server:
                         progressed = True
                         continue
                 if urgent:
+                    continue
+                if a["req"].particles >= self.large_particles and rid not in large_turn:
                     continue
                 # the first chunk of a side run is one step, which measures its step time
                 k = chunk_steps([rid], 0, a.get("ms_per_step", 1e9 if preempt else 0.0))

@@ -162,7 +162,10 @@ def test_one_step_2d(case, prec):
 
 @pytest.mark.parametrize("prec", [pic.PIC_FP64, pic.PIC_FP32_MIXED], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("case", [((12, 10, 8), 0.3, 2, 1), ((12, 10, 8), 0.3, 2, 0),
-                                  ((10, 9, 7), 0.25, 3, 1), ((9, 8, 8), 0.5, 1, 1)],
+                                  ((10, 9, 7), 0.25, 3, 1), ((9, 8, 8), 0.5, 1, 1),
+                                  # grids narrower than a deposit window: the padded FP32
+                                  # current folds several periodic images onto one node
+                                  ((4, 3, 5), 0.3, 2, 1), ((5, 4, 3), 0.25, 3, 1)],
                          ids=lambda c: "g%dx%dx%d_l%d_s%d" % (c[0] + (c[2], c[3])))
 def test_one_step_3d(case, prec):
     grid, cdt, l, scheme = case
