@@ -659,6 +659,7 @@ def served_form(n_req=48, steps=500, budget=150e9, seed=None, alone_steps=100):
             "makespan_s": makespan, "max_concurrent_runs": srv.max_active,
             "batch_builds": srv.batch_builds, "batch_set_changes": srv.set_changes,
             "batch_lane_runs": srv.lane_runs, "longest_host_block_s": srv.host_block_s,
+            "hold_releases": srv.hold_releases,
             "batch_lanes": [{"chunks": st["chunks"], "steps": st["steps"],
                              "mean_runs_per_step": st["run_steps"] / max(st["steps"], 1),
                              "ms_per_step": st["gpu_ms"] / max(st["steps"], 1)}

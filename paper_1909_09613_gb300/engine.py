@@ -259,6 +259,30 @@ class Served:
         return self.done - self.arrival
 
 
+class HoldPolicy:
+    """Whether the server holds its other lanes for short requests: while short requests run
+    (`urgent`), hold, except that a hold longer than `max_hold_s` is released for one round
+    (then holding starts over), so that a steady stream of short requests cannot starve the
+    others."""
+
+    def __init__(self, max_hold_s: float):
+        self.max_hold_s = float(max_hold_s)
+        self.since = None
+        self.releases = 0
+
+    def hold(self, urgent: bool, now: float) -> bool:
+        if not urgent:
+            self.since = None
+            return False
+        if self.since is None:
+            self.since = now
+        elif now - self.since > self.max_hold_s:
+            self.since = now
+            self.releases += 1
+            return False
+        return True
+
+
 class _BatchLane:
     """One batch of the server: its stream, the pic batch, the runs it holds and the chunk of
     steps it has on the GPU."""
@@ -298,7 +322,8 @@ class Server:
     0.1-0.2 ms for one such run alone).  So short requests go first (`preempt`): while the batch
     of small runs holds runs, the other lanes get no new chunks, and their chunks are sized to
     about `chunk_ms` of GPU time, which bounds how long a short request shares the GPU with
-    them; the persistent particle kernel of the batch of larger runs takes one CTA per SM
+    them (a hold longer than `max_hold_s` releases one round of their chunks, so that a steady
+    stream of short requests cannot starve them); the persistent particle kernel of the batch of larger runs takes one CTA per SM
     (`large_lane_ctas_per_sm`), leaving the other slot to the batch of small runs.  Side runs of
     `large_particles` and more take turns (`max_large` at a time, in arrival order)."""
 
@@ -307,7 +332,7 @@ class Server:
                  large_particles: int = 1 << 24, small_particles: int = 1 << 20,
                  depth: int = 2, batch_reserve_bytes: int = 1 << 21,
                  large_lane_ctas_per_sm: int = 1, preempt: bool = True,
-                 chunk_ms: float = 4.0, max_large: int = 1):
+                 chunk_ms: float = 4.0, max_large: int = 1, max_hold_s: float = 0.5):
         self.budget = float(budget_bytes)
         self.depth = max(1, int(depth))   # chunks a batch lane keeps queued on its stream
         # budget held for the device tables of a batch lane that has none yet (its first
@@ -327,6 +352,8 @@ class Server:
         # such run already fills the GPU, so several at once only share it (each finishing as
         # late as the last) where turns let the earlier ones finish first
         self.max_large = max(1, int(max_large))
+        self.max_hold_s = float(max_hold_s)
+        self.hold_releases = 0   # rounds released by the hold limit in the last serve
         self.large_particles = int(large_particles)
         self.small_particles = int(small_particles)
         self.chunk = int(chunk)
@@ -396,6 +423,7 @@ class Server:
                  _BatchLane(torch.cuda.Stream(priority=-2))]   # batch of larger 2D runs
 
         reserved = set()   # lanes whose batch tables are held in the budget by batch_reserve
+        hold = HoldPolicy(self.max_hold_s)
 
         def install(li, ids):
             """Make lane li's batch hold the runs `ids` (a new batch when none fits)."""
@@ -515,6 +543,7 @@ class Server:
             # last step and no admitted run waits to join
             urgent = preempt and (any(a["lane"] == 0 for a in active.values())
                                         or any(v[3] == 0 for v in loading.values()))
+            urgent = hold.hold(urgent, time.perf_counter())
             for li, lane in enumerate(lanes):
                 done_chunk = False
                 while lane.inflight and lane.inflight[0][0].query():
@@ -610,6 +639,7 @@ class Server:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - (time.perf_counter() - t0))))
                 else:
                     time.sleep(0.0002)
+        self.hold_releases = hold.releases
         loader.shutdown()
         for lane in lanes:
             if lane.batch is not None:
