@@ -123,8 +123,9 @@ __device__ __forceinline__ R gather3_global(const F *f, int64_t nx, int64_t ny, 
 // One particle, 3D: fields from the tile's shared-memory stage (STAGED, FP32 form: sf, tile
 // origin x0, y0, z0) or through L1 (FP64 form), current by global reductions (FP32 form: into
 // the padded FP32 current RunDev::J32, whose windows need no wrapping, so each row of a window
-// is one pointer and the node offsets along x are immediate; FP64 form and deterministic
-// runs: into F[6..8]).  Called by all 32 lanes of a warp together (the window-row skips of the
+// is one pointer and its x nodes go in as aligned pairs, red.global.add.v2.f32 -- fewer
+// reduction requests for the L2, which bounds this kernel; FP64 form and deterministic runs:
+// into F[6..8]).  Called by all 32 lanes of a warp together (the window-row skips of the
 // deposit are decided per warp); lanes with act == false carry no particle.  raw: the
 // particle's stored state, loaded by the caller.
 template <int L, int KT, typename R, bool STAGED = false>
@@ -259,6 +260,7 @@ __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &
         const int PX = rd.jp[0], PXY = rd.jp[0] * rd.jp[1];
         const int w0 = ((s.c[2] + S[2].wb + rd.jp_lo) * rd.jp[1] + (s.c[1] + S[1].wb + rd.jp_lo)) * PX
                        + (s.c[0] + S[0].wb + rd.jp_lo);
+        const int xodd = (s.c[0] + S[0].wb + rd.jp_lo) & 1;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             const int bx = (ax + 1) % 3, cx = (ax + 2) % 3;
@@ -271,7 +273,11 @@ __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &
             int nk[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) nk[a] = (a == ax ? L : L + 1) + (mv[a] ? 1 : 0);
-            float *J = (float *)rd.J32[ax] + w0;
+            // the row's x nodes as aligned pairs from the even node at or below its first node
+            // (x rows have even length, so every pair is 8-byte aligned): npair pairs cover
+            // the nk[0] nodes shifted by the lane's parity
+            float *J = (float *)rd.J32[ax] + (w0 - xodd);
+            const int npair = (nk[0] + 2) / 2;
 #pragma unroll
             for (int kz = 0; kz < L + 2; ++kz) {
                 if (kz >= nk[2]) break;
@@ -279,17 +285,25 @@ __device__ __forceinline__ void particle_3d(const RunDev &rd, const SpeciesDev &
                 for (int ky = 0; ky < L + 2; ++ky) {
                     if (ky >= nk[1]) break;
                     float *row = J + (kz * PXY + ky * PX);
+                    float v[L + 2];
 #pragma unroll
                     for (int kx = 0; kx < L + 2; ++kx) {
-                        if (kx >= nk[0]) break;
                         const int k3[3] = {kx, ky, kz};
                         const int ka = k3[ax], kb = k3[bx], kc = k3[cx];
-                        if (ka > L) break;  // (ax = 0 only: compile time)
+                        if (ka > L || kx >= nk[0]) { v[kx] = 0.0f; continue; }
                         const R perp = S[bx].s0[kb] * fc0[cx][kc] + DS[bx][kb] * fc1[cx][kc];
-                        const R v = kP[ka] * perp;
-                        // FP32 L2 reductions: 2.4x the FP64 rate, and no FP32 -> FP64
-                        // conversion on the FP64 pipe per contribution
-                        if (act && v != R(0)) atomicAdd(row + kx, (float)v);
+                        v[kx] = (float)(kP[ka] * perp);
+                    }
+#pragma unroll
+                    for (int j = 0; j < (L + 3) / 2 + 1; ++j) {
+                        if (j >= npair) break;
+                        const float lo = xodd ? (2 * j >= 1 && 2 * j - 1 < L + 2 ? v[2 * j - 1] : 0.0f)
+                                              : (2 * j < L + 2 ? v[2 * j] : 0.0f);
+                        const float hi = xodd ? (2 * j < L + 2 ? v[2 * j] : 0.0f)
+                                              : (2 * j + 1 < L + 2 ? v[2 * j + 1] : 0.0f);
+                        if (act && (lo != 0.0f || hi != 0.0f))
+                            asm volatile("red.global.add.v2.f32 [%0], {%1, %2};"
+                                         ::"l"(row + 2 * j), "f"(lo), "f"(hi) : "memory");
                     }
                 }
             }
