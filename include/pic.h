@@ -72,7 +72,9 @@ typedef struct {
     int32_t precision;      /* PIC_FP64: FP64 positions/momenta/gather/push/deposit.
                                PIC_FP32_MIXED: int32 cell + FP32 in-cell offset, FP32 momenta,
                                FP32 gather/push and tile accumulation; FP64 Yee fields, FP64
-                               global current and FP64 diagnostics                           */
+                               global current and FP64 diagnostics (in 3D the current is summed
+                               by FP32 L2 reductions into a padded FP32 buffer, whose periodic
+                               images are added in FP64 after the particle pass)             */
     int32_t n_species;      /* species this context will hold (1..PIC_MAX_SPECIES)          */
     int64_t capacity[PIC_MAX_SPECIES]; /* max particles per species                         */
     uint64_t stream;        /* cudaStream_t to issue work on (0 = legacy default stream)    */
@@ -120,7 +122,8 @@ typedef struct {
 int pic_create(const int32_t grid[3], const double dx[3], double dt, int spline_order,
                int scheme, const pic_options *opt, pic_ctx **out);
 
-/* Bytes of device memory the context needs (fields, particle stores x2, sort scratch). */
+/* Bytes of device memory the context needs (fields, particle stores x2, sort scratch, the
+ * diagnostics' charge densities and, in the 3D FP32 form, the padded FP32 current). */
 int pic_footprint(const pic_ctx *ctx, size_t *bytes);
 
 /* Hand the context a device buffer of at least pic_footprint bytes (e.g. a torch tensor's
