@@ -370,3 +370,17 @@ def test_tile_order_threshold_depends_on_spline_order(lib, l, per_species, cell_
             assert slot_major == want, (l, per_species, prec)
         finally:
             pic.pic_destroy(ctx)
+
+
+@pytest.mark.parametrize("l,per_species,cell_major", [(2, 4, True), (2, 3, False), (3, 4, True)])
+def test_tile_order_threshold_3d(lib, l, per_species, cell_major):
+    """3D FP32 runs (current by L2 reductions, no warp frame) use the cell-major order from 4
+    particles of a species per cell for every spline order."""
+    grid = (32, 16, 16)
+    n = grid[0] * grid[1] * grid[2] * per_species
+    ctx = pic.pic_create(grid, (1.0, 1.0, 1.0), 0.3, l, pic.PIC_SCHEME_WT,
+                         _opt((n, n), pic.PIC_FP32_MIXED))
+    try:
+        assert pic.pic_tile_info(ctx)[3] == (0 if cell_major else 1)
+    finally:
+        pic.pic_destroy(ctx)
